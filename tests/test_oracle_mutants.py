@@ -1,0 +1,97 @@
+"""The pins must catch plausible oracle mistakes.  Each case copies the oracle's C
+source to a temporary directory, plants one mistake there (a flipped comparison,
+a swapped index, a dropped phase), compiles the copy and checks that a pin from
+test_oracle_pins.py now fails.  The committed oracle is never modified.  CPU only."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+SRC = open(os.path.join(os.path.dirname(oracle.__file__), "bcf_oracle.c")).read()
+
+
+def _mutant(tmp_path, old, new):
+    assert SRC.count(old) >= 1, old
+    path = tmp_path / "mutant.c"
+    path.write_text(SRC.replace(old, new, 1))
+    so = str(tmp_path / "libmutant.so")
+    oracle.build(str(path), so, force=True)
+    return oracle.load(so)
+
+
+def _sort_pins(L):
+    # stability and order against Python's stable sort on a duplicate-heavy input
+    keys = synth.random_labels(500, 4, seed=1)
+    ko, vo = oracle.sort_kv(keys, synth.index_payload(500), L=L)
+    ref = np.argsort(keys, kind="stable")
+    assert np.array_equal(vo, ref.astype(np.uint32))
+    small = synth.random_labels(20, 3, seed=2)
+    ko, vo = oracle.sort_kv(small, synth.index_payload(20), L=L)
+    assert np.array_equal(vo, np.argsort(small, kind="stable").astype(np.uint32))
+
+
+def _partition_pins(L):
+    keys = synth.partition_keys(64, 4, seed=3)
+    ko, vo = oracle.partition_kv(keys, synth.index_payload(64), 4, balanced=True, L=L)
+    assert np.array_equal(ko, (np.arange(64) // 16).astype(np.uint32))
+    for b in range(4):
+        assert np.array_equal(vo[16 * b:16 * b + 16], np.flatnonzero(keys == b).astype(np.uint32))
+
+
+def _permute_pins(L):
+    pi = synth.random_perm(50, seed=4)
+    inv = oracle.permute(synth.index_payload(50), pi, L=L)
+    assert np.array_equal(inv, np.argsort(pi).astype(np.uint32))
+
+
+def _lemma1_pins(L):
+    g = synth.rng(5)
+    for _ in range(200):
+        M = g.integers(0, 2, size=(3, 9), dtype=np.uint32)
+        out = oracle.lemma1_sort(M, L=L)
+        assert np.all(np.diff(out.reshape(-1).astype(np.int64)) >= 0)
+
+
+def _bank_pins(L):
+    n = 32
+    req = np.zeros(n, np.int64)
+    lane = np.arange(n, dtype=np.int32)
+    for width in (8, 16):
+        addr = (np.arange(n) * width).astype(np.uint32)
+        assert oracle.bank_count(req, lane, addr, np.full(n, width, np.int32), L=L)[1] == 0
+    addr = (np.arange(n) * 4 * 6).astype(np.uint32)  # runs of 6: gcd(6,32) = 2
+    assert oracle.bank_count(req, lane, addr, np.full(n, 4, np.int32), L=L)[0] == 2
+    same = np.full(n, 128, np.uint32)  # one word read by every lane: a broadcast
+    assert oracle.bank_count(req, lane, same, np.full(n, 4, np.int32), L=L)[:2] == (1, 0)
+
+
+MUTANTS = [
+    ("merge takes right run on ties", "if (src[j].key < src[i].key)", "if (src[j].key <= src[i].key)", _sort_pins),
+    ("insertion sort moves past equal keys", "while (j >= 0 && a[j].key > x.key)", "while (j >= 0 && a[j].key >= x.key)", _sort_pins),
+    ("merge copies a wrong right tail", "while (j < hi) dst[k++] = src[j++];", "while (j < hi) { dst[k++] = src[mid - 1]; j++; }", _sort_pins),
+    ("partition scans backwards", "for (int64_t i = 0; i < n; ++i) {\n        int64_t p = count[keys[i]]++;",
+     "for (int64_t i = n - 1; i >= 0; --i) {\n        int64_t p = count[keys[i]]++;", _partition_pins),
+    ("permute writes gather-style", "memcpy((char*)dst + (int64_t)pi[i] * elem_bytes, (const char*)src + i * elem_bytes,",
+     "memcpy((char*)dst + i * elem_bytes, (const char*)src + (int64_t)pi[i] * elem_bytes,", _permute_pins),
+    ("row->col conversion transposed", "for (int64_t r = 0; r < w; ++r) M[r * m + c] = seq[c * w + r];",
+     "for (int64_t r = 0; r < w; ++r) M[r * m + c] = seq[r * m + c];", _lemma1_pins),
+    ("Lemma 1 runs its loop once", "for (int rep = 0; rep < 2; ++rep) {", "for (int rep = 0; rep < 1; ++rep) {", _lemma1_pins),
+    ("bank model ignores phases", "int lanes_per_phase = 32 / words_per_lane;", "int lanes_per_phase = 32;", _bank_pins),
+    ("bank model counts lanes not words", "if (words[bank][q] == word) dup = 1;", "if (0) dup = 1;", _bank_pins),
+]
+
+
+@pytest.mark.parametrize("name,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, name, old, new, pins):
+    L = _mutant(tmp_path, old, new)
+    with pytest.raises((AssertionError, oracle.OracleError)):
+        pins(L)
+
+
+def test_unmutated_copy_passes_the_same_pins(tmp_path):
+    L = _mutant(tmp_path, "#include <stdlib.h>", "#include <stdlib.h>")
+    for pins in (_sort_pins, _partition_pins, _permute_pins, _lemma1_pins, _bank_pins):
+        pins(L)

@@ -1,0 +1,336 @@
+"""Pins for the CPU oracle: each function is checked against something other than
+itself -- brute force over every input of tiny sizes, closed forms the paper
+states, invariants that determine the answer uniquely, and library routines
+(numpy's stable argsort, Python's sorted) for special cases.  CPU only."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+
+# ----------------------------------------------------------------- sorting ----
+def _stable_sorted_order(keys):
+    # Python's sort is documented to be stable: an independent reference.
+    return sorted(range(len(keys)), key=lambda i: keys[i])
+
+
+def test_sort_bruteforce_all_sequences_n8(orc):
+    """Every key sequence of length 8 over {0,1,2,3} (4^8 = 65536 inputs), with
+    payload = original index: keys ascending and equal keys in input order."""
+    L = orc.lib()
+    idx = np.arange(8, dtype=np.uint32)
+    for seq in itertools.product(range(4), repeat=8):
+        keys = np.array(seq, dtype=np.uint32)
+        ko, vo = orc.sort_kv(keys, idx, L=L)
+        order = _stable_sorted_order(seq)
+        assert vo.tolist() == order
+        assert ko.tolist() == [seq[i] for i in order]
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 63, 64, 65, 1000, 4097, 100_003])
+@pytest.mark.parametrize("kind", ["uniform", "few", "zipf"])
+def test_sort_matches_numpy_stable(orc, n, kind):
+    if kind == "uniform":
+        keys = synth.uniform_keys(n, seed=n + 1)
+    elif kind == "few":
+        keys = synth.random_labels(n, 5, seed=n + 2)
+    else:
+        keys = synth.zipf_keys(n, seed=n + 3)
+    vals = synth.index_payload(n)
+    ko, vo = orc.sort_kv(keys, vals)
+    ref = np.argsort(keys, kind="stable")
+    assert np.array_equal(vo, ref.astype(np.uint32))
+    assert np.array_equal(ko, keys[ref])
+
+
+def test_sort_special_cases(orc):
+    n = 5000
+    # all keys equal -> identity
+    keys = np.full(n, 7, dtype=np.uint32)
+    ko, vo = orc.sort_kv(keys, synth.index_payload(n))
+    assert np.array_equal(vo, np.arange(n, dtype=np.uint32))
+    # keys form a permutation of [n] -> keys become 0..n-1, payload the inverse
+    pi = synth.random_perm(n, seed=11)
+    ko, vo = orc.sort_kv(pi, synth.index_payload(n))
+    assert np.array_equal(ko, np.arange(n, dtype=np.uint32))
+    assert np.array_equal(pi[vo], np.arange(n, dtype=np.uint32))
+    # reverse-sorted input with duplicates
+    keys = np.repeat(np.arange(100, 0, -1, dtype=np.uint32), 30)
+    ko, vo = orc.sort_kv(keys, synth.index_payload(keys.size))
+    assert np.all(np.diff(ko.astype(np.int64)) >= 0)
+
+
+def test_sort_payload_bits_and_widths(orc):
+    n = 3000
+    keys = synth.random_labels(n, 17, seed=5)
+    f = synth.float_bits_payload(n, seed=6)  # NaN / -0.0 patterns included
+    ko, vo = orc.sort_kv(keys, f)
+    ref = np.argsort(keys, kind="stable")
+    assert np.array_equal(vo.view(np.uint32), f.view(np.uint32)[ref])
+    v8 = np.arange(n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+    ko, vo = orc.sort_kv(keys, v8)
+    assert np.array_equal(vo, v8[ref])
+    ko, vo = orc.sort_kv(keys, None)
+    assert vo is None and np.array_equal(ko, keys[ref])
+
+
+def test_stable_rank_is_sorted_position(orc):
+    keys = synth.random_labels(777, 9, seed=3)
+    ko, vo = orc.sort_kv(keys, synth.index_payload(keys.size))
+    for p in range(0, 777, 37):
+        assert orc.stable_rank(keys, int(vo[p])) == p
+
+
+# --------------------------------------------------------------- partition ----
+def _check_partition_closed_form(ko, vo, keys, w):
+    """Partition problem: exactly m = n/w copies of each label, so label b fills
+    positions [b*m, (b+1)*m) -- key_out[p] = floor(p/m); the payload (original
+    index) of bucket b lists the positions of label b in increasing order."""
+    n = keys.size
+    m = n // w
+    assert np.array_equal(ko, (np.arange(n) // m).astype(np.uint32))
+    for b in range(w):
+        assert np.array_equal(vo[b * m:(b + 1) * m], np.flatnonzero(keys == b).astype(np.uint32))
+
+
+def _multiset_arrangements(counts):
+    """Every distinct sequence holding counts[b] copies of label b."""
+    total = sum(counts)
+    if total == 0:
+        yield ()
+        return
+    for b, c in enumerate(counts):
+        if c:
+            counts[b] -= 1
+            for rest in _multiset_arrangements(counts):
+                yield (b,) + rest
+            counts[b] += 1
+
+
+@pytest.mark.parametrize("w,m", [(2, 4), (4, 2), (3, 3), (2, 8)])
+def test_partition_bruteforce_all_arrangements(orc, w, m):
+    L = orc.lib()
+    seen = set()
+    for arr in _multiset_arrangements([m] * w):
+        seen.add(arr)
+        keys = np.array(arr, dtype=np.uint32)
+        ko, vo = orc.partition_kv(keys, synth.index_payload(keys.size), w, balanced=True, L=L)
+        _check_partition_closed_form(ko, vo, keys, w)
+    assert len(seen) == math.factorial(w * m) // math.factorial(m) ** w
+
+
+@pytest.mark.parametrize("n,w", [(65536, 32), (1 << 16, 256), (4096, 1), (99, 3)])
+def test_partition_balanced_closed_form(orc, n, w):
+    keys = synth.partition_keys(n, w, seed=n + w)
+    ko, vo = orc.partition_kv(keys, synth.index_payload(n), w, balanced=True)
+    _check_partition_closed_form(ko, vo, keys, w)
+
+
+def test_partition_unbalanced_and_errors(orc):
+    keys = synth.random_labels(10_000, 37, seed=1)
+    ko, vo = orc.partition_kv(keys, synth.index_payload(keys.size), 37)
+    ref = np.argsort(keys, kind="stable")
+    assert np.array_equal(vo, ref.astype(np.uint32)) and np.array_equal(ko, keys[ref])
+    with pytest.raises(orc.OracleError):
+        orc.partition_kv(keys, None, 36)  # a label equals w
+    with pytest.raises(orc.OracleError):
+        orc.partition_kv(keys[:370], None, 37, balanced=True)  # counts are not n/w
+    with pytest.raises(orc.OracleError):
+        orc.partition_kv(keys[:100], None, 37, balanced=True)  # n % w != 0
+
+
+# ------------------------------------------------------------- permutation ----
+def test_permute_all_permutations_n8(orc):
+    """For every pi of [8]: permuting the index array yields pi^-1, which numpy's
+    argsort of pi also yields; permuting then gathering by pi is the identity."""
+    L = orc.lib()
+    x = np.arange(100, 108, dtype=np.uint32)
+    iota = np.arange(8, dtype=np.uint32)
+    for p in itertools.permutations(range(8)):
+        pi = np.array(p, dtype=np.uint32)
+        inv = orc.permute(iota, pi, L=L)
+        assert np.array_equal(inv, np.argsort(pi).astype(np.uint32))
+        y = orc.permute(x, pi, L=L)
+        assert np.array_equal(orc.gather(y, pi, L=L), x)
+
+
+@pytest.mark.parametrize("n", [0, 1, 33, 4096, 1 << 20])
+def test_permute_invariants(orc, n):
+    pi = synth.random_perm(n, seed=n + 9)
+    iota = synth.index_payload(n)
+    inv = orc.permute(iota, pi)
+    assert np.array_equal(inv, np.argsort(pi, kind="stable").astype(np.uint32))
+    f = synth.float_bits_payload(n, seed=4)
+    y = orc.permute(f, pi)
+    assert np.array_equal(orc.gather(y, pi).view(np.uint32), f.view(np.uint32))
+    # composing with the inverse gives the identity permutation
+    assert np.array_equal(orc.permute(orc.permute(iota, pi), inv), iota)
+
+
+def test_permute_rejects_non_bijection(orc):
+    pi = np.array([0, 1, 1, 3], dtype=np.uint32)
+    with pytest.raises(orc.OracleError):
+        orc.permute(np.zeros(4, np.uint32), pi)
+    with pytest.raises(orc.OracleError):
+        orc.permute(np.zeros(4, np.uint32), np.array([0, 1, 2, 4], dtype=np.uint32))
+    with pytest.raises(orc.OracleError):
+        orc.gather(np.zeros(4, np.uint32), np.array([0, 9], dtype=np.uint32))
+
+
+@pytest.mark.parametrize("n,tile", [(4096 * 3, 4096), (4096 * 2 + 1000, 4096), (50, 16), (7, 4096)])
+def test_permute_tiles_matches_global_permute(orc, n, tile):
+    lpi = synth.tile_local_perms(n, tile, seed=n)
+    src = synth.uniform_keys(n, seed=1)
+    tiles = np.arange(n, dtype=np.int64) // tile
+    gpi = (tiles * tile + lpi.astype(np.int64)).astype(np.uint32)
+    assert np.array_equal(orc.permute_tiles(src, lpi, tile), orc.permute(src, gpi))
+    ident = (np.arange(n) % tile).astype(np.uint16)
+    assert np.array_equal(orc.permute_tiles(src, ident, tile), src)
+    bad = lpi.copy()
+    bad[0] = bad[1]
+    with pytest.raises(orc.OracleError):
+        orc.permute_tiles(src, bad, tile)
+
+
+# ---------------------------------------------------------------- segmented ----
+def test_segmented_sort_per_segment(orc):
+    sizes = [0, 1, 5, 0, 300, 1024, 33, 0]
+    offs = synth.offsets_from_sizes(sizes)
+    keys = synth.random_labels(int(offs[-1]), 50, seed=2)
+    vals = synth.index_payload(keys.size)
+    ko, vo = orc.segmented_sort_kv(keys, vals, offs)
+    for s in range(len(sizes)):
+        lo, hi = offs[s], offs[s + 1]
+        ref = lo + np.argsort(keys[lo:hi], kind="stable")
+        assert np.array_equal(vo[lo:hi], ref.astype(np.uint32))
+
+
+def test_segmented_partition_closed_form(orc):
+    keys, offs, w = synth.segmented_partition_input(12, seed=5, hi_log2=11)
+    vals = synth.index_payload(keys.size)
+    ko, vo = orc.segmented_partition_kv(keys, vals, offs, w, balanced=True)
+    for s in range(w.size):
+        lo, hi = int(offs[s]), int(offs[s + 1])
+        _check_partition_closed_form(ko[lo:hi], vo[lo:hi] - lo, keys[lo:hi], int(w[s]))
+
+
+# ------------------------------------------------------------ Lemma 1 model ----
+def _dirty_rows(M):
+    return int(sum(1 for r in M if 0 < r.sum() < r.size))
+
+
+def _dirty_cols(M):
+    return _dirty_rows(M.T)
+
+
+def _dirty_row_indices(M):
+    return [i for i, r in enumerate(M) if 0 < r.sum() < r.size]
+
+
+def _lemma1_with_dirt(orc, M, L):
+    """Run Lemma 1 step by step on a 0-1 matrix and assert the dirty-row and
+    dirty-column bounds used in its proof (Sec. 2, proof of Lemma 1)."""
+    w, m = M.shape
+    oracle = orc
+    oracle.l1_sort_rows(M, True, L=L)
+    oracle.l1_row_to_col(M, L=L)
+    assert _dirty_cols(M) <= w               # at most w dirty columns
+    oracle.l1_sort_rows(M, False, L=L)
+    oracle.l1_col_to_row(M, L=L)
+    d = _dirty_row_indices(M)
+    assert len(d) <= 2                        # two dirty rows ...
+    if len(d) == 2:
+        assert d[1] == d[0] + 1               # ... and they are adjacent
+    oracle.l1_sort_rows(M, True, L=L)
+    oracle.l1_row_to_col(M, L=L)
+    assert _dirty_cols(M) <= 2
+    oracle.l1_sort_rows(M, False, L=L)
+    assert _dirty_cols(M) <= 1                # one dirty column after step 3
+    oracle.l1_col_to_row(M, L=L)
+    assert _dirty_rows(M) <= 1                # one dirty row after step 4
+    oracle.l1_sort_rows(M, False, L=L)
+    flat = M.reshape(-1)
+    assert np.all(np.diff(flat.astype(np.int64)) >= 0)
+
+
+def test_lemma1_zero_one_exhaustive_2x4(orc):
+    L = orc.lib()
+    for bits in range(1 << 8):
+        M = np.array([(bits >> k) & 1 for k in range(8)], dtype=np.uint32).reshape(2, 4)
+        _lemma1_with_dirt(orc, M.copy(), L)
+
+
+@pytest.mark.parametrize("w,m", [(3, 9), (4, 16), (2, 6), (3, 12)])
+def test_lemma1_zero_one_sampled(orc, w, m):
+    L = orc.lib()
+    g = synth.rng(w * 100 + m)
+    for _ in range(3000):
+        M = g.integers(0, 2, size=(w, m), dtype=np.uint32)
+        # bias toward few ones / few zeros, where dirt concentrates
+        if _ % 3 == 1:
+            M = (g.random((w, m)) < 0.1).astype(np.uint32)
+        elif _ % 3 == 2:
+            M = (g.random((w, m)) < 0.9).astype(np.uint32)
+        _lemma1_with_dirt(orc, np.ascontiguousarray(M), L)
+
+
+def test_lemma1_all_permutations_2x4(orc):
+    L = orc.lib()
+    for p in itertools.permutations(range(8)):
+        M = np.array(p, dtype=np.uint32).reshape(2, 4)
+        out = orc.lemma1_sort(M, L=L)
+        assert out.reshape(-1).tolist() == list(range(8))
+
+
+@pytest.mark.parametrize("w,m", [(4, 16), (8, 64), (16, 256), (32, 1024)])
+def test_lemma1_sorts_random_matrices(orc, w, m):
+    g = synth.rng(w)
+    M = g.integers(0, 1000, size=(w, m), dtype=np.uint32)
+    out = orc.lemma1_sort(M)
+    assert np.array_equal(out.reshape(-1), np.sort(M.reshape(-1)))
+
+
+# --------------------------------------------------------------- bank model ----
+def _request(addrs, width=4):
+    n = len(addrs)
+    return (np.zeros(n, np.int64), np.arange(n, dtype=np.int32),
+            np.array(addrs, dtype=np.uint32), np.full(n, width, np.int32))
+
+
+def test_bank_strided_access_is_conflict_free(orc):
+    """Strided access A[w*i + t] keeps lane t in bank t (Sec. 1): no conflicts."""
+    for i in range(5):
+        wf, hw, strict = orc.bank_count(*_request([4 * (32 * i + t) for t in range(32)]))
+        assert (wf, hw, strict) == (1, 0, 0)
+
+
+@pytest.mark.parametrize("s", list(range(1, 70)))
+def test_bank_contiguous_runs_gcd(orc, s):
+    """Contiguous runs of s words per lane: lane t reads word t*s + i.  The number
+    of lanes sharing a bank is gcd(s, 32), so runs are conflict-free exactly when
+    s is co-prime to 32 (Sec. 1, the padding remark)."""
+    for i in (0, 3):
+        wf, hw, strict = orc.bank_count(*_request([4 * (t * s + i) for t in range(32)]))
+        g = math.gcd(s, 32)
+        assert wf == g and hw == g - 1 and strict == g - 1
+
+
+def test_bank_broadcast_and_wide_accesses(orc):
+    # every lane reads one word: the hardware broadcasts; the strict model does not
+    assert orc.bank_count(*_request([64] * 32)) == (1, 0, 31)
+    # 8-byte consecutive accesses: two half-warp phases, no conflict
+    assert orc.bank_count(*_request([8 * t for t in range(32)], 8)) == (2, 0, 1)
+    # 16-byte consecutive accesses: four quarter-warp phases, no conflict
+    assert orc.bank_count(*_request([16 * t for t in range(32)], 16)) == (4, 0, 3)
+    # 8-byte accesses at a 16-byte stride: each half-warp hits every used bank twice
+    wf, hw, _ = orc.bank_count(*_request([16 * t for t in range(32)], 8))
+    assert wf == 4 and hw == 2
+    # two requests are counted separately
+    req, lane, addr, width = _request([4 * 32 * t for t in range(32)])
+    req2 = np.concatenate([req, req + 1])
+    res = orc.bank_count(req2, np.concatenate([lane, lane]),
+                         np.concatenate([addr, addr]), np.concatenate([width, width]))
+    assert res == (64, 62, 62)

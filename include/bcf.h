@@ -1,0 +1,170 @@
+/*
+ * bcf.h -- bank-conflict-free sort, permute and w-way partition on B300 (sm_103a).
+ *
+ * C ABI of libbcf.so.  The operations are the three problems of Afshani &
+ * Sitchinava, "Sorting and Permuting without Bank Conflicts on GPUs" (Sec. 1,
+ * "Problems of interest"): sorting, w-way partitioning (sorting an input that
+ * holds labels in [0, w)) and permuting (sending the item at position i to
+ * position pi[i]).  The paper's w processors over w banks are the 32 lanes of a
+ * warp over the 32 four-byte shared-memory banks of an SM.
+ *
+ * Conventions shared by every entry point
+ *  - Every data pointer is a DEVICE pointer owned by the caller.  Except where a
+ *    function says otherwise, the library allocates and frees no device memory:
+ *    scratch comes from a caller-provided workspace whose size the matching
+ *    *_workspace_size() call returns.  Key, value, index and workspace pointers
+ *    must be 16-byte aligned (cudaMalloc and torch allocations are); a misaligned
+ *    pointer returns BCF_E_INVAL.
+ *  - Calls are asynchronous on `stream` (NULL is the legacy default stream).  The
+ *    return code reports argument errors and launch failures only.  Errors found
+ *    by the GPU while it runs (a label >= w, an unbalanced partition, a pi that is
+ *    not a bijection, a look-back wait that gave up) are recorded in a device
+ *    status word that bcf_get_status() reads; outputs are then unspecified, but
+ *    no kernel writes outside the caller's buffers and no kernel waits forever.
+ *  - Keys are uint32.  Payload ("value") elements are 0, 4 or 8 bytes and are
+ *    moved as raw bits (float NaN / -0.0 patterns survive).  Sizes are int64.
+ *  - Nothing here throws; no function keeps host state between calls.
+ */
+#ifndef BCF_H
+#define BCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared without pulling in the CUDA headers. */
+typedef struct CUstream_st* bcf_stream_t;
+
+/* ---- status codes ---- */
+#define BCF_OK 0
+#define BCF_E_INVAL 1          /* bad argument: null pointer, size, alignment, width */
+#define BCF_E_WORKSPACE 2      /* workspace smaller than *_workspace_size() */
+#define BCF_E_UNSUPPORTED 3    /* valid request outside what this build handles */
+#define BCF_E_CUDA 4           /* a CUDA launch or copy failed */
+#define BCF_E_TIMEOUT 5        /* device: a bounded inter-block wait gave up */
+#define BCF_E_NOT_BALANCED 6   /* device: balanced partition saw a count != n/w */
+#define BCF_E_BAD_PERM 7       /* device: pi not a bijection / index out of range */
+#define BCF_E_BAD_KEY 8        /* device: partition label >= w */
+
+/* ---- flags ---- */
+#define BCF_ASSUME_BALANCED 0x1   /* partition: exactly n/w copies of each label */
+#define BCF_CHECK_PERM 0x2        /* permute: verify pi is a bijection (needs ws) */
+#define BCF_TILES_COLOURED 0x10   /* permute_tiles: randomized colouring schedule */
+#define BCF_PARTITION_LEMMA1 0x20 /* partition (w <= 32): Lemma 1 tile schedule */
+
+/* Message for a status code (static string; never NULL). */
+const char* bcf_status_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int bcf_version(void);
+
+/* Synchronises `stream`, then reads and clears the device status word.  *out is
+ * BCF_OK or the most severe device error recorded since the last call, in the
+ * order BCF_E_TIMEOUT > BCF_E_BAD_PERM > BCF_E_NOT_BALANCED > BCF_E_BAD_KEY.  The
+ * word is shared by all calls on the device.  Returns BCF_E_CUDA if the sync or
+ * the read fails. */
+int bcf_get_status(bcf_stream_t stream, int* out);
+
+/* ---------------------------------------------------------------------------
+ * Sorting (Sec. 1; the paper sorts in O((n/w) log n) time, Lemma 1 and
+ * Theorem 1).  Stable ascending sort of n (key, value) pairs by key.
+ *  keys_in/vals_in   input, n keys and n values (vals_in NULL iff val_bytes 0)
+ *  keys_out/vals_out output; may equal the inputs (in place); must not overlap
+ *                    them otherwise
+ *  val_bytes         0, 4 or 8
+ *  key_bits          1..32; every key must be < 2^key_bits (fewer digit passes)
+ *  ws, ws_bytes      workspace of at least bcf_sort_workspace_size() bytes
+ * Method: least-significant-digit radix passes of at most 8 bits; each pass ranks
+ * and scatters tiles in shared memory and finds each tile's global offsets by a
+ * bounded decoupled look-back.  n must be < 2^30. */
+int bcf_sort_workspace_size(int64_t n, int val_bytes, int key_bits, size_t* bytes);
+int bcf_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+             void* vals_out, int64_t n, int val_bytes, int key_bits, void* ws,
+             size_t ws_bytes, bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * w-way partition (Sec. 1 and abstract; Corollary 1 and Theorem 1 solve it in
+ * O(n/w) time).  Stable: item i with label keys_in[i] in [0, w) goes to the block
+ * of its label, blocks in label order, input order kept inside a block.
+ *  w        1..256 buckets
+ *  flags    BCF_ASSUME_BALANCED: exactly n/w copies of every label, so block b
+ *           starts at b*n/w without a counting pass; n % w != 0 -> BCF_E_INVAL,
+ *           other counts -> device status BCF_E_NOT_BALANCED.
+ *           BCF_PARTITION_LEMMA1 (w <= 32, balanced): the Lemma 1 schedule --
+ *           row sorts inside each bank plus conflict-free transposes.
+ *  A label >= w -> device status BCF_E_BAD_KEY.  In place allowed (uses ws).
+ * n must be < 2^30. */
+int bcf_partition_workspace_size(int64_t n, int w, int val_bytes, int flags, size_t* bytes);
+int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                  void* vals_out, int64_t n, int w, int val_bytes, int flags, void* ws,
+                  size_t ws_bytes, bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Permutation (Sec. 1): dst[pi[i]] = src[i] for i in [0, n).
+ *  elem_bytes  4 or 8 (bcf_permute); src and dst must not overlap.
+ *  flags       BCF_CHECK_PERM: also verify that pi is a bijection (device status
+ *              BCF_E_BAD_PERM otherwise); needs bcf_permute_workspace_size() of
+ *              ws, else ws may be NULL.
+ * An index pi[i] >= n is never written; it sets BCF_E_BAD_PERM. */
+int bcf_permute_workspace_size(int64_t n, int flags, size_t* bytes);
+int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int elem_bytes,
+                int flags, void* ws, size_t ws_bytes, bcf_stream_t stream);
+/* Keys and values moved by one pi in one pass. */
+int bcf_permute_kv(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                   const uint32_t* pi, int64_t n, int val_bytes, int flags, void* ws,
+                   size_t ws_bytes, bcf_stream_t stream);
+
+/* Tile-local permutation (the paper's permutation problem on one shared-memory
+ * matrix, Sec. 3): tile t covers [t*tile, min(n,(t+1)*tile)); the key at local
+ * position i moves to local position lpi[t*tile + i].  tile in {1024, 2048, 4096}.
+ * flags BCF_TILES_COLOURED selects the randomized colouring schedule of Sec. 3
+ * (colour k = (j - h(i)) mod m; conflict-free sends; leftovers retried with a
+ * fresh h, then sent one bank at a time), seeded by `seed`; otherwise a direct
+ * scatter into shared memory.  Results are identical either way.  A local index
+ * outside the tile sets BCF_E_BAD_PERM and is not written. */
+int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
+                      int tile, int flags, uint64_t seed, bcf_stream_t stream);
+
+/* Gather: dst[i] = src[idx[i]] for i in [0, n); idx[i] < n_src, else the element
+ * is not read and BCF_E_BAD_PERM is set.  The inverse direction of bcf_permute
+ * (used by the backward pass of a permutation).  elem_bytes 4 or 8. */
+int bcf_gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
+               int elem_bytes, bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Tile sort (Lemma 1, Sec. 2): each tile of `tile` consecutive keys (the last may
+ * be shorter) is sorted on its own, stably, in shared memory, following the
+ * Lemma 1 schedule -- rows sorted inside their own bank, row-major <->
+ * column-major conversions between them.  tile in {256, 512, 1024, 2048, 4096}. */
+int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                   void* vals_out, int64_t n, int tile, int val_bytes, bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Segmented forms.  offs is a DEVICE array of nseg+1 int64 CSR offsets (offs[0]
+ * = 0, nondecreasing, offs[nseg] = n_total).  Each segment is sorted (or
+ * partitioned) on its own.  No host synchronisation and no allocation: the whole
+ * call can be captured in a CUDA graph.  Small segments are sorted whole in
+ * shared memory by persistent blocks that pull work from a queue; large ones go
+ * through shared digit passes.  n_total < 2^30. */
+int bcf_segmented_sort_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,
+                                      size_t* bytes);
+int bcf_segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                       void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
+                       int val_bytes, void* ws, size_t ws_bytes, bcf_stream_t stream);
+
+/* w_per_seg: DEVICE int32[nseg], each in 1..256.  flags: BCF_ASSUME_BALANCED. */
+int bcf_segmented_partition_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,
+                                           size_t* bytes);
+int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
+                            uint32_t* keys_out, void* vals_out, int64_t n_total,
+                            const int64_t* offs, const int32_t* w_per_seg, int64_t nseg,
+                            int val_bytes, int flags, void* ws, size_t ws_bytes,
+                            bcf_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BCF_H */

@@ -1,0 +1,268 @@
+// abi.cu -- extern "C" entry points of libbcf.so (declared in include/bcf.h).
+//
+// Argument checking, workspace carving and launch sequencing only; all data work
+// happens in the kernels of radix.cu, permute.cu, tile_permute.cu, tile_sort.cu and
+// segmented.cu.  No entry point allocates device memory.
+#include <cuda_runtime.h>
+
+#include "bcf.h"
+#include "common.cuh"
+#include "internal.h"
+
+// Device status word: bits of bcf::DEV_* OR-ed in by kernels.
+static __device__ unsigned g_bcf_status;
+
+namespace bcf {
+
+unsigned* status_word() {
+  // Cached per device; cudaGetSymbolAddress only looks the address up.
+  static unsigned* addr[64] = {nullptr};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bcf_status) == cudaSuccess) addr[dev] = static_cast<unsigned*>(p);
+  }
+  return addr[dev];
+}
+
+}  // namespace bcf
+
+namespace {
+
+constexpr int64_t kMaxSweepN = (int64_t)1 << 30;
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+bool valid_vb(int vb) { return vb == 0 || vb == 4 || vb == 8; }
+
+// [a, a+na) and [b, b+nb) either coincide exactly or do not overlap at all.
+bool same_or_disjoint(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  if (x == y) return true;
+  return x + na <= y || y + nb <= x;
+}
+bool disjoint(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return na == 0 || nb == 0 || x + na <= y || y + nb <= x;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? BCF_OK : BCF_E_CUDA; }
+
+// Kernels record errors through the status word; without its address (no usable
+// device) nothing may be launched.
+bool device_ready() { return bcf::status_word() != nullptr; }
+
+int check_kv(const uint32_t* ki, const void* vi, const uint32_t* ko, const void* vo, int64_t n,
+             int vb) {
+  if (n < 0 || !valid_vb(vb)) return BCF_E_INVAL;
+  if (n == 0) return BCF_OK;
+  if (!ki || !ko || !aligned16(ki) || !aligned16(ko)) return BCF_E_INVAL;
+  if (vb && (!vi || !vo || !aligned16(vi) || !aligned16(vo))) return BCF_E_INVAL;
+  if (!vb && (vi || vo)) return BCF_E_INVAL;
+  const size_t kb = (size_t)n * 4, vbb = (size_t)n * vb;
+  if (!same_or_disjoint(ki, kb, ko, kb)) return BCF_E_INVAL;
+  if (vb && !same_or_disjoint(vi, vbb, vo, vbb)) return BCF_E_INVAL;
+  if (vb && ((ki == ko) != (vi == vo))) return BCF_E_INVAL;  // both in place or neither
+  return BCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bcf_status_string(int status) {
+  switch (status) {
+    case BCF_OK: return "ok";
+    case BCF_E_INVAL: return "invalid argument (null pointer, size, width, alignment or overlap)";
+    case BCF_E_WORKSPACE: return "workspace smaller than the *_workspace_size() result";
+    case BCF_E_UNSUPPORTED: return "request outside what this build supports";
+    case BCF_E_CUDA: return "a CUDA launch or copy failed";
+    case BCF_E_TIMEOUT: return "a bounded inter-block wait gave up on the device";
+    case BCF_E_NOT_BALANCED: return "balanced partition: a label count differs from n/w";
+    case BCF_E_BAD_PERM: return "permutation index out of range or repeated";
+    case BCF_E_BAD_KEY: return "partition label >= w";
+  }
+  return "unknown status";
+}
+
+int bcf_version(void) { return 10000 * 1 + 100 * 0 + 0; }
+
+int bcf_get_status(bcf_stream_t stream, int* out) {
+  if (!out) return BCF_E_INVAL;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BCF_E_CUDA;
+  unsigned bits = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&bits, g_bcf_status, sizeof(bits)) != cudaSuccess) return BCF_E_CUDA;
+  if (bits && cudaMemcpyToSymbol(g_bcf_status, &zero, sizeof(zero)) != cudaSuccess) return BCF_E_CUDA;
+  if (bits & bcf::DEV_TIMEOUT) *out = BCF_E_TIMEOUT;
+  else if (bits & bcf::DEV_BAD_PERM) *out = BCF_E_BAD_PERM;
+  else if (bits & bcf::DEV_NOT_BALANCED) *out = BCF_E_NOT_BALANCED;
+  else if (bits & bcf::DEV_BAD_KEY) *out = BCF_E_BAD_KEY;
+  else *out = BCF_OK;
+  return BCF_OK;
+}
+
+// ------------------------------------------------------------------ sort
+int bcf_sort_workspace_size(int64_t n, int val_bytes, int key_bits, size_t* bytes) {
+  if (!bytes || n < 0 || !valid_vb(val_bytes) || key_bits < 1 || key_bits > 32) return BCF_E_INVAL;
+  if (n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  const bcf::PassPlan pl = bcf::plan_passes(key_bits);
+  *bytes = bcf::sweep_layout(n, val_bytes, pl.passes, 256, true).total;
+  return BCF_OK;
+}
+
+int bcf_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out, void* vals_out,
+             int64_t n, int val_bytes, int key_bits, void* ws, size_t ws_bytes,
+             bcf_stream_t stream) {
+  int rc = check_kv(keys_in, vals_in, keys_out, vals_out, n, val_bytes);
+  if (rc) return rc;
+  if (key_bits < 1 || key_bits > 32) return BCF_E_INVAL;
+  if (n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  if (n == 0) return BCF_OK;
+  const bcf::PassPlan pl = bcf::plan_passes(key_bits);
+  const bcf::SweepLayout L = bcf::sweep_layout(n, val_bytes, pl.passes, 256, true);
+  if (!ws || !aligned16(ws)) return BCF_E_INVAL;
+  if (ws_bytes < L.total) return BCF_E_WORKSPACE;
+  if (!disjoint(ws, ws_bytes, keys_in, (size_t)n * 4) || !disjoint(ws, ws_bytes, keys_out, (size_t)n * 4))
+    return BCF_E_INVAL;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::radix_sort(keys_in, vals_in, keys_out, vals_out, n, val_bytes, pl,
+                                 static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------- partition
+static bcf::SweepLayout partition_layout(int64_t n, int w, int vb) {
+  return bcf::sweep_layout(n, vb, 1, w <= 32 ? 32 : 256, true);
+}
+
+int bcf_partition_workspace_size(int64_t n, int w, int val_bytes, int flags, size_t* bytes) {
+  (void)flags;
+  if (!bytes || n < 0 || w < 1 || !valid_vb(val_bytes)) return BCF_E_INVAL;
+  if (w > 256 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  *bytes = partition_layout(n, w, val_bytes).total;
+  return BCF_OK;
+}
+
+int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                  void* vals_out, int64_t n, int w, int val_bytes, int flags, void* ws,
+                  size_t ws_bytes, bcf_stream_t stream) {
+  int rc = check_kv(keys_in, vals_in, keys_out, vals_out, n, val_bytes);
+  if (rc) return rc;
+  if (w < 1) return BCF_E_INVAL;
+  if (w > 256 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  const bool balanced = (flags & BCF_ASSUME_BALANCED) != 0;
+  if (balanced && n % w) return BCF_E_INVAL;
+  if (flags & BCF_PARTITION_LEMMA1) return BCF_E_UNSUPPORTED;
+  if (n == 0) return BCF_OK;
+  const bcf::SweepLayout L = partition_layout(n, w, val_bytes);
+  if (!ws || !aligned16(ws)) return BCF_E_INVAL;
+  if (ws_bytes < L.total) return BCF_E_WORKSPACE;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::partition(keys_in, vals_in, keys_out, vals_out, n, w, val_bytes, balanced,
+                                static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------ permutations
+int bcf_permute_workspace_size(int64_t n, int flags, size_t* bytes) {
+  if (!bytes || n < 0) return BCF_E_INVAL;
+  *bytes = (flags & BCF_CHECK_PERM) ? bcf::align_up((size_t)((n + 31) / 32) * 4) : 0;
+  return BCF_OK;
+}
+
+static int permute_common(const void* sk, const void* sv, void* dk, void* dv, const uint32_t* pi,
+                          int64_t n, int kb, int vb, int flags, void* ws, size_t ws_bytes,
+                          cudaStream_t s) {
+  if (n < 0 || (kb != 4 && kb != 8) || !valid_vb(vb)) return BCF_E_INVAL;
+  if (n > (int64_t)0xFFFFFFFFLL) return BCF_E_UNSUPPORTED;
+  if (n == 0) return BCF_OK;
+  if (!sk || !dk || !pi || !aligned16(sk) || !aligned16(dk) || !aligned16(pi)) return BCF_E_INVAL;
+  if (vb && (!sv || !dv || !aligned16(sv) || !aligned16(dv))) return BCF_E_INVAL;
+  if (!disjoint(sk, (size_t)n * kb, dk, (size_t)n * kb)) return BCF_E_INVAL;
+  if (vb && !disjoint(sv, (size_t)n * vb, dv, (size_t)n * vb)) return BCF_E_INVAL;
+  uint32_t* seen = nullptr;
+  if (flags & BCF_CHECK_PERM) {
+    size_t need = 0;
+    bcf_permute_workspace_size(n, flags, &need);
+    if (!ws || !aligned16(ws)) return BCF_E_INVAL;
+    if (ws_bytes < need) return BCF_E_WORKSPACE;
+    seen = static_cast<uint32_t*>(ws);
+  }
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::permute(sk, sv, dk, dv, pi, n, kb, vb, seen, s));
+}
+
+int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int elem_bytes,
+                int flags, void* ws, size_t ws_bytes, bcf_stream_t stream) {
+  return permute_common(src, nullptr, dst, nullptr, pi, n, elem_bytes, 0, flags, ws, ws_bytes,
+                        (cudaStream_t)stream);
+}
+
+int bcf_permute_kv(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                   const uint32_t* pi, int64_t n, int val_bytes, int flags, void* ws,
+                   size_t ws_bytes, bcf_stream_t stream) {
+  if (!val_bytes && (src_v || dst_v)) return BCF_E_INVAL;
+  return permute_common(src_k, src_v, dst_k, dst_v, pi, n, 4, val_bytes, flags, ws, ws_bytes,
+                        (cudaStream_t)stream);
+}
+
+int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
+                      int tile, int flags, uint64_t seed, bcf_stream_t stream) {
+  if (n < 0 || (tile != 1024 && tile != 2048 && tile != 4096)) return BCF_E_INVAL;
+  if (n >= ((int64_t)1 << 40)) return BCF_E_UNSUPPORTED;
+  if (n == 0) return BCF_OK;
+  if (!src || !dst || !lpi || !aligned16(src) || !aligned16(dst) || !aligned16(lpi)) return BCF_E_INVAL;
+  if (!disjoint(src, (size_t)n * 4, dst, (size_t)n * 4)) return BCF_E_INVAL;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::permute_tiles(src, dst, lpi, n, tile, (flags & BCF_TILES_COLOURED) != 0,
+                                    seed, (cudaStream_t)stream));
+}
+
+int bcf_gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
+               int elem_bytes, bcf_stream_t stream) {
+  if (n < 0 || n_src < 0 || (elem_bytes != 4 && elem_bytes != 8)) return BCF_E_INVAL;
+  if (n == 0) return BCF_OK;
+  if (!dst || !idx || !aligned16(dst) || !aligned16(idx)) return BCF_E_INVAL;
+  if (n_src > 0 && !src) return BCF_E_INVAL;
+  if (!disjoint(src, (size_t)n_src * elem_bytes, dst, (size_t)n * elem_bytes)) return BCF_E_INVAL;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::gather(src, dst, idx, n, n_src, elem_bytes, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------- tiles / segments
+int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                   void* vals_out, int64_t n, int tile, int val_bytes, bcf_stream_t stream) {
+  (void)keys_in; (void)vals_in; (void)keys_out; (void)vals_out; (void)n; (void)tile;
+  (void)val_bytes; (void)stream;
+  return BCF_E_UNSUPPORTED;
+}
+
+int bcf_segmented_sort_workspace_size(int64_t n_total, int64_t nseg, int val_bytes, size_t* bytes) {
+  (void)n_total; (void)nseg; (void)val_bytes; (void)bytes;
+  return BCF_E_UNSUPPORTED;
+}
+
+int bcf_segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                       void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
+                       int val_bytes, void* ws, size_t ws_bytes, bcf_stream_t stream) {
+  (void)keys_in; (void)vals_in; (void)keys_out; (void)vals_out; (void)n_total; (void)offs;
+  (void)nseg; (void)val_bytes; (void)ws; (void)ws_bytes; (void)stream;
+  return BCF_E_UNSUPPORTED;
+}
+
+int bcf_segmented_partition_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,
+                                           size_t* bytes) {
+  (void)n_total; (void)nseg; (void)val_bytes; (void)bytes;
+  return BCF_E_UNSUPPORTED;
+}
+
+int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                            void* vals_out, int64_t n_total, const int64_t* offs,
+                            const int32_t* w_per_seg, int64_t nseg, int val_bytes, int flags,
+                            void* ws, size_t ws_bytes, bcf_stream_t stream) {
+  (void)keys_in; (void)vals_in; (void)keys_out; (void)vals_out; (void)n_total; (void)offs;
+  (void)w_per_seg; (void)nseg; (void)val_bytes; (void)flags; (void)ws; (void)ws_bytes;
+  (void)stream;
+  return BCF_E_UNSUPPORTED;
+}
+
+}  // extern "C"

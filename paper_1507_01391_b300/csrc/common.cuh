@@ -1,0 +1,107 @@
+// common.cuh -- shared device helpers for libbcf (sm_103a).
+//
+// Device status word, shared-memory bulk staging (cp.async.bulk + mbarrier) and
+// bounded waits.  Every wait in this library has an iteration limit: when it runs
+// out the kernel records BCF_DEV_TIMEOUT and carries on, so no launch can hang.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bcf {
+
+// Bits of the device status word (see bcf_get_status()).
+enum : unsigned {
+  DEV_BAD_KEY = 1u << 0,
+  DEV_NOT_BALANCED = 1u << 1,
+  DEV_BAD_PERM = 1u << 2,
+  DEV_TIMEOUT = 1u << 3,
+};
+
+// Polls before a wait gives up (each poll also backs off a little).
+constexpr unsigned kSpinLimit = 1u << 24;
+
+__device__ __forceinline__ void set_status(unsigned* status, unsigned bit) {
+  atomicOr(status, bit);
+}
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- relaxed gpu-scope loads/stores for inter-block flags ----
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---- mbarrier + bulk copy (the TMA engine's non-tensor form) ----
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Returns false (after recording a timeout)
+// if the phase never completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned* status) {
+  for (unsigned it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+  }
+  set_status(status, DEV_TIMEOUT);
+  return false;
+}
+
+// Global -> shared bulk copy completed on `bar`.  dst, src and bytes must be
+// multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <int VB>
+struct ValT {
+  using type = uint32_t;
+};
+template <>
+struct ValT<8> {
+  using type = unsigned long long;
+};
+
+__host__ __device__ constexpr int ceil_div_i(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace bcf

@@ -1,0 +1,186 @@
+// permute.cu -- the permutation problem (Sec. 1): dst[pi[i]] = src[i], its inverse
+// direction (gather) and the optional bijectivity check.
+//
+// Global scatter: every thread reads four consecutive items of src and pi with
+// 128-bit loads and issues four scattered 4- or 8-byte stores.  The destination
+// lines are merged in L2 before they reach HBM, so DRAM traffic stays close to
+// one write per output byte when the output fits the 126 MB L2 working set.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bcf {
+
+template <int KB>
+struct Elem;
+template <>
+struct Elem<4> {
+  using T = uint32_t;
+  using V4 = uint4;
+};
+template <>
+struct Elem<8> {
+  using T = unsigned long long;
+  using V4 = ulonglong2;  // two elements per 16-byte load
+};
+
+__device__ __forceinline__ bool claim(uint32_t* seen, uint32_t d) {
+  const uint32_t bit = 1u << (d & 31);
+  return (atomicOr(seen + (d >> 5), bit) & bit) == 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, int64_t i, T (&out)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p + i));
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else {
+    const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(p + i));
+    const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(p + i + 2));
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+  }
+}
+
+// KB: key/element bytes (4 or 8).  VB: payload bytes (0, 4 or 8).
+template <int KB, int VB>
+__global__ void __launch_bounds__(256) k_permute(const void* __restrict__ src_k,
+                                                  const void* __restrict__ src_v,
+                                                  void* __restrict__ dst_k,
+                                                  void* __restrict__ dst_v,
+                                                  const uint32_t* __restrict__ pi, int64_t n,
+                                                  uint32_t* seen, unsigned* status) {
+  using KT = typename Elem<KB>::T;
+  using VT = typename ValT<VB>::type;
+  const KT* sk = reinterpret_cast<const KT*>(src_k);
+  KT* dk = reinterpret_cast<KT*>(dst_k);
+  const VT* sv = reinterpret_cast<const VT*>(src_v);
+  VT* dv = reinterpret_cast<VT*>(dst_v);
+  const int64_t nvec = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    const int64_t i = v * 4;
+    const uint4 p4 = __ldcs(reinterpret_cast<const uint4*>(pi + i));
+    const uint32_t d[4] = {p4.x, p4.y, p4.z, p4.w};
+    KT k[4];
+    load4(sk, i, k);
+    VT val[4];
+    if (VB) load4(sv, i, val);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      bool ok = (int64_t)d[c] < n;
+      if (ok && seen) ok = claim(seen, d[c]);
+      if (!ok) {
+        set_status(status, DEV_BAD_PERM);
+        continue;
+      }
+      dk[d[c]] = k[c];
+      if (VB) dv[d[c]] = val[c];
+    }
+  }
+  for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t d = pi[i];
+    bool ok = (int64_t)d < n;
+    if (ok && seen) ok = claim(seen, d);
+    if (!ok) {
+      set_status(status, DEV_BAD_PERM);
+      continue;
+    }
+    dk[d] = sk[i];
+    if (VB) dv[d] = sv[i];
+  }
+}
+
+template <int EB>
+__global__ void __launch_bounds__(256) k_gather(const void* __restrict__ src,
+                                                 void* __restrict__ dst,
+                                                 const uint32_t* __restrict__ idx, int64_t n,
+                                                 int64_t n_src, unsigned* status) {
+  using T = typename Elem<EB>::T;
+  const T* s = reinterpret_cast<const T*>(src);
+  T* d = reinterpret_cast<T*>(dst);
+  const int64_t nvec = n >> 2;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+    const int64_t i = v * 4;
+    const uint4 p4 = __ldcs(reinterpret_cast<const uint4*>(idx + i));
+    const uint32_t q[4] = {p4.x, p4.y, p4.z, p4.w};
+    T out[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if ((int64_t)q[c] < n_src) {
+        out[c] = s[q[c]];
+      } else {
+        out[c] = T(0);
+        set_status(status, DEV_BAD_PERM);
+      }
+    }
+    if constexpr (EB == 4) {
+      __stcs(reinterpret_cast<uint4*>(d + i), make_uint4(out[0], out[1], out[2], out[3]));
+    } else {
+      __stcs(reinterpret_cast<ulonglong2*>(d + i), make_ulonglong2(out[0], out[1]));
+      __stcs(reinterpret_cast<ulonglong2*>(d + i + 2), make_ulonglong2(out[2], out[3]));
+    }
+  }
+  for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint32_t q = idx[i];
+    if ((int64_t)q < n_src) {
+      d[i] = s[q];
+    } else {
+      d[i] = T(0);
+      set_status(status, DEV_BAD_PERM);
+    }
+  }
+}
+
+static int sm_count() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+static unsigned grid_for(int64_t n) {
+  const int64_t want = (n / 4 + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 8;  // 8 resident blocks of 256 per SM
+  int64_t g = want < cap ? want : cap;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+template <int KB>
+static cudaError_t permute_kb(const void* sk, const void* sv, void* dk, void* dv,
+                              const uint32_t* pi, int64_t n, int vb, uint32_t* seen,
+                              cudaStream_t s) {
+  const unsigned g = grid_for(n);
+  unsigned* st = status_word();
+  switch (vb) {
+    case 0: k_permute<KB, 0><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, seen, st); break;
+    case 4: k_permute<KB, 4><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, seen, st); break;
+    case 8: k_permute<KB, 8><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, seen, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
+                    const uint32_t* pi, int64_t n, int kbytes, int vbytes,
+                    uint32_t* seen_bitmap, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  if (seen_bitmap) {
+    cudaError_t e = cudaMemsetAsync(seen_bitmap, 0, (size_t)((n + 31) / 32) * 4, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (kbytes == 4) return permute_kb<4>(src_k, src_v, dst_k, dst_v, pi, n, vbytes, seen_bitmap, s);
+  if (kbytes == 8) return permute_kb<8>(src_k, src_v, dst_k, dst_v, pi, n, vbytes, seen_bitmap, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
+                   int eb, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const unsigned g = grid_for(n);
+  if (eb == 4) k_gather<4><<<g, 256, 0, s>>>(src, dst, idx, n, n_src, status_word());
+  else if (eb == 8) k_gather<8><<<g, 256, 0, s>>>(src, dst, idx, n, n_src, status_word());
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace bcf

@@ -1,0 +1,215 @@
+// tile_permute.cu -- permutation inside shared-memory tiles (Sec. 3).
+//
+// A tile of T keys is the paper's w x m matrix with w = 32 rows (banks) and
+// m = T/32 columns: the key at tile position q sits in bank q mod 32, slot q/32,
+// and its label p = lpi[q] names bank p mod 32 ("row i") and slot p/32 ("j").
+//
+// Two schedules, same result:
+//  * scatter  -- every thread writes out_s[p] = in_s[q]; a warp's 32 stores land
+//                in arbitrary banks, so they conflict (about 3.5 wavefronts each
+//                for a random permutation).
+//  * coloured -- the randomized algorithm of Sec. 3.  A random hash h: [32] -> [m]
+//                colours label (i, j) with k = (j - h(i)) mod m.  Within one
+//                colour class every destination bank appears exactly once, so a
+//                warp request that sends only colour-k items never conflicts
+//                (the CAC argument of the Communication step).  Each row sends
+//                at most one item of each colour per round; items whose colour
+//                was already taken are retried next round with a fresh h (the
+//                Synchronization loop), and the few left after the last round
+//                are sent greedily, one item per destination bank per request.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bcf {
+
+constexpr int kTPThreads = 128;  // four warps per tile
+
+__device__ __forceinline__ uint32_t mix32(uint64_t x) {
+  // splitmix64 finaliser (Steele, Lea & Flood 2014), folded to 32 bits
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (uint32_t)x;
+}
+
+template <int T>
+struct TPSmem {
+  static constexpr int M = T / 32;
+  static constexpr size_t in = 0;
+  static constexpr size_t lpi = in + (size_t)T * 4;
+  static constexpr size_t out = lpi + (size_t)T * 2;
+  static constexpr size_t tbl = out + (size_t)T * 4;
+  static constexpr size_t mbar = tbl + (size_t)T * 4;
+  static constexpr size_t misc = mbar + 8;
+  static constexpr size_t bytes = misc + 8;
+};
+
+// Stage the tile's keys and local labels into shared memory.  Returns len.
+template <int T>
+__device__ __forceinline__ int stage_tile(const uint32_t* src, const uint16_t* lpi,
+                                          int64_t n, int64_t tile, uint32_t* in_s,
+                                          uint16_t* lpi_s, uint64_t* mbar, unsigned* status) {
+  const int64_t start = tile * T;
+  const int len = (int)min((int64_t)T, n - start);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    const unsigned bk = (unsigned)(len * 4) & ~15u;
+    const unsigned bl = (unsigned)(len * 2) & ~15u;
+    mbar_arrive_expect_tx(mbar, bk + bl);
+    if (bk) bulk_g2s(in_s, src + start, bk, mbar);
+    if (bl) bulk_g2s(lpi_s, lpi + start, bl, mbar);
+  }
+  __syncthreads();
+  for (int i = (((len * 4) & ~15) >> 2) + threadIdx.x; i < len; i += blockDim.x) in_s[i] = src[start + i];
+  for (int i = (((len * 2) & ~15) >> 1) + threadIdx.x; i < len; i += blockDim.x) lpi_s[i] = lpi[start + i];
+  mbar_wait(mbar, 0, status);
+  __syncthreads();
+  return len;
+}
+
+template <int T>
+__device__ __forceinline__ void write_tile(uint32_t* dst, int64_t start, int len,
+                                          const uint32_t* out_s) {
+  if (len == T) {
+    const uint4* o4 = reinterpret_cast<const uint4*>(out_s);
+    uint4* d4 = reinterpret_cast<uint4*>(dst + start);
+    for (int i = threadIdx.x; i < T / 4; i += blockDim.x) __stcs(d4 + i, o4[i]);
+  } else {
+    for (int i = threadIdx.x; i < len; i += blockDim.x) dst[start + i] = out_s[i];
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(kTPThreads) k_tile_scatter(const uint32_t* __restrict__ src,
+                                                             uint32_t* __restrict__ dst,
+                                                             const uint16_t* __restrict__ lpi,
+                                                             int64_t n, unsigned* status) {
+  using S = TPSmem<T>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* in_s = reinterpret_cast<uint32_t*>(smem + S::in);
+  uint16_t* lpi_s = reinterpret_cast<uint16_t*>(smem + S::lpi);
+  uint32_t* out_s = reinterpret_cast<uint32_t*>(smem + S::out);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
+  const int len = stage_tile<T>(src, lpi, n, blockIdx.x, in_s, lpi_s, mbar, status);
+  for (int q = threadIdx.x; q < len; q += kTPThreads) {
+    const uint32_t p = lpi_s[q];
+    if ((int)p < len) out_s[p] = in_s[q];
+    else set_status(status, DEV_BAD_PERM);
+  }
+  __syncthreads();
+  write_tile<T>(dst, (int64_t)blockIdx.x * T, len, out_s);
+}
+
+// Coloured schedule.  Thread (warp g, lane l) owns row l's slots [g*M/4, (g+1)*M/4)
+// and, in the send phase, colours [g*M/4, (g+1)*M/4).  Table entry tbl[k*32 + l]
+// holds the item of colour k that row l sends this round: (label << 8) | slot.
+template <int T>
+__global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __restrict__ src,
+                                                              uint32_t* __restrict__ dst,
+                                                              const uint16_t* __restrict__ lpi,
+                                                              int64_t n, uint64_t seed,
+                                                              int rounds, unsigned* status) {
+  using S = TPSmem<T>;
+  constexpr int M = S::M;          // columns (slots per bank) = colours
+  constexpr int WARPS = kTPThreads / 32;
+  constexpr int SPW = M / WARPS;   // slots (and colours) per warp
+  static_assert(SPW <= 32, "one pending bit per owned slot");
+  constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* in_s = reinterpret_cast<uint32_t*>(smem + S::in);
+  uint16_t* lpi_s = reinterpret_cast<uint16_t*>(smem + S::lpi);
+  uint32_t* out_s = reinterpret_cast<uint32_t*>(smem + S::out);
+  uint32_t* tbl = reinterpret_cast<uint32_t*>(smem + S::tbl);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t tile = blockIdx.x;
+  const int len = stage_tile<T>(src, lpi, n, tile, in_s, lpi_s, mbar, status);
+
+  // Pending slots of this thread; labels outside the tile are dropped (and flagged).
+  uint32_t pending = 0;
+  for (int c = 0; c < SPW; ++c) {
+    const int s = warp * SPW + c, q = s * 32 + lane;
+    if (q < len) {
+      if ((int)lpi_s[q] < len) pending |= 1u << c;
+      else set_status(status, DEV_BAD_PERM);
+    }
+  }
+
+  for (int r = 0; r < rounds; ++r) {
+    // Coloring: h(i) for destination bank i, drawn fresh every round (held by lane i).
+    const uint32_t h_lane = mix32(seed ^ ((uint64_t)tile << 20) ^ ((uint64_t)r << 8) ^ (uint64_t)lane) & (M - 1);
+    for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) tbl[k * 32 + lane] = EMPTY;
+    __syncthreads();
+    // Claim the first free entry of each colour in this row; an item whose colour
+    // is already taken stays pending for the next round.
+    uint32_t todo = pending;
+    while (__any_sync(0xffffffffu, todo != 0)) {
+      const int c = todo ? __ffs(todo) - 1 : 0;
+      const int s = warp * SPW + c;
+      const uint32_t p = todo ? (uint32_t)lpi_s[s * 32 + lane] : 0u;
+      const uint32_t hi = __shfl_sync(0xffffffffu, h_lane, p & 31u);  // h(i), i = p mod 32
+      if (todo) {
+        todo &= todo - 1;
+        const uint32_t k = ((p >> 5) - hi) & (M - 1);
+        if (atomicCAS(&tbl[k * 32 + lane], EMPTY, (p << 8) | (uint32_t)s) == EMPTY)
+          pending &= ~(1u << c);
+      }
+    }
+    __syncthreads();
+    // Communication: in step k every row sends its colour-k item (if any); the
+    // destination banks of one step are distinct.
+#pragma unroll 4
+    for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) {
+      const uint32_t e = tbl[k * 32 + lane];
+      if (e != EMPTY) out_s[e >> 8] = in_s[(e & 0xFFu) * 32 + lane];
+    }
+    __syncthreads();
+  }
+
+  // Finish: greedy conflict-free sends.  Each lane offers its next pending item;
+  // among lanes aiming at one destination bank only the lowest sends.
+  while (__any_sync(0xffffffffu, pending != 0)) {
+    const int c = pending ? __ffs(pending) - 1 : 0;
+    const int s = warp * SPW + c;
+    const uint32_t p = pending ? (uint32_t)lpi_s[s * 32 + lane] : 0u;
+    const uint32_t bank = pending ? (p & 31u) : 32u + (uint32_t)lane;  // idle lanes never collide
+    const unsigned peers = __match_any_sync(0xffffffffu, bank);
+    if (pending && lane == __ffs(peers) - 1) {
+      out_s[p] = in_s[s * 32 + lane];
+      pending &= ~(1u << c);
+    }
+  }
+  __syncthreads();
+  write_tile<T>(dst, tile * T, len, out_s);
+}
+
+template <int T>
+static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi,
+                                int64_t n, bool coloured, uint64_t seed, cudaStream_t s) {
+  using S = TPSmem<T>;
+  const int64_t tiles = (n + T - 1) / T;
+  if (coloured) {
+    auto k = k_tile_coloured<T>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    k<<<(unsigned)tiles, kTPThreads, S::bytes, s>>>(src, dst, lpi, n, seed, 3, status_word());
+  } else {
+    auto k = k_tile_scatter<T>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    k<<<(unsigned)tiles, kTPThreads, S::bytes, s>>>(src, dst, lpi, n, status_word());
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
+                          int tile, bool coloured, uint64_t seed, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  switch (tile) {
+    case 1024: return launch_tiles<1024>(src, dst, lpi, n, coloured, seed, s);
+    case 2048: return launch_tiles<2048>(src, dst, lpi, n, coloured, seed, s);
+    case 4096: return launch_tiles<4096>(src, dst, lpi, n, coloured, seed, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace bcf

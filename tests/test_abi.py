@@ -1,0 +1,85 @@
+"""The C ABI library loads and exports every function include/bcf.h declares, and
+its host-side argument checks reject bad calls before touching the GPU.  CPU only:
+no call here launches a kernel."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import paper_1507_01391_b300 as bcf
+
+
+def test_library_exports_every_header_function():
+    L = bcf.lib()
+    names = bcf.header_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # and the binding knows every one of them
+    assert set(names) == set(bcf._SIGS)
+
+
+def test_exports_listed_by_nm():
+    out = subprocess.run(["nm", "-D", "--defined-only", bcf._LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(bcf.header_functions()) <= exported
+
+
+def test_status_strings_and_version():
+    L = bcf.lib()
+    for code in range(9):
+        assert L.bcf_status_string(code)
+    assert L.bcf_status_string(99) == b"unknown status"
+    assert L.bcf_version() >= 10000
+
+
+def test_workspace_queries():
+    L = bcf.lib()
+    sz = ctypes.c_size_t(0)
+    assert L.bcf_sort_workspace_size(1 << 20, 4, 32, ctypes.byref(sz)) == bcf.OK
+    assert sz.value >= (1 << 20) * 8  # ping-pong buffers for keys and values
+    assert L.bcf_sort_workspace_size(-1, 4, 32, ctypes.byref(sz)) == bcf.E_INVAL
+    assert L.bcf_sort_workspace_size(10, 3, 32, ctypes.byref(sz)) == bcf.E_INVAL
+    assert L.bcf_sort_workspace_size(10, 4, 33, ctypes.byref(sz)) == bcf.E_INVAL
+    assert L.bcf_sort_workspace_size(1 << 30, 4, 32, ctypes.byref(sz)) == bcf.E_UNSUPPORTED
+    assert L.bcf_partition_workspace_size(4096, 257, 4, 0, ctypes.byref(sz)) == bcf.E_UNSUPPORTED
+    assert L.bcf_partition_workspace_size(4096, 0, 4, 0, ctypes.byref(sz)) == bcf.E_INVAL
+    assert L.bcf_permute_workspace_size(100, 0, ctypes.byref(sz)) == bcf.OK and sz.value == 0
+    assert L.bcf_permute_workspace_size(100, bcf.CHECK_PERM, ctypes.byref(sz)) == bcf.OK and sz.value >= 16
+
+
+def test_argument_checks_reject_without_launching():
+    """Null, misaligned or overlapping pointers fail on the host: fake addresses
+    are safe here because nothing is launched for a rejected call."""
+    L = bcf.lib()
+    P = ctypes.c_void_p
+    a, b, ws = P(0x10000), P(0x20000), P(0x40000)
+    mis = P(0x10004)
+    assert L.bcf_sort(None, None, b, None, 10, 0, 32, ws, 1 << 20, None) == bcf.E_INVAL
+    assert L.bcf_sort(mis, None, b, None, 10, 0, 32, ws, 1 << 20, None) == bcf.E_INVAL
+    assert L.bcf_sort(a, None, b, None, 10, 0, 32, ws, 8, None) == bcf.E_WORKSPACE
+    assert L.bcf_sort(a, None, P(0x10008), None, 10, 0, 32, ws, 1 << 20, None) == bcf.E_INVAL
+    assert L.bcf_sort(a, None, b, None, 10, 4, 32, ws, 1 << 20, None) == bcf.E_INVAL  # vals missing
+    assert L.bcf_partition(a, None, b, None, 10, 3, 0, bcf.ASSUME_BALANCED, ws, 1 << 20, None) == bcf.E_INVAL
+    assert L.bcf_partition(a, None, b, None, 10, 300, 0, 0, ws, 1 << 20, None) == bcf.E_UNSUPPORTED
+    assert L.bcf_permute(a, P(0x10010), b, 64, 4, 0, None, 0, None) == bcf.E_INVAL  # overlap
+    assert L.bcf_permute(a, b, None, 64, 4, 0, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute(a, b, ws, 64, 3, 0, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute(a, b, ws, 64, 4, bcf.CHECK_PERM, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute_tiles(a, b, ws, 64, 1000, 0, 0, None) == bcf.E_INVAL
+    assert L.bcf_gather(a, b, ws, 64, 64, 2, None) == bcf.E_INVAL
+    # empty inputs are valid no-ops
+    assert L.bcf_sort(None, None, None, None, 0, 0, 32, None, 0, None) == bcf.OK
+    assert L.bcf_permute(None, None, None, 0, 4, 0, None, 0, None) == bcf.OK
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bcf_copy", os.path.join(os.path.dirname(bcf.__file__), "__init__.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    monkeypatch.setattr(mod, "_LIB_PATH", str(tmp_path / "missing.so"))
+    mod._lib = None
+    with pytest.raises(ImportError):
+        mod.lib()

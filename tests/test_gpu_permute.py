@@ -1,0 +1,131 @@
+"""GPU parity: permutation scatter, gather and tile-local permutation through the C
+ABI, bit-exact against the CPU oracle, including NaN / -0.0 payload bits, ragged
+tails, the full-size 2^24 workload and the bad-permutation error path."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import bits_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bcf():
+    import paper_1507_01391_b300 as m
+    m.lib()
+    return m
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 31, 1000, 4097, 100_003])
+def test_permute_kv_float_payload(bcf, n):
+    keys = synth.uniform_keys(n, seed=n)
+    vals = synth.float_bits_payload(n, seed=n + 1)
+    pi = synth.random_perm(n, seed=n + 2)
+    ko, vo = bcf.permute_kv(dev(keys), dev(vals), dev(pi), check=True)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+    assert bits_equal(host(vo, np.float32), oracle.permute(vals, pi))
+
+
+@pytest.mark.parametrize("n", [7, 4096, 65_537])
+@pytest.mark.parametrize("dtype", [np.uint32, np.uint64])
+def test_permute_and_gather_elements(bcf, n, dtype):
+    x = synth.uniform_keys(n * (np.dtype(dtype).itemsize // 4), seed=3).view(dtype)
+    pi = synth.random_perm(n, seed=4)
+    y = bcf.permute(dev(x), dev(pi))
+    assert bits_equal(host(y, dtype), oracle.permute(x, pi))
+    z = bcf.gather(y, dev(pi))
+    assert bits_equal(host(z, dtype), oracle.gather(oracle.permute(x, pi), pi))
+    assert bits_equal(host(z, dtype), x)
+    assert bcf.get_status() == bcf.OK
+
+
+def test_permute_keys_only(bcf):
+    n = 12_345
+    keys = synth.uniform_keys(n, seed=8)
+    pi = synth.random_perm(n, seed=9)
+    ko, vo = bcf.permute_kv(dev(keys), None, dev(pi))
+    assert vo is None
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+
+
+@pytest.mark.slow
+def test_permute_full_size_2pow24(bcf):
+    n = 1 << 24
+    keys = synth.uniform_keys(n, seed=0x1A)
+    vals = synth.float_bits_payload(n, seed=0x1B)
+    pi = synth.random_perm(n, seed=0x1C)
+    ko, vo = bcf.permute_kv(dev(keys), dev(vals), dev(pi))
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+    assert bits_equal(host(vo, np.float32), oracle.permute(vals, pi))
+
+
+def test_permute_reports_non_bijection(bcf):
+    n = 1000
+    pi = synth.random_perm(n, seed=1)
+    pi[10] = pi[11]
+    bcf.permute(dev(synth.uniform_keys(n, seed=2)), dev(pi), check=True)
+    assert bcf.get_status() == bcf.E_BAD_PERM
+    pi = synth.random_perm(n, seed=1)
+    pi[3] = n + 5  # out of range: never written, always reported
+    bcf.permute(dev(synth.uniform_keys(n, seed=2)), dev(pi))
+    assert bcf.get_status() == bcf.E_BAD_PERM
+
+
+def test_gather_reports_out_of_range(bcf):
+    idx = np.array([0, 1, 99, 2], dtype=np.uint32)
+    bcf.gather(dev(np.arange(4, dtype=np.uint32)), dev(idx))
+    assert bcf.get_status() == bcf.E_BAD_PERM
+
+
+# ------------------------------------------------------------ tile-local
+@pytest.mark.parametrize("coloured", [False, True])
+@pytest.mark.parametrize("tile", [1024, 2048, 4096])
+@pytest.mark.parametrize("n_tiles,extra", [(1, 0), (3, 0), (5, 77), (0, 33)])
+def test_permute_tiles(bcf, coloured, tile, n_tiles, extra):
+    n = n_tiles * tile + extra
+    src = synth.uniform_keys(n, seed=n + tile)
+    lpi = synth.tile_local_perms(n, tile, seed=n)
+    out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(out, np.uint32), oracle.permute_tiles(src, lpi, tile))
+
+
+@pytest.mark.parametrize("coloured", [False, True])
+def test_permute_tiles_structured(bcf, coloured):
+    """Adversarial labels for the colouring: identity, reversal, a transpose of
+    the 32 x 128 bank matrix (every row sends all its items to one bank), and all
+    items of a row aimed at one slot column."""
+    tile, m = 4096, 128
+    q = np.arange(tile)
+    cases = [q, q[::-1], (q % 32) * m + q // 32, ((q % 32) * 32 + (q // 32) % 32 + 1024 * ((q // 32) // 32)) % tile]
+    for lab in cases:
+        lpi = np.asarray(lab, dtype=np.uint16)
+        assert len(np.unique(lpi)) == tile
+        src = synth.uniform_keys(tile, seed=5)
+        out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured, seed=123)
+        assert bits_equal(host(out, np.uint32), oracle.permute_tiles(src, lpi, tile))
+    assert bcf.get_status() == bcf.OK
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("coloured", [False, True])
+def test_permute_tiles_full_size(bcf, coloured):
+    n, tile = 1 << 24, 4096
+    src = synth.uniform_keys(n, seed=0x1D)
+    lpi = synth.tile_local_perms(n, tile, seed=0x1E)
+    out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(out, np.uint32), oracle.permute_tiles(src, lpi, tile))
+
+
+def test_permute_tiles_reports_bad_label(bcf):
+    tile = 1024
+    lpi = synth.tile_local_perms(tile + 100, tile, seed=1)
+    lpi[tile + 5] = 500  # outside the 100-item ragged tile
+    for coloured in (False, True):
+        bcf.permute_tiles(dev(synth.uniform_keys(tile + 100, seed=2)), dev(lpi), tile=tile, coloured=coloured)
+        assert bcf.get_status() == bcf.E_BAD_PERM

@@ -1,0 +1,159 @@
+"""GPU parity: radix sort and w-way partition through the C ABI, bit-exact against
+the CPU oracle (keys and payloads), on seeded inputs that span several tiles and
+a ragged tail, plus the full-size workloads and the device-side error paths."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import bits_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+
+TILE = 4096
+SIZES = [1, 2, 31, 32, 33, 1000, TILE - 1, TILE, TILE + 1, 3 * TILE + 5, 50_001]
+
+
+@pytest.fixture(scope="module")
+def bcf():
+    import paper_1507_01391_b300 as m
+    m.lib()
+    return m
+
+
+def _sort_case(bcf, keys, vals, key_bits=32, in_place=False):
+    kd = dev(keys)
+    vd = None if vals is None else dev(vals)
+    if in_place:
+        ko, vo = bcf.sort(kd, vd, key_bits=key_bits, keys_out=kd, vals_out=vd)
+    else:
+        ko, vo = bcf.sort(kd, vd, key_bits=key_bits)
+    assert bcf.get_status() == bcf.OK
+    rk, rv = oracle.sort_kv(keys, vals)
+    assert bits_equal(host(ko, np.uint32), rk)
+    if vals is not None:
+        assert bits_equal(host(vo, vals.dtype), rv)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_sort_uniform_kv(bcf, n):
+    _sort_case(bcf, synth.uniform_keys(n, seed=n), synth.index_payload(n))
+
+
+@pytest.mark.parametrize("kind", ["equal", "sorted", "reverse", "few", "zipf"])
+def test_sort_structured(bcf, kind):
+    n = 2 * TILE + 77
+    if kind == "equal":
+        keys = np.full(n, 0xDEADBEEF, np.uint32)
+    elif kind == "sorted":
+        keys = np.sort(synth.uniform_keys(n, seed=1))
+    elif kind == "reverse":
+        keys = np.sort(synth.uniform_keys(n, seed=2))[::-1].copy()
+    elif kind == "few":
+        keys = synth.random_labels(n, 3, seed=3)
+    else:
+        keys = synth.zipf_keys(n, seed=4)
+    _sort_case(bcf, keys, synth.index_payload(n))
+
+
+@pytest.mark.parametrize("vb", [0, 4, 8])
+@pytest.mark.parametrize("key_bits", [1, 7, 8, 9, 20, 31, 32])
+def test_sort_widths_and_key_bits(bcf, vb, key_bits):
+    n = 2 * TILE + 333
+    keys = synth.uniform_keys(n, seed=key_bits, bits=key_bits)
+    vals = None
+    if vb == 4:
+        vals = synth.float_bits_payload(n, seed=5)  # NaN / -0.0 bit patterns
+    elif vb == 8:
+        vals = synth.uniform_keys(2 * n, seed=6).view(np.uint64)
+    _sort_case(bcf, keys, vals, key_bits=key_bits)
+
+
+@pytest.mark.parametrize("key_bits", [8, 20, 32])
+def test_sort_in_place(bcf, key_bits):
+    n = 3 * TILE + 1
+    _sort_case(bcf, synth.uniform_keys(n, seed=9, bits=key_bits), synth.index_payload(n),
+               key_bits=key_bits, in_place=True)
+
+
+def test_sort_empty(bcf):
+    import torch
+    k = torch.empty(0, dtype=torch.int32, device="cuda")
+    ko, _ = bcf.sort(k, None)
+    assert ko.numel() == 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kind", ["uniform", "zipf"])
+def test_sort_full_size_2pow26(bcf, kind):
+    """The 2^26 key-value sort workload, compared in full with the oracle."""
+    n = 1 << 26
+    keys = synth.uniform_keys(n, seed=0x2A) if kind == "uniform" else synth.zipf_keys(n, seed=0x2B)
+    _sort_case(bcf, keys, synth.index_payload(n))
+
+
+# ---------------------------------------------------------------- partition
+def _partition_case(bcf, keys, vals, w, balanced, in_place=False):
+    kd = dev(keys)
+    vd = None if vals is None else dev(vals)
+    if in_place:
+        ko, vo = bcf.partition(kd, vd, w, balanced=balanced, keys_out=kd, vals_out=vd)
+    else:
+        ko, vo = bcf.partition(kd, vd, w, balanced=balanced)
+    assert bcf.get_status() == bcf.OK
+    rk, rv = oracle.partition_kv(keys, vals, w, balanced=balanced)
+    assert bits_equal(host(ko, np.uint32), rk)
+    if vals is not None:
+        assert bits_equal(host(vo, vals.dtype), rv)
+
+
+def test_partition_w32_n65536_balanced(bcf):
+    """The w = 32, n = 65536 workload: 2048 copies of each label."""
+    n, w = 65536, 32
+    _partition_case(bcf, synth.partition_keys(n, w, seed=0x1507), synth.index_payload(n), w, True)
+
+
+@pytest.mark.parametrize("w", [1, 2, 5, 31, 32, 33, 64, 100, 255, 256])
+@pytest.mark.parametrize("balanced", [True, False])
+def test_partition_widths(bcf, w, balanced):
+    n = w * (3 * TILE // w + 7)
+    keys = synth.partition_keys(n, w, seed=w) if balanced else synth.random_labels(n, w, seed=w)
+    _partition_case(bcf, keys, synth.index_payload(n), w, balanced)
+
+
+@pytest.mark.parametrize("n", [1, 33, TILE + 1, 3 * TILE + 5])
+@pytest.mark.parametrize("vb", [0, 8])
+def test_partition_ragged_and_widths(bcf, n, vb):
+    w = 7
+    keys = synth.random_labels(n, w, seed=n)
+    vals = None if vb == 0 else synth.uniform_keys(2 * n, seed=1).view(np.uint64)
+    _partition_case(bcf, keys, vals, w, False)
+
+
+def test_partition_in_place(bcf):
+    n, w = 4 * TILE, 64
+    _partition_case(bcf, synth.partition_keys(n, w, seed=3), synth.index_payload(n), w, True, in_place=True)
+
+
+@pytest.mark.slow
+def test_partition_full_size_w256(bcf):
+    n, w = 1 << 26, 256
+    _partition_case(bcf, synth.partition_keys(n, w, seed=0x2C), synth.index_payload(n), w, True)
+
+
+def test_partition_reports_bad_label(bcf):
+    n, w = 2 * TILE, 16
+    keys = synth.random_labels(n, w, seed=1)
+    keys[777] = 16
+    kd = dev(keys)
+    bcf.partition(kd, None, w)
+    assert bcf.get_status() == bcf.E_BAD_KEY
+    assert bcf.get_status() == bcf.OK  # reading clears the word
+
+
+def test_partition_reports_unbalanced(bcf):
+    n, w = 2 * TILE, 16
+    keys = synth.partition_keys(n, w, seed=2)
+    keys[5] = (keys[5] + 1) % w  # one label too many, another too few
+    bcf.partition(dev(keys), None, w, balanced=True)
+    assert bcf.get_status() == bcf.E_NOT_BALANCED

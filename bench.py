@@ -1,0 +1,611 @@
+"""Benchmark: bank-conflict-free permute / sort / partition on one B300.
+
+Prints ONE JSON line.  Headline workload (one "step"): the key-value permutation
+of n = 2^24 uint32 keys with float32 payloads by a uniform random pi
+(out[pi[i]] = in[i]) followed by the tile-local permutation of 2^24 uint32 keys in
+4096-key tiles; value = keys moved per second over both (2 x 2^24 keys per step),
+inputs resident in HBM.  Every input is seeded synthetic data; every input is
+larger than the 126 MB L2, so no flush runs between steps.
+
+Also reported, per hot-path row (`rows`): the 2^26 key-value radix sort (uniform
+and Zipf keys), the 2^26 w = 256 partition, the 65536-key w = 32 partition, both
+tile-permutation schedules, and whatever else the library implements, each with
+its own CUDA-event timing, bytes model and roofline fraction.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-rows]
+
+Under torchrun (N > 1) every rank runs its own replica of the step (weak scaling,
+no data exchange); rank 0 prints the aggregate.  --impl reference times the CPU
+oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_PERM = 1 << 24
+TILE = 4096
+METRIC = "Gkeys/s and % of HBM roofline (sort/permute/w-partition); smem bank conflicts"
+UNIT = "Gkeys/s"
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6400.0
+
+# Per-launch DRAM traffic of the dominant kernel from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
+# it was taken on: if permute.cu changes, the figure is dropped (null).
+NCU_TRAFFIC = {"kernel": "k_permute<4,4>", "source_sha1": None, "bytes": None,
+               "summary": "profiles/k_permute_kv_2pow24.md"}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="bcf", choices=["bcf", "reference"])
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-row breakdown")
+    ap.add_argument("--rows-only", default="", help="comma list of rows to run")
+    ap.add_argument("--case", default="", choices=[""] + sorted(CASES),
+                    help="run one named workload --warmup + --steps times (for profiler captures)")
+    return ap.parse_args()
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def file_sha1(path):
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling around the timed region.
+
+    The sampler starts before the warm-up and waits for its first sample; samples
+    whose host timestamp falls inside [t0, t1] of the timed region are kept (if
+    the region is shorter than the sampling period, the nearest sample is used)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index, period_ms=20):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.path = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+            self.rows = []
+            import threading
+
+            def reader():
+                for line in self.proc.stdout:
+                    self.rows.append((time.time(), line.strip()))
+            self.thread = threading.Thread(target=reader, daemon=True)
+            self.thread.start()
+            t = time.time()
+            while not self.rows and time.time() - t < 10:
+                time.sleep(0.01)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(2 * self.period / 1000.0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        parsed = []
+        for ts, line in self.rows:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                parsed.append((ts, parts))
+        if self.path and os.path.exists(self.path):
+            os.unlink(self.path)
+        if not parsed:
+            return None
+        inside = [r for ts, r in parsed if self.t0 is not None and self.t0 <= ts <= (self.t1 or ts)]
+        if not inside and self.t0 is not None:  # region shorter than one period: nearest after t0
+            after = [(ts, r) for ts, r in parsed if ts >= self.t0]
+            inside = [after[0][1]] if after else [parsed[-1][1]]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in inside if num(r[0]) is not None]
+        mx = [num(r[1]) for r in inside if num(r[1]) is not None]
+        reasons = sorted({self.NAMES[k] for r in inside for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inside), "period_ms": self.period}
+
+
+# ------------------------------------------------------------------ inputs
+def headline_inputs(seed_base, rank):
+    import synth
+    s = seed_base + 1000 * rank
+    return {
+        "keys": synth.uniform_keys(N_PERM, seed=s + 1),
+        "vals": synth.float_bits_payload(N_PERM, seed=s + 2),
+        "pi": synth.random_perm(N_PERM, seed=s + 3),
+        "tsrc": synth.uniform_keys(N_PERM, seed=s + 4),
+        "lpi": synth.tile_local_perms(N_PERM, TILE, seed=s + 5),
+    }
+
+
+def to_dev(a):
+    import torch
+    view = {4: np.int32, 2: np.int16, 8: np.int64}[a.dtype.itemsize]
+    return torch.from_numpy(np.ascontiguousarray(a).view(view)).cuda()
+
+
+def ev_ms(fn, warmup=3, iters=10):
+    """Median CUDA-event time of fn() on the current stream, in ms."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(iters):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts), ts
+
+
+# ------------------------------------------------------------------ headline
+def run_headline(args, rank, world, local):
+    import torch
+
+    import paper_1507_01391_b300 as bcf
+    bcf.lib()
+    x = headline_inputs(0x150701391, rank)
+    d = {k: to_dev(v) for k, v in x.items()}
+    ko = torch.empty_like(d["keys"])
+    vo = torch.empty_like(d["vals"])
+    to = torch.empty_like(d["tsrc"])
+
+    def step(kev=None):
+        if kev is not None:
+            kev[0].record()
+        bcf.permute_kv(d["keys"], d["vals"], d["pi"], keys_out=ko, vals_out=vo)
+        if kev is not None:
+            kev[1].record()
+        bcf.permute_tiles(d["tsrc"], d["lpi"], tile=TILE, dst=to)
+
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    sampler.mark(0)
+    t0.record()
+    for k in range(args.steps):
+        step(kevs[k])
+    t1.record()
+    torch.cuda.synchronize()
+    sampler.mark(1)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    ms_total = t0.elapsed_time(t1)
+    kern_ms = statistics.mean(a.elapsed_time(b) for a, b in kevs)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    st = bcf.get_status()
+    # correctness of the timed outputs (cheap spot check on the device)
+    ok = bool(st == bcf.OK)
+    # end to end through the public API with pinned host buffers
+    e2e = run_e2e(args, bcf, x)
+    return {"ms_total": ms_total, "kern_ms": kern_ms, "clocks": clocks, "status_ok": ok, "e2e": e2e}
+
+
+def run_e2e(args, bcf, x):
+    import torch
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v).view({4: np.int32, 2: np.int16}[v.dtype.itemsize])).pin_memory()
+           for k, v in x.items()}
+    dev = {k: torch.empty_like(v, device="cuda") for k, v in pin.items()}
+    outs_h = [torch.empty(N_PERM, dtype=torch.int32).pin_memory() for _ in range(2)]
+    outs_h.append(torch.empty(N_PERM, dtype=torch.float32).pin_memory())
+    ko = torch.empty(N_PERM, dtype=torch.int32, device="cuda")
+    vo = torch.empty(N_PERM, dtype=torch.float32, device="cuda")
+    to = torch.empty(N_PERM, dtype=torch.int32, device="cuda")
+    h2d = sum(v.numel() * v.element_size() for v in pin.values())
+    d2h = 3 * N_PERM * 4
+
+    def step():
+        for k in pin:
+            dev[k].copy_(pin[k], non_blocking=True)
+        bcf.permute_kv(dev["keys"], dev["vals"].view(torch.float32), dev["pi"], keys_out=ko, vals_out=vo)
+        bcf.permute_tiles(dev["tsrc"], dev["lpi"], tile=TILE, dst=to)
+        outs_h[0].copy_(ko, non_blocking=True)
+        outs_h[1].copy_(to, non_blocking=True)
+        outs_h[2].copy_(vo, non_blocking=True)
+
+    steps = max(3, args.steps // 2)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / steps
+    return {"value": round(2 * N_PERM / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3)}
+
+
+# ------------------------------------------------------------------ CPU leg
+def oracle_inputs(n, seed_base=0x150701391):
+    import synth
+    return (synth.uniform_keys(n, seed=seed_base + 1), synth.float_bits_payload(n, seed=seed_base + 2),
+            synth.random_perm(n, seed=seed_base + 3), synth.uniform_keys(n, seed=seed_base + 4),
+            synth.tile_local_perms(n, TILE, seed=seed_base + 5))
+
+
+def oracle_step(inp):
+    """One CPU-oracle step on a sample of the headline workload; returns seconds."""
+    import oracle
+    keys, vals, pi, tsrc, lpi = inp
+    L = oracle.lib()
+    t = time.perf_counter()
+    oracle.permute(keys, pi, L=L)
+    oracle.permute(vals, pi, L=L)
+    oracle.permute_tiles(tsrc, lpi, TILE, L=L)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(budget_s=12.0, n=1 << 22):
+    inp = oracle_inputs(n)
+    total, reps = 0.0, 0
+    while total < budget_s and reps < 20:
+        total += oracle_step(inp)
+        reps += 1
+    return {"value": round(2 * n * reps / total / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d repetitions of the step on an n=2^%d sample (kv permute + tile permute), "
+                      "single-threaded plain C" % (reps, int(np.log2(n)))}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    n = 1 << 22
+    inp = oracle_inputs(n)
+    for _ in range(max(args.warmup, 1)):
+        oracle_step(inp)
+    ts = [oracle_step(inp) for _ in range(args.steps)]
+    total = sum(ts)
+    value = 2 * n * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": headline_config(),
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: n=2^22 sample of the workload (kv permute + tile permute), single-threaded plain C oracle"},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def headline_config():
+    return {"workload": "permute 2^24 uint32 keys + float32 payloads by a uniform random pi "
+                        "(out[pi[i]] = in[i]), then tile-local permute of 2^24 uint32 keys in "
+                        "4096-key tiles by per-tile uniform random uint16 permutations",
+            "n": N_PERM, "tile": TILE, "keys_per_step": 2 * N_PERM,
+            "l2": "every input larger than the 126 MB L2 (no flush between steps)",
+            "tile_schedule": "scatter"}
+
+
+# ------------------------------------------------------------------ rows
+def run_rows(which, peak):
+    import torch
+
+    import paper_1507_01391_b300 as bcf
+    import synth
+    rows = {}
+
+    def add(name, nkeys, bytes_model, ms, note=""):
+        gbs = bytes_model / (ms * 1e-3) / 1e9
+        rows[name] = {"ms": round(ms, 4), "gkeys_s": round(nkeys / (ms * 1e-3) / 1e9, 3),
+                      "bytes_model": int(bytes_model), "achieved_gbs": round(gbs, 1),
+                      "frac_measured": round(gbs / peak, 4), "frac_8tbs": round(gbs / NOMINAL_HBM_GBS, 4)}
+        if note:
+            rows[name]["note"] = note
+        log("row %-34s %9.4f ms %8.2f Gkeys/s %7.1f GB/s" % (name, ms, rows[name]["gkeys_s"], gbs))
+
+    def want(name):
+        return not which or name in which
+
+    if want("partition_w32_n65536"):
+        n, w = 65536, 32
+        k = to_dev(synth.partition_keys(n, w, seed=0x150701391))
+        v = to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED))
+        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 5, 50)
+        add("partition_w32_n65536", n, 16 * n, ms, "launch-latency bound at this size")
+    if want("permute_kv_2pow24") or want("tile_permute_scatter_2pow24") or want("tile_permute_coloured_2pow24"):
+        n = N_PERM
+        k = to_dev(synth.uniform_keys(n, seed=1))
+        v = to_dev(synth.float_bits_payload(n, seed=2))
+        pi = to_dev(synth.random_perm(n, seed=3))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        if want("permute_kv_2pow24"):
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo))
+            add("permute_kv_2pow24", n, 20 * n, ms, "keys pass + payload pass (chosen form)")
+        if want("permute_kv_fused_2pow24"):
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, fused=True))
+            add("permute_kv_fused_2pow24", n, 20 * n, ms, "one fused pass (plain form)")
+        lpi = to_dev(synth.tile_local_perms(n, TILE, seed=4))
+        for coloured in (False, True):
+            name = "tile_permute_%s_2pow24" % ("coloured" if coloured else "scatter")
+            if want(name):
+                ms, _ = ev_ms(lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=coloured, dst=ko))
+                add(name, n, 10 * n, ms)
+        del k, v, pi, ko, vo, lpi
+    for kind in ("uniform", "zipf"):
+        name = "sort_kv_2pow26_%s" % kind
+        if not want(name):
+            continue
+        n = 1 << 26
+        keys = synth.uniform_keys(n, seed=0x2A) if kind == "uniform" else synth.zipf_keys(n, seed=0x2B)
+        k = to_dev(keys)
+        v = to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
+        ms, _ = ev_ms(lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+        add(name, n, (4 + 4 * 16) * n, ms, "4 passes of 8 bits + one histogram read")
+        del k, v, ko, vo, ws
+    if want("partition_w256_2pow26"):
+        n, w = 1 << 26, 256
+        k = to_dev(synth.partition_keys(n, w, seed=0x2C))
+        v = to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED))
+        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+        add("partition_w256_2pow26", n, 16 * n, ms)
+        del k, v, ko, vo, ws
+    if want("tile_sort_lemma1_2pow24"):
+        n = N_PERM
+        k = to_dev(synth.uniform_keys(n, seed=7))
+        v = to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ms, _ = ev_ms(lambda: bcf.sort_tiles(k, v, keys_out=ko, vals_out=vo))
+        add("tile_sort_lemma1_2pow24", n, 16 * n, ms,
+            "4096-key tiles, Lemma 1 comparison sort (ALU bound); bytes: key r/w + payload gather r/w")
+        del k, v, ko, vo
+    plain_ns = {}
+    if want("segmented_sort_batched_10k") or want("segmented_partition_batched_10k"):
+        sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
+        offs_np = synth.offsets_from_sizes(sizes)
+        n = int(offs_np[-1])
+        small = sizes[sizes <= 4096].sum()
+        offs = torch.from_numpy(offs_np).cuda()
+        if want("segmented_sort_batched_10k"):
+            k = to_dev(synth.uniform_keys(n, seed=0x4B))
+            v = to_dev(synth.index_payload(n))
+            ko, vo = torch.empty_like(k), torch.empty_like(v)
+            ws = bcf.workspace(bcf.segmented_sort_workspace_size(n, 10_000, 4, 32))
+            ms, _ = ev_ms(lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws), 2, 5)
+            add("segmented_sort_batched_10k", n, 16 * small + 68 * (n - small), ms,
+                "%d keys; segments <= 4096 keys sorted whole in shared memory (16 B/key), longer ones "
+                "by 4 digit passes + histogram (68 B/key)" % n)
+            del k, v, ko, vo, ws
+        if want("segmented_partition_batched_10k"):
+            keys, poffs, w = synth.segmented_partition_input(10_000, seed=0x4C)
+            n2 = keys.size
+            k = to_dev(keys)
+            v = to_dev(synth.index_payload(n2))
+            po = torch.from_numpy(poffs).cuda()
+            wd = to_dev(w)
+            ko, vo = torch.empty_like(k), torch.empty_like(v)
+            ws = bcf.workspace(bcf.segmented_partition_workspace_size(n2, 10_000, 4))
+            ms, _ = ev_ms(lambda: bcf.segmented_partition(k, v, po, wd, balanced=True, keys_out=ko,
+                                                          vals_out=vo, ws=ws), 2, 5)
+            add("segmented_partition_batched_10k", n2, 16 * n2, ms, "%d keys, w in {32..256} per segment" % n2)
+            del k, v, ko, vo, ws
+    if want("autograd_sort_by_key_64x65536") or want("autograd_permute_rows_64x65536"):
+        from paper_1507_01391_b300 import autograd
+        B, n = 64, 65536
+        keys = to_dev(synth.uniform_keys(B * n, seed=0x3A, bits=20)).view(B, n)
+        vals = torch.from_numpy(synth.normal_f32((B, n), seed=0x3B)).cuda().requires_grad_(True)
+        g = torch.from_numpy(synth.normal_f32((B, n), seed=0x3C)).cuda()
+        if want("autograd_sort_by_key_64x65536"):
+            def fb():
+                vals.grad = None
+                _, y = autograd.sort_by_key(keys, vals, 20)
+                y.backward(g)
+            ms, _ = ev_ms(fb, 3, 10)
+            # plain form: one key-value sort of the same 2^22 keys (20-bit keys)
+            kf = keys.reshape(-1)
+            vf = to_dev(synth.index_payload(B * n))
+            ko, vo = torch.empty_like(kf), torch.empty_like(vf)
+            ws = bcf.workspace(bcf.sort_workspace_size(B * n, 4, 20))
+            ms_plain, _ = ev_ms(lambda: bcf.sort(kf, vf, key_bits=20, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+            add("autograd_sort_by_key_64x65536", B * n, B * n * (3 * 16 + 4 + 12 + 12), ms,
+                "forward (3 digit passes + gather) and backward scatter; plain kv sort of the same "
+                "keys %.4f ms -> ratio %.2f" % (ms_plain, ms / ms_plain))
+            rows["autograd_sort_by_key_64x65536"]["plain_sort_ms"] = round(ms_plain, 4)
+            rows["autograd_sort_by_key_64x65536"]["ratio_vs_plain"] = round(ms / ms_plain, 3)
+        if want("autograd_permute_rows_64x65536"):
+            pi = to_dev(np.concatenate([synth.random_perm(n, seed=100 + b) for b in range(B)])).view(B, n)
+
+            def fb2():
+                vals.grad = None
+                autograd.permute_rows(vals, pi).backward(g)
+            ms, _ = ev_ms(fb2, 3, 10)
+            add("autograd_permute_rows_64x65536", B * n, B * n * 24, ms,
+                "forward scatter (12 B/key) + backward gather (12 B/key)")
+    assert bcf.get_status() == bcf.OK, "device status after the rows"
+    torch.cuda.empty_cache()
+    return rows
+
+
+# ------------------------------------------------------------------ cases
+def _case_inputs(name):
+    import torch
+
+    import paper_1507_01391_b300 as bcf
+    import synth
+    n = 1 << 24
+    if name == "permute_kv":
+        k, v, pi = (to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.float_bits_payload(n, seed=2)),
+                    to_dev(synth.random_perm(n, seed=3)))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        return lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo)
+    if name in ("tile_scatter", "tile_coloured"):
+        k, lpi = to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.tile_local_perms(n, TILE, seed=4))
+        ko = torch.empty_like(k)
+        return lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=(name == "tile_coloured"), dst=ko)
+    if name == "sort_kv":
+        k, v = to_dev(synth.uniform_keys(n, seed=0x2A)), to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
+        return lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws)
+    if name in ("partition_w32", "partition_w256"):
+        w = 32 if name == "partition_w32" else 256
+        m = 65536 if w == 32 else n
+        k, v = to_dev(synth.partition_keys(m, w, seed=5)), to_dev(synth.index_payload(m))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.partition_workspace_size(m, w, 4, bcf.ASSUME_BALANCED))
+        return lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws)
+    raise ValueError(name)
+
+
+CASES = ("permute_kv", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256")
+
+
+def run_case(args):
+    import torch
+
+    import paper_1507_01391_b300 as bcf
+    fn = _case_inputs(args.case)
+    for _ in range(args.warmup + args.steps):
+        fn()
+    torch.cuda.synchronize()
+    st = bcf.get_status()
+    print("case %s: %d calls, status %d" % (args.case, args.warmup + args.steps, st), flush=True)
+    return 0 if st == bcf.OK else 1
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.case:
+        import torch
+        torch.cuda.set_device(local)
+        return run_case(args)
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    peak, peak_kind = measured_peaks()
+    h = run_headline(args, rank, world, local)
+    ms_step = h["ms_total"] / args.steps
+    keys_step = 2 * N_PERM
+    value = world * keys_step / (ms_step * 1e-3) / 1e9
+    bytes_launch = 20 * N_PERM
+    achieved = bytes_launch / (h["kern_ms"] * 1e-3) / 1e9
+    src_sha = file_sha1(os.path.join(ROOT, "paper_1507_01391_b300", "csrc", "permute.cu"))
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["source_sha1"] == src_sha else None
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded: uniform keys, random float32 bit patterns, uniform pi, per-tile uniform uint16 labels)",
+        "config": headline_config(),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic,
+                     "kernel": NCU_TRAFFIC["kernel"], "bytes_per_launch": bytes_launch,
+                     "kernel_ms": round(h["kern_ms"], 4), "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                     "frac_of_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4)},
+        "gpu_launches": 3 * args.steps,  # keys pass + payload pass + tile permute
+        "clocks": h["clocks"],
+        "e2e": h["e2e"],
+        "status_ok": h["status_ok"],
+    }
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+        if not args.no_rows:
+            which = set(filter(None, args.rows_only.split(",")))
+            line["rows"] = run_rows(which, peak)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

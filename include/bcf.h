@@ -23,6 +23,9 @@
  *    no kernel writes outside the caller's buffers and no kernel waits forever.
  *  - Keys are uint32.  Payload ("value") elements are 0, 4 or 8 bytes and are
  *    moved as raw bits (float NaN / -0.0 patterns survive).  Sizes are int64.
+ *  - Index payload: for the sorts, vals_in == NULL with val_bytes == 4 means the
+ *    payload of item i is i (its input position, counted from the start of the
+ *    array), so vals_out receives the sorting permutation (an argsort).
  *  - Nothing here throws; no function keeps host state between calls.
  */
 #ifndef BCF_H
@@ -48,12 +51,14 @@ typedef struct CUstream_st* bcf_stream_t;
 #define BCF_E_NOT_BALANCED 6   /* device: balanced partition saw a count != n/w */
 #define BCF_E_BAD_PERM 7       /* device: pi not a bijection / index out of range */
 #define BCF_E_BAD_KEY 8        /* device: partition label >= w */
+/* (device-detected bad CSR offsets or per-segment widths report BCF_E_INVAL) */
 
 /* ---- flags ---- */
 #define BCF_ASSUME_BALANCED 0x1   /* partition: exactly n/w copies of each label */
 #define BCF_CHECK_PERM 0x2        /* permute: verify pi is a bijection (needs ws) */
 #define BCF_TILES_COLOURED 0x10   /* permute_tiles: randomized colouring schedule */
 #define BCF_PARTITION_LEMMA1 0x20 /* partition (w <= 32): Lemma 1 tile schedule */
+#define BCF_PERMUTE_FUSED 0x40    /* permute_kv: one pass for keys and payloads */
 
 /* Message for a status code (static string; never NULL). */
 const char* bcf_status_string(int status);
@@ -63,15 +68,18 @@ int bcf_version(void);
 
 /* Synchronises `stream`, then reads and clears the device status word.  *out is
  * BCF_OK or the most severe device error recorded since the last call, in the
- * order BCF_E_TIMEOUT > BCF_E_BAD_PERM > BCF_E_NOT_BALANCED > BCF_E_BAD_KEY.  The
- * word is shared by all calls on the device.  Returns BCF_E_CUDA if the sync or
- * the read fails. */
+ * order BCF_E_TIMEOUT > BCF_E_INVAL > BCF_E_BAD_PERM > BCF_E_NOT_BALANCED >
+ * BCF_E_BAD_KEY.  The
+ * word is shared by all calls on the device; bad segment offsets or widths found
+ * on the device report BCF_E_INVAL.  Returns BCF_E_CUDA if the sync or the read
+ * fails. */
 int bcf_get_status(bcf_stream_t stream, int* out);
 
 /* ---------------------------------------------------------------------------
  * Sorting (Sec. 1; the paper sorts in O((n/w) log n) time, Lemma 1 and
  * Theorem 1).  Stable ascending sort of n (key, value) pairs by key.
- *  keys_in/vals_in   input, n keys and n values (vals_in NULL iff val_bytes 0)
+ *  keys_in/vals_in   input, n keys and n values (vals_in NULL: no payload when
+ *                    val_bytes is 0, index payload when it is 4)
  *  keys_out/vals_out output; may equal the inputs (in place); must not overlap
  *                    them otherwise
  *  val_bytes         0, 4 or 8
@@ -105,17 +113,22 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
 /* ---------------------------------------------------------------------------
  * Permutation (Sec. 1): dst[pi[i]] = src[i] for i in [0, n).
  *  elem_bytes  4 or 8 (bcf_permute); src and dst must not overlap.
+ *  row_len     0: pi holds global indices.  > 0: the arrays are rows of row_len
+ *              items and pi[i] is local to the row of i (a batch of independent
+ *              permutations): dst[row(i)*row_len + pi[i]] = src[i].
  *  flags       BCF_CHECK_PERM: also verify that pi is a bijection (device status
  *              BCF_E_BAD_PERM otherwise); needs bcf_permute_workspace_size() of
  *              ws, else ws may be NULL.
- * An index pi[i] >= n is never written; it sets BCF_E_BAD_PERM. */
+ * An index outside its range is never written; it sets BCF_E_BAD_PERM. */
 int bcf_permute_workspace_size(int64_t n, int flags, size_t* bytes);
-int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int elem_bytes,
-                int flags, void* ws, size_t ws_bytes, bcf_stream_t stream);
-/* Keys and values moved by one pi in one pass. */
+int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int64_t row_len,
+                int elem_bytes, int flags, void* ws, size_t ws_bytes, bcf_stream_t stream);
+/* Keys and values moved by one pi (val_bytes 0, 4 or 8).  By default the keys
+ * and the payloads are scattered in two passes, each of whose outputs stays in
+ * L2 while it fills; BCF_PERMUTE_FUSED scatters both in one pass. */
 int bcf_permute_kv(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
-                   const uint32_t* pi, int64_t n, int val_bytes, int flags, void* ws,
-                   size_t ws_bytes, bcf_stream_t stream);
+                   const uint32_t* pi, int64_t n, int64_t row_len, int val_bytes, int flags,
+                   void* ws, size_t ws_bytes, bcf_stream_t stream);
 
 /* Tile-local permutation (the paper's permutation problem on one shared-memory
  * matrix, Sec. 3): tile t covers [t*tile, min(n,(t+1)*tile)); the key at local
@@ -129,16 +142,19 @@ int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, i
                       int tile, int flags, uint64_t seed, bcf_stream_t stream);
 
 /* Gather: dst[i] = src[idx[i]] for i in [0, n); idx[i] < n_src, else the element
- * is not read and BCF_E_BAD_PERM is set.  The inverse direction of bcf_permute
- * (used by the backward pass of a permutation).  elem_bytes 4 or 8. */
+ * is not read, dst[i] is 0 and BCF_E_BAD_PERM is set.  row_len > 0: idx[i] is
+ * local to the row of i (rows of row_len items in both arrays).  The inverse
+ * direction of bcf_permute (the backward pass of a permutation).  elem_bytes 4
+ * or 8. */
 int bcf_gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
-               int elem_bytes, bcf_stream_t stream);
+               int64_t row_len, int elem_bytes, bcf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Tile sort (Lemma 1, Sec. 2): each tile of `tile` consecutive keys (the last may
  * be shorter) is sorted on its own, stably, in shared memory, following the
- * Lemma 1 schedule -- rows sorted inside their own bank, row-major <->
- * column-major conversions between them.  tile in {256, 512, 1024, 2048, 4096}. */
+ * Lemma 1 schedule on a 16 x 256 matrix (w*w <= m) -- rows sorted inside their
+ * own banks, conflict-free row-major <-> column-major conversions between them.
+ * tile must be 4096.  Out of place: outputs must not overlap the inputs. */
 int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                    void* vals_out, int64_t n, int tile, int val_bytes, bcf_stream_t stream);
 
@@ -146,14 +162,18 @@ int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_
  * Segmented forms.  offs is a DEVICE array of nseg+1 int64 CSR offsets (offs[0]
  * = 0, nondecreasing, offs[nseg] = n_total).  Each segment is sorted (or
  * partitioned) on its own.  No host synchronisation and no allocation: the whole
- * call can be captured in a CUDA graph.  Small segments are sorted whole in
- * shared memory by persistent blocks that pull work from a queue; large ones go
- * through shared digit passes.  n_total < 2^30. */
+ * call can be captured in a CUDA graph.  Segments of at most 4096 keys are
+ * sorted whole in shared memory (Lemma 1 tile sort) by persistent blocks that
+ * pull them from a queue; longer ones go through digit sweeps whose tiles cover
+ * all long segments at once.  Offsets that break the rules set the device status
+ * BCF_E_INVAL (the bad segments are skipped).  Out of place only: outputs must
+ * not overlap the inputs.  n_total < 2^30. */
 int bcf_segmented_sort_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,
-                                      size_t* bytes);
+                                      int key_bits, size_t* bytes);
 int bcf_segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
-                       int val_bytes, void* ws, size_t ws_bytes, bcf_stream_t stream);
+                       int val_bytes, int key_bits, void* ws, size_t ws_bytes,
+                       bcf_stream_t stream);
 
 /* w_per_seg: DEVICE int32[nseg], each in 1..256.  flags: BCF_ASSUME_BALANCED. */
 int bcf_segmented_partition_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,

@@ -27,6 +27,7 @@ ASSUME_BALANCED = 0x1
 CHECK_PERM = 0x2
 TILES_COLOURED = 0x10
 PARTITION_LEMMA1 = 0x20
+PERMUTE_FUSED = 0x40
 
 
 class BcfError(RuntimeError):
@@ -48,13 +49,13 @@ _SIGS = {
     "bcf_partition_workspace_size": ([_I64, _I, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_partition": ([_P, _P, _P, _P, _I64, _I, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_workspace_size": ([_I64, _I, ctypes.POINTER(_SZ)], _I),
-    "bcf_permute": ([_P, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
-    "bcf_permute_kv": ([_P, _P, _P, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
+    "bcf_permute": ([_P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
+    "bcf_permute_kv": ([_P, _P, _P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_tiles": ([_P, _P, _P, _I64, _I, _I, _U64, _P], _I),
-    "bcf_gather": ([_P, _P, _P, _I64, _I64, _I, _P], _I),
+    "bcf_gather": ([_P, _P, _P, _I64, _I64, _I64, _I, _P], _I),
     "bcf_sort_tiles": ([_P, _P, _P, _P, _I64, _I, _I, _P], _I),
-    "bcf_segmented_sort_workspace_size": ([_I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
-    "bcf_segmented_sort": ([_P, _P, _P, _P, _I64, _P, _I64, _I, _P, _SZ, _P], _I),
+    "bcf_segmented_sort_workspace_size": ([_I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "bcf_segmented_sort": ([_P, _P, _P, _P, _I64, _P, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_segmented_partition_workspace_size": ([_I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_segmented_partition": ([_P, _P, _P, _P, _I64, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
 }
@@ -153,15 +154,17 @@ def workspace(nbytes, device=None):
     return torch.empty(max(int(nbytes), 16), dtype=torch.uint8, device=device or "cuda")
 
 
-def sort(keys, vals=None, key_bits=32, keys_out=None, vals_out=None, ws=None, stream=None):
-    """Stable ascending sort by uint32 key (bcf_sort).  Returns (keys, vals)."""
+def sort(keys, vals=None, key_bits=32, keys_out=None, vals_out=None, ws=None, stream=None,
+         index_payload=False):
+    """Stable ascending sort by uint32 key (bcf_sort).  Returns (keys, vals).
+    index_payload=True (vals None): vals_out receives the sorting permutation."""
     torch = _torch()
     _dev_u32(keys, "keys")
     n = keys.numel()
-    vb = _vb(vals)
+    vb = 4 if index_payload else _vb(vals)
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
-    if vals is not None and vals_out is None:
-        vals_out = torch.empty_like(vals)
+    if vals_out is None and (vals is not None or index_payload):
+        vals_out = torch.empty_like(keys) if index_payload else torch.empty_like(vals)
     need = sort_workspace_size(n, vb, key_bits)
     ws = workspace(need, keys.device) if ws is None else ws
     _check(lib().bcf_sort(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n, vb, key_bits,
@@ -188,8 +191,9 @@ def partition(keys, vals, w, balanced=False, keys_out=None, vals_out=None, ws=No
     return keys_out, vals_out
 
 
-def permute(src, pi, dst=None, check=False, stream=None):
-    """dst[pi[i]] = src[i] for 4- or 8-byte elements (bcf_permute)."""
+def permute(src, pi, dst=None, check=False, row_len=0, stream=None):
+    """dst[pi[i]] = src[i] for 4- or 8-byte elements (bcf_permute); with row_len,
+    pi is local to rows of row_len items."""
     torch = _torch()
     _dev_u32(pi, "pi")
     n = src.numel()
@@ -200,26 +204,27 @@ def permute(src, pi, dst=None, check=False, stream=None):
         sz = ctypes.c_size_t(0)
         lib().bcf_permute_workspace_size(n, flags, ctypes.byref(sz))
         ws = workspace(sz.value, src.device)
-    _check(lib().bcf_permute(_ptr(src), _ptr(dst), _ptr(pi), n, src.element_size(), flags, _ptr(ws),
+    _check(lib().bcf_permute(_ptr(src), _ptr(dst), _ptr(pi), n, row_len, src.element_size(), flags, _ptr(ws),
                              0 if ws is None else ws.numel(), _stream(stream)), "bcf_permute")
     return dst
 
 
-def permute_kv(keys, vals, pi, keys_out=None, vals_out=None, check=False, stream=None):
+def permute_kv(keys, vals, pi, keys_out=None, vals_out=None, check=False, row_len=0, stream=None,
+               fused=False):
     """Keys and payloads moved by one permutation in one pass (bcf_permute_kv)."""
     torch = _torch()
     n = keys.numel()
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
     if vals is not None and vals_out is None:
         vals_out = torch.empty_like(vals)
-    flags = CHECK_PERM if check else 0
+    flags = (CHECK_PERM if check else 0) | (PERMUTE_FUSED if fused else 0)
     ws = None
     if check:
         sz = ctypes.c_size_t(0)
         lib().bcf_permute_workspace_size(n, flags, ctypes.byref(sz))
         ws = workspace(sz.value, keys.device)
     _check(lib().bcf_permute_kv(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), _ptr(pi), n,
-                                _vb(vals), flags, _ptr(ws), 0 if ws is None else ws.numel(),
+                                row_len, _vb(vals), flags, _ptr(ws), 0 if ws is None else ws.numel(),
                                 _stream(stream)), "bcf_permute_kv")
     return keys_out, vals_out
 
@@ -234,13 +239,13 @@ def permute_tiles(src, lpi, tile=4096, coloured=False, seed=0x150701391, dst=Non
     return dst
 
 
-def gather(src, idx, dst=None, stream=None):
-    """dst[i] = src[idx[i]] (bcf_gather)."""
+def gather(src, idx, dst=None, row_len=0, stream=None):
+    """dst[i] = src[idx[i]] (bcf_gather); with row_len, idx is local to rows."""
     torch = _torch()
     n = idx.numel()
     dst = torch.empty(n, dtype=src.dtype, device=src.device) if dst is None else dst
-    _check(lib().bcf_gather(_ptr(src), _ptr(dst), _ptr(idx), n, src.numel(), src.element_size(),
-                            _stream(stream)), "bcf_gather")
+    _check(lib().bcf_gather(_ptr(src), _ptr(dst), _ptr(idx), n, src.numel(), row_len,
+                            src.element_size(), _stream(stream)), "bcf_gather")
     return dst
 
 
@@ -255,22 +260,36 @@ def sort_tiles(keys, vals=None, tile=4096, keys_out=None, vals_out=None, stream=
     return keys_out, vals_out
 
 
-def segmented_sort(keys, vals, offs, keys_out=None, vals_out=None, ws=None, stream=None):
-    """Sort each CSR segment on its own (bcf_segmented_sort); offs is an int64 CUDA tensor."""
+def segmented_sort_workspace_size(n_total, nseg, val_bytes=4, key_bits=32) -> int:
+    sz = ctypes.c_size_t(0)
+    _check(lib().bcf_segmented_sort_workspace_size(n_total, nseg, val_bytes, key_bits, ctypes.byref(sz)),
+           "workspace")
+    return sz.value
+
+
+def segmented_partition_workspace_size(n_total, nseg, val_bytes=4) -> int:
+    sz = ctypes.c_size_t(0)
+    _check(lib().bcf_segmented_partition_workspace_size(n_total, nseg, val_bytes, ctypes.byref(sz)),
+           "workspace")
+    return sz.value
+
+
+def segmented_sort(keys, vals, offs, key_bits=32, keys_out=None, vals_out=None, ws=None, stream=None,
+                   index_payload=False):
+    """Sort each CSR segment on its own (bcf_segmented_sort); offs is an int64 CUDA tensor.
+    index_payload=True (vals None): vals_out receives global input positions."""
     torch = _torch()
     n = keys.numel()
     nseg = offs.numel() - 1
-    vb = _vb(vals)
+    vb = 4 if index_payload else _vb(vals)
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
-    if vals is not None and vals_out is None:
-        vals_out = torch.empty_like(vals)
+    if vals_out is None and (vals is not None or index_payload):
+        vals_out = torch.empty_like(keys) if index_payload else torch.empty_like(vals)
     if ws is None:
-        sz = ctypes.c_size_t(0)
-        _check(lib().bcf_segmented_sort_workspace_size(n, nseg, vb, ctypes.byref(sz)), "workspace")
-        ws = workspace(sz.value, keys.device)
+        ws = workspace(segmented_sort_workspace_size(n, nseg, vb, key_bits), keys.device)
     _check(lib().bcf_segmented_sort(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n,
-                                    _ptr(offs), nseg, vb, _ptr(ws), ws.numel(), _stream(stream)),
-           "bcf_segmented_sort")
+                                    _ptr(offs), nseg, vb, key_bits, _ptr(ws), ws.numel(),
+                                    _stream(stream)), "bcf_segmented_sort")
     return keys_out, vals_out
 
 
@@ -285,9 +304,7 @@ def segmented_partition(keys, vals, offs, w_per_seg, balanced=False, keys_out=No
     if vals is not None and vals_out is None:
         vals_out = torch.empty_like(vals)
     if ws is None:
-        sz = ctypes.c_size_t(0)
-        _check(lib().bcf_segmented_partition_workspace_size(n, nseg, vb, ctypes.byref(sz)), "workspace")
-        ws = workspace(sz.value, keys.device)
+        ws = workspace(segmented_partition_workspace_size(n, nseg, vb), keys.device)
     flags = ASSUME_BALANCED if balanced else 0
     _check(lib().bcf_segmented_partition(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n,
                                          _ptr(offs), _ptr(w_per_seg), nseg, vb, flags, _ptr(ws),

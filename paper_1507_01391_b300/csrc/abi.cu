@@ -58,12 +58,14 @@ int check_kv(const uint32_t* ki, const void* vi, const uint32_t* ko, const void*
   if (n < 0 || !valid_vb(vb)) return BCF_E_INVAL;
   if (n == 0) return BCF_OK;
   if (!ki || !ko || !aligned16(ki) || !aligned16(ko)) return BCF_E_INVAL;
-  if (vb && (!vi || !vo || !aligned16(vi) || !aligned16(vo))) return BCF_E_INVAL;
+  // vi == NULL with 4-byte payloads: index payload (item i carries i)
+  const bool iota = (vb == 4 && !vi);
+  if (vb && (!vo || !aligned16(vo) || (!iota && (!vi || !aligned16(vi))))) return BCF_E_INVAL;
   if (!vb && (vi || vo)) return BCF_E_INVAL;
   const size_t kb = (size_t)n * 4, vbb = (size_t)n * vb;
   if (!same_or_disjoint(ki, kb, ko, kb)) return BCF_E_INVAL;
-  if (vb && !same_or_disjoint(vi, vbb, vo, vbb)) return BCF_E_INVAL;
-  if (vb && ((ki == ko) != (vi == vo))) return BCF_E_INVAL;  // both in place or neither
+  if (vb && !iota && !same_or_disjoint(vi, vbb, vo, vbb)) return BCF_E_INVAL;
+  if (vb && !iota && ((ki == ko) != (vi == vo))) return BCF_E_INVAL;  // both in place or neither
   return BCF_OK;
 }
 
@@ -95,6 +97,7 @@ int bcf_get_status(bcf_stream_t stream, int* out) {
   if (cudaMemcpyFromSymbol(&bits, g_bcf_status, sizeof(bits)) != cudaSuccess) return BCF_E_CUDA;
   if (bits && cudaMemcpyToSymbol(g_bcf_status, &zero, sizeof(zero)) != cudaSuccess) return BCF_E_CUDA;
   if (bits & bcf::DEV_TIMEOUT) *out = BCF_E_TIMEOUT;
+  else if (bits & bcf::DEV_BAD_SEGMENTS) *out = BCF_E_INVAL;
   else if (bits & bcf::DEV_BAD_PERM) *out = BCF_E_BAD_PERM;
   else if (bits & bcf::DEV_NOT_BALANCED) *out = BCF_E_NOT_BALANCED;
   else if (bits & bcf::DEV_BAD_KEY) *out = BCF_E_BAD_KEY;
@@ -170,9 +173,9 @@ int bcf_permute_workspace_size(int64_t n, int flags, size_t* bytes) {
 }
 
 static int permute_common(const void* sk, const void* sv, void* dk, void* dv, const uint32_t* pi,
-                          int64_t n, int kb, int vb, int flags, void* ws, size_t ws_bytes,
-                          cudaStream_t s) {
-  if (n < 0 || (kb != 4 && kb != 8) || !valid_vb(vb)) return BCF_E_INVAL;
+                          int64_t n, int64_t row_len, int kb, int vb, int flags, void* ws,
+                          size_t ws_bytes, cudaStream_t s) {
+  if (n < 0 || row_len < 0 || (kb != 4 && kb != 8) || !valid_vb(vb)) return BCF_E_INVAL;
   if (n > (int64_t)0xFFFFFFFFLL) return BCF_E_UNSUPPORTED;
   if (n == 0) return BCF_OK;
   if (!sk || !dk || !pi || !aligned16(sk) || !aligned16(dk) || !aligned16(pi)) return BCF_E_INVAL;
@@ -188,21 +191,22 @@ static int permute_common(const void* sk, const void* sv, void* dk, void* dv, co
     seen = static_cast<uint32_t*>(ws);
   }
   if (!device_ready()) return BCF_E_CUDA;
-  return cuda_rc(bcf::permute(sk, sv, dk, dv, pi, n, kb, vb, seen, s));
+  return cuda_rc(bcf::permute(sk, sv, dk, dv, pi, n, row_len, kb, vb, seen,
+                              (flags & BCF_PERMUTE_FUSED) != 0, s));
 }
 
-int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int elem_bytes,
-                int flags, void* ws, size_t ws_bytes, bcf_stream_t stream) {
-  return permute_common(src, nullptr, dst, nullptr, pi, n, elem_bytes, 0, flags, ws, ws_bytes,
-                        (cudaStream_t)stream);
+int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int64_t row_len,
+                int elem_bytes, int flags, void* ws, size_t ws_bytes, bcf_stream_t stream) {
+  return permute_common(src, nullptr, dst, nullptr, pi, n, row_len, elem_bytes, 0, flags, ws,
+                        ws_bytes, (cudaStream_t)stream);
 }
 
 int bcf_permute_kv(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
-                   const uint32_t* pi, int64_t n, int val_bytes, int flags, void* ws,
-                   size_t ws_bytes, bcf_stream_t stream) {
+                   const uint32_t* pi, int64_t n, int64_t row_len, int val_bytes, int flags,
+                   void* ws, size_t ws_bytes, bcf_stream_t stream) {
   if (!val_bytes && (src_v || dst_v)) return BCF_E_INVAL;
-  return permute_common(src_k, src_v, dst_k, dst_v, pi, n, 4, val_bytes, flags, ws, ws_bytes,
-                        (cudaStream_t)stream);
+  return permute_common(src_k, src_v, dst_k, dst_v, pi, n, row_len, 4, val_bytes, flags, ws,
+                        ws_bytes, (cudaStream_t)stream);
 }
 
 int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
@@ -218,51 +222,97 @@ int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, i
 }
 
 int bcf_gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
-               int elem_bytes, bcf_stream_t stream) {
-  if (n < 0 || n_src < 0 || (elem_bytes != 4 && elem_bytes != 8)) return BCF_E_INVAL;
+               int64_t row_len, int elem_bytes, bcf_stream_t stream) {
+  if (n < 0 || n_src < 0 || row_len < 0 || (elem_bytes != 4 && elem_bytes != 8)) return BCF_E_INVAL;
+  if (n_src > (int64_t)0xFFFFFFFFLL) return BCF_E_UNSUPPORTED;
   if (n == 0) return BCF_OK;
   if (!dst || !idx || !aligned16(dst) || !aligned16(idx)) return BCF_E_INVAL;
   if (n_src > 0 && !src) return BCF_E_INVAL;
   if (!disjoint(src, (size_t)n_src * elem_bytes, dst, (size_t)n * elem_bytes)) return BCF_E_INVAL;
   if (!device_ready()) return BCF_E_CUDA;
-  return cuda_rc(bcf::gather(src, dst, idx, n, n_src, elem_bytes, (cudaStream_t)stream));
+  return cuda_rc(bcf::gather(src, dst, idx, n, n_src, row_len, elem_bytes, (cudaStream_t)stream));
 }
 
 // ------------------------------------------------------- tiles / segments
 int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                    void* vals_out, int64_t n, int tile, int val_bytes, bcf_stream_t stream) {
-  (void)keys_in; (void)vals_in; (void)keys_out; (void)vals_out; (void)n; (void)tile;
-  (void)val_bytes; (void)stream;
-  return BCF_E_UNSUPPORTED;
+  if (tile != 4096) return BCF_E_INVAL;
+  int rc = check_kv(keys_in, vals_in, keys_out, vals_out, n, val_bytes);
+  if (rc) return rc;
+  if (n >= ((int64_t)1 << 40)) return BCF_E_UNSUPPORTED;
+  if (n == 0) return BCF_OK;
+  if (!disjoint(keys_in, (size_t)n * 4, keys_out, (size_t)n * 4)) return BCF_E_INVAL;
+  if (val_bytes && !disjoint(vals_in, (size_t)n * val_bytes, vals_out, (size_t)n * val_bytes))
+    return BCF_E_INVAL;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::sort_tiles(keys_in, vals_in, keys_out, vals_out, n, val_bytes, (cudaStream_t)stream));
 }
 
-int bcf_segmented_sort_workspace_size(int64_t n_total, int64_t nseg, int val_bytes, size_t* bytes) {
-  (void)n_total; (void)nseg; (void)val_bytes; (void)bytes;
-  return BCF_E_UNSUPPORTED;
+static int check_segments(const uint32_t* ki, const void* vi, const uint32_t* ko, const void* vo,
+                          int64_t n_total, const int64_t* offs, int64_t nseg, int vb) {
+  int rc = check_kv(ki, vi, ko, vo, n_total, vb);
+  if (rc) return rc;
+  if (nseg < 0) return BCF_E_INVAL;
+  if (n_total >= kMaxSweepN || nseg >= ((int64_t)1 << 31)) return BCF_E_UNSUPPORTED;
+  if (nseg > 0 && (!offs || (reinterpret_cast<uintptr_t>(offs) & 7u))) return BCF_E_INVAL;
+  if (n_total > 0 && nseg == 0) return BCF_E_INVAL;
+  if (n_total > 0) {
+    if (!disjoint(ki, (size_t)n_total * 4, ko, (size_t)n_total * 4)) return BCF_E_INVAL;
+    if (vb && !disjoint(vi, (size_t)n_total * vb, vo, (size_t)n_total * vb)) return BCF_E_INVAL;
+  }
+  return BCF_OK;
+}
+
+int bcf_segmented_sort_workspace_size(int64_t n_total, int64_t nseg, int val_bytes, int key_bits,
+                                      size_t* bytes) {
+  if (!bytes || n_total < 0 || nseg < 0 || !valid_vb(val_bytes) || key_bits < 1 || key_bits > 32)
+    return BCF_E_INVAL;
+  if (n_total >= kMaxSweepN || nseg >= ((int64_t)1 << 31)) return BCF_E_UNSUPPORTED;
+  *bytes = bcf::seg_layout(n_total, nseg, val_bytes, bcf::plan_passes(key_bits).passes, true).total;
+  return BCF_OK;
 }
 
 int bcf_segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
-                       int val_bytes, void* ws, size_t ws_bytes, bcf_stream_t stream) {
-  (void)keys_in; (void)vals_in; (void)keys_out; (void)vals_out; (void)n_total; (void)offs;
-  (void)nseg; (void)val_bytes; (void)ws; (void)ws_bytes; (void)stream;
-  return BCF_E_UNSUPPORTED;
+                       int val_bytes, int key_bits, void* ws, size_t ws_bytes,
+                       bcf_stream_t stream) {
+  int rc = check_segments(keys_in, vals_in, keys_out, vals_out, n_total, offs, nseg, val_bytes);
+  if (rc) return rc;
+  if (key_bits < 1 || key_bits > 32) return BCF_E_INVAL;
+  if (nseg == 0) return BCF_OK;
+  const bcf::PassPlan pl = bcf::plan_passes(key_bits);
+  const bcf::SegLayout L = bcf::seg_layout(n_total, nseg, val_bytes, pl.passes, true);
+  if (!ws || !aligned16(ws)) return BCF_E_INVAL;
+  if (ws_bytes < L.total) return BCF_E_WORKSPACE;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::segmented_sort(keys_in, vals_in, keys_out, vals_out, n_total, offs, nseg,
+                                     val_bytes, pl, static_cast<unsigned char*>(ws), L,
+                                     (cudaStream_t)stream));
 }
 
 int bcf_segmented_partition_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,
                                            size_t* bytes) {
-  (void)n_total; (void)nseg; (void)val_bytes; (void)bytes;
-  return BCF_E_UNSUPPORTED;
+  if (!bytes || n_total < 0 || nseg < 0 || !valid_vb(val_bytes)) return BCF_E_INVAL;
+  if (n_total >= kMaxSweepN || nseg >= ((int64_t)1 << 31)) return BCF_E_UNSUPPORTED;
+  *bytes = bcf::seg_layout(n_total, nseg, val_bytes, 1, false).total;
+  return BCF_OK;
 }
 
 int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                             void* vals_out, int64_t n_total, const int64_t* offs,
                             const int32_t* w_per_seg, int64_t nseg, int val_bytes, int flags,
                             void* ws, size_t ws_bytes, bcf_stream_t stream) {
-  (void)keys_in; (void)vals_in; (void)keys_out; (void)vals_out; (void)n_total; (void)offs;
-  (void)w_per_seg; (void)nseg; (void)val_bytes; (void)flags; (void)ws; (void)ws_bytes;
-  (void)stream;
-  return BCF_E_UNSUPPORTED;
+  int rc = check_segments(keys_in, vals_in, keys_out, vals_out, n_total, offs, nseg, val_bytes);
+  if (rc) return rc;
+  if (nseg > 0 && (!w_per_seg || (reinterpret_cast<uintptr_t>(w_per_seg) & 3u))) return BCF_E_INVAL;
+  if (nseg == 0) return BCF_OK;
+  const bcf::SegLayout L = bcf::seg_layout(n_total, nseg, val_bytes, 1, false);
+  if (!ws || !aligned16(ws)) return BCF_E_INVAL;
+  if (ws_bytes < L.total) return BCF_E_WORKSPACE;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::segmented_partition(keys_in, vals_in, keys_out, vals_out, n_total, offs, w_per_seg,
+                                          nseg, val_bytes, (flags & BCF_ASSUME_BALANCED) != 0,
+                                          static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
 }
 
 }  // extern "C"

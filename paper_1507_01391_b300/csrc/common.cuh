@@ -16,6 +16,7 @@ enum : unsigned {
   DEV_NOT_BALANCED = 1u << 1,
   DEV_BAD_PERM = 1u << 2,
   DEV_TIMEOUT = 1u << 3,
+  DEV_BAD_SEGMENTS = 1u << 4,  // CSR offsets or per-segment w out of range
 };
 
 // Polls before a wait gives up (each poll also backs off a little).
@@ -41,6 +42,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint4 ld_relaxed_v4(const uint32_t* p) {  // 16-byte aligned
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
   return v;
 }
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {

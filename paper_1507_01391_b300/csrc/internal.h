@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 namespace bcf {
@@ -15,9 +17,26 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 
 // ---------------------------------------------------------------- digit sweeps
-constexpr int kSweepThreads = 256;
-constexpr int kSweepIPT = 16;
+// Tuning of the digit sweep (compile-time; the defaults are the shipped values).
+#ifndef BCF_SWEEP_THREADS
+#define BCF_SWEEP_THREADS 256
+#endif
+#ifndef BCF_SWEEP_IPT
+#define BCF_SWEEP_IPT 16
+#endif
+#ifndef BCF_SWEEP_MINBLOCKS
+#define BCF_SWEEP_MINBLOCKS 4
+#endif
+#ifndef BCF_LB_WINDOW
+#define BCF_LB_WINDOW 8       // look-back status words read per round trip (multiple of 4)
+#endif
+#ifndef BCF_PEERS_MATCH
+#define BCF_PEERS_MATCH 0     // 1: peers from __match_any_sync instead of per-bit ballots
+#endif
+constexpr int kSweepThreads = BCF_SWEEP_THREADS;
+constexpr int kSweepIPT = BCF_SWEEP_IPT;
 constexpr int kSweepTile = kSweepThreads * kSweepIPT;  // keys per tile
+constexpr int kLookbackWindow = BCF_LB_WINDOW;
 
 struct PassPlan {
   int passes = 0;
@@ -33,6 +52,7 @@ struct SweepLayout {
   size_t hist = 0, counters = 0, lookback = 0, digit_base = 0;
   size_t total = 0;
   int64_t tiles = 0;
+  int64_t lb_stride = 0;  // look-back status words per digit (tiles rounded up to 8)
   int radix = 256;
 };
 SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp);
@@ -49,11 +69,36 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
 
 // ---------------------------------------------------------------- permutations
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
-                    const uint32_t* pi, int64_t n, int kbytes, int vbytes,
-                    uint32_t* seen_bitmap, cudaStream_t s);
+                    const uint32_t* pi, int64_t n, int64_t row_len, int kbytes, int vbytes,
+                    uint32_t* seen_bitmap, bool fused, cudaStream_t s);
 cudaError_t gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
-                   int elem_bytes, cudaStream_t s);
+                   int64_t row_len, int elem_bytes, cudaStream_t s);
 cudaError_t permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
                           int tile, bool coloured, uint64_t seed, cudaStream_t s);
+
+// ---------------------------------------------------------------- segments
+struct SegLayout {
+  int small_max = 0;        // segments of 1..small_max keys take the small path
+  int64_t slots_cap = 0;    // capacity for long segments
+  int64_t tiles_cap = 0;    // capacity for sweep tiles of long segments
+  int64_t lb_stride = 0;    // look-back status words per digit
+  int passes = 0;
+  size_t keys_tmp = 0, vals_tmp = 0, small_ids = 0, seg_slot = 0, seg_tile0 = 0, slot_seg = 0;
+  size_t tile_seg = 0, seg_base = 0, ctr = 0, seg_hist = 0, lookback = 0;
+  size_t zero_begin = 0, zero_bytes = 0, total = 0;
+};
+SegLayout seg_layout(int64_t n_total, int64_t nseg, int val_bytes, int passes, bool sort);
+
+cudaError_t segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                           void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
+                           int val_bytes, const PassPlan& plan, unsigned char* ws,
+                           const SegLayout& L, cudaStream_t s);
+cudaError_t segmented_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                                void* vals_out, int64_t n_total, const int64_t* offs,
+                                const int32_t* w_per_seg, int64_t nseg, int val_bytes,
+                                bool balanced, unsigned char* ws, const SegLayout& L,
+                                cudaStream_t s);
+cudaError_t sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                       void* vals_out, int64_t n, int val_bytes, cudaStream_t s);
 
 }  // namespace bcf

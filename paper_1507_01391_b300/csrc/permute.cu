@@ -2,9 +2,11 @@
 // direction (gather) and the optional bijectivity check.
 //
 // Global scatter: every thread reads four consecutive items of src and pi with
-// 128-bit loads and issues four scattered 4- or 8-byte stores.  The destination
-// lines are merged in L2 before they reach HBM, so DRAM traffic stays close to
-// one write per output byte when the output fits the 126 MB L2 working set.
+// 128-bit loads and issues four scattered 4- or 8-byte stores.  Scattered stores
+// only reach HBM efficiently when L2 can hold every partially written line until
+// all of it has arrived, so key-value permutations run as two passes (keys, then
+// payloads) whose outputs each fit the 126 MB L2; the fused one-pass form, whose
+// 2 x 64 MB output at n = 2^24 does not fit, is kept for comparison.
 #include "common.cuh"
 #include "internal.h"
 
@@ -22,6 +24,20 @@ struct Elem<8> {
   using T = unsigned long long;
   using V4 = ulonglong2;  // two elements per 16-byte load
 };
+
+// Indices local to rows of row_len items (row_len 0: one row) -> global indices
+// of items i, i+1, ...; an index outside its row becomes n (rejected by callers).
+template <int C>
+__device__ __forceinline__ void local_to_global(uint32_t (&d)[C], int64_t i, int64_t n, int64_t row_len) {
+  if (row_len <= 0) return;
+  int64_t row0 = (i / row_len) * row_len;
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    if (i + c >= row0 + row_len) row0 += row_len;
+    const int64_t g = (int64_t)d[c] < row_len ? row0 + d[c] : n;
+    d[c] = (uint32_t)(g < n ? g : n);
+  }
+}
 
 __device__ __forceinline__ bool claim(uint32_t* seen, uint32_t d) {
   const uint32_t bit = 1u << (d & 31);
@@ -47,7 +63,8 @@ __global__ void __launch_bounds__(256) k_permute(const void* __restrict__ src_k,
                                                   void* __restrict__ dst_k,
                                                   void* __restrict__ dst_v,
                                                   const uint32_t* __restrict__ pi, int64_t n,
-                                                  uint32_t* seen, unsigned* status) {
+                                                  int64_t row_len, uint32_t* seen,
+                                                  unsigned* status) {
   using KT = typename Elem<KB>::T;
   using VT = typename ValT<VB>::type;
   const KT* sk = reinterpret_cast<const KT*>(src_k);
@@ -59,7 +76,8 @@ __global__ void __launch_bounds__(256) k_permute(const void* __restrict__ src_k,
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
     const int64_t i = v * 4;
     const uint4 p4 = __ldcs(reinterpret_cast<const uint4*>(pi + i));
-    const uint32_t d[4] = {p4.x, p4.y, p4.z, p4.w};
+    uint32_t d[4] = {p4.x, p4.y, p4.z, p4.w};
+    local_to_global(d, i, n, row_len);
     KT k[4];
     load4(sk, i, k);
     VT val[4];
@@ -77,7 +95,9 @@ __global__ void __launch_bounds__(256) k_permute(const void* __restrict__ src_k,
     }
   }
   for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t d = pi[i];
+    uint32_t d1[1] = {pi[i]};
+    local_to_global(d1, i, n, row_len);
+    const uint32_t d = d1[0];
     bool ok = (int64_t)d < n;
     if (ok && seen) ok = claim(seen, d);
     if (!ok) {
@@ -93,7 +113,7 @@ template <int EB>
 __global__ void __launch_bounds__(256) k_gather(const void* __restrict__ src,
                                                  void* __restrict__ dst,
                                                  const uint32_t* __restrict__ idx, int64_t n,
-                                                 int64_t n_src, unsigned* status) {
+                                                 int64_t n_src, int64_t row_len, unsigned* status) {
   using T = typename Elem<EB>::T;
   const T* s = reinterpret_cast<const T*>(src);
   T* d = reinterpret_cast<T*>(dst);
@@ -102,7 +122,8 @@ __global__ void __launch_bounds__(256) k_gather(const void* __restrict__ src,
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
     const int64_t i = v * 4;
     const uint4 p4 = __ldcs(reinterpret_cast<const uint4*>(idx + i));
-    const uint32_t q[4] = {p4.x, p4.y, p4.z, p4.w};
+    uint32_t q[4] = {p4.x, p4.y, p4.z, p4.w};
+    local_to_global(q, i, n_src, row_len);
     T out[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -121,7 +142,9 @@ __global__ void __launch_bounds__(256) k_gather(const void* __restrict__ src,
     }
   }
   for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const uint32_t q = idx[i];
+    uint32_t q1[1] = {idx[i]};
+    local_to_global(q1, i, n_src, row_len);
+    const uint32_t q = q1[0];
     if ((int64_t)q < n_src) {
       d[i] = s[q];
     } else {
@@ -147,38 +170,46 @@ static unsigned grid_for(int64_t n) {
 
 template <int KB>
 static cudaError_t permute_kb(const void* sk, const void* sv, void* dk, void* dv,
-                              const uint32_t* pi, int64_t n, int vb, uint32_t* seen,
-                              cudaStream_t s) {
+                              const uint32_t* pi, int64_t n, int64_t row_len, int vb,
+                              uint32_t* seen, cudaStream_t s) {
   const unsigned g = grid_for(n);
   unsigned* st = status_word();
   switch (vb) {
-    case 0: k_permute<KB, 0><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, seen, st); break;
-    case 4: k_permute<KB, 4><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, seen, st); break;
-    case 8: k_permute<KB, 8><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, seen, st); break;
+    case 0: k_permute<KB, 0><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, row_len, seen, st); break;
+    case 4: k_permute<KB, 4><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, row_len, seen, st); break;
+    case 8: k_permute<KB, 8><<<g, 256, 0, s>>>(sk, sv, dk, dv, pi, n, row_len, seen, st); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
-                    const uint32_t* pi, int64_t n, int kbytes, int vbytes,
-                    uint32_t* seen_bitmap, cudaStream_t s) {
+                    const uint32_t* pi, int64_t n, int64_t row_len, int kbytes, int vbytes,
+                    uint32_t* seen_bitmap, bool fused, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  if (seen_bitmap) {
+  if (seen_bitmap && (fused || !vbytes)) {
     cudaError_t e = cudaMemsetAsync(seen_bitmap, 0, (size_t)((n + 31) / 32) * 4, s);
     if (e != cudaSuccess) return e;
   }
-  if (kbytes == 4) return permute_kb<4>(src_k, src_v, dst_k, dst_v, pi, n, vbytes, seen_bitmap, s);
-  if (kbytes == 8) return permute_kb<8>(src_k, src_v, dst_k, dst_v, pi, n, vbytes, seen_bitmap, s);
+  if (!fused && vbytes) {
+    // Keys, then payloads: each pass scatters into one output array, whose
+    // partially written lines then stay in L2 until they are complete.
+    cudaError_t e = permute(src_k, nullptr, dst_k, nullptr, pi, n, row_len, kbytes, 0, seen_bitmap,
+                            true, s);
+    if (e != cudaSuccess) return e;
+    return permute(src_v, nullptr, dst_v, nullptr, pi, n, row_len, vbytes, 0, nullptr, true, s);
+  }
+  if (kbytes == 4) return permute_kb<4>(src_k, src_v, dst_k, dst_v, pi, n, row_len, vbytes, seen_bitmap, s);
+  if (kbytes == 8) return permute_kb<8>(src_k, src_v, dst_k, dst_v, pi, n, row_len, vbytes, seen_bitmap, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
-                   int eb, cudaStream_t s) {
+                   int64_t row_len, int eb, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const unsigned g = grid_for(n);
-  if (eb == 4) k_gather<4><<<g, 256, 0, s>>>(src, dst, idx, n, n_src, status_word());
-  else if (eb == 8) k_gather<8><<<g, 256, 0, s>>>(src, dst, idx, n, n_src, status_word());
+  if (eb == 4) k_gather<4><<<g, 256, 0, s>>>(src, dst, idx, n, n_src, row_len, status_word());
+  else if (eb == 8) k_gather<8><<<g, 256, 0, s>>>(src, dst, idx, n, n_src, row_len, status_word());
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

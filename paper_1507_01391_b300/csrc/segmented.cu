@@ -1,0 +1,397 @@
+// segmented.cu -- batched forms: many independent CSR segments in one call, and
+// the tile sort (Lemma 1) on its own.
+//
+// Everything is planned on the device, so a call issues a fixed sequence of
+// launches with no host synchronisation and no allocation (capturable in a CUDA
+// graph):
+//   1. k_seg_plan   one block scans the CSR offsets: segments up to one tile go to
+//                   the small-segment queue, longer ones get a run of sweep tiles;
+//   2. k_seg_small  (sort only) persistent blocks pull small segments from the
+//                   queue and sort each whole in shared memory with the Lemma 1
+//                   schedule (tile_sort.cuh): one read and one write per key;
+//   3. k_seg_hist + k_seg_scan   per-segment digit counts -> absolute digit starts;
+//   4. k_sweep (segment mode)    one launch per digit pass covers the tiles of
+//                   every long segment; look-back chains stop at segment starts.
+// Launch grids are host-side upper bounds; blocks without work exit at once.
+#include "common.cuh"
+#include "internal.h"
+#include "sweep.cuh"
+#include "tile_sort.cuh"
+
+namespace bcf {
+
+enum : int { C_NSMALL = 0, C_NLARGE = 1, C_NTILES = 2, C_QUEUE = 3, C_TICKET = 4 /* +pass */ };
+
+struct PlanParams {
+  const int64_t* offs;
+  int64_t nseg, n_total;
+  int small_max;        // segments with 1..small_max keys go to the small queue
+  int tile;             // sweep tile
+  int64_t tiles_cap;    // capacity of tile_seg
+  int64_t slots_cap;    // capacity of slot_seg
+  const int32_t* seg_w; // partition widths (checked when given)
+  int32_t* small_ids;
+  int32_t* seg_slot;
+  int32_t* seg_tile0;
+  int32_t* tile_seg;
+  int32_t* slot_seg;
+  uint32_t* ctr;
+  unsigned* status;
+};
+
+constexpr int kPlanThreads = 1024;
+
+__global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
+  __shared__ uint32_t scratch[32];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = (p.nseg > 0 && (p.offs[0] != 0 || p.offs[p.nseg] != p.n_total)) ? 1 : 0;
+  __syncthreads();
+  uint32_t run_small = 0, run_large = 0, run_tiles = 0;
+  for (int64_t base = 0; base < p.nseg; base += kPlanThreads) {
+    const int64_t s = base + tid;
+    int64_t len = 0;
+    if (s < p.nseg) {
+      const int64_t a = p.offs[s], b = p.offs[s + 1];
+      if (a < 0 || b < a || b > p.n_total) bad = 1;  // benign race: every writer stores 1
+      else len = b - a;
+      if (p.seg_w && (p.seg_w[s] < 1 || p.seg_w[s] > 256)) {
+        bad = 1;
+        len = 0;
+      }
+    }
+    const bool small = len > 0 && len <= p.small_max;
+    const bool large = len > p.small_max;
+    const uint32_t tiles = large ? (uint32_t)((len + p.tile - 1) / p.tile) : 0u;
+    uint32_t tot;
+    const uint32_t es = block_excl_scan<kPlanThreads>(small ? 1u : 0u, scratch, &tot);
+    const uint32_t add_small = tot;
+    const uint32_t el = block_excl_scan<kPlanThreads>(large ? 1u : 0u, scratch, &tot);
+    const uint32_t add_large = tot;
+    const uint32_t et = block_excl_scan<kPlanThreads>(tiles, scratch, &tot);
+    const uint32_t add_tiles = tot;
+    if (s < p.nseg) {
+      p.seg_slot[s] = -1;
+      p.seg_tile0[s] = -1;
+      if (small) p.small_ids[run_small + es] = (int32_t)s;
+      if (large) {
+        const uint32_t slot = run_large + el, t0 = run_tiles + et;
+        if ((int64_t)slot < p.slots_cap && (int64_t)(t0 + tiles) <= p.tiles_cap) {
+          p.seg_slot[s] = (int32_t)slot;
+          p.seg_tile0[s] = (int32_t)t0;
+          p.slot_seg[slot] = (int32_t)s;
+          for (uint32_t t = 0; t < tiles; ++t) p.tile_seg[t0 + t] = (int32_t)s;
+        } else {
+          bad = 1;
+        }
+      }
+    }
+    run_small += add_small;
+    run_large += add_large;
+    run_tiles += add_tiles;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    p.ctr[C_NSMALL] = run_small;
+    p.ctr[C_NLARGE] = (int64_t)run_large <= p.slots_cap ? run_large : (uint32_t)p.slots_cap;
+    p.ctr[C_NTILES] = (int64_t)run_tiles <= p.tiles_cap ? run_tiles : (uint32_t)p.tiles_cap;
+    if (bad) set_status(p.status, DEV_BAD_SEGMENTS);
+  }
+}
+
+// Per-segment digit counts of every pass (segments in sweep tiles).
+struct SegHistParams {
+  const uint32_t* keys;
+  const int64_t* offs;
+  const int32_t* tile_seg;
+  const int32_t* seg_tile0;
+  const int32_t* seg_slot;
+  const uint32_t* ctr;
+  int tile, passes, label_bits;
+  int shift[4], nbits[4];
+  uint32_t* seg_hist;  // slot x passes x 256
+};
+
+__global__ void __launch_bounds__(256) k_seg_hist(SegHistParams p) {
+  __shared__ uint32_t h[4 * 256];
+  const int tid = threadIdx.x;
+  const int64_t tile = blockIdx.x;
+  if (tile >= (int64_t)p.ctr[C_NTILES]) return;
+  const int seg = p.tile_seg[tile];
+  const int64_t lo = p.offs[seg], hi = p.offs[seg + 1];
+  const int64_t start = lo + (tile - p.seg_tile0[seg]) * (int64_t)p.tile;
+  const int64_t end = min(hi, start + p.tile);
+  for (int i = tid; i < 4 * 256; i += 256) h[i] = 0;
+  __syncthreads();
+  uint32_t mask[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    mask[q] = p.label_bits ? ((1u << p.label_bits) - 1u) : ((1u << p.nbits[q]) - 1u);
+  for (int64_t i = start + tid; i < end; i += 256) {
+    const uint32_t k = p.keys[i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < p.passes) atomicAdd(&h[q * 256 + ((k >> p.shift[q]) & mask[q])], 1u);
+  }
+  __syncthreads();
+  uint32_t* dst = p.seg_hist + (size_t)p.seg_slot[seg] * p.passes * 256;
+  for (int i = tid; i < p.passes * 256; i += 256)
+    if (h[i]) atomicAdd(&dst[i], h[i]);
+}
+
+// Exclusive scan of each long segment's counts -> absolute digit starts.
+__global__ void __launch_bounds__(256) k_seg_scan(const uint32_t* __restrict__ seg_hist,
+                                                  uint32_t* __restrict__ seg_base,
+                                                  const int32_t* __restrict__ slot_seg,
+                                                  const int64_t* __restrict__ offs,
+                                                  const uint32_t* __restrict__ ctr, int passes,
+                                                  int64_t slots_cap) {
+  __shared__ uint32_t scratch[32];
+  const int64_t slot = blockIdx.x;
+  if (slot >= (int64_t)ctr[C_NLARGE]) return;
+  const uint32_t start = (uint32_t)offs[slot_seg[slot]];
+  for (int q = 0; q < passes; ++q) {
+    const uint32_t c = seg_hist[((size_t)slot * passes + q) * 256 + threadIdx.x];
+    uint32_t tot;
+    const uint32_t e = block_excl_scan<256>(c, scratch, &tot);
+    seg_base[((size_t)q * slots_cap + slot) * 256 + threadIdx.x] = start + e;
+  }
+}
+
+// Persistent blocks: sort every small segment whole with the Lemma 1 schedule.
+template <int VB>
+__global__ void __launch_bounds__(kL1Threads) k_seg_small(const uint32_t* __restrict__ keys_in,
+                                                          const void* __restrict__ vals_in,
+                                                          uint32_t* __restrict__ keys_out,
+                                                          void* __restrict__ vals_out,
+                                                          const int64_t* __restrict__ offs,
+                                                          const int32_t* __restrict__ small_ids,
+                                                          uint32_t* ctr) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* X = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* Y = X + kL1Tile;
+  __shared__ int item;
+  while (true) {
+    if (threadIdx.x == 0) item = (int)atomicAdd(&ctr[C_QUEUE], 1u);
+    __syncthreads();
+    const int i = item;
+    __syncthreads();
+    if (i >= (int)ctr[C_NSMALL]) break;
+    const int seg = small_ids[i];
+    const int64_t lo = offs[seg];
+    lemma1_tile<VB>(keys_in, vals_in, keys_out, vals_out, lo, (int)(offs[seg + 1] - lo), X, Y);
+  }
+}
+
+// Standalone tile sort: tile t = [t*4096, min(n, (t+1)*4096)).
+template <int VB>
+__global__ void __launch_bounds__(kL1Threads) k_sort_tiles(const uint32_t* __restrict__ keys_in,
+                                                           const void* __restrict__ vals_in,
+                                                           uint32_t* __restrict__ keys_out,
+                                                           void* __restrict__ vals_out, int64_t n) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* X = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* Y = X + kL1Tile;
+  const int64_t start = (int64_t)blockIdx.x * kL1Tile;
+  lemma1_tile<VB>(keys_in, vals_in, keys_out, vals_out, start, (int)min((int64_t)kL1Tile, n - start), X, Y);
+}
+
+// ------------------------------------------------------------------ host
+static int sms() {
+  int dev = 0, c = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+  return c;
+}
+
+SegLayout seg_layout(int64_t n_total, int64_t nseg, int vb, int passes, bool sort) {
+  SegLayout L;
+  const int64_t T = kSweepTile;
+  L.small_max = sort ? kL1Tile : 0;
+  // long segments hold more than small_max keys each
+  const int64_t max_large = sort ? std::min<int64_t>(nseg, n_total / (L.small_max + 1) + 1) : nseg;
+  L.slots_cap = max_large > 0 ? max_large : 1;
+  L.tiles_cap = n_total / T + max_large + 1;
+  L.lb_stride = (L.tiles_cap + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
+  L.passes = passes;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  L.keys_tmp = take((size_t)n_total * 4);
+  L.vals_tmp = take((size_t)n_total * vb);
+  L.small_ids = take((size_t)std::max<int64_t>(nseg, 1) * 4);
+  L.seg_slot = take((size_t)std::max<int64_t>(nseg, 1) * 4);
+  L.seg_tile0 = take((size_t)std::max<int64_t>(nseg, 1) * 4);
+  L.slot_seg = take((size_t)L.slots_cap * 4);
+  L.tile_seg = take((size_t)L.tiles_cap * 4);
+  L.seg_base = take((size_t)passes * L.slots_cap * 256 * 4);
+  L.zero_begin = off;
+  L.ctr = take(16 * 4);
+  L.seg_hist = take((size_t)L.slots_cap * passes * 256 * 4);
+  L.lookback = take((size_t)passes * L.lb_stride * 256 * 4);
+  L.zero_bytes = off - L.zero_begin;
+  L.total = off;
+  return L;
+}
+
+template <int VB>
+static cudaError_t small_sort(const uint32_t* ki, const void* vi, uint32_t* ko, void* vo,
+                              const int64_t* offs, const int32_t* ids, uint32_t* ctr, int64_t nseg,
+                              cudaStream_t s) {
+  auto k = k_seg_small<VB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL1SmemBytes);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(nseg, (int64_t)sms() * 3);
+  if (grid <= 0) return cudaSuccess;
+  k<<<(unsigned)grid, kL1Threads, kL1SmemBytes, s>>>(ki, vi, ko, vo, offs, ids, ctr);
+  return cudaGetLastError();
+}
+
+static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                                void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
+                                const int32_t* seg_w, int vb, const PassPlan& plan, bool label,
+                                bool balanced, unsigned char* ws, const SegLayout& L, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
+  if (e != cudaSuccess) return e;
+  auto I32 = [&](size_t o) { return reinterpret_cast<int32_t*>(ws + o); };
+  auto U32 = [&](size_t o) { return reinterpret_cast<uint32_t*>(ws + o); };
+  uint32_t* ctr = U32(L.ctr);
+  unsigned* st = status_word();
+
+  PlanParams pp{};
+  pp.offs = offs;
+  pp.nseg = nseg;
+  pp.n_total = n_total;
+  pp.small_max = L.small_max;
+  pp.tile = kSweepTile;
+  pp.tiles_cap = L.tiles_cap;
+  pp.slots_cap = L.slots_cap;
+  pp.seg_w = seg_w;
+  pp.small_ids = I32(L.small_ids);
+  pp.seg_slot = I32(L.seg_slot);
+  pp.seg_tile0 = I32(L.seg_tile0);
+  pp.tile_seg = I32(L.tile_seg);
+  pp.slot_seg = I32(L.slot_seg);
+  pp.ctr = ctr;
+  pp.status = st;
+  k_seg_plan<<<1, kPlanThreads, 0, s>>>(pp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  if (L.small_max > 0) {
+    switch (vb) {
+      case 0: e = small_sort<0>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), ctr, nseg, s); break;
+      case 4: e = small_sort<4>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), ctr, nseg, s); break;
+      case 8: e = small_sort<8>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), ctr, nseg, s); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+
+  const int P = plan.passes;
+  if (!balanced) {
+    SegHistParams hp{};
+    hp.keys = keys_in;
+    hp.offs = offs;
+    hp.tile_seg = I32(L.tile_seg);
+    hp.seg_tile0 = I32(L.seg_tile0);
+    hp.seg_slot = I32(L.seg_slot);
+    hp.ctr = ctr;
+    hp.tile = kSweepTile;
+    hp.passes = P;
+    hp.label_bits = label ? 8 : 0;
+    for (int q = 0; q < 4; ++q) {
+      hp.shift[q] = plan.shift[q];
+      hp.nbits[q] = plan.nbits[q] ? plan.nbits[q] : 1;
+    }
+    hp.seg_hist = U32(L.seg_hist);
+    k_seg_hist<<<(unsigned)L.tiles_cap, 256, 0, s>>>(hp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_seg_scan<<<(unsigned)L.slots_cap, 256, 0, s>>>(U32(L.seg_hist), U32(L.seg_base), I32(L.slot_seg),
+                                                     offs, ctr, P, L.slots_cap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+
+  uint32_t* kt = U32(L.keys_tmp);
+  void* vt = vb ? (void*)(ws + L.vals_tmp) : nullptr;
+  const uint32_t* src_k = keys_in;
+  const void* src_v = vals_in;
+  for (int q = 0; q < P; ++q) {
+    const bool to_out = ((P - 1 - q) % 2) == 0;
+    uint32_t* dk = to_out ? keys_out : kt;
+    void* dv = to_out ? vals_out : vt;
+    SweepParams sp{};
+    sp.keys_in = src_k;
+    sp.vals_in = src_v;
+    sp.keys_out = dk;
+    sp.vals_out = dv;
+    sp.n = n_total;
+    sp.shift = plan.shift[q];
+    sp.nbits = plan.nbits[q];
+    sp.w = label ? 256 : 0;  // per-segment widths come from seg_w
+    sp.balanced = balanced ? 1 : 0;
+    sp.lookback = U32(L.lookback) + (size_t)q * L.lb_stride * 256;
+    sp.lb_stride = L.lb_stride;
+    sp.ticket = ctr + C_TICKET + q;
+    sp.status = st;
+    sp.seg_offs = offs;
+    sp.tile_seg = I32(L.tile_seg);
+    sp.seg_tile0 = I32(L.seg_tile0);
+    sp.seg_slot = I32(L.seg_slot);
+    sp.seg_base = U32(L.seg_base) + (size_t)q * L.slots_cap * 256;
+    sp.seg_w = seg_w;
+    sp.num_tiles = ctr + C_NTILES;
+    if ((e = sweep_dispatch<8>(sp, L.tiles_cap, vb, s)) != cudaSuccess) return e;
+    src_k = dk;
+    src_v = dv;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                           void* vals_out, int64_t n_total, const int64_t* offs, int64_t nseg,
+                           int vb, const PassPlan& plan, unsigned char* ws, const SegLayout& L,
+                           cudaStream_t s) {
+  if (nseg == 0) return cudaSuccess;
+  return run_segments(keys_in, vals_in, keys_out, vals_out, n_total, offs, nseg, nullptr, vb, plan,
+                      false, false, ws, L, s);
+}
+
+cudaError_t segmented_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                                void* vals_out, int64_t n_total, const int64_t* offs,
+                                const int32_t* w_per_seg, int64_t nseg, int vb, bool balanced,
+                                unsigned char* ws, const SegLayout& L, cudaStream_t s) {
+  if (nseg == 0) return cudaSuccess;
+  PassPlan one;
+  one.passes = 1;
+  one.shift[0] = 0;
+  one.nbits[0] = 8;
+  return run_segments(keys_in, vals_in, keys_out, vals_out, n_total, offs, nseg, w_per_seg, vb, one,
+                      true, balanced, ws, L, s);
+}
+
+cudaError_t sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                       void* vals_out, int64_t n, int vb, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int64_t tiles = (n + kL1Tile - 1) / kL1Tile;
+  cudaError_t e = cudaSuccess;
+  switch (vb) {
+#define BCF_TS(VB)                                                                                 \
+  case VB:                                                                                         \
+    e = cudaFuncSetAttribute(k_sort_tiles<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                             (int)kL1SmemBytes);                                                   \
+    if (e != cudaSuccess) return e;                                                                \
+    k_sort_tiles<VB><<<(unsigned)tiles, kL1Threads, kL1SmemBytes, s>>>(keys_in, vals_in, keys_out, \
+                                                                       vals_out, n);               \
+    break;
+    BCF_TS(0)
+    BCF_TS(4)
+    BCF_TS(8)
+#undef BCF_TS
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace bcf

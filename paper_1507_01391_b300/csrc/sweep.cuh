@@ -1,0 +1,521 @@
+// sweep.cuh -- one stable digit sweep over tiles (shared by radix.cu and
+// segmented.cu).
+//
+// One sweep moves every key to the block of its digit (or partition label).  It
+// is the paper's partition problem (Sec. 1) at GPU scale: each block of threads
+// ranks one tile of keys in shared memory -- the per-row "radix sort" of
+// Corollary 1 done per warp -- and finds the tile's global offsets with a
+// decoupled look-back over earlier tiles.  Keys and payloads are staged into
+// shared memory by bulk copies (TMA engine), read back with the conflict-free
+// strided pattern of Sec. 1 (lane t reads word 32i + t), and written out in
+// digit order so that global stores form contiguous runs.
+//
+// Segment mode: tiles belong to CSR segments; a segment's first tile starts the
+// look-back chain, digit bases are per segment, and segment starts need not be
+// 16-byte aligned (the bulk copy starts at the aligned-down address and the tile
+// is read at an offset).
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace bcf {
+
+constexpr uint32_t LB_AGG = 1u << 30;   // tile aggregate published
+constexpr uint32_t LB_INC = 2u << 30;   // inclusive prefix published
+constexpr uint32_t LB_MASK = (1u << 30) - 1;
+
+struct SweepParams {
+  const uint32_t* keys_in;
+  const void* vals_in;         // nullptr with 4-byte payloads: payload = input position
+  uint32_t* keys_out;
+  void* vals_out;
+  int64_t n;
+  int shift, nbits;            // radix digit = (key >> shift) & (2^nbits - 1)
+  int w;                       // > 0: partition by label, labels must be < w
+  int balanced;                // partition: block b starts at b * len / w
+  const uint32_t* digit_base;  // exclusive global start of every digit
+  uint32_t* lookback;          // RADIX x lb_stride status words (digit-major), zero on entry
+  int64_t lb_stride;           // tiles rounded up to a multiple of the look-back window
+  uint32_t* ticket;            // tile counter, zero on entry
+  unsigned* status;
+  // reduce-then-scan mode (tile_offsets != nullptr): absolute start of every
+  // (digit, tile) run, digit-major with stride lb_stride; no look-back
+  const uint32_t* tile_offsets;
+  // segment mode (seg_offs != nullptr)
+  const int64_t* seg_offs;     // CSR offsets (nseg + 1)
+  const int32_t* tile_seg;     // tile -> segment
+  const int32_t* seg_tile0;    // segment -> its first tile
+  const int32_t* seg_slot;     // segment -> row of seg_base
+  const uint32_t* seg_base;    // slot x RADIX absolute digit starts
+  const int32_t* seg_w;        // partition: labels of segment s are < seg_w[s]
+  const uint32_t* num_tiles;   // tiles of this launch (device count)
+};
+
+template <int BITS>
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, int label_mode, int shift, int nbits) {
+  if (label_mode) return key & ((1u << BITS) - 1u);
+  return (key >> shift) & ((1u << nbits) - 1u);
+}
+
+// Exclusive scan of one value per thread over the block; *total gets the sum.
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratch,
+                                                    uint32_t* total) {
+  constexpr int WARPS = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < WARPS ? scratch[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < WARPS) scratch[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t before = warp ? scratch[warp - 1] : 0u;
+  *total = scratch[WARPS - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// ------------------------------------------------------------- histogram
+struct HistParams {
+  const uint32_t* keys;
+  int64_t n;
+  int passes;
+  int shift[4];
+  int nbits[4];
+  int label_bits;        // > 0: partition, one "pass" with digit = key & mask
+  uint32_t* hist;        // passes x 256, zero on entry
+  uint32_t* digit_base;  // passes x 256, written by the last block
+  uint32_t* done;        // zero on entry
+};
+
+// Counts every digit of every pass in one read of the keys; the last block to
+// finish turns the counts into exclusive starts.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
+  __shared__ uint32_t h[4 * 256];
+  __shared__ uint32_t scratch[32];
+  __shared__ int is_last;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 4 * 256; i += THREADS) h[i] = 0;
+  __syncthreads();
+  uint32_t mask[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    mask[q] = p.label_bits ? ((1u << p.label_bits) - 1u) : ((1u << p.nbits[q]) - 1u);
+  const int64_t nvec = p.n >> 2;
+  const uint4* kv = reinterpret_cast<const uint4*>(p.keys);
+  const int64_t stride = (int64_t)gridDim.x * THREADS;
+  for (int64_t i = (int64_t)blockIdx.x * THREADS + tid; i < nvec; i += stride) {
+    uint4 k4 = __ldcs(kv + i);
+    uint32_t k[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < p.passes) atomicAdd(&h[q * 256 + ((k[c] >> p.shift[q]) & mask[q])], 1u);
+    }
+  }
+  for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * THREADS + tid; i < p.n; i += stride) {
+    uint32_t k = p.keys[i];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q < p.passes) atomicAdd(&h[q * 256 + ((k >> p.shift[q]) & mask[q])], 1u);
+  }
+  __syncthreads();
+  for (int i = tid; i < p.passes * 256; i += THREADS)
+    if (h[i]) atomicAdd(&p.hist[i], h[i]);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = (atomicAdd(p.done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int q = 0; q < p.passes; ++q) {
+    uint32_t c = tid < 256 ? ld_relaxed(&p.hist[q * 256 + tid]) : 0u;
+    uint32_t total;
+    uint32_t e = block_excl_scan<THREADS>(c, scratch, &total);
+    if (tid < 256) p.digit_base[q * 256 + tid] = e;
+  }
+}
+
+// ------------------------------------------------------------- reduce-then-scan
+// Per-tile digit counts of one pass (digit-major), plus the pass's digit totals.
+struct CountParams {
+  const uint32_t* keys;
+  int64_t n;
+  int shift, nbits, label_bits;  // label_bits > 0: digit = key & (2^label_bits - 1)
+  uint32_t* counts;              // RADIX x stride
+  int64_t stride;
+  uint32_t* totals;              // RADIX, zero on entry
+};
+
+template <int BITS, int T>
+__global__ void __launch_bounds__(256) k_tile_counts(CountParams p) {
+  constexpr int RADIX = 1 << BITS;
+  __shared__ uint32_t h[RADIX];
+  const int tid = threadIdx.x;
+  const int64_t tile = blockIdx.x;
+  const int64_t start = tile * T;
+  const int cnt = (int)min((int64_t)T, p.n - start);
+  for (int i = tid; i < RADIX; i += 256) h[i] = 0;
+  __syncthreads();
+  const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : ((1u << p.nbits) - 1u);
+  const int shift = p.label_bits ? 0 : p.shift;
+  const uint32_t* k = p.keys + start;
+  const int nv = cnt >> 2;
+  for (int v = tid; v < nv; v += 256) {
+    const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
+    atomicAdd(&h[(x.x >> shift) & mask], 1u);
+    atomicAdd(&h[(x.y >> shift) & mask], 1u);
+    atomicAdd(&h[(x.z >> shift) & mask], 1u);
+    atomicAdd(&h[(x.w >> shift) & mask], 1u);
+  }
+  for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[(k[i] >> shift) & mask], 1u);
+  __syncthreads();
+  for (int d = tid; d < RADIX; d += 256) {
+    const uint32_t c = h[d];
+    p.counts[(size_t)d * p.stride + tile] = c;
+    if (c) atomicAdd(&p.totals[d], c);
+  }
+}
+
+// One block per digit: exclusive scan of the digit's tile counts, offset by the
+// digit's global start (sum of smaller digits' totals, or b*n/w for a balanced
+// partition, whose counts are checked here).
+constexpr int kScanThreads = 1024;
+constexpr int kScanPerThread = 16;
+
+static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* counts, int64_t tiles,
+                                                               int64_t stride, const uint32_t* totals,
+                                                               int balanced, int64_t n, int w,
+                                                               unsigned* status) {
+  __shared__ uint32_t scratch[32];
+  __shared__ uint32_t s_base;
+  const int d = blockIdx.x;
+  if (threadIdx.x == 0) {
+    uint32_t b = 0;
+    if (balanced) {
+      b = (uint32_t)min((int64_t)d * (n / w), n);
+      const uint32_t expect = d < w ? (uint32_t)(n / w) : 0u;
+      if (totals[d] != expect) set_status(status, DEV_NOT_BALANCED);
+    } else {
+      for (int e = 0; e < d; ++e) b += totals[e];
+    }
+    s_base = b;
+  }
+  __syncthreads();
+  uint32_t carry = s_base;
+  uint32_t* row = counts + (size_t)d * stride;
+  for (int64_t c0 = 0; c0 < tiles; c0 += (int64_t)kScanThreads * kScanPerThread) {
+    const int64_t i0 = c0 + (int64_t)threadIdx.x * kScanPerThread;
+    uint32_t v[kScanPerThread];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; ++j) {
+      v[j] = (i0 + j < tiles) ? row[i0 + j] : 0u;
+      sum += v[j];
+    }
+    uint32_t total;
+    uint32_t run = carry + block_excl_scan<kScanThreads>(sum, scratch, &total);
+#pragma unroll
+    for (int j = 0; j < kScanPerThread; ++j) {
+      if (i0 + j < tiles) row[i0 + j] = run;
+      run += v[j];
+    }
+    carry += total;
+  }
+}
+
+// ------------------------------------------------------------- one sweep
+template <int THREADS, int IPT, int BITS, int VB>
+struct SweepSmem {
+  static constexpr int T = THREADS * IPT;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int RADIX = 1 << BITS;
+  static constexpr size_t keys = 0;                        // T + 4 slots (staging offset)
+  static constexpr size_t vals = keys + (size_t)(T + 4) * 4;
+  static constexpr size_t whist = vals + (size_t)(T + 4) * VB;
+  static constexpr size_t tstart = whist + (size_t)WARPS * RADIX * 4;
+  static constexpr size_t gofs = tstart + (size_t)RADIX * 4;
+  static constexpr size_t scratch = gofs + (size_t)RADIX * 4;
+  static constexpr size_t mbar = scratch + 32 * 4;
+  static constexpr size_t info = mbar + 8;                 // tile, seg
+  static constexpr size_t bytes = info + 16;
+};
+
+template <int THREADS, int IPT, int BITS, int VB>
+__global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_sweep(SweepParams p) {
+  using VT = typename ValT<VB>::type;
+  using S = SweepSmem<THREADS, IPT, BITS, VB>;
+  constexpr int T = S::T, RADIX = S::RADIX;
+  static_assert(RADIX <= THREADS, "one thread per digit");
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* keys_s = reinterpret_cast<uint32_t*>(smem + S::keys);
+  VT* vals_s = reinterpret_cast<VT*>(smem + S::vals);
+  uint32_t* whist = reinterpret_cast<uint32_t*>(smem + S::whist);
+  uint32_t* tstart = reinterpret_cast<uint32_t*>(smem + S::tstart);
+  uint32_t* gofs = reinterpret_cast<uint32_t*>(smem + S::gofs);
+  uint32_t* scratch = reinterpret_cast<uint32_t*>(smem + S::scratch);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
+  int* s_info = reinterpret_cast<int*>(smem + S::info);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool segmented = p.seg_offs != nullptr;
+
+  // Tiles are taken in launch order so that every tile a look-back waits on
+  // belongs to a block that is already running.
+  if (tid == 0) {
+    const int tile = p.tile_offsets ? (int)blockIdx.x : (int)atomicAdd(p.ticket, 1u);
+    s_info[0] = tile;
+    s_info[1] = (segmented && (uint32_t)tile < ld_relaxed(p.num_tiles)) ? p.tile_seg[tile] : -1;
+  }
+  __syncthreads();
+  const int tile = s_info[0];
+  if (segmented && s_info[1] < 0) return;  // more blocks than tiles this time
+  const int seg = s_info[1];
+  int64_t lo = 0, hi = p.n;  // bounds of the problem this tile belongs to
+  int t_in = tile, w = p.w;
+  if (segmented) {
+    lo = p.seg_offs[seg];
+    hi = p.seg_offs[seg + 1];
+    t_in = tile - p.seg_tile0[seg];
+    if (p.seg_w) w = p.seg_w[seg];
+  }
+  const int64_t start = lo + (int64_t)t_in * T;
+  const int cnt = (int)min((int64_t)T, hi - start);
+  const bool last_tile = start + cnt >= hi;
+
+  // Stage the tile: bulk copy of the 16-byte-aligned window, plain loads for the
+  // ragged end.  Element i of the tile is keys_s[ksh + i].
+  const int ksh = (int)((reinterpret_cast<uintptr_t>(p.keys_in + start) & 15u) >> 2);
+  // vals_in == nullptr with 4-byte payloads: the payload is the input position
+  const bool iota = VB == 4 && p.vals_in == nullptr;
+  const int vsh = (VB && !iota) ? (int)((reinterpret_cast<uintptr_t>(reinterpret_cast<const VT*>(p.vals_in) + start) & 15u) / VB) : 0;
+  const int kfull = ((ksh + cnt) * 4 & ~15) / 4;  // elements covered by the bulk copy
+  const int vfull = (VB && !iota) ? (((vsh + cnt) * VB) & ~15) / VB : 0;
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    mbar_arrive_expect_tx(mbar, (unsigned)(kfull * 4 + vfull * VB));
+    if (kfull) bulk_g2s(keys_s, p.keys_in + start - ksh, (unsigned)kfull * 4, mbar);
+    if (VB && vfull)
+      bulk_g2s(vals_s, reinterpret_cast<const VT*>(p.vals_in) + start - vsh, (unsigned)(vfull * VB), mbar);
+  }
+  for (int i = tid; i < S::WARPS * RADIX; i += THREADS) whist[i] = 0;
+  for (int i = max(kfull - ksh, 0) + tid; i < cnt; i += THREADS) keys_s[ksh + i] = p.keys_in[start + i];
+  if (VB && !iota) {
+    for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
+      vals_s[vsh + i] = reinterpret_cast<const VT*>(p.vals_in)[start + i];
+  }
+  __syncthreads();  // mbarrier initialised before anyone waits on it
+  mbar_wait(mbar, 0, p.status);
+  __syncthreads();
+
+  // Registers, warp-striped: lane l of warp q holds tile items q*32*IPT + 32j + l.
+  // Reading them is the strided pattern: lane l always in bank (l + shift).
+  const int label_mode = w > 0;
+  const int nb = label_mode ? BITS : p.nbits;
+  uint32_t key[IPT];
+  VT val[IPT];
+  const int wbase = warp * 32 * IPT;
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const int idx = wbase + j * 32 + lane;
+    const bool valid = idx < cnt;
+    key[j] = valid ? keys_s[ksh + idx] : 0u;
+    if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
+    if (valid && label_mode && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
+  }
+  auto digit = [&](uint32_t k) { return digit_of<BITS>(k, label_mode, p.shift, p.nbits); };
+
+  // Phase A -- counts: every warp histograms its own keys (the row "radix sort"
+  // count of Corollary 1, one histogram per warp).
+  uint32_t* wh = whist + warp * RADIX;
+#pragma unroll
+  for (int j = 0; j < IPT; ++j)
+    if (wbase + j * 32 + lane < cnt) atomicAdd(&wh[digit(key[j])], 1u);
+  __syncthreads();
+
+  // Phase B -- per digit: tile count, tile-exclusive start, and each warp's base
+  // (tile start + counts of earlier warps).  The tile count is published at once
+  // so that later tiles can look back past this one while it ranks.
+  uint32_t count = 0;
+  if (tid < RADIX) {
+#pragma unroll 4
+    for (int q = 0; q < S::WARPS; ++q) count += whist[q * RADIX + tid];
+  }
+  uint32_t total;
+  const uint32_t tile_excl = block_excl_scan<THREADS>(tid < RADIX ? count : 0u, scratch, &total);
+  uint32_t* lbd = p.lookback + (size_t)tid * p.lb_stride;  // digit-major status words
+  if (tid < RADIX) {
+    if (!p.tile_offsets) st_relaxed(lbd + tile, (t_in == 0 ? LB_INC : LB_AGG) | count);
+    tstart[tid] = tile_excl;
+    uint32_t run = tile_excl;
+#pragma unroll 4
+    for (int q = 0; q < S::WARPS; ++q) {
+      const uint32_t c = whist[q * RADIX + tid];
+      whist[q * RADIX + tid] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+
+  // Phase C -- rank and scatter into shared memory in digit order.  Peers with the
+  // same digit come from one ballot per digit bit; the lowest peer claims the
+  // run for all of them with one shared atomic.
+  const unsigned lt = lanemask_lt();
+  unsigned long long* kv_s = reinterpret_cast<unsigned long long*>(smem + S::keys);
+#pragma unroll
+  for (int j = 0; j < IPT; ++j) {
+    const bool valid = wbase + j * 32 + lane < cnt;
+    const uint32_t d = digit(key[j]);
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#if BCF_PEERS_MATCH
+    peers &= __match_any_sync(0xffffffffu, valid ? d : 0xFFFFFFFFu);
+#else
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+      if (b < nb) {
+        const bool bit = (d >> b) & 1u;
+        const unsigned bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+      }
+    }
+#endif
+    const int leader = valid ? __ffs(peers) - 1 : lane;
+    uint32_t old = 0;
+    if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+    old = __shfl_sync(0xffffffffu, old, leader);
+    if (valid) {
+      const uint32_t pos = old + __popc(peers & lt);
+      if constexpr (VB == 4) {
+        kv_s[pos] = ((unsigned long long)val[j] << 32) | key[j];
+      } else {
+        keys_s[pos] = key[j];
+        if (VB) vals_s[pos] = val[j];
+      }
+    }
+  }
+
+  // Global offsets.  Reduce-then-scan mode: the run start was scanned ahead of
+  // this launch.  Otherwise decoupled look-back (one thread per digit): add
+  // earlier tiles' counts until one has published its inclusive prefix; the
+  // digit's status words of consecutive tiles are contiguous, so one read of
+  // kLookbackWindow words covers that many tiles.
+  if (tid < RADIX && p.tile_offsets) {
+    gofs[tid] = p.tile_offsets[(size_t)tid * p.lb_stride + tile] - tstart[tid];
+  } else if (tid < RADIX) {
+    uint32_t excl = 0;
+    if (t_in > 0) {
+      const int first = tile - t_in;
+      int j = tile - 1;  // next tile to consume
+      unsigned spins = 0;
+      constexpr int W = kLookbackWindow;
+      while (j >= first) {
+        const int ws = j - (j % W);  // W-aligned window [ws, ws + W)
+        uint32_t wv[W];
+#pragma unroll
+        for (int q = 0; q < W; q += 4) {
+          const uint4 a = ld_relaxed_v4(lbd + ws + q);
+          wv[q] = a.x;
+          wv[q + 1] = a.y;
+          wv[q + 2] = a.z;
+          wv[q + 3] = a.w;
+        }
+        bool done = false, stalled = false;
+#pragma unroll
+        for (int q = W - 1; q >= 0; --q) {
+          const int tt = ws + q;
+          if (done || stalled || tt > j || tt < first) continue;
+          const uint32_t f = wv[q] & ~LB_MASK;
+          if (f == 0) {
+            stalled = true;  // not published yet: poll this tile again
+            continue;
+          }
+          excl += wv[q] & LB_MASK;
+          j = tt - 1;
+          if (f == LB_INC) done = true;
+        }
+        if (done) break;
+        if (stalled && ++spins > kSpinLimit) {
+          set_status(p.status, DEV_TIMEOUT);
+          break;
+        }
+        if (!stalled && j >= ws) j = ws - 1;  // window below `first`: finished
+      }
+      st_relaxed(lbd + tile, LB_INC | (excl + count));
+    }
+    uint32_t base;  // absolute start of this digit's block
+    if (p.balanced) {
+      const int64_t len = hi - lo;
+      const int64_t b = lo + (int64_t)tid * (len / max(w, 1));
+      base = (uint32_t)min(b, hi);
+      if (last_tile) {
+        const uint32_t expect = tid < w ? (uint32_t)(len / max(w, 1)) : 0u;
+        if (excl + count != expect) set_status(p.status, DEV_NOT_BALANCED);
+      }
+    } else if (segmented) {
+      base = p.seg_base[(size_t)p.seg_slot[seg] * RADIX + tid];
+    } else {
+      base = p.digit_base[tid];
+    }
+    gofs[tid] = base + excl - tstart[tid];
+  }
+  __syncthreads();
+
+  // Write out: consecutive threads take consecutive sorted positions, so the
+  // stores of one digit's run are contiguous in global memory.
+  VT* vout = reinterpret_cast<VT*>(p.vals_out);
+  for (int i = tid; i < cnt; i += THREADS) {
+    uint32_t k;
+    VT v = VT(0);
+    if constexpr (VB == 4) {
+      const unsigned long long x = kv_s[i];
+      k = (uint32_t)x;
+      v = (uint32_t)(x >> 32);
+    } else {
+      k = keys_s[i];
+      if (VB) v = vals_s[i];
+    }
+    const uint32_t dst = gofs[digit(k)] + (uint32_t)i;
+    if ((int64_t)dst >= lo && (int64_t)dst < hi) {
+      p.keys_out[dst] = k;
+      if (VB) vout[dst] = v;
+    }
+  }
+}
+
+template <int BITS, int VB>
+inline cudaError_t launch_sweep(const SweepParams& p, int64_t grid, cudaStream_t s) {
+  using S = SweepSmem<kSweepThreads, kSweepIPT, BITS, VB>;
+  auto kern = k_sweep<kSweepThreads, kSweepIPT, BITS, VB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+  if (e != cudaSuccess) return e;
+  if (grid <= 0) return cudaSuccess;
+  kern<<<(unsigned)grid, kSweepThreads, S::bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int BITS>
+inline cudaError_t sweep_dispatch(const SweepParams& p, int64_t grid, int vb, cudaStream_t s) {
+  switch (vb) {
+    case 0: return launch_sweep<BITS, 0>(p, grid, s);
+    case 4: return launch_sweep<BITS, 4>(p, grid, s);
+    case 8: return launch_sweep<BITS, 8>(p, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace bcf

@@ -1,0 +1,173 @@
+// tile_sort.cuh -- Lemma 1 ("short and wide" sort, Sec. 2) on one shared-memory tile.
+//
+// A tile of up to 4096 keys is the paper's w x m matrix with w = 16 rows and
+// m = 256 columns (w*w <= m, the condition of Lemma 1).  Items are 64-bit
+// (key << 32 | position in the tile): all distinct, so sorting them sorts the keys
+// stably.  Item (r, c) sits at index c*16 + r of a u64 array, so row r always lives
+// in the bank pair {2r, 2r+1}.  A 64-bit shared access is served per half-warp;
+// in every half-warp the 16 lanes work on the 16 different rows, so every access
+// below touches 16 distinct bank pairs: no bank conflicts (the CAC of Sec. 1).
+//
+// Schedule (Lemma 1): twice { sort rows alternating (row 0 ascending); convert
+// row-major -> column-major; sort rows ascending; convert column-major ->
+// row-major }, then sort rows ascending.  A final row -> column-major conversion
+// puts sorted position t at index t, ready for a linear write-out.
+//
+// Row sort: the 16 threads of a row's team (one lane in each half-warp of the 8
+// warps) each sort 16 consecutive items of the row in registers with Batcher's
+// bitonic network, then four merge-path rounds merge runs of 16 -> 256 inside the
+// row's own banks.  Conversions move one item per row per half-warp phase along
+// a diagonal, so the 16 lanes of a phase read 16 different rows as well.
+#pragma once
+
+#include "common.cuh"
+
+namespace bcf {
+
+constexpr int kL1Threads = 256;   // 8 warps = 16 half-warps = 16 team members per row
+constexpr int kL1Rows = 16;       // w
+constexpr int kL1Cols = 256;      // m
+constexpr int kL1Tile = kL1Rows * kL1Cols;
+constexpr int kL1PerThread = kL1Cols / 16;  // items of a row per team member
+constexpr size_t kL1SmemBytes = 2ull * kL1Tile * 8;
+
+__device__ __forceinline__ void cas_u64(unsigned long long& a, unsigned long long& b, bool up) {
+  const bool swap = up ? (a > b) : (a < b);
+  const unsigned long long x = swap ? b : a, y = swap ? a : b;
+  a = x;
+  b = y;
+}
+
+// Bitonic sort of 16 registers, ascending if up.
+__device__ __forceinline__ void sort16(unsigned long long (&v)[16], bool up) {
+#pragma unroll
+  for (int k = 2; k <= 16; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool dir = ((i & k) == 0) ? up : !up;
+          cas_u64(v[i], v[l], dir);
+        }
+      }
+    }
+  }
+}
+
+// Sort every row of S (ascending, or alternating when alt: row 0 ascending).
+// Uses D as the merge buffer; the sorted rows end in S.
+__device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned long long* D, bool alt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int r = lane & 15;                    // row
+  const int t = warp * 2 + (lane >> 4);       // team member 0..15
+  const bool up = !(alt && (r & 1));
+  unsigned long long v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = S[(t * 16 + i) * kL1Rows + r];
+  sort16(v, up);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) S[(t * 16 + i) * kL1Rows + r] = v[i];
+  __syncthreads();
+  unsigned long long* src = S;
+  unsigned long long* dst = D;
+#pragma unroll 1
+  for (int L = 16; L < kL1Cols; L <<= 1) {
+    // merge runs [2bL, 2bL+L) and [2bL+L, 2bL+2L) of row r; this thread writes
+    // merged positions [16t, 16t+16) of its block
+    const int o0 = t * 16;
+    const int base = (o0 / (2 * L)) * (2 * L);
+    const int d = o0 - base;
+    const unsigned long long* A = src + (size_t)base * kL1Rows + r;
+    const unsigned long long* B = src + (size_t)(base + L) * kL1Rows + r;
+    int lo = d > L ? d - L : 0, hi = d < L ? d : L;
+    while (lo < hi) {  // smallest i whose A[i] comes after B[d-1-i]
+      const int mid = (lo + hi) >> 1;
+      const unsigned long long a = A[mid * kL1Rows], b = B[(d - 1 - mid) * kL1Rows];
+      const bool a_first = up ? (a < b) : (a > b);
+      if (a_first) lo = mid + 1;
+      else hi = mid;
+    }
+    int i = lo, j = d - lo;
+    unsigned long long* out = dst + (size_t)(base + d) * kL1Rows + r;
+#pragma unroll 4
+    for (int s = 0; s < 16; ++s) {
+      const unsigned long long a = i < L ? A[i * kL1Rows] : 0ull;
+      const unsigned long long b = j < L ? B[j * kL1Rows] : 0ull;
+      const bool take_a = (j >= L) || (i < L && (up ? (a < b) : (a > b)));
+      out[s * kL1Rows] = take_a ? a : b;
+      i += take_a;
+      j += !take_a;
+    }
+    __syncthreads();
+    unsigned long long* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  // four rounds (16 -> 256): the result is back in S
+}
+
+// Row-major -> column-major: N(r, c) = M(c / 16, (c % 16) * 16 + r).
+// Half-warp g (0..15), lane p writes row p at c = ((p + g) % 16) * 16 + j, reading
+// row (p + g) % 16 of M: distinct rows within the phase.
+__device__ __forceinline__ void l1_row_to_col(const unsigned long long* M, unsigned long long* N) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 15, g = warp * 2 + (lane >> 4);
+  const int R = (p + g) & 15;
+#pragma unroll 4
+  for (int j = 0; j < 16; ++j) {
+    const int c = R * 16 + j;
+    N[c * kL1Rows + p] = M[(j * 16 + p) * kL1Rows + R];
+  }
+  __syncthreads();
+}
+
+// Column-major -> row-major: M(R, C) = N(C % 16, R * 16 + C / 16).
+__device__ __forceinline__ void l1_col_to_row(const unsigned long long* N, unsigned long long* M) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = lane & 15, g = warp * 2 + (lane >> 4);
+  const int r = (p + g) & 15;
+#pragma unroll 4
+  for (int j = 0; j < 16; ++j) {
+    const int C = j * 16 + r;
+    M[C * kL1Rows + p] = N[(p * 16 + j) * kL1Rows + r];
+  }
+  __syncthreads();
+}
+
+// Sort one tile [start, start + len), len <= 4096, from keys_in/vals_in into
+// keys_out/vals_out.  X and Y are two kL1Tile-item shared buffers.
+template <int VB>
+__device__ __forceinline__ void lemma1_tile(const uint32_t* __restrict__ keys_in,
+                                            const void* __restrict__ vals_in,
+                                            uint32_t* __restrict__ keys_out,
+                                            void* __restrict__ vals_out, int64_t start, int len,
+                                            unsigned long long* X, unsigned long long* Y) {
+  using VT = typename ValT<VB>::type;
+  // item (r, c) of the initial matrix = tile position q = c*16 + r
+  for (int q = threadIdx.x; q < kL1Tile; q += kL1Threads) {
+    const unsigned long long key = q < len ? (unsigned long long)keys_in[start + q] : 0xFFFFFFFFull;
+    X[q] = (key << 32) | (unsigned)q;  // padding sorts last (position >= len)
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int rep = 0; rep < 2; ++rep) {
+    l1_sort_rows(X, Y, true);
+    l1_row_to_col(X, Y);
+    l1_sort_rows(Y, X, false);
+    l1_col_to_row(Y, X);
+  }
+  l1_sort_rows(X, Y, false);
+  l1_row_to_col(X, Y);  // Y[t] = item of sorted position t
+  const VT* vin = reinterpret_cast<const VT*>(vals_in);
+  VT* vout = reinterpret_cast<VT*>(vals_out);
+  for (int t = threadIdx.x; t < len; t += kL1Threads) {
+    const unsigned long long it = Y[t];
+    keys_out[start + t] = (uint32_t)(it >> 32);
+    if (VB) vout[start + t] = vin ? vin[start + (uint32_t)it] : VT(start + (uint32_t)it);
+  }
+  __syncthreads();
+}
+
+}  // namespace bcf

@@ -63,15 +63,22 @@ def test_argument_checks_reject_without_launching():
     assert L.bcf_sort(a, None, b, None, 10, 4, 32, ws, 1 << 20, None) == bcf.E_INVAL  # vals missing
     assert L.bcf_partition(a, None, b, None, 10, 3, 0, bcf.ASSUME_BALANCED, ws, 1 << 20, None) == bcf.E_INVAL
     assert L.bcf_partition(a, None, b, None, 10, 300, 0, 0, ws, 1 << 20, None) == bcf.E_UNSUPPORTED
-    assert L.bcf_permute(a, P(0x10010), b, 64, 4, 0, None, 0, None) == bcf.E_INVAL  # overlap
-    assert L.bcf_permute(a, b, None, 64, 4, 0, None, 0, None) == bcf.E_INVAL
-    assert L.bcf_permute(a, b, ws, 64, 3, 0, None, 0, None) == bcf.E_INVAL
-    assert L.bcf_permute(a, b, ws, 64, 4, bcf.CHECK_PERM, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute(a, P(0x10010), b, 64, 0, 4, 0, None, 0, None) == bcf.E_INVAL  # overlap
+    assert L.bcf_permute(a, b, None, 64, 0, 4, 0, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute(a, b, ws, 64, 0, 3, 0, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute(a, b, ws, 64, -1, 4, 0, None, 0, None) == bcf.E_INVAL
+    assert L.bcf_permute(a, b, ws, 64, 0, 4, bcf.CHECK_PERM, None, 0, None) == bcf.E_INVAL
     assert L.bcf_permute_tiles(a, b, ws, 64, 1000, 0, 0, None) == bcf.E_INVAL
-    assert L.bcf_gather(a, b, ws, 64, 64, 2, None) == bcf.E_INVAL
+    assert L.bcf_gather(a, b, ws, 64, 64, 0, 2, None) == bcf.E_INVAL
     # empty inputs are valid no-ops
     assert L.bcf_sort(None, None, None, None, 0, 0, 32, None, 0, None) == bcf.OK
-    assert L.bcf_permute(None, None, None, 0, 4, 0, None, 0, None) == bcf.OK
+    assert L.bcf_permute(None, None, None, 0, 0, 4, 0, None, 0, None) == bcf.OK
+    # segmented forms: out-of-place only, offsets required
+    assert L.bcf_segmented_sort(a, None, a, None, 10, ws, 1, 0, 32, ws, 1 << 30, None) == bcf.E_INVAL
+    assert L.bcf_segmented_sort(a, None, b, None, 10, None, 1, 0, 32, ws, 1 << 30, None) == bcf.E_INVAL
+    assert L.bcf_segmented_sort(a, None, b, None, 10, ws, 1, 0, 32, ws, 8, None) == bcf.E_WORKSPACE
+    assert L.bcf_sort_tiles(a, None, b, None, 10, 1024, 0, None) == bcf.E_INVAL
+    assert L.bcf_sort_tiles(a, None, a, None, 10, 4096, 0, None) == bcf.E_INVAL
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

@@ -184,6 +184,27 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
                             int val_bytes, int flags, void* ws, size_t ws_bytes,
                             bcf_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * Partition without a workspace.  The paper has no counterpart: this is a
+ * calling convention for users who cannot allocate device memory when they call
+ * the library -- code running inside CUDA stream capture (cudaMalloc is not
+ * allowed while a global-mode capture is active), plugins whose host framework
+ * owns all device memory, and latency-critical loops that must never enter the
+ * allocator.  Same operation, flags and errors as bcf_partition, out of place
+ * only (outputs must not overlap the inputs; an overlap returns BCF_E_INVAL),
+ * for n <= BCF_NOALLOC_MAX_N (larger n returns BCF_E_UNSUPPORTED).
+ * Scratch lives in a fixed device array of about 1 MiB inside libbcf.so, held on
+ * every device that loads the library until the process exits; nothing is
+ * allocated or freed.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: each call clears what must start at zero on its
+ * stream, and calls whose work overlaps on the GPU (different streams with no
+ * ordering between them) race on it. */
+#define BCF_NOALLOC_MAX_N (1 << 22)
+int bcf_partition_noalloc(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                          void* vals_out, int64_t n, int w, int val_bytes, int flags,
+                          bcf_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

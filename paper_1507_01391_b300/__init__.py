@@ -58,7 +58,9 @@ _SIGS = {
     "bcf_segmented_sort": ([_P, _P, _P, _P, _I64, _P, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_segmented_partition_workspace_size": ([_I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_segmented_partition": ([_P, _P, _P, _P, _I64, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
+    "bcf_partition_noalloc": ([_P, _P, _P, _P, _I64, _I, _I, _I, _P], _I),
 }
+NOALLOC_MAX_N = 1 << 22
 
 
 def header_functions(path: str = HEADER) -> list[str]:
@@ -309,4 +311,21 @@ def segmented_partition(keys, vals, offs, w_per_seg, balanced=False, keys_out=No
     _check(lib().bcf_segmented_partition(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n,
                                          _ptr(offs), _ptr(w_per_seg), nseg, vb, flags, _ptr(ws),
                                          ws.numel(), _stream(stream)), "bcf_segmented_partition")
+    return keys_out, vals_out
+
+
+def partition_noalloc(keys, vals, w, balanced=False, keys_out=None, vals_out=None, stream=None):
+    """Stable w-way partition whose scratch is a fixed array inside the library
+    (bcf_partition_noalloc): for callers that cannot allocate device memory at
+    call time.  n <= NOALLOC_MAX_N, out of place only.  The outputs are
+    allocated here only when not given."""
+    torch = _torch()
+    _dev_u32(keys, "keys")
+    n = keys.numel()
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    if vals is not None and vals_out is None:
+        vals_out = torch.empty_like(vals)
+    flags = ASSUME_BALANCED if balanced else 0
+    _check(lib().bcf_partition_noalloc(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n, w,
+                                       _vb(vals), flags, _stream(stream)), "bcf_partition_noalloc")
     return keys_out, vals_out

@@ -7,15 +7,16 @@
 namespace bcf {
 
 // ------------------------------------------------------------- host side
+// Passes of 8-bit digits from the least significant end; the last pass of a key
+// width that is not a multiple of 8 starts at key_bits - 8 and overlaps the one
+// before it.  That is still a correct LSD sort: every pass is stable, so after a
+// pass the keys are ordered by all the bits it and the earlier passes covered.
 PassPlan plan_passes(int key_bits) {
   PassPlan pl;
   pl.passes = (key_bits + 7) / 8;
-  int shift = 0;
   for (int q = 0; q < pl.passes; ++q) {
-    int bits = key_bits / pl.passes + (q < key_bits % pl.passes ? 1 : 0);
-    pl.shift[q] = shift;
-    pl.nbits[q] = bits;
-    shift += bits;
+    pl.shift[q] = std::min(8 * q, std::max(key_bits - 8, 0));
+    pl.nbits[q] = 8;
   }
   return pl;
 }
@@ -57,7 +58,8 @@ static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_
   cp.counts = offsets;
   cp.stride = L.lb_stride;
   cp.totals = totals;
-  k_tile_counts<BITS, kSweepTile><<<(unsigned)L.tiles, 256, 0, s>>>(cp);
+  const int64_t count_blocks = (L.tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
+  k_tile_counts<BITS, kSweepTile><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_scan_offsets<<<RADIX, kScanThreads, 0, s>>>(offsets, L.tiles, L.lb_stride, totals, balanced ? 1 : 0, n,

@@ -16,6 +16,8 @@
 // is read at an offset).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -162,34 +164,43 @@ struct CountParams {
   uint32_t* totals;              // RADIX, zero on entry
 };
 
+constexpr int kCountTilesPerBlock = 16;
+
 template <int BITS, int T>
-__global__ void __launch_bounds__(256) k_tile_counts(CountParams p) {
+__global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tiles) {
   constexpr int RADIX = 1 << BITS;
   __shared__ uint32_t h[RADIX];
+  __shared__ uint32_t tot[RADIX];
   const int tid = threadIdx.x;
-  const int64_t tile = blockIdx.x;
-  const int64_t start = tile * T;
-  const int cnt = (int)min((int64_t)T, p.n - start);
-  for (int i = tid; i < RADIX; i += 256) h[i] = 0;
-  __syncthreads();
-  const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : ((1u << p.nbits) - 1u);
+  for (int i = tid; i < RADIX; i += 256) tot[i] = 0;
+  const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
   const int shift = p.label_bits ? 0 : p.shift;
-  const uint32_t* k = p.keys + start;
-  const int nv = cnt >> 2;
-  for (int v = tid; v < nv; v += 256) {
-    const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
-    atomicAdd(&h[(x.x >> shift) & mask], 1u);
-    atomicAdd(&h[(x.y >> shift) & mask], 1u);
-    atomicAdd(&h[(x.z >> shift) & mask], 1u);
-    atomicAdd(&h[(x.w >> shift) & mask], 1u);
+  const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
+  for (int64_t tile = t0; tile < min(t0 + kCountTilesPerBlock, tiles); ++tile) {
+    const int64_t start = tile * T;
+    const int cnt = (int)min((int64_t)T, p.n - start);
+    for (int i = tid; i < RADIX; i += 256) h[i] = 0;
+    __syncthreads();
+    const uint32_t* k = p.keys + start;
+    const int nv = cnt >> 2;
+    for (int v = tid; v < nv; v += 256) {
+      const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
+      atomicAdd(&h[(x.x >> shift) & mask], 1u);
+      atomicAdd(&h[(x.y >> shift) & mask], 1u);
+      atomicAdd(&h[(x.z >> shift) & mask], 1u);
+      atomicAdd(&h[(x.w >> shift) & mask], 1u);
+    }
+    for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[(k[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int d = tid; d < RADIX; d += 256) {
+      const uint32_t c = h[d];
+      p.counts[(size_t)d * p.stride + tile] = c;
+      tot[d] += c;
+    }
+    __syncthreads();
   }
-  for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[(k[i] >> shift) & mask], 1u);
-  __syncthreads();
-  for (int d = tid; d < RADIX; d += 256) {
-    const uint32_t c = h[d];
-    p.counts[(size_t)d * p.stride + tile] = c;
-    if (c) atomicAdd(&p.totals[d], c);
-  }
+  for (int d = tid; d < RADIX; d += 256)
+    if (tot[d]) atomicAdd(&p.totals[d], tot[d]);
 }
 
 // One block per digit: exclusive scan of the digit's tile counts, offset by the
@@ -261,10 +272,12 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   using VT = typename ValT<VB>::type;
   using S = SweepSmem<THREADS, IPT, BITS, VB>;
   constexpr int T = S::T, RADIX = S::RADIX;
+  constexpr uint32_t DMASK = RADIX - 1;
   static_assert(RADIX <= THREADS, "one thread per digit");
   extern __shared__ __align__(128) unsigned char smem[];
   uint32_t* keys_s = reinterpret_cast<uint32_t*>(smem + S::keys);
   VT* vals_s = reinterpret_cast<VT*>(smem + S::vals);
+  unsigned long long* kv_s = reinterpret_cast<unsigned long long*>(smem + S::keys);
   uint32_t* whist = reinterpret_cast<uint32_t*>(smem + S::whist);
   uint32_t* tstart = reinterpret_cast<uint32_t*>(smem + S::tstart);
   uint32_t* gofs = reinterpret_cast<uint32_t*>(smem + S::gofs);
@@ -275,8 +288,8 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool segmented = p.seg_offs != nullptr;
 
-  // Tiles are taken in launch order so that every tile a look-back waits on
-  // belongs to a block that is already running.
+  // Look-back mode takes tiles in launch order (atomic ticket) so that every tile
+  // a look-back waits on belongs to a block that is already running.
   if (tid == 0) {
     const int tile = p.tile_offsets ? (int)blockIdx.x : (int)atomicAdd(p.ticket, 1u);
     s_info[0] = tile;
@@ -297,6 +310,8 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   const int64_t start = lo + (int64_t)t_in * T;
   const int cnt = (int)min((int64_t)T, hi - start);
   const bool last_tile = start + cnt >= hi;
+  const int shift = p.shift;  // digit = (key >> shift) & (RADIX - 1); labels use shift 0
+  const bool label_mode = w > 0;
 
   // Stage the tile: bulk copy of the 16-byte-aligned window, plain loads for the
   // ragged end.  Element i of the tile is keys_s[ksh + i].
@@ -323,101 +338,105 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   mbar_wait(mbar, 0, p.status);
   __syncthreads();
 
-  // Registers, warp-striped: lane l of warp q holds tile items q*32*IPT + 32j + l.
-  // Reading them is the strided pattern: lane l always in bank (l + shift).
-  const int label_mode = w > 0;
-  const int nb = label_mode ? BITS : p.nbits;
-  uint32_t key[IPT];
-  VT val[IPT];
-  const int wbase = warp * 32 * IPT;
-#pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const int idx = wbase + j * 32 + lane;
-    const bool valid = idx < cnt;
-    key[j] = valid ? keys_s[ksh + idx] : 0u;
-    if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
-    if (valid && label_mode && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
-  }
-  auto digit = [&](uint32_t k) { return digit_of<BITS>(k, label_mode, p.shift, p.nbits); };
+  // The rest is written once for full tiles (no per-key bounds tests) and once
+  // for the ragged last tile.
+  auto body = [&](auto full_tag) {
+    constexpr bool FULL = decltype(full_tag)::value;
+    auto in_tile = [&](int idx) { return FULL || idx < cnt; };
 
-  // Phase A -- counts: every warp histograms its own keys (the row "radix sort"
-  // count of Corollary 1, one histogram per warp).
-  uint32_t* wh = whist + warp * RADIX;
+    // Registers, warp-striped: lane l of warp q holds tile items q*32*IPT + 32j + l.
+    // Reading them is the strided pattern: lane l always in bank (l + shift).
+    uint32_t key[IPT];
+    VT val[IPT];
+    const int wbase = warp * 32 * IPT;
 #pragma unroll
-  for (int j = 0; j < IPT; ++j)
-    if (wbase + j * 32 + lane < cnt) atomicAdd(&wh[digit(key[j])], 1u);
-  __syncthreads();
-
-  // Phase B -- per digit: tile count, tile-exclusive start, and each warp's base
-  // (tile start + counts of earlier warps).  The tile count is published at once
-  // so that later tiles can look back past this one while it ranks.
-  uint32_t count = 0;
-  if (tid < RADIX) {
-#pragma unroll 4
-    for (int q = 0; q < S::WARPS; ++q) count += whist[q * RADIX + tid];
-  }
-  uint32_t total;
-  const uint32_t tile_excl = block_excl_scan<THREADS>(tid < RADIX ? count : 0u, scratch, &total);
-  uint32_t* lbd = p.lookback + (size_t)tid * p.lb_stride;  // digit-major status words
-  if (tid < RADIX) {
-    if (!p.tile_offsets) st_relaxed(lbd + tile, (t_in == 0 ? LB_INC : LB_AGG) | count);
-    tstart[tid] = tile_excl;
-    uint32_t run = tile_excl;
-#pragma unroll 4
-    for (int q = 0; q < S::WARPS; ++q) {
-      const uint32_t c = whist[q * RADIX + tid];
-      whist[q * RADIX + tid] = run;
-      run += c;
+    for (int j = 0; j < IPT; ++j) {
+      const int idx = wbase + j * 32 + lane;
+      const bool valid = in_tile(idx);
+      key[j] = valid ? keys_s[ksh + idx] : 0u;
+      if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
+      if (label_mode && valid && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
     }
-  }
-  __syncthreads();
 
-  // Phase C -- rank and scatter into shared memory in digit order.  Peers with the
-  // same digit come from one ballot per digit bit; the lowest peer claims the
-  // run for all of them with one shared atomic.
-  const unsigned lt = lanemask_lt();
-  unsigned long long* kv_s = reinterpret_cast<unsigned long long*>(smem + S::keys);
+    // Phase A -- counts: every warp histograms its own keys (the row "radix sort"
+    // count of Corollary 1, one histogram per warp).
+    uint32_t* wh = whist + warp * RADIX;
 #pragma unroll
-  for (int j = 0; j < IPT; ++j) {
-    const bool valid = wbase + j * 32 + lane < cnt;
-    const uint32_t d = digit(key[j]);
-    unsigned peers = __ballot_sync(0xffffffffu, valid);
+    for (int j = 0; j < IPT; ++j)
+      if (in_tile(wbase + j * 32 + lane)) atomicAdd(&wh[(key[j] >> shift) & DMASK], 1u);
+    __syncthreads();
+
+    // Phase B -- per digit: tile count, tile-exclusive start, and each warp's base
+    // (tile start + counts of earlier warps).  In look-back mode the tile count is
+    // published at once so that later tiles can look past this one while it ranks.
+    uint32_t count = 0;
+    if (tid < RADIX) {
+#pragma unroll 4
+      for (int q = 0; q < S::WARPS; ++q) count += whist[q * RADIX + tid];
+    }
+    uint32_t total;
+    const uint32_t tile_excl = block_excl_scan<THREADS>(tid < RADIX ? count : 0u, scratch, &total);
+    uint32_t* lbd = p.lookback + (size_t)tid * p.lb_stride;  // digit-major status words
+    if (tid < RADIX) {
+      if (!p.tile_offsets) st_relaxed(lbd + tile, (t_in == 0 ? LB_INC : LB_AGG) | count);
+      tstart[tid] = tile_excl;
+      uint32_t run = tile_excl;
+#pragma unroll 4
+      for (int q = 0; q < S::WARPS; ++q) {
+        const uint32_t c = whist[q * RADIX + tid];
+        whist[q * RADIX + tid] = run;
+        run += c;
+      }
+    }
+    __syncthreads();
+
+    // Phase C -- rank and scatter into shared memory in digit order.  Peers with
+    // the same digit come from one ballot per digit bit; the lowest peer claims the
+    // run for all of them with one shared atomic.
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+      const bool valid = in_tile(wbase + j * 32 + lane);
+      const uint32_t d = (key[j] >> shift) & DMASK;
+      unsigned peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
 #if BCF_PEERS_MATCH
-    peers &= __match_any_sync(0xffffffffu, valid ? d : 0xFFFFFFFFu);
+      peers &= __match_any_sync(0xffffffffu, valid ? d : 0xFFFFFFFFu);
 #else
 #pragma unroll
-    for (int b = 0; b < BITS; ++b) {
-      if (b < nb) {
-        const bool bit = (d >> b) & 1u;
-        const unsigned bal = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? bal : ~bal;
+      for (int b = 0; b < BITS; ++b) {
+        const unsigned bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+        peers &= ((d >> b) & 1u) ? bal : ~bal;
       }
-    }
 #endif
-    const int leader = valid ? __ffs(peers) - 1 : lane;
-    uint32_t old = 0;
-    if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
-    old = __shfl_sync(0xffffffffu, old, leader);
-    if (valid) {
-      const uint32_t pos = old + __popc(peers & lt);
-      if constexpr (VB == 4) {
-        kv_s[pos] = ((unsigned long long)val[j] << 32) | key[j];
-      } else {
-        keys_s[pos] = key[j];
-        if (VB) vals_s[pos] = val[j];
+      const int leader = valid ? __ffs(peers) - 1 : lane;
+      uint32_t old = 0;
+      if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+      old = __shfl_sync(0xffffffffu, old, leader);
+      if (valid) {
+        const uint32_t pos = old + __popc(peers & lt);
+        if constexpr (VB == 4) {
+          kv_s[pos] = ((unsigned long long)val[j] << 32) | key[j];
+        } else {
+          keys_s[pos] = key[j];
+          if (VB) vals_s[pos] = val[j];
+        }
       }
     }
-  }
+  };
+  if (cnt == T) body(std::true_type{});
+  else body(std::false_type{});
 
   // Global offsets.  Reduce-then-scan mode: the run start was scanned ahead of
   // this launch.  Otherwise decoupled look-back (one thread per digit): add
   // earlier tiles' counts until one has published its inclusive prefix; the
   // digit's status words of consecutive tiles are contiguous, so one read of
   // kLookbackWindow words covers that many tiles.
+  uint32_t* lbd = p.lookback + (size_t)tid * p.lb_stride;
   if (tid < RADIX && p.tile_offsets) {
     gofs[tid] = p.tile_offsets[(size_t)tid * p.lb_stride + tile] - tstart[tid];
   } else if (tid < RADIX) {
     uint32_t excl = 0;
+    const uint32_t count = ld_relaxed(lbd + tile) & LB_MASK;  // own aggregate, published above
     if (t_in > 0) {
       const int first = tile - t_in;
       int j = tile - 1;  // next tile to consume
@@ -476,8 +495,11 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   __syncthreads();
 
   // Write out: consecutive threads take consecutive sorted positions, so the
-  // stores of one digit's run are contiguous in global memory.
+  // stores of one digit's run are contiguous in global memory.  Positions are
+  // below 2^30, so 32-bit arithmetic suffices; dst outside [lo, hi) (only possible
+  // with invalid labels) is never written.
   VT* vout = reinterpret_cast<VT*>(p.vals_out);
+  const uint32_t lo32 = (uint32_t)lo, len32 = (uint32_t)(hi - lo);
   for (int i = tid; i < cnt; i += THREADS) {
     uint32_t k;
     VT v = VT(0);
@@ -489,8 +511,8 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
       k = keys_s[i];
       if (VB) v = vals_s[i];
     }
-    const uint32_t dst = gofs[digit(k)] + (uint32_t)i;
-    if ((int64_t)dst >= lo && (int64_t)dst < hi) {
+    const uint32_t dst = gofs[(k >> shift) & DMASK] + (uint32_t)i;
+    if (dst - lo32 < len32) {
       p.keys_out[dst] = k;
       if (VB) vout[dst] = v;
     }

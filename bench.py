@@ -45,7 +45,7 @@ FALLBACK_HBM_GBS = 6400.0
 # Per-launch DRAM traffic of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
 # it was taken on: if permute.cu changes, the figure is dropped (null).
-NCU_TRAFFIC = {"kernel": "k_permute<4,4>", "source_sha1": None, "bytes": None,
+NCU_TRAFFIC = {"kernel": "k_permute<4,0> x2 (keys pass + payload pass)", "source_sha1": None, "bytes": None,
                "summary": "profiles/k_permute_kv_2pow24.md"}
 
 
@@ -537,10 +537,15 @@ def _case_inputs(name):
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.partition_workspace_size(m, w, 4, bcf.ASSUME_BALANCED))
         return lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws)
+    if name == "tile_sort":
+        k, v = to_dev(synth.uniform_keys(n, seed=7)), to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        return lambda: bcf.sort_tiles(k, v, keys_out=ko, vals_out=vo)
     raise ValueError(name)
 
 
-CASES = ("permute_kv", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256")
+CASES = ("permute_kv", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256",
+         "tile_sort")
 
 
 def run_case(args):

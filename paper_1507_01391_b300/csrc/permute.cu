@@ -44,15 +44,66 @@ __device__ __forceinline__ bool claim(uint32_t* seen, uint32_t d) {
   return (atomicOr(seen + (d >> 5), bit) & bit) == 0;
 }
 
+#ifndef BCF_PERMUTE_HINTS
+#define BCF_PERMUTE_HINTS 1   // L2 policy: streaming inputs evict first, scattered outputs evict last
+#endif
+#ifndef BCF_PERMUTE_VEC
+#define BCF_PERMUTE_VEC 4     // items per thread per step (4 or 8)
+#endif
+
+// L2 eviction policies.  The scattered stores fill each output sector piece by
+// piece; keeping those lines (evict_last) while the streaming reads go first
+// lets most sectors complete in L2 before they are written to HBM.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ uint4 ld_stream_v4(const void* p, uint64_t pol) {
+#if BCF_PERMUTE_HINTS
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+#else
+  (void)pol;
+  return __ldcs(reinterpret_cast<const uint4*>(p));
+#endif
+}
+
 template <typename T>
-__device__ __forceinline__ void load4(const T* p, int64_t i, T (&out)[4]) {
+__device__ __forceinline__ void st_keep(T* p, T v, uint64_t pol) {
+#if BCF_PERMUTE_HINTS
+  if constexpr (sizeof(T) == 4)
+    asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"((uint32_t)v), "l"(pol) : "memory");
+  else
+    asm volatile("st.global.L2::cache_hint.b64 [%0], %1, %2;" ::"l"(p), "l"((unsigned long long)v), "l"(pol)
+                 : "memory");
+#else
+  (void)pol;
+  *p = v;
+#endif
+}
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, int64_t i, T (&out)[4], uint64_t pol) {
   if constexpr (sizeof(T) == 4) {
-    const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p + i));
+    const uint4 v = ld_stream_v4(p + i, pol);
     out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
   } else {
-    const ulonglong2 a = __ldcs(reinterpret_cast<const ulonglong2*>(p + i));
-    const ulonglong2 b = __ldcs(reinterpret_cast<const ulonglong2*>(p + i + 2));
-    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+    const uint4 a = ld_stream_v4(p + i, pol);
+    const uint4 b = ld_stream_v4(p + i + 2, pol);
+    out[0] = ((unsigned long long)a.y << 32) | a.x;
+    out[1] = ((unsigned long long)a.w << 32) | a.z;
+    out[2] = ((unsigned long long)b.y << 32) | b.x;
+    out[3] = ((unsigned long long)b.w << 32) | b.z;
   }
 }
 
@@ -71,30 +122,44 @@ __global__ void __launch_bounds__(256) k_permute(const void* __restrict__ src_k,
   KT* dk = reinterpret_cast<KT*>(dst_k);
   const VT* sv = reinterpret_cast<const VT*>(src_v);
   VT* dv = reinterpret_cast<VT*>(dst_v);
-  const int64_t nvec = n >> 2;
+  const uint64_t keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
+  constexpr int V = BCF_PERMUTE_VEC;
+  const int64_t nvec = n / V;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
-    const int64_t i = v * 4;
-    const uint4 p4 = __ldcs(reinterpret_cast<const uint4*>(pi + i));
-    uint32_t d[4] = {p4.x, p4.y, p4.z, p4.w};
-    local_to_global(d, i, n, row_len);
-    KT k[4];
-    load4(sk, i, k);
-    VT val[4];
-    if (VB) load4(sv, i, val);
+    const int64_t i0 = v * V;
+    uint32_t d[V];
+    KT k[V];
+    VT val[V];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int h = 0; h < V; h += 4) {  // issue every load of the step before any store
+      const uint4 p4 = ld_stream_v4(pi + i0 + h, stream);
+      d[h] = p4.x; d[h + 1] = p4.y; d[h + 2] = p4.z; d[h + 3] = p4.w;
+      KT kk[4];
+      load4(sk, i0 + h, kk, stream);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) k[h + c] = kk[c];
+      if (VB) {
+        VT vv[4];
+        load4(sv, i0 + h, vv, stream);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) val[h + c] = vv[c];
+      }
+    }
+    local_to_global(d, i0, n, row_len);
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
       bool ok = (int64_t)d[c] < n;
       if (ok && seen) ok = claim(seen, d[c]);
       if (!ok) {
         set_status(status, DEV_BAD_PERM);
         continue;
       }
-      dk[d[c]] = k[c];
-      if (VB) dv[d[c]] = val[c];
+      st_keep(dk + d[c], k[c], keep);
+      if (VB) st_keep(dv + d[c], val[c], keep);
     }
   }
-  for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+  for (int64_t i = nvec * V + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     uint32_t d1[1] = {pi[i]};
     local_to_global(d1, i, n, row_len);
     const uint32_t d = d1[0];
@@ -162,7 +227,7 @@ static int sm_count() {
 }
 
 static unsigned grid_for(int64_t n) {
-  const int64_t want = (n / 4 + 255) / 256;
+  const int64_t want = (n / BCF_PERMUTE_VEC + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 8;  // 8 resident blocks of 256 per SM
   int64_t g = want < cap ? want : cap;
   return (unsigned)(g > 0 ? g : 1);

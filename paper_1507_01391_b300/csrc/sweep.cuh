@@ -164,7 +164,10 @@ struct CountParams {
   uint32_t* totals;              // RADIX, zero on entry
 };
 
-constexpr int kCountTilesPerBlock = 16;
+#ifndef BCF_COUNT_TILES_PER_BLOCK
+#define BCF_COUNT_TILES_PER_BLOCK 4
+#endif
+constexpr int kCountTilesPerBlock = BCF_COUNT_TILES_PER_BLOCK;
 
 template <int BITS, int T>
 __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tiles) {
@@ -182,15 +185,29 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     for (int i = tid; i < RADIX; i += 256) h[i] = 0;
     __syncthreads();
     const uint32_t* k = p.keys + start;
-    const int nv = cnt >> 2;
-    for (int v = tid; v < nv; v += 256) {
-      const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
-      atomicAdd(&h[(x.x >> shift) & mask], 1u);
-      atomicAdd(&h[(x.y >> shift) & mask], 1u);
-      atomicAdd(&h[(x.z >> shift) & mask], 1u);
-      atomicAdd(&h[(x.w >> shift) & mask], 1u);
+    if (cnt == T) {  // full tile: all T/1024 vector loads in flight before counting
+      constexpr int NV = T / 1024;
+      uint4 x[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) x[q] = __ldcs(reinterpret_cast<const uint4*>(k) + tid + 256 * q);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        atomicAdd(&h[(x[q].x >> shift) & mask], 1u);
+        atomicAdd(&h[(x[q].y >> shift) & mask], 1u);
+        atomicAdd(&h[(x[q].z >> shift) & mask], 1u);
+        atomicAdd(&h[(x[q].w >> shift) & mask], 1u);
+      }
+    } else {
+      const int nv = cnt >> 2;
+      for (int v = tid; v < nv; v += 256) {
+        const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
+        atomicAdd(&h[(x.x >> shift) & mask], 1u);
+        atomicAdd(&h[(x.y >> shift) & mask], 1u);
+        atomicAdd(&h[(x.z >> shift) & mask], 1u);
+        atomicAdd(&h[(x.w >> shift) & mask], 1u);
+      }
+      for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[(k[i] >> shift) & mask], 1u);
     }
-    for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[(k[i] >> shift) & mask], 1u);
     __syncthreads();
     for (int d = tid; d < RADIX; d += 256) {
       const uint32_t c = h[d];

@@ -39,10 +39,11 @@ struct TPSmem {
   static constexpr size_t in = 0;
   static constexpr size_t lpi = in + (size_t)T * 4;
   static constexpr size_t out = lpi + (size_t)T * 2;
-  static constexpr size_t tbl = out + (size_t)T * 4;
-  static constexpr size_t mbar = tbl + (size_t)T * 4;
-  static constexpr size_t misc = mbar + 8;
-  static constexpr size_t bytes = misc + 8;
+  static constexpr size_t mbar = out + (size_t)T * 4;
+  static constexpr size_t bytes = mbar + 8;             // direct scatter
+  static constexpr size_t tbl = mbar + 16;
+  static constexpr size_t lab = tbl + (size_t)T * 4;    // labels widened to one word each
+  static constexpr size_t bytes_coloured = lab + (size_t)T * 4;
 };
 
 // Stage the tile's keys and local labels into shared memory.  Returns len.
@@ -121,17 +122,22 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
   uint16_t* lpi_s = reinterpret_cast<uint16_t*>(smem + S::lpi);
   uint32_t* out_s = reinterpret_cast<uint32_t*>(smem + S::out);
   uint32_t* tbl = reinterpret_cast<uint32_t*>(smem + S::tbl);
+  uint32_t* lab = reinterpret_cast<uint32_t*>(smem + S::lab);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = blockIdx.x;
   const int len = stage_tile<T>(src, lpi, n, tile, in_s, lpi_s, mbar, status);
+  // Row l's labels must sit in bank l: with 16-bit labels two lanes share a word,
+  // and lanes reading different slots of one row pair would collide.
+  for (int q = threadIdx.x; q < T; q += kTPThreads) lab[q] = q < len ? (uint32_t)lpi_s[q] : 0u;
+  __syncthreads();
 
   // Pending slots of this thread; labels outside the tile are dropped (and flagged).
   uint32_t pending = 0;
   for (int c = 0; c < SPW; ++c) {
     const int s = warp * SPW + c, q = s * 32 + lane;
     if (q < len) {
-      if ((int)lpi_s[q] < len) pending |= 1u << c;
+      if ((int)lab[q] < len) pending |= 1u << c;
       else set_status(status, DEV_BAD_PERM);
     }
   }
@@ -147,7 +153,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
     while (__any_sync(0xffffffffu, todo != 0)) {
       const int c = todo ? __ffs(todo) - 1 : 0;
       const int s = warp * SPW + c;
-      const uint32_t p = todo ? (uint32_t)lpi_s[s * 32 + lane] : 0u;
+      const uint32_t p = todo ? lab[s * 32 + lane] : 0u;
       const uint32_t hi = __shfl_sync(0xffffffffu, h_lane, p & 31u);  // h(i), i = p mod 32
       if (todo) {
         todo &= todo - 1;
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
   while (__any_sync(0xffffffffu, pending != 0)) {
     const int c = pending ? __ffs(pending) - 1 : 0;
     const int s = warp * SPW + c;
-    const uint32_t p = pending ? (uint32_t)lpi_s[s * 32 + lane] : 0u;
+    const uint32_t p = pending ? lab[s * 32 + lane] : 0u;
     const uint32_t bank = pending ? (p & 31u) : 32u + (uint32_t)lane;  // idle lanes never collide
     const unsigned peers = __match_any_sync(0xffffffffu, bank);
     if (pending && lane == __ffs(peers) - 1) {
@@ -191,8 +197,8 @@ static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16
   const int64_t tiles = (n + T - 1) / T;
   if (coloured) {
     auto k = k_tile_coloured<T>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    k<<<(unsigned)tiles, kTPThreads, S::bytes, s>>>(src, dst, lpi, n, seed, 3, status_word());
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_coloured);
+    k<<<(unsigned)tiles, kTPThreads, S::bytes_coloured, s>>>(src, dst, lpi, n, seed, 3, status_word());
   } else {
     auto k = k_tile_scatter<T>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);

@@ -189,6 +189,22 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a).view(view)).cuda()
 
 
+def graph_ms(fn, warmup=3, iters=10):
+    """Median CUDA-event time of one replay of a CUDA graph that captures fn()."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(warmup):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return ev_ms(g.replay, warmup, iters)
+
+
 def ev_ms(fn, warmup=3, iters=10):
     """Median CUDA-event time of fn() on the current stream, in ms."""
     import torch
@@ -371,6 +387,7 @@ def run_rows(which, peak):
     import paper_1507_01391_b300 as bcf
     import synth
     rows = {}
+    plain_ns = {}  # ns per key of the plain forms, for the batched / autograd ratios
 
     def add(name, nkeys, bytes_model, ms, note=""):
         gbs = bytes_model / (ms * 1e-3) / 1e9
@@ -422,7 +439,9 @@ def run_rows(which, peak):
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
         ms, _ = ev_ms(lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
-        add(name, n, (4 + 4 * 16) * n, ms, "4 passes of 8 bits + one histogram read")
+        add(name, n, (4 + 4 * 16) * n, ms, "4 passes of 8 bits; per pass: tile counts (4 B/key) + sweep "
+            "(16 B/key); model charges 68 B/key")
+        plain_ns[name] = ms * 1e6 / n
         del k, v, ko, vo, ws
     if want("partition_w256_2pow26"):
         n, w = 1 << 26, 256
@@ -442,7 +461,6 @@ def run_rows(which, peak):
         add("tile_sort_lemma1_2pow24", n, 16 * n, ms,
             "4096-key tiles, Lemma 1 comparison sort (ALU bound); bytes: key r/w + payload gather r/w")
         del k, v, ko, vo
-    plain_ns = {}
     if want("segmented_sort_batched_10k") or want("segmented_partition_batched_10k"):
         sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
         offs_np = synth.offsets_from_sizes(sizes)
@@ -454,10 +472,12 @@ def run_rows(which, peak):
             v = to_dev(synth.index_payload(n))
             ko, vo = torch.empty_like(k), torch.empty_like(v)
             ws = bcf.workspace(bcf.segmented_sort_workspace_size(n, 10_000, 4, 32))
-            ms, _ = ev_ms(lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws), 2, 5)
+            ms_eager, _ = ev_ms(lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws), 2, 5)
+            ms, _ = graph_ms(lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws), 2, 5)
             add("segmented_sort_batched_10k", n, 16 * small + 68 * (n - small), ms,
-                "%d keys; segments <= 4096 keys sorted whole in shared memory (16 B/key), longer ones "
-                "by 4 digit passes + histogram (68 B/key)" % n)
+                "%d keys, one CUDA-graph replay (eager call %.3f ms); segments <= 4096 keys sorted whole in "
+                "shared memory (16 B/key), longer ones by 4 digit passes + counts (68 B/key model)" % (n, ms_eager))
+            plain_ns["segmented_sort_batched_10k"] = ms * 1e6 / n
             del k, v, ko, vo, ws
         if want("segmented_partition_batched_10k"):
             keys, poffs, w = synth.segmented_partition_input(10_000, seed=0x4C)
@@ -468,9 +488,10 @@ def run_rows(which, peak):
             wd = to_dev(w)
             ko, vo = torch.empty_like(k), torch.empty_like(v)
             ws = bcf.workspace(bcf.segmented_partition_workspace_size(n2, 10_000, 4))
-            ms, _ = ev_ms(lambda: bcf.segmented_partition(k, v, po, wd, balanced=True, keys_out=ko,
-                                                          vals_out=vo, ws=ws), 2, 5)
-            add("segmented_partition_batched_10k", n2, 16 * n2, ms, "%d keys, w in {32..256} per segment" % n2)
+            ms, _ = graph_ms(lambda: bcf.segmented_partition(k, v, po, wd, balanced=True, keys_out=ko,
+                                                             vals_out=vo, ws=ws), 2, 5)
+            add("segmented_partition_batched_10k", n2, 16 * n2, ms,
+                "%d keys, w in {32..256} per segment, one CUDA-graph replay" % n2)
             del k, v, ko, vo, ws
     if want("autograd_sort_by_key_64x65536") or want("autograd_permute_rows_64x65536"):
         from paper_1507_01391_b300 import autograd
@@ -483,27 +504,39 @@ def run_rows(which, peak):
                 vals.grad = None
                 _, y = autograd.sort_by_key(keys, vals, 20)
                 y.backward(g)
-            ms, _ = ev_ms(fb, 3, 10)
+            ms_eager, _ = ev_ms(fb, 3, 10)
+            ms, _ = graph_ms(fb, 3, 10)
             # plain form: one key-value sort of the same 2^22 keys (20-bit keys)
             kf = keys.reshape(-1)
             vf = to_dev(synth.index_payload(B * n))
             ko, vo = torch.empty_like(kf), torch.empty_like(vf)
             ws = bcf.workspace(bcf.sort_workspace_size(B * n, 4, 20))
-            ms_plain, _ = ev_ms(lambda: bcf.sort(kf, vf, key_bits=20, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
-            add("autograd_sort_by_key_64x65536", B * n, B * n * (3 * 16 + 4 + 12 + 12), ms,
-                "forward (3 digit passes + gather) and backward scatter; plain kv sort of the same "
-                "keys %.4f ms -> ratio %.2f" % (ms_plain, ms / ms_plain))
+            ms_plain, _ = graph_ms(lambda: bcf.sort(kf, vf, key_bits=20, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+            add("autograd_sort_by_key_64x65536", B * n, B * n * (3 * 16 + 12 + 12), ms,
+                "forward (3 digit passes + gather) and backward scatter, one CUDA-graph replay (eager "
+                "%.3f ms); plain kv sort of the same keys %.4f ms -> ratio %.2f" % (ms_eager, ms_plain, ms / ms_plain))
             rows["autograd_sort_by_key_64x65536"]["plain_sort_ms"] = round(ms_plain, 4)
             rows["autograd_sort_by_key_64x65536"]["ratio_vs_plain"] = round(ms / ms_plain, 3)
+            rows["autograd_sort_by_key_64x65536"]["eager_ms"] = round(ms_eager, 4)
         if want("autograd_permute_rows_64x65536"):
             pi = to_dev(np.concatenate([synth.random_perm(n, seed=100 + b) for b in range(B)])).view(B, n)
 
             def fb2():
                 vals.grad = None
                 autograd.permute_rows(vals, pi).backward(g)
-            ms, _ = ev_ms(fb2, 3, 10)
+            ms_eager, _ = ev_ms(fb2, 3, 10)
+            ms, _ = graph_ms(fb2, 3, 10)
+            # plain form: one permutation of the same 2^22 values
+            vflat = vals.detach().reshape(-1)
+            yo = torch.empty_like(vflat)
+            ms_plain, _ = graph_ms(lambda: bcf.permute(vflat, pi.reshape(-1), dst=yo, row_len=n), 3, 10)
             add("autograd_permute_rows_64x65536", B * n, B * n * 24, ms,
-                "forward scatter (12 B/key) + backward gather (12 B/key)")
+                "forward scatter (12 B/key) + backward gather (12 B/key), one CUDA-graph replay (eager "
+                "%.3f ms); plain permutation %.4f ms" % (ms_eager, ms_plain))
+            rows["autograd_permute_rows_64x65536"]["ratio_vs_plain_fwd"] = round(ms / ms_plain, 3)
+    if "segmented_sort_batched_10k" in plain_ns and "sort_kv_2pow26_uniform" in plain_ns:
+        rows["segmented_sort_batched_10k"]["ratio_vs_plain_per_key"] = round(
+            plain_ns["segmented_sort_batched_10k"] / plain_ns["sort_kv_2pow26_uniform"], 3)
     assert bcf.get_status() == bcf.OK, "device status after the rows"
     torch.cuda.empty_cache()
     return rows

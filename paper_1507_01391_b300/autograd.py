@@ -34,6 +34,20 @@ def _row_offsets(B: int, n: int, device) -> torch.Tensor:
     return t
 
 
+_WS = {}
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    """Workspace reused across calls of the same size on the same stream and
+    device (the library only needs it for the duration of a call)."""
+    key = (int(nbytes), str(device), torch.cuda.current_stream(device).cuda_stream)
+    t = _WS.get(key)
+    if t is None:
+        t = workspace(nbytes, device)
+        _WS[key] = t
+    return t
+
+
 class SortByKey(torch.autograd.Function):
     """(keys [B, n] int32, values [B, n] float) -> (sorted keys, values in key order)."""
 
@@ -45,7 +59,7 @@ class SortByKey(torch.autograd.Function):
         k = keys.contiguous().view(-1)
         v = values.contiguous().view(-1)
         offs = _row_offsets(B, n, keys.device)
-        ws = workspace(segmented_sort_workspace_size(B * n, B, 4, key_bits), keys.device)
+        ws = _workspace(segmented_sort_workspace_size(B * n, B, 4, key_bits), keys.device)
         ko, perm = segmented_sort(k, None, offs, key_bits=key_bits, ws=ws, index_payload=True)
         y = gather(v, perm)  # perm holds global positions
         ctx.save_for_backward(perm)

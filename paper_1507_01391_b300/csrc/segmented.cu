@@ -231,7 +231,7 @@ SegLayout seg_layout(int64_t n_total, int64_t nseg, int vb, int passes, bool sor
   L.zero_begin = off;
   L.ctr = take(16 * 4);
   L.seg_hist = take((size_t)L.slots_cap * passes * 256 * 4);
-  L.lookback = take((size_t)passes * L.lb_stride * 256 * 4);
+  L.lookback = take((size_t)L.lb_stride * 256 * 4);  // tile counts -> running sums (one pass at a time)
   L.zero_bytes = off - L.zero_begin;
   L.total = off;
   return L;
@@ -317,11 +317,32 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
   void* vt = vb ? (void*)(ws + L.vals_tmp) : nullptr;
   const uint32_t* src_k = keys_in;
   const void* src_v = vals_in;
+  uint32_t* offsets = U32(L.lookback);  // per-(digit, tile) counts, scanned in place
   for (int q = 0; q < P; ++q) {
     const bool to_out = ((P - 1 - q) % 2) == 0;
     uint32_t* dk = to_out ? keys_out : kt;
     void* dv = to_out ? vals_out : vt;
+    // reduce-then-scan: tile counts of this pass, running sums over all tiles
+    CountParams cp{};
+    cp.keys = src_k;
+    cp.n = n_total;
+    cp.shift = plan.shift[q];
+    cp.nbits = 8;
+    cp.label_bits = label ? 8 : 0;
+    cp.counts = offsets;
+    cp.stride = L.lb_stride;
+    cp.totals = nullptr;
+    cp.seg_offs = offs;
+    cp.tile_seg = I32(L.tile_seg);
+    cp.seg_tile0 = I32(L.seg_tile0);
+    cp.num_tiles = ctr + C_NTILES;
+    const int64_t count_blocks = (L.tiles_cap + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
+    k_tile_counts<8, kSweepTile><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles_cap);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_scan_offsets<<<256, kScanThreads, 0, s>>>(offsets, L.tiles_cap, L.lb_stride, nullptr, 0, n_total, 1, st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     SweepParams sp{};
+    sp.tile_offsets = offsets;
     sp.keys_in = src_k;
     sp.vals_in = src_v;
     sp.keys_out = dk;
@@ -331,7 +352,7 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
     sp.nbits = plan.nbits[q];
     sp.w = label ? 256 : 0;  // per-segment widths come from seg_w
     sp.balanced = balanced ? 1 : 0;
-    sp.lookback = U32(L.lookback) + (size_t)q * L.lb_stride * 256;
+    sp.lookback = nullptr;
     sp.lb_stride = L.lb_stride;
     sp.ticket = ctr + C_TICKET + q;
     sp.status = st;

@@ -161,7 +161,12 @@ struct CountParams {
   int shift, nbits, label_bits;  // label_bits > 0: digit = key & (2^label_bits - 1)
   uint32_t* counts;              // RADIX x stride
   int64_t stride;
-  uint32_t* totals;              // RADIX, zero on entry
+  uint32_t* totals;              // RADIX, zero on entry (nullptr: not needed)
+  // segment mode (seg_offs != nullptr): tile ranges come from the segment plan
+  const int64_t* seg_offs;
+  const int32_t* tile_seg;
+  const int32_t* seg_tile0;
+  const uint32_t* num_tiles;
 };
 
 #ifndef BCF_COUNT_TILES_PER_BLOCK
@@ -179,13 +184,22 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
   const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
   const int shift = p.label_bits ? 0 : p.shift;
   const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
+  const bool segmented = p.seg_offs != nullptr;
+  if (segmented) tiles = min(tiles, (int64_t)ld_relaxed(p.num_tiles));
   for (int64_t tile = t0; tile < min(t0 + kCountTilesPerBlock, tiles); ++tile) {
-    const int64_t start = tile * T;
-    const int cnt = (int)min((int64_t)T, p.n - start);
+    int64_t start = tile * T, hi = p.n;
+    if (segmented) {
+      const int seg = p.tile_seg[tile];
+      start = p.seg_offs[seg] + (tile - p.seg_tile0[seg]) * (int64_t)T;
+      hi = p.seg_offs[seg + 1];
+    }
+    const int cnt = (int)min((int64_t)T, hi - start);
     for (int i = tid; i < RADIX; i += 256) h[i] = 0;
     __syncthreads();
     const uint32_t* k = p.keys + start;
-    if (cnt == T) {  // full tile: all T/1024 vector loads in flight before counting
+    if (segmented) {  // segment starts need not be 16-byte aligned: scalar loads
+      for (int i = tid; i < cnt; i += 256) atomicAdd(&h[(__ldcs(k + i) >> shift) & mask], 1u);
+    } else if (cnt == T) {  // full tile: all T/1024 vector loads in flight before counting
       constexpr int NV = T / 1024;
       uint4 x[NV];
 #pragma unroll
@@ -216,8 +230,9 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     }
     __syncthreads();
   }
-  for (int d = tid; d < RADIX; d += 256)
-    if (tot[d]) atomicAdd(&p.totals[d], tot[d]);
+  if (p.totals)
+    for (int d = tid; d < RADIX; d += 256)
+      if (tot[d]) atomicAdd(&p.totals[d], tot[d]);
 }
 
 // One block per digit: exclusive scan of the digit's tile counts, offset by the
@@ -235,7 +250,9 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
   const int d = blockIdx.x;
   if (threadIdx.x == 0) {
     uint32_t b = 0;
-    if (balanced) {
+    if (!totals) {
+      // segment mode: plain running sums (each segment subtracts its first tile's)
+    } else if (balanced) {
       b = (uint32_t)min((int64_t)d * (n / w), n);
       const uint32_t expect = d < w ? (uint32_t)(n / w) : 0u;
       if (totals[d] != expect) set_status(status, DEV_NOT_BALANCED);
@@ -450,7 +467,24 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   // kLookbackWindow words covers that many tiles.
   uint32_t* lbd = p.lookback + (size_t)tid * p.lb_stride;
   if (tid < RADIX && p.tile_offsets) {
-    gofs[tid] = p.tile_offsets[(size_t)tid * p.lb_stride + tile] - tstart[tid];
+    const uint32_t* row = p.tile_offsets + (size_t)tid * p.lb_stride;
+    uint32_t base = row[tile];
+    if (segmented) {  // running sums cover all tiles: rebase at the segment's first tile
+      const int first = tile - t_in;
+      const uint32_t before = base - row[first];  // this digit in earlier tiles of the segment
+      const uint32_t mine = (tid + 1 < RADIX ? tstart[tid + 1] : (uint32_t)cnt) - tstart[tid];
+      if (p.balanced) {
+        const int64_t len = hi - lo;
+        base = (uint32_t)min(lo + (int64_t)tid * (len / max(w, 1)), hi) + before;
+        if (last_tile) {
+          const uint32_t expect = tid < w ? (uint32_t)(len / max(w, 1)) : 0u;
+          if (before + mine != expect) set_status(p.status, DEV_NOT_BALANCED);
+        }
+      } else {
+        base = p.seg_base[(size_t)p.seg_slot[seg] * RADIX + tid] + before;
+      }
+    }
+    gofs[tid] = base - tstart[tid];
   } else if (tid < RADIX) {
     uint32_t excl = 0;
     const uint32_t count = ld_relaxed(lbd + tile) & LB_MASK;  // own aggregate, published above

@@ -36,8 +36,8 @@ def _deps_mtime(src: str) -> float:
     return max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in hdrs])
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra: list[str], out_dir: str = BUILD) -> str:
+    obj = os.path.join(out_dir, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime(src):
         return obj
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
@@ -48,21 +48,35 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile every CUDA source and link libbcf.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    extra = list(extra or [])
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if (not os.path.exists(LIB)) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"]
+TRACE_LIB = os.path.join(PKG, "libbcf_trace.so")
+
+
+def _link(objs: list[str], lib: str) -> None:
+    if (not os.path.exists(lib)) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        cmd = [nvcc(), *ARCH, "-shared", "-o", lib + ".tmp", *objs, "-lcudart"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (" ".join(cmd), res.stderr))
-        os.replace(LIB + ".tmp", LIB)
+        os.replace(lib + ".tmp", lib)
+
+
+def build(verbose: bool = False, extra: list[str] | None = None, trace: bool = True) -> str:
+    """Compile every CUDA source and link libbcf.so (and the trace build
+    libbcf_trace.so, the same sources with -DBCF_TRACE); returns libbcf.so's path."""
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    extra = list(extra or [])
+    jobs = [(s, extra, BUILD) for s in srcs if not s.endswith("trace_abi.cu")]
+    if trace:
+        os.makedirs(os.path.join(BUILD, "trace"), exist_ok=True)
+        jobs += [(s, extra + ["-DBCF_TRACE"], os.path.join(BUILD, "trace")) for s in srcs]
+    with cf.ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+        objs = list(ex.map(lambda j: _compile(*j), jobs))
+    _link([o for o in objs if os.path.dirname(o) == BUILD], LIB)
+    if trace:
+        _link([o for o in objs if os.path.dirname(o) != BUILD], TRACE_LIB)
     if verbose:
-        print("built", LIB)
+        print("built", LIB, "and", TRACE_LIB if trace else "")
     return LIB
 
 

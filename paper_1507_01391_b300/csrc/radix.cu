@@ -146,4 +146,6 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
   return pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, 8, w, balanced, totals, offsets, L, s);
 }
 
+BCF_TRACE_INSTALLER(radix)
+
 }  // namespace bcf

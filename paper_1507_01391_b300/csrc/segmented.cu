@@ -415,4 +415,6 @@ cudaError_t sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* k
   return cudaGetLastError();
 }
 
+BCF_TRACE_INSTALLER(segmented)
+
 }  // namespace bcf

@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "trace.cuh"
 
 namespace bcf {
 
@@ -387,7 +388,9 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
     for (int j = 0; j < IPT; ++j) {
       const int idx = wbase + j * 32 + lane;
       const bool valid = in_tile(idx);
+      if (valid) BCF_TR(&keys_s[ksh + idx], 4, 0, TS_STAGE_READ);
       key[j] = valid ? keys_s[ksh + idx] : 0u;
+      if (VB && valid && !iota) BCF_TR(&vals_s[vsh + idx], VB, 0, TS_STAGE_READ);
       if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
       if (label_mode && valid && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
     }
@@ -397,7 +400,10 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
     uint32_t* wh = whist + warp * RADIX;
 #pragma unroll
     for (int j = 0; j < IPT; ++j)
-      if (in_tile(wbase + j * 32 + lane)) atomicAdd(&wh[(key[j] >> shift) & DMASK], 1u);
+      if (in_tile(wbase + j * 32 + lane)) {
+        BCF_TR(&wh[(key[j] >> shift) & DMASK], 4, 2, TS_COUNT_ATOM);
+        atomicAdd(&wh[(key[j] >> shift) & DMASK], 1u);
+      }
     __syncthreads();
 
     // Phase B -- per digit: tile count, tile-exclusive start, and each warp's base
@@ -444,14 +450,20 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
 #endif
       const int leader = valid ? __ffs(peers) - 1 : lane;
       uint32_t old = 0;
-      if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+      if (valid && lane == leader) {
+        BCF_TR(&wh[d], 4, 2, TS_CLAIM_ATOM);
+        old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+      }
       old = __shfl_sync(0xffffffffu, old, leader);
       if (valid) {
         const uint32_t pos = old + __popc(peers & lt);
         if constexpr (VB == 4) {
+          BCF_TR(&kv_s[pos], 8, 1, TS_SCATTER);
           kv_s[pos] = ((unsigned long long)val[j] << 32) | key[j];
         } else {
+          BCF_TR(&keys_s[pos], 4, 1, TS_SCATTER);
           keys_s[pos] = key[j];
+          if (VB) BCF_TR(&vals_s[pos], VB, 1, TS_SCATTER);
           if (VB) vals_s[pos] = val[j];
         }
       }
@@ -555,13 +567,17 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
     uint32_t k;
     VT v = VT(0);
     if constexpr (VB == 4) {
+      BCF_TR(&kv_s[i], 8, 0, TS_WRITEOUT_READ);
       const unsigned long long x = kv_s[i];
       k = (uint32_t)x;
       v = (uint32_t)(x >> 32);
     } else {
+      BCF_TR(&keys_s[i], 4, 0, TS_WRITEOUT_READ);
       k = keys_s[i];
+      if (VB) BCF_TR(&vals_s[i], VB, 0, TS_WRITEOUT_READ);
       if (VB) v = vals_s[i];
     }
+    BCF_TR(&gofs[(k >> shift) & DMASK], 4, 0, TS_OFFSET_READ);
     const uint32_t dst = gofs[(k >> shift) & DMASK] + (uint32_t)i;
     if (dst - lo32 < len32) {
       p.keys_out[dst] = k;

@@ -19,6 +19,7 @@
 //                are sent greedily, one item per destination bank per request.
 #include "common.cuh"
 #include "internal.h"
+#include "trace.cuh"
 
 namespace bcf {
 
@@ -75,7 +76,10 @@ __device__ __forceinline__ void write_tile(uint32_t* dst, int64_t start, int len
   if (len == T) {
     const uint4* o4 = reinterpret_cast<const uint4*>(out_s);
     uint4* d4 = reinterpret_cast<uint4*>(dst + start);
-    for (int i = threadIdx.x; i < T / 4; i += blockDim.x) __stcs(d4 + i, o4[i]);
+    for (int i = threadIdx.x; i < T / 4; i += blockDim.x) {
+      BCF_TR(&o4[i], 16, 0, TS_WRITEOUT_READ);
+      __stcs(d4 + i, o4[i]);
+    }
   } else {
     for (int i = threadIdx.x; i < len; i += blockDim.x) dst[start + i] = out_s[i];
   }
@@ -94,9 +98,15 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_scatter(const uint32_t* __r
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
   const int len = stage_tile<T>(src, lpi, n, blockIdx.x, in_s, lpi_s, mbar, status);
   for (int q = threadIdx.x; q < len; q += kTPThreads) {
+    BCF_TR_WORD(&lpi_s[q], 0, TS_STAGE_READ);
     const uint32_t p = lpi_s[q];
-    if ((int)p < len) out_s[p] = in_s[q];
-    else set_status(status, DEV_BAD_PERM);
+    BCF_TR(&in_s[q], 4, 0, TS_STAGE_READ);
+    if ((int)p < len) {
+      BCF_TR(&out_s[p], 4, 1, TS_SCATTER);
+      out_s[p] = in_s[q];
+    } else {
+      set_status(status, DEV_BAD_PERM);
+    }
   }
   __syncthreads();
   write_tile<T>(dst, (int64_t)blockIdx.x * T, len, out_s);
@@ -129,7 +139,11 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
   const int len = stage_tile<T>(src, lpi, n, tile, in_s, lpi_s, mbar, status);
   // Row l's labels must sit in bank l: with 16-bit labels two lanes share a word,
   // and lanes reading different slots of one row pair would collide.
-  for (int q = threadIdx.x; q < T; q += kTPThreads) lab[q] = q < len ? (uint32_t)lpi_s[q] : 0u;
+  for (int q = threadIdx.x; q < T; q += kTPThreads) {
+    if (q < len) BCF_TR_WORD(&lpi_s[q], 0, TS_COL_READ);
+    BCF_TR(&lab[q], 4, 1, TS_COL_READ);
+    lab[q] = q < len ? (uint32_t)lpi_s[q] : 0u;
+  }
   __syncthreads();
 
   // Pending slots of this thread; labels outside the tile are dropped (and flagged).
@@ -137,6 +151,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
   for (int c = 0; c < SPW; ++c) {
     const int s = warp * SPW + c, q = s * 32 + lane;
     if (q < len) {
+      BCF_TR(&lab[q], 4, 0, TS_COL_READ);
       if ((int)lab[q] < len) pending |= 1u << c;
       else set_status(status, DEV_BAD_PERM);
     }
@@ -145,7 +160,10 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
   for (int r = 0; r < rounds; ++r) {
     // Coloring: h(i) for destination bank i, drawn fresh every round (held by lane i).
     const uint32_t h_lane = mix32(seed ^ ((uint64_t)tile << 20) ^ ((uint64_t)r << 8) ^ (uint64_t)lane) & (M - 1);
-    for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) tbl[k * 32 + lane] = EMPTY;
+    for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) {
+      BCF_TR(&tbl[k * 32 + lane], 4, 1, TS_COL_TABLE);
+      tbl[k * 32 + lane] = EMPTY;
+    }
     __syncthreads();
     // Claim the first free entry of each colour in this row; an item whose colour
     // is already taken stays pending for the next round.
@@ -153,11 +171,13 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
     while (__any_sync(0xffffffffu, todo != 0)) {
       const int c = todo ? __ffs(todo) - 1 : 0;
       const int s = warp * SPW + c;
+      if (todo) BCF_TR(&lab[s * 32 + lane], 4, 0, TS_COL_READ);
       const uint32_t p = todo ? lab[s * 32 + lane] : 0u;
       const uint32_t hi = __shfl_sync(0xffffffffu, h_lane, p & 31u);  // h(i), i = p mod 32
       if (todo) {
         todo &= todo - 1;
         const uint32_t k = ((p >> 5) - hi) & (M - 1);
+        BCF_TR(&tbl[k * 32 + lane], 4, 2, TS_COL_TABLE);
         if (atomicCAS(&tbl[k * 32 + lane], EMPTY, (p << 8) | (uint32_t)s) == EMPTY)
           pending &= ~(1u << c);
       }
@@ -167,8 +187,13 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
     // destination banks of one step are distinct.
 #pragma unroll 4
     for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) {
+      BCF_TR(&tbl[k * 32 + lane], 4, 0, TS_COL_TABLE);
       const uint32_t e = tbl[k * 32 + lane];
-      if (e != EMPTY) out_s[e >> 8] = in_s[(e & 0xFFu) * 32 + lane];
+      if (e != EMPTY) {
+        BCF_TR(&in_s[(e & 0xFFu) * 32 + lane], 4, 0, TS_COL_READ);
+        BCF_TR(&out_s[e >> 8], 4, 1, TS_COL_SEND);
+        out_s[e >> 8] = in_s[(e & 0xFFu) * 32 + lane];
+      }
     }
     __syncthreads();
   }
@@ -178,10 +203,13 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
   while (__any_sync(0xffffffffu, pending != 0)) {
     const int c = pending ? __ffs(pending) - 1 : 0;
     const int s = warp * SPW + c;
+    if (pending) BCF_TR(&lab[s * 32 + lane], 4, 0, TS_COL_READ);
     const uint32_t p = pending ? lab[s * 32 + lane] : 0u;
     const uint32_t bank = pending ? (p & 31u) : 32u + (uint32_t)lane;  // idle lanes never collide
     const unsigned peers = __match_any_sync(0xffffffffu, bank);
     if (pending && lane == __ffs(peers) - 1) {
+      BCF_TR(&in_s[s * 32 + lane], 4, 0, TS_COL_READ);
+      BCF_TR(&out_s[p], 4, 1, TS_COL_FINISH);
       out_s[p] = in_s[s * 32 + lane];
       pending &= ~(1u << c);
     }
@@ -217,5 +245,7 @@ cudaError_t permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lp
   }
   return cudaErrorInvalidValue;
 }
+
+BCF_TRACE_INSTALLER(tile_permute)
 
 }  // namespace bcf

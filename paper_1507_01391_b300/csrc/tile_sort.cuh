@@ -21,6 +21,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "trace.cuh"
 
 namespace bcf {
 
@@ -65,10 +66,16 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
   const bool up = !(alt && (r & 1));
   unsigned long long v[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = S[(t * 16 + i) * kL1Rows + r];
+  for (int i = 0; i < 16; ++i) {
+    BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 0, TS_L1_ROW_LD);
+    v[i] = S[(t * 16 + i) * kL1Rows + r];
+  }
   sort16(v, up);
 #pragma unroll
-  for (int i = 0; i < 16; ++i) S[(t * 16 + i) * kL1Rows + r] = v[i];
+  for (int i = 0; i < 16; ++i) {
+    BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 1, TS_L1_ROW_ST);
+    S[(t * 16 + i) * kL1Rows + r] = v[i];
+  }
   __syncthreads();
   unsigned long long* src = S;
   unsigned long long* dst = D;
@@ -84,6 +91,8 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
     int lo = d > L ? d - L : 0, hi = d < L ? d : L;
     while (lo < hi) {  // smallest i whose A[i] comes after B[d-1-i]
       const int mid = (lo + hi) >> 1;
+      BCF_TR(&A[mid * kL1Rows], 8, 0, TS_L1_ROW_LD);
+      BCF_TR(&B[(d - 1 - mid) * kL1Rows], 8, 0, TS_L1_ROW_LD);
       const unsigned long long a = A[mid * kL1Rows], b = B[(d - 1 - mid) * kL1Rows];
       const bool a_first = up ? (a < b) : (a > b);
       if (a_first) lo = mid + 1;
@@ -93,9 +102,12 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
     unsigned long long* out = dst + (size_t)(base + d) * kL1Rows + r;
 #pragma unroll 4
     for (int s = 0; s < 16; ++s) {
+      if (i < L) BCF_TR(&A[i * kL1Rows], 8, 0, TS_L1_ROW_LD);
+      if (j < L) BCF_TR(&B[j * kL1Rows], 8, 0, TS_L1_ROW_LD);
       const unsigned long long a = i < L ? A[i * kL1Rows] : 0ull;
       const unsigned long long b = j < L ? B[j * kL1Rows] : 0ull;
       const bool take_a = (j >= L) || (i < L && (up ? (a < b) : (a > b)));
+      BCF_TR(&out[s * kL1Rows], 8, 1, TS_L1_ROW_ST);
       out[s * kL1Rows] = take_a ? a : b;
       i += take_a;
       j += !take_a;
@@ -118,6 +130,8 @@ __device__ __forceinline__ void l1_row_to_col(const unsigned long long* M, unsig
 #pragma unroll 4
   for (int j = 0; j < 16; ++j) {
     const int c = R * 16 + j;
+    BCF_TR(&M[(j * 16 + p) * kL1Rows + R], 8, 0, TS_L1_CONVERT);
+    BCF_TR(&N[c * kL1Rows + p], 8, 1, TS_L1_CONVERT);
     N[c * kL1Rows + p] = M[(j * 16 + p) * kL1Rows + R];
   }
   __syncthreads();
@@ -131,6 +145,8 @@ __device__ __forceinline__ void l1_col_to_row(const unsigned long long* N, unsig
 #pragma unroll 4
   for (int j = 0; j < 16; ++j) {
     const int C = j * 16 + r;
+    BCF_TR(&N[(p * 16 + j) * kL1Rows + r], 8, 0, TS_L1_CONVERT);
+    BCF_TR(&M[C * kL1Rows + p], 8, 1, TS_L1_CONVERT);
     M[C * kL1Rows + p] = N[(p * 16 + j) * kL1Rows + r];
   }
   __syncthreads();
@@ -148,6 +164,7 @@ __device__ __forceinline__ void lemma1_tile(const uint32_t* __restrict__ keys_in
   // item (r, c) of the initial matrix = tile position q = c*16 + r
   for (int q = threadIdx.x; q < kL1Tile; q += kL1Threads) {
     const unsigned long long key = q < len ? (unsigned long long)keys_in[start + q] : 0xFFFFFFFFull;
+    BCF_TR(&X[q], 8, 1, TS_L1_IO);
     X[q] = (key << 32) | (unsigned)q;  // padding sorts last (position >= len)
   }
   __syncthreads();
@@ -163,6 +180,7 @@ __device__ __forceinline__ void lemma1_tile(const uint32_t* __restrict__ keys_in
   const VT* vin = reinterpret_cast<const VT*>(vals_in);
   VT* vout = reinterpret_cast<VT*>(vals_out);
   for (int t = threadIdx.x; t < len; t += kL1Threads) {
+    BCF_TR(&Y[t], 8, 0, TS_L1_IO);
     const unsigned long long it = Y[t];
     keys_out[start + t] = (uint32_t)(it >> 32);
     if (VB) vout[start + t] = vin ? vin[start + (uint32_t)it] : VT(start + (uint32_t)it);

@@ -1,0 +1,76 @@
+// trace.cuh -- optional shared-memory access tracing (builds with -DBCF_TRACE).
+//
+// In a trace build every instrumented shared-memory access appends one record per
+// active lane to a caller-provided device buffer: (request id, lane, shared-window
+// byte address, width | store << 8 | site << 16).  All lanes of one warp-wide
+// access share the request id, so the trace can be replayed through the bank model
+// of Sec. 1 (32 banks of 4-byte words; a request conflicts when two of its lanes
+// need different words of one bank).  Without BCF_TRACE the macro is empty and the
+// kernels are unchanged.
+#pragma once
+
+#include "common.cuh"
+
+namespace bcf {
+
+// Access sites (the `site` field of a record).
+enum TraceSite : uint32_t {
+  TS_STAGE_READ = 1,    // strided read of a staged tile into registers
+  TS_COUNT_ATOM = 2,    // per-warp digit count
+  TS_CLAIM_ATOM = 3,    // leader claims a digit run
+  TS_SCATTER = 4,       // store into digit / label order
+  TS_WRITEOUT_READ = 5, // read of the ordered tile for the global write-out
+  TS_OFFSET_READ = 6,   // per-digit offset lookup
+  TS_L1_ROW_LD = 10,    // Lemma 1: row sort loads (register sort and merges)
+  TS_L1_ROW_ST = 11,    // Lemma 1: row sort stores
+  TS_L1_CONVERT = 12,   // Lemma 1: row <-> column conversions
+  TS_L1_IO = 13,        // Lemma 1: building the items / final read
+  TS_COL_TABLE = 20,    // colouring: table reset / claims
+  TS_COL_SEND = 21,     // colouring: conflict-free sends
+  TS_COL_READ = 22,     // colouring: reading own row (labels, items)
+  TS_COL_FINISH = 23,   // colouring: greedy finishing sends
+};
+
+#ifdef BCF_TRACE
+struct TraceState {
+  unsigned long long* count;  // records written so far (may exceed cap)
+  uint32_t* rec;              // 4 words per record
+  unsigned long long cap;     // records that fit
+};
+// One copy per translation unit (no relocatable device code); each unit that
+// includes this header installs its copy through BCF_TRACE_INSTALLER.
+static __device__ TraceState g_bcf_trace;
+#define BCF_TRACE_INSTALLER(name)                                        \
+  cudaError_t trace_install_##name(const ::bcf::TraceState& t) {         \
+    return cudaMemcpyToSymbol(::bcf::g_bcf_trace, &t, sizeof(t));       \
+  }
+
+__device__ __forceinline__ void trace_access(const void* p, uint32_t width, uint32_t store,
+                                             uint32_t site) {
+  const TraceState t = g_bcf_trace;
+  if (!t.count) return;
+  const unsigned mask = __activemask();
+  const int lane = (int)(threadIdx.x & 31u);
+  const int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(t.count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  const unsigned long long r = base + (unsigned long long)__popc(mask & lanemask_lt());
+  if (r < t.cap) {
+    uint32_t* o = t.rec + 4 * r;
+    o[0] = (uint32_t)base;
+    o[1] = (uint32_t)lane;
+    o[2] = smem_u32(p);
+    o[3] = width | (store << 8) | (site << 16);
+  }
+}
+#define BCF_TR(ptr, width, store, site) ::bcf::trace_access((ptr), (width), (store), (site))
+#else
+#define BCF_TR(ptr, width, store, site) ((void)0)
+#define BCF_TRACE_INSTALLER(name)
+#endif
+// Sub-word accesses are traced as the 4-byte word that holds them.
+#define BCF_TR_WORD(ptr, store, site) \
+  BCF_TR(reinterpret_cast<const void*>(reinterpret_cast<uintptr_t>(ptr) & ~(uintptr_t)3), 4, (store), (site))
+
+}  // namespace bcf

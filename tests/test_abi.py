@@ -90,3 +90,18 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     mod._lib = None
     with pytest.raises(ImportError):
         mod.lib()
+
+
+def test_trace_build_exports_both_headers():
+    """libbcf_trace.so (the same kernels compiled with -DBCF_TRACE) exports the
+    library functions and the trace functions; libbcf.so has no trace code."""
+    import re
+    hdr = os.path.join(os.path.dirname(bcf.HEADER), "bcf_trace.h")
+    text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
+    trace_names = set(re.findall(r"\b(bcf_[a-z0-9_]+)\s*\(", text))
+    assert trace_names == {"bcf_trace_begin", "bcf_trace_end"}
+    nm = lambda p: {l.split()[-1] for l in subprocess.run(["nm", "-D", "--defined-only", p], capture_output=True,
+                                                          text=True).stdout.splitlines() if " T " in l}
+    tlib = os.path.join(os.path.dirname(bcf._LIB_PATH), "libbcf_trace.so")
+    assert set(bcf.header_functions()) | trace_names <= nm(tlib)
+    assert not (trace_names & nm(bcf._LIB_PATH))

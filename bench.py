@@ -380,6 +380,24 @@ def headline_config():
             "tile_schedule": "scatter"}
 
 
+# ------------------------------------------------------------------ tuning
+def run_tuning():
+    """Pick the sweep tile configuration for the sizes the rows use (the
+    library's autotuner, timed on this device)."""
+    from paper_1507_01391_b300 import tune
+    res = tune.autotune(ops=("sort",), log2_sizes=[22, 26], reps=3)
+    res.update({"partition": {}})
+    res["partition"].update(tune.autotune(ops=("partition",), log2_sizes=[26], w=256, reps=3)["partition"])
+    res["partition"].update(tune.autotune(ops=("partition",), log2_sizes=[16], w=32, reps=5)["partition"])
+    out = {}
+    for op, tab in res.items():
+        out[op] = {"2^%d" % k: {"config": best, "threads_x_keys": "%dx%d" % tune.configs()[best],
+                               "ms": {str(c): round(t, 4) for c, t in times.items()}}
+                   for k, (best, times) in tab.items()}
+        log("tuned", op, {k: v["threads_x_keys"] for k, v in out[op].items()})
+    return out
+
+
 # ------------------------------------------------------------------ rows
 def run_rows(which, peak):
     import torch
@@ -637,6 +655,7 @@ def main():
         line["cpu_baseline"] = cpu_baseline()
         if not args.no_rows:
             which = set(filter(None, args.rows_only.split(",")))
+            line["tuning"] = run_tuning()
             line["rows"] = run_rows(which, peak)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -185,6 +185,26 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
                             bcf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Tuning of the sort and partition sweeps (no counterpart in the paper).  Each
+ * digit pass can run with one of bcf_tune_num_configs() tile configurations
+ * (threads per block x keys per thread).  The library keeps a small host-side
+ * table, per operation and per ceil(log2 n), of the configuration to use; an
+ * entry of -1 (the initial state) applies a size rule (tiles of 1024 keys up to
+ * n = 2^20, 4096 above).  The table is process-wide host state and is not
+ * synchronised: set it before concurrent calls.  Workspace sizes already cover
+ * every configuration.  paper_1507_01391_b300.tune measures the configurations
+ * on the device and fills the table (with a JSON cache per device). */
+#define BCF_OP_SORT 0
+#define BCF_OP_PARTITION 1
+int bcf_tune_num_configs(void);
+/* BCF_E_INVAL for an unknown configuration or a null output. */
+int bcf_tune_config_info(int config, int* threads, int* keys_per_thread);
+/* config in [-1, num_configs); log2_n in [0, 63].  BCF_E_INVAL otherwise. */
+int bcf_tune_set(int op, int log2_n, int config);
+/* The configuration a call of n keys would use now. */
+int bcf_tune_get(int op, int64_t n, int* config);
+
+/* ---------------------------------------------------------------------------
  * Partition without a workspace.  The paper has no counterpart: this is a
  * calling convention for users who cannot allocate device memory when they call
  * the library -- code running inside CUDA stream capture (cudaMalloc is not

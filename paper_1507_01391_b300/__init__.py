@@ -59,7 +59,12 @@ _SIGS = {
     "bcf_segmented_partition_workspace_size": ([_I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_segmented_partition": ([_P, _P, _P, _P, _I64, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_partition_noalloc": ([_P, _P, _P, _P, _I64, _I, _I, _I, _P], _I),
+    "bcf_tune_num_configs": ([], _I),
+    "bcf_tune_config_info": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "bcf_tune_set": ([_I, _I, _I], _I),
+    "bcf_tune_get": ([_I, _I64, ctypes.POINTER(_I)], _I),
 }
+OP_SORT, OP_PARTITION = 0, 1
 NOALLOC_MAX_N = 1 << 22
 
 

@@ -130,7 +130,8 @@ int bcf_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out, v
     return BCF_E_INVAL;
   if (!device_ready()) return BCF_E_CUDA;
   return cuda_rc(bcf::radix_sort(keys_in, vals_in, keys_out, vals_out, n, val_bytes, pl,
-                                 static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
+                                 static_cast<unsigned char*>(ws), L, (cudaStream_t)stream,
+                                 bcf::tuned_config(BCF_OP_SORT, n)));
 }
 
 // ------------------------------------------------------------- partition
@@ -162,7 +163,8 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
   if (ws_bytes < L.total) return BCF_E_WORKSPACE;
   if (!device_ready()) return BCF_E_CUDA;
   return cuda_rc(bcf::partition(keys_in, vals_in, keys_out, vals_out, n, w, val_bytes, balanced,
-                                static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
+                                static_cast<unsigned char*>(ws), L, (cudaStream_t)stream,
+                                bcf::tuned_config(BCF_OP_PARTITION, n)));
 }
 
 // ------------------------------------------------------------ permutations
@@ -313,6 +315,26 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in, uint32
   return cuda_rc(bcf::segmented_partition(keys_in, vals_in, keys_out, vals_out, n_total, offs, w_per_seg,
                                           nseg, val_bytes, (flags & BCF_ASSUME_BALANCED) != 0,
                                           static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
+}
+
+// ------------------------------------------------------------------ tuning
+int bcf_tune_num_configs(void) { return bcf::kNumSweepConfigs; }
+
+int bcf_tune_config_info(int config, int* threads, int* keys_per_thread) {
+  if (config < 0 || config >= bcf::kNumSweepConfigs || !threads || !keys_per_thread) return BCF_E_INVAL;
+  *threads = bcf::kSweepCfgThreads[config];
+  *keys_per_thread = bcf::kSweepCfgIPT[config];
+  return BCF_OK;
+}
+
+int bcf_tune_set(int op, int log2_n, int config) {
+  return bcf::tune_set(op, log2_n, config) == 0 ? BCF_OK : BCF_E_INVAL;
+}
+
+int bcf_tune_get(int op, int64_t n, int* config) {
+  if ((op != BCF_OP_SORT && op != BCF_OP_PARTITION) || n < 0 || !config) return BCF_E_INVAL;
+  *config = bcf::tuned_config(op, n);
+  return BCF_OK;
 }
 
 }  // extern "C"

@@ -35,8 +35,21 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 #endif
 constexpr int kSweepThreads = BCF_SWEEP_THREADS;
 constexpr int kSweepIPT = BCF_SWEEP_IPT;
-constexpr int kSweepTile = kSweepThreads * kSweepIPT;  // keys per tile
+constexpr int kSweepTile = kSweepThreads * kSweepIPT;  // keys per tile (default configuration)
 constexpr int kLookbackWindow = BCF_LB_WINDOW;
+
+// Tile configurations of the sort / partition sweeps that the tuner picks from
+// (threads per block x keys per thread).  Configuration 0 is the default above.
+constexpr int kNumSweepConfigs = 4;
+constexpr int kSweepCfgThreads[kNumSweepConfigs] = {kSweepThreads, 256, 512, 256};
+constexpr int kSweepCfgIPT[kNumSweepConfigs] = {kSweepIPT, 4, 16, 8};
+constexpr int kMinSweepTile = 1024;  // smallest tile of any configuration (sizes workspaces)
+inline int sweep_cfg_tile(int cfg) { return kSweepCfgThreads[cfg] * kSweepCfgIPT[cfg]; }
+
+// Tuning table (host state): configuration used by a sort (op 0) or partition
+// (op 1) of n keys.  Entries of -1 fall back to a size rule.
+int tuned_config(int op, int64_t n);
+int tune_set(int op, int log2_n, int cfg);
 
 struct PassPlan {
   int passes = 0;
@@ -55,17 +68,21 @@ struct SweepLayout {
   int64_t lb_stride = 0;  // look-back status words per digit (tiles rounded up to 8)
   int radix = 256;
 };
-SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp);
+// Workspace carve-up; the per-(digit, tile) count buffer is sized for tiles of
+// `tile` keys (kMinSweepTile fits every configuration).
+SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp,
+                         int tile = kMinSweepTile);
 
 // Radix sort launch sequence (see bcf_sort in include/bcf.h).
+// `cfg` is a sweep configuration whose tiles fit the layout's count buffer.
 cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n, int val_bytes, const PassPlan& plan,
-                       unsigned char* ws, const SweepLayout& L, cudaStream_t s);
+                       unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg = 0);
 
 // Single-pass stable partition by label (see bcf_partition).
 cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                       void* vals_out, int64_t n, int w, int val_bytes, bool balanced,
-                      unsigned char* ws, const SweepLayout& L, cudaStream_t s);
+                      unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg = 0);
 
 // ---------------------------------------------------------------- permutations
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,

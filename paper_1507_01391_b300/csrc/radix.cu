@@ -21,10 +21,44 @@ PassPlan plan_passes(int key_bits) {
   return pl;
 }
 
-SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp) {
+// ------------------------------------------------------------- tuning table
+namespace {
+int8_t g_tune[2][64];  // [op][log2 n]: configuration, -1 = size rule
+bool g_tune_init = false;
+
+void tune_init() {
+  if (g_tune_init) return;
+  for (int op = 0; op < 2; ++op)
+    for (int b = 0; b < 64; ++b) g_tune[op][b] = -1;
+  g_tune_init = true;
+}
+
+int ilog2_ceil(int64_t n) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+}  // namespace
+
+int tuned_config(int op, int64_t n) {
+  tune_init();
+  const int b = ilog2_ceil(n);
+  const int cfg = (op == 0 || op == 1) ? g_tune[op][b] : -1;
+  if (cfg >= 0 && cfg < kNumSweepConfigs) return cfg;
+  return n <= ((int64_t)1 << 20) ? 1 : 0;  // small inputs: more, smaller tiles
+}
+
+int tune_set(int op, int log2_n, int cfg) {
+  tune_init();
+  if ((op != 0 && op != 1) || log2_n < 0 || log2_n >= 64 || cfg < -1 || cfg >= kNumSweepConfigs) return -1;
+  g_tune[op][log2_n] = (int8_t)cfg;
+  return 0;
+}
+
+SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp, int tile) {
   SweepLayout L;
   L.radix = radix;
-  L.tiles = (n + kSweepTile - 1) / kSweepTile;
+  L.tiles = (n + tile - 1) / tile;
   L.lb_stride = (L.tiles + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
   size_t off = 0;
   if (need_tmp) {
@@ -43,12 +77,17 @@ SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool n
   return L;
 }
 
-// One digit pass, reduce-then-scan: tile counts -> run starts -> sweep.
-template <int BITS>
-static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
-                        int64_t n, int vb, int shift, int nbits, int w, bool balanced,
-                        uint32_t* totals, uint32_t* offsets, const SweepLayout& L, cudaStream_t s) {
+// One digit pass, reduce-then-scan: tile counts -> run starts -> sweep, with
+// tiles of THREADS x IPT keys.
+template <int BITS, int THREADS, int IPT>
+static cudaError_t pass_t(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                          int64_t n, int vb, int shift, int nbits, int w, bool balanced,
+                          uint32_t* totals, uint32_t* offsets, cudaStream_t s) {
   constexpr int RADIX = 1 << BITS;
+  constexpr int T = THREADS * IPT;
+  SweepLayout L;  // this configuration's tile count and status stride
+  L.tiles = (n + T - 1) / T;
+  L.lb_stride = (L.tiles + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
   CountParams cp{};
   cp.keys = src_k;
   cp.n = n;
@@ -59,7 +98,7 @@ static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_
   cp.stride = L.lb_stride;
   cp.totals = totals;
   const int64_t count_blocks = (L.tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
-  k_tile_counts<BITS, kSweepTile><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles);
+  k_tile_counts<BITS, T><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_scan_offsets<<<RADIX, kScanThreads, 0, s>>>(offsets, L.tiles, L.lb_stride, totals, balanced ? 1 : 0, n,
@@ -78,12 +117,30 @@ static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_
   sp.lb_stride = L.lb_stride;
   sp.tile_offsets = offsets;
   sp.status = status_word();
-  return sweep_dispatch<BITS>(sp, L.tiles, vb, s);
+  return sweep_dispatch<BITS, THREADS, IPT>(sp, L.tiles, vb, s);
+}
+
+template <int BITS>
+static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                        int64_t n, int vb, int shift, int nbits, int w, bool balanced,
+                        uint32_t* totals, uint32_t* offsets, cudaStream_t s, int cfg) {
+  switch (cfg) {
+#define BCF_PASS(C)                                                                                  \
+  case C:                                                                                            \
+    return pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C]>(src_k, src_v, dst_k, dst_v, n, vb, shift, \
+                                                              nbits, w, balanced, totals, offsets, s);
+    BCF_PASS(0)
+    BCF_PASS(1)
+    BCF_PASS(2)
+    BCF_PASS(3)
+#undef BCF_PASS
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n, int vb, const PassPlan& plan,
-                       unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
+                       unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
@@ -105,7 +162,7 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
     uint32_t* dk = to_out ? keys_out : kt;
     void* dv = to_out ? vals_out : vt;
     e = pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], plan.nbits[q], 0, false, totals + q * 256,
-                offsets, L, s);
+                offsets, s, cfg);
     if (e != cudaSuccess) return e;
     src_k = dk;
     src_v = dv;
@@ -121,7 +178,7 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
 
 cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                       void* vals_out, int64_t n, int w, int vb, bool balanced,
-                      unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
+                      unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
@@ -142,8 +199,8 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
     }
   }
   if (L.radix == 32)
-    return pass<5>(src_k, src_v, keys_out, vals_out, n, vb, 0, 5, w, balanced, totals, offsets, L, s);
-  return pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, 8, w, balanced, totals, offsets, L, s);
+    return pass<5>(src_k, src_v, keys_out, vals_out, n, vb, 0, 5, w, balanced, totals, offsets, s, cfg);
+  return pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, 8, w, balanced, totals, offsets, s, cfg);
 }
 
 BCF_TRACE_INSTALLER(radix)

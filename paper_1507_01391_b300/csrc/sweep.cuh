@@ -303,7 +303,9 @@ struct SweepSmem {
 };
 
 template <int THREADS, int IPT, int BITS, int VB>
-__global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_sweep(SweepParams p) {
+__global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) * 256 / THREADS > 0
+                                               ? (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) * 256 / THREADS
+                                               : 1) k_sweep(SweepParams p) {
   using VT = typename ValT<VB>::type;
   using S = SweepSmem<THREADS, IPT, BITS, VB>;
   constexpr int T = S::T, RADIX = S::RADIX;
@@ -586,23 +588,23 @@ __global__ void __launch_bounds__(THREADS, VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) k_
   }
 }
 
-template <int BITS, int VB>
+template <int BITS, int VB, int THREADS = kSweepThreads, int IPT = kSweepIPT>
 inline cudaError_t launch_sweep(const SweepParams& p, int64_t grid, cudaStream_t s) {
-  using S = SweepSmem<kSweepThreads, kSweepIPT, BITS, VB>;
-  auto kern = k_sweep<kSweepThreads, kSweepIPT, BITS, VB>;
+  using S = SweepSmem<THREADS, IPT, BITS, VB>;
+  auto kern = k_sweep<THREADS, IPT, BITS, VB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
-  kern<<<(unsigned)grid, kSweepThreads, S::bytes, s>>>(p);
+  kern<<<(unsigned)grid, THREADS, S::bytes, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int BITS>
+template <int BITS, int THREADS = kSweepThreads, int IPT = kSweepIPT>
 inline cudaError_t sweep_dispatch(const SweepParams& p, int64_t grid, int vb, cudaStream_t s) {
   switch (vb) {
-    case 0: return launch_sweep<BITS, 0>(p, grid, s);
-    case 4: return launch_sweep<BITS, 4>(p, grid, s);
-    case 8: return launch_sweep<BITS, 8>(p, grid, s);
+    case 0: return launch_sweep<BITS, 0, THREADS, IPT>(p, grid, s);
+    case 4: return launch_sweep<BITS, 4, THREADS, IPT>(p, grid, s);
+    case 8: return launch_sweep<BITS, 8, THREADS, IPT>(p, grid, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -1,0 +1,142 @@
+"""Autotuner for the sort and partition sweeps.
+
+Every digit pass can run with one of ``configs()`` tile shapes (threads per block x
+keys per thread, compiled into libbcf.so).  ``autotune()`` times each shape through
+the C ABI on random keys of each requested size, keeps the fastest in the library's
+host-side table (``bcf_tune_set``) and returns the choices; ``save()``/``load()``
+keep them in a JSON file keyed by device name and SM count, so a process can load
+the table at start-up instead of measuring again.  The inputs are random keys made
+on the device with torch; they only exist to time the kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import statistics
+
+from . import OK, OP_PARTITION, OP_SORT, BcfError, lib
+
+OPS = {"sort": OP_SORT, "partition": OP_PARTITION}
+
+
+def configs():
+    """[(threads, keys_per_thread)] of the compiled tile configurations."""
+    L = lib()
+    out = []
+    for c in range(L.bcf_tune_num_configs()):
+        t, k = ctypes.c_int(0), ctypes.c_int(0)
+        if L.bcf_tune_config_info(c, ctypes.byref(t), ctypes.byref(k)) != OK:
+            raise BcfError(1, "bcf_tune_config_info")
+        out.append((t.value, k.value))
+    return out
+
+
+def set_config(op: str, log2_n: int, config: int) -> None:
+    rc = lib().bcf_tune_set(OPS[op], int(log2_n), int(config))
+    if rc != OK:
+        raise BcfError(rc, "bcf_tune_set")
+
+
+def get_config(op: str, n: int) -> int:
+    c = ctypes.c_int(0)
+    rc = lib().bcf_tune_get(OPS[op], int(n), ctypes.byref(c))
+    if rc != OK:
+        raise BcfError(rc, "bcf_tune_get")
+    return c.value
+
+
+def _device_key():
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return "%s/%dsm" % (p.name, p.multi_processor_count)
+
+
+def _time(fn, reps):
+    import torch
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def _workload(op, n, w):
+    import torch
+
+    from . import partition, partition_workspace_size, sort, sort_workspace_size, workspace
+    g = torch.Generator(device="cuda").manual_seed(0x150701391 + n)
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    ko, vo = torch.empty_like(vals), torch.empty_like(vals)
+    if op == "sort":
+        keys = torch.randint(-2**31, 2**31, (n,), dtype=torch.int32, device="cuda", generator=g)
+        ws = workspace(sort_workspace_size(n, 4, 32))
+        return lambda: sort(keys, vals, keys_out=ko, vals_out=vo, ws=ws)
+    keys = (torch.randperm(n, device="cuda", generator=g) % w).to(torch.int32)
+    ws = workspace(partition_workspace_size(n, w, 4, 1))
+    return lambda: partition(keys, vals, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws)
+
+
+def autotune(ops=("sort", "partition"), log2_sizes=range(12, 27, 2), w=256, reps=5, verbose=False):
+    """Time every configuration for each op and size 2^k, keep the fastest in the
+    library's table and return {op: {k: (config, {config: ms})}}."""
+    result = {}
+    for op in ops:
+        result[op] = {}
+        for k in log2_sizes:
+            n = 1 << k
+            if op == "partition":
+                n -= n % w
+            fn = _workload(op, n, w)
+            times = {}
+            for c in range(len(configs())):
+                set_config(op, k, c)
+                times[c] = _time(fn, reps)
+            best = min(times, key=times.get)
+            set_config(op, k, best)
+            result[op][k] = (best, times)
+            if verbose:
+                print("tune %-9s 2^%-2d -> config %d  %s" % (op, k, best,
+                      " ".join("%d:%.4fms" % (c, t) for c, t in times.items())))
+    return result
+
+
+def cache_path():
+    return os.environ.get("BCF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "bcf", "tune.json"))
+
+
+def save(result, path=None):
+    path = path or cache_path()
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
+    data[_device_key()] = {op: {str(k): v[0] for k, v in tab.items()} for op, tab in result.items()}
+    with open(path, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    return path
+
+
+def load(path=None) -> bool:
+    """Apply the cached table of this device, if any; returns whether one was found."""
+    path = path or cache_path()
+    if not os.path.exists(path):
+        return False
+    with open(path) as f:
+        data = json.load(f)
+    tab = data.get(_device_key())
+    if not tab:
+        return False
+    for op, entries in tab.items():
+        for k, c in entries.items():
+            set_config(op, int(k), int(c))
+    return True

@@ -1,0 +1,57 @@
+"""GPU: every sweep tile configuration gives the oracle's result, and the
+autotuner picks a configuration per size and caches it per device."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from helpers import bits_equal, dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bcf():
+    import paper_1507_01391_b300 as m
+    m.lib()
+    yield m
+    for op in (m.OP_SORT, m.OP_PARTITION):
+        for k in range(64):
+            m.lib().bcf_tune_set(op, k, -1)
+
+
+@pytest.mark.parametrize("n", [1, 1000, 1023, 1024, 1025, 3 * 8192 + 17, 100_000])
+def test_every_config_sorts_and_partitions(bcf, n):
+    from paper_1507_01391_b300 import tune
+    k = (n - 1).bit_length() if n > 1 else 0
+    keys = synth.uniform_keys(n, seed=n)
+    vals = synth.index_payload(n)
+    rk, rv = oracle.sort_kv(keys, vals)
+    lab = synth.random_labels(n, 200, seed=n + 1)
+    pk, pv = oracle.partition_kv(lab, vals, 200)
+    for c in range(len(tune.configs())):
+        tune.set_config("sort", k, c)
+        tune.set_config("partition", k, c)
+        assert tune.get_config("sort", n) == c
+        ko, vo = bcf.sort(dev(keys), dev(vals))
+        assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.uint32), rv), c
+        ko, vo = bcf.partition(dev(lab), dev(vals), 200)
+        assert bits_equal(host(ko, np.uint32), pk) and bits_equal(host(vo, np.uint32), pv), c
+    assert bcf.get_status() == bcf.OK
+
+
+def test_autotune_and_cache(bcf, tmp_path):
+    from paper_1507_01391_b300 import tune
+    res = tune.autotune(ops=("sort", "partition"), log2_sizes=[14, 18], reps=2)
+    for op in ("sort", "partition"):
+        for k in (14, 18):
+            best, times = res[op][k]
+            assert best == min(times, key=times.get)
+            assert tune.get_config(op, 1 << k) == best
+    path = tune.save(res, str(tmp_path / "tune.json"))
+    for op in ("sort", "partition"):
+        tune.set_config(op, 14, -1)
+    assert tune.load(path)
+    assert tune.get_config("sort", 1 << 14) == res["sort"][14][0]

@@ -427,6 +427,10 @@ def run_rows(which, peak):
         ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED))
         ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 5, 50)
         add("partition_w32_n65536", n, 16 * n, ms, "launch-latency bound at this size")
+        wsl = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED | bcf.PARTITION_LEMMA1))
+        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
+                                            flags=bcf.PARTITION_LEMMA1), 5, 50)
+        add("partition_w32_n65536_lemma1", n, 16 * n, ms, "Lemma 1 tile schedule (conflict-free)")
     if want("permute_kv_2pow24") or want("tile_permute_scatter_2pow24") or want("tile_permute_coloured_2pow24"):
         n = N_PERM
         k = to_dev(synth.uniform_keys(n, seed=1))
@@ -469,6 +473,11 @@ def run_rows(which, peak):
         ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED))
         ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
         add("partition_w256_2pow26", n, 16 * n, ms)
+        wsl = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED | bcf.PARTITION_LEMMA1))
+        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
+                                            flags=bcf.PARTITION_LEMMA1), 2, 5)
+        add("partition_w256_2pow26_lemma1", n, 16 * n, ms, "Lemma 1 tile schedule (conflict-free), plain form")
+        del wsl
         del k, v, ko, vo, ws
     if want("tile_sort_lemma1_2pow24"):
         n = N_PERM

@@ -57,7 +57,7 @@ typedef struct CUstream_st* bcf_stream_t;
 #define BCF_ASSUME_BALANCED 0x1   /* partition: exactly n/w copies of each label */
 #define BCF_CHECK_PERM 0x2        /* permute: verify pi is a bijection (needs ws) */
 #define BCF_TILES_COLOURED 0x10   /* permute_tiles: randomized colouring schedule */
-#define BCF_PARTITION_LEMMA1 0x20 /* partition (w <= 32): Lemma 1 tile schedule */
+#define BCF_PARTITION_LEMMA1 0x20 /* partition: Lemma 1 tile schedule */
 #define BCF_PERMUTE_FUSED 0x40    /* permute_kv: one pass for keys and payloads */
 
 /* Message for a status code (static string; never NULL). */
@@ -101,8 +101,11 @@ int bcf_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
  *  flags    BCF_ASSUME_BALANCED: exactly n/w copies of every label, so block b
  *           starts at b*n/w without a counting pass; n % w != 0 -> BCF_E_INVAL,
  *           other counts -> device status BCF_E_NOT_BALANCED.
- *           BCF_PARTITION_LEMMA1 (w <= 32, balanced): the Lemma 1 schedule --
- *           row sorts inside each bank plus conflict-free transposes.
+ *           BCF_PARTITION_LEMMA1: order each 4096-key tile with the Lemma 1
+ *           schedule (Sec. 2) on (label, position) items -- row sorts inside
+ *           their own banks, conflict-free row/column conversions -- instead of
+ *           the rank-and-scatter sweep.  Same (stable) result, slower; its
+ *           shared-memory schedule has no bank conflicts.
  *  A label >= w -> device status BCF_E_BAD_KEY.  In place allowed (uses ws).
  * n must be < 2^30. */
 int bcf_partition_workspace_size(int64_t n, int w, int val_bytes, int flags, size_t* bytes);

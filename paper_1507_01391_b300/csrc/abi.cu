@@ -140,10 +140,13 @@ static bcf::SweepLayout partition_layout(int64_t n, int w, int vb) {
 }
 
 int bcf_partition_workspace_size(int64_t n, int w, int val_bytes, int flags, size_t* bytes) {
-  (void)flags;
   if (!bytes || n < 0 || w < 1 || !valid_vb(val_bytes)) return BCF_E_INVAL;
   if (w > 256 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
   *bytes = partition_layout(n, w, val_bytes).total;
+  if (flags & BCF_PARTITION_LEMMA1) {
+    const size_t l1 = bcf::sweep_layout(n, val_bytes, 1, 256, true).total;
+    if (l1 > *bytes) *bytes = l1;
+  }
   return BCF_OK;
 }
 
@@ -156,11 +159,18 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
   if (w > 256 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
   const bool balanced = (flags & BCF_ASSUME_BALANCED) != 0;
   if (balanced && n % w) return BCF_E_INVAL;
-  if (flags & BCF_PARTITION_LEMMA1) return BCF_E_UNSUPPORTED;
   if (n == 0) return BCF_OK;
   const bcf::SweepLayout L = partition_layout(n, w, val_bytes);
   if (!ws || !aligned16(ws)) return BCF_E_INVAL;
   if (ws_bytes < L.total) return BCF_E_WORKSPACE;
+  if (flags & BCF_PARTITION_LEMMA1) {
+    if (!device_ready()) return BCF_E_CUDA;
+    // 256-label counts at 4096-key tiles fit the workspace sized for the sweeps
+    const bcf::SweepLayout L1 = bcf::sweep_layout(n, val_bytes, 1, 256, true);
+    if (ws_bytes < L1.total) return BCF_E_WORKSPACE;
+    return cuda_rc(bcf::partition_lemma1(keys_in, vals_in, keys_out, vals_out, n, w, val_bytes, balanced,
+                                         static_cast<unsigned char*>(ws), L1, (cudaStream_t)stream));
+  }
   if (!device_ready()) return BCF_E_CUDA;
   return cuda_rc(bcf::partition(keys_in, vals_in, keys_out, vals_out, n, w, val_bytes, balanced,
                                 static_cast<unsigned char*>(ws), L, (cudaStream_t)stream,

@@ -84,6 +84,11 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
                       void* vals_out, int64_t n, int w, int val_bytes, bool balanced,
                       unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg = 0);
 
+// Partition with the Lemma 1 tile schedule (BCF_PARTITION_LEMMA1); same layout.
+cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                             void* vals_out, int64_t n, int w, int val_bytes, bool balanced,
+                             unsigned char* ws, const SweepLayout& L, cudaStream_t s);
+
 // ---------------------------------------------------------------- permutations
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
                     const uint32_t* pi, int64_t n, int64_t row_len, int kbytes, int vbytes,

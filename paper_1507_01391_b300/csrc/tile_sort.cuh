@@ -152,6 +152,20 @@ __device__ __forceinline__ void l1_col_to_row(const unsigned long long* N, unsig
   __syncthreads();
 }
 
+// The Lemma 1 schedule on items already built in X; afterwards Y[t] holds the
+// item of sorted position t.
+__device__ __forceinline__ void lemma1_schedule(unsigned long long* X, unsigned long long* Y) {
+#pragma unroll 1
+  for (int rep = 0; rep < 2; ++rep) {
+    l1_sort_rows(X, Y, true);
+    l1_row_to_col(X, Y);
+    l1_sort_rows(Y, X, false);
+    l1_col_to_row(Y, X);
+  }
+  l1_sort_rows(X, Y, false);
+  l1_row_to_col(X, Y);
+}
+
 // Sort one tile [start, start + len), len <= 4096, from keys_in/vals_in into
 // keys_out/vals_out.  X and Y are two kL1Tile-item shared buffers.
 template <int VB>
@@ -168,15 +182,7 @@ __device__ __forceinline__ void lemma1_tile(const uint32_t* __restrict__ keys_in
     X[q] = (key << 32) | (unsigned)q;  // padding sorts last (position >= len)
   }
   __syncthreads();
-#pragma unroll 1
-  for (int rep = 0; rep < 2; ++rep) {
-    l1_sort_rows(X, Y, true);
-    l1_row_to_col(X, Y);
-    l1_sort_rows(Y, X, false);
-    l1_col_to_row(Y, X);
-  }
-  l1_sort_rows(X, Y, false);
-  l1_row_to_col(X, Y);  // Y[t] = item of sorted position t
+  lemma1_schedule(X, Y);  // Y[t] = item of sorted position t
   const VT* vin = reinterpret_cast<const VT*>(vals_in);
   VT* vout = reinterpret_cast<VT*>(vals_out);
   for (int t = threadIdx.x; t < len; t += kL1Threads) {

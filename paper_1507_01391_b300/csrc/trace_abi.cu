@@ -13,6 +13,7 @@ namespace bcf {
 cudaError_t trace_install_radix(const TraceState& t);
 cudaError_t trace_install_segmented(const TraceState& t);
 cudaError_t trace_install_tile_permute(const TraceState& t);
+cudaError_t trace_install_partition_l1(const TraceState& t);
 }  // namespace bcf
 
 namespace {
@@ -22,6 +23,7 @@ int install(const bcf::TraceState& t) {
   if (bcf::trace_install_radix(t) != cudaSuccess) return BCF_E_CUDA;
   if (bcf::trace_install_segmented(t) != cudaSuccess) return BCF_E_CUDA;
   if (bcf::trace_install_tile_permute(t) != cudaSuccess) return BCF_E_CUDA;
+  if (bcf::trace_install_partition_l1(t) != cudaSuccess) return BCF_E_CUDA;
   return BCF_OK;
 }
 }  // namespace

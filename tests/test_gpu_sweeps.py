@@ -157,3 +157,24 @@ def test_partition_reports_unbalanced(bcf):
     keys[5] = (keys[5] + 1) % w  # one label too many, another too few
     bcf.partition(dev(keys), None, w, balanced=True)
     assert bcf.get_status() == bcf.E_NOT_BALANCED
+
+
+# ------------------------------------------------- Lemma 1 tile partition
+@pytest.mark.parametrize("w,balanced,n", [(32, True, 65536), (32, False, 3 * 4096 + 5), (256, True, 1 << 16),
+                                          (7, False, 1000), (1, True, 4096), (200, False, 1 << 20)])
+def test_partition_lemma1_schedule(bcf, w, balanced, n):
+    if balanced:
+        n -= n % w
+    keys = synth.partition_keys(n, w, seed=w + n) if balanced else synth.random_labels(n, w, seed=w + n)
+    vals = synth.float_bits_payload(n, seed=3)
+    ko, vo = bcf.partition(dev(keys), dev(vals), w, balanced=balanced, flags=bcf.PARTITION_LEMMA1)
+    assert bcf.get_status() == bcf.OK
+    rk, rv = oracle.partition_kv(keys, vals, w, balanced=balanced)
+    assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.float32), rv)
+
+
+def test_partition_lemma1_reports_bad_label(bcf):
+    keys = synth.random_labels(5000, 16, seed=1)
+    keys[123] = 40
+    bcf.partition(dev(keys), None, 16, flags=bcf.PARTITION_LEMMA1)
+    assert bcf.get_status() == bcf.E_BAD_KEY

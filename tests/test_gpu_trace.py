@@ -114,3 +114,22 @@ def test_sweep_strided_reads_are_conflict_free(tr):
     assert _replay(tr, rec, "writeout_read")["hw_conflicts"] == 0
     sc = _replay(tr, rec, "scatter")
     assert sc is not None and sc["requests"] == n // 32
+
+
+def test_lemma1_partition_replays_conflict_free(tr):
+    """The Lemma 1 tile partition: every shared access of its schedule replays
+    with zero hardware conflicts (the label counts are the only atomics)."""
+    import paper_1507_01391_b300 as bcf
+    n, w = 4096, 32
+    keys = synth.partition_keys(n, w, seed=9)
+    vals = synth.index_payload(n)
+    out = {}
+
+    def run():
+        out["k"], out["v"] = bcf.partition(dev(keys), dev(vals), w, balanced=True, flags=bcf.PARTITION_LEMMA1)
+    rec, _ = tr.capture(run)
+    rk, rv = oracle.partition_kv(keys, vals, w, balanced=True)
+    assert bits_equal(host(out["k"], np.uint32), rk) and bits_equal(host(out["v"], np.uint32), rv)
+    for site in ("l1_row_ld", "l1_row_st", "l1_convert", "l1_io"):
+        r = _replay(tr, rec, site)
+        assert r is not None and r["hw_conflicts"] == 0, (site, r)

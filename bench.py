@@ -189,8 +189,10 @@ def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a).view(view)).cuda()
 
 
-def graph_ms(fn, warmup=3, iters=10):
-    """Median CUDA-event time of one replay of a CUDA graph that captures fn()."""
+def graph_ms(fn, warmup=3, iters=10, inner=1):
+    """Median CUDA-event time of fn() from replays of a CUDA graph that captures
+    `inner` calls back to back (the replay time divided by `inner`): device time
+    without the host's per-call launch overhead."""
     import torch
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -201,8 +203,10 @@ def graph_ms(fn, warmup=3, iters=10):
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        fn()
-    return ev_ms(g.replay, warmup, iters)
+        for _ in range(inner):
+            fn()
+    ms, ts = ev_ms(g.replay, warmup, iters)
+    return ms / inner, [t / inner for t in ts]
 
 
 def ev_ms(fn, warmup=3, iters=10):
@@ -425,12 +429,20 @@ def run_rows(which, peak):
         v = to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED))
+        # Device time per call from graph replays of 20 calls: one call from Python
+        # costs more host time than its kernels take at this size.
+        ms, _ = graph_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws),
+                         3, 20, inner=20)
+        add("partition_w32_n65536", n, 16 * n, ms, "memset + one look-back sweep; graph replay")
         ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 5, 50)
-        add("partition_w32_n65536", n, 16 * n, ms, "launch-latency bound at this size")
+        add("partition_w32_n65536_eager", n, 16 * n, ms, "one call from Python, host launch cost included")
         wsl = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED | bcf.PARTITION_LEMMA1))
-        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
-                                            flags=bcf.PARTITION_LEMMA1), 5, 50)
-        add("partition_w32_n65536_lemma1", n, 16 * n, ms, "Lemma 1 tile schedule (conflict-free)")
+        ms, _ = graph_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
+                                               flags=bcf.PARTITION_LEMMA1), 3, 20, inner=20)
+        add("partition_w32_n65536_lemma1", n, 16 * n, ms, "Lemma 1 tile schedule (conflict-free); graph replay")
+        ku = to_dev(synth.random_labels(n, w, seed=0x150701392))
+        ms, _ = graph_ms(lambda: bcf.partition(ku, v, w, keys_out=ko, vals_out=vo, ws=ws), 3, 20, inner=20)
+        add("partition_w32_n65536_unbalanced", n, 20 * n, ms, "histogram read + one sweep; graph replay")
     if want("permute_kv_2pow24") or want("tile_permute_scatter_2pow24") or want("tile_permute_coloured_2pow24"):
         n = N_PERM
         k = to_dev(synth.uniform_keys(n, seed=1))

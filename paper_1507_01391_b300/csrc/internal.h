@@ -44,6 +44,9 @@ constexpr int kNumSweepConfigs = 4;
 constexpr int kSweepCfgThreads[kNumSweepConfigs] = {kSweepThreads, 256, 512, 256};
 constexpr int kSweepCfgIPT[kNumSweepConfigs] = {kSweepIPT, 4, 16, 8};
 constexpr int kMinSweepTile = 1024;  // smallest tile of any configuration (sizes workspaces)
+// Inputs up to this size run each digit pass as one look-back sweep launch (fewer
+// launches); larger ones use tile counts + scan + sweep.
+constexpr int64_t kSmallSweepN = (int64_t)1 << 18;
 inline int sweep_cfg_tile(int cfg) { return kSweepCfgThreads[cfg] * kSweepCfgIPT[cfg]; }
 
 // Tuning table (host state): configuration used by a sort (op 0) or partition
@@ -62,7 +65,7 @@ PassPlan plan_passes(int key_bits);
 struct SweepLayout {
   size_t keys_tmp = 0, vals_tmp = 0;   // ping-pong buffers (0 bytes when unused)
   size_t zero_begin = 0, zero_bytes = 0;  // region cleared before the passes
-  size_t hist = 0, counters = 0, lookback = 0, digit_base = 0;
+  size_t hist = 0, counters = 0, lookback = 0, digit_base = 0, status = 0;
   size_t total = 0;
   int64_t tiles = 0;
   int64_t lb_stride = 0;  // look-back status words per digit (tiles rounded up to 8)
@@ -106,7 +109,7 @@ struct SegLayout {
   int64_t lb_stride = 0;    // look-back status words per digit
   int passes = 0;
   size_t keys_tmp = 0, vals_tmp = 0, small_ids = 0, seg_slot = 0, seg_tile0 = 0, slot_seg = 0;
-  size_t tile_seg = 0, seg_base = 0, ctr = 0, seg_hist = 0, lookback = 0;
+  size_t tile_seg = 0, seg_base = 0, ctr = 0, lookback = 0;
   size_t zero_begin = 0, zero_bytes = 0, total = 0;
 };
 SegLayout seg_layout(int64_t n_total, int64_t nseg, int val_bytes, int passes, bool sort);

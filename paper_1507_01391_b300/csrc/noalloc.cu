@@ -23,12 +23,14 @@
 namespace {
 
 constexpr int64_t kNoAllocMaxN = BCF_NOALLOC_MAX_N;
-// Largest workspace the partition needs at kNoAllocMaxN keys without an in-place
-// copy: label totals (4 x 256 words, 256-byte aligned) + 256 x tiles counts.
+// Largest workspace the partition needs without an in-place copy, reached at
+// kNoAllocMaxN keys: label starts and label totals (4 x 256 words each, 256-byte
+// aligned), the tile tickets (256 bytes) and 256 x tiles counts.  (Inputs small
+// enough for the single-launch look-back path add status words instead, far fewer.)
 constexpr size_t kNoAllocTiles = (size_t)((kNoAllocMaxN + bcf::kSweepTile - 1) / bcf::kSweepTile);
 constexpr size_t kNoAllocStride =
-    (kNoAllocTiles + bcf::kLookbackWindow - 1) / bcf::kLookbackWindow * bcf::kLookbackWindow;
-constexpr size_t kNoAllocScratchBytes = 4 * 256 * 4 + kNoAllocStride * 256 * 4 + 256;
+    (kNoAllocTiles + bcf::kLookbackWindow) / bcf::kLookbackWindow * bcf::kLookbackWindow;
+constexpr size_t kNoAllocScratchBytes = 2 * 4 * 256 * 4 + 256 + kNoAllocStride * 256 * 4;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 

@@ -88,7 +88,7 @@ cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint3
     }
   }
   const int64_t tiles = (n + kL1Tile - 1) / kL1Tile;
-  const int64_t stride = (tiles + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
+  const int64_t stride = (tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;  // > tiles
   CountParams cp{};
   cp.keys = src_k;
   cp.n = n;

@@ -59,7 +59,7 @@ SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool n
   SweepLayout L;
   L.radix = radix;
   L.tiles = (n + tile - 1) / tile;
-  L.lb_stride = (L.tiles + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
+  L.lb_stride = (L.tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;  // > tiles
   size_t off = 0;
   if (need_tmp) {
     L.keys_tmp = off;
@@ -67,9 +67,15 @@ SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool n
     L.vals_tmp = off;
     off = align_up(off + (size_t)n * val_bytes);
   }
+  L.digit_base = off;  // small inputs: global digit starts from k_histogram
+  off = align_up(off + 4 * 256 * 4);
   L.zero_begin = off;
   L.hist = off;  // per-pass digit totals
   off = align_up(off + 4 * 256 * 4);
+  L.counters = off;  // small inputs: tile tickets per pass + histogram done flag
+  off = align_up(off + 8 * 4);
+  L.status = off;  // small inputs: look-back status words, one region per pass
+  if (n <= kSmallSweepN) off = align_up(off + (size_t)(passes > 0 ? passes : 1) * L.lb_stride * radix * 4);
   L.zero_bytes = off - L.zero_begin;
   L.lookback = off;  // per-(digit, tile) counts, scanned in place into run starts
   off = align_up(off + (size_t)L.lb_stride * radix * 4);
@@ -87,7 +93,7 @@ static cudaError_t pass_t(const uint32_t* src_k, const void* src_v, uint32_t* ds
   constexpr int T = THREADS * IPT;
   SweepLayout L;  // this configuration's tile count and status stride
   L.tiles = (n + T - 1) / T;
-  L.lb_stride = (L.tiles + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
+  L.lb_stride = (L.tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;  // > tiles
   CountParams cp{};
   cp.keys = src_k;
   cp.n = n;
@@ -138,12 +144,86 @@ static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_
   return cudaErrorInvalidValue;
 }
 
+// Small inputs: one sweep launch per pass with a decoupled look-back over at most
+// kSmallSweepN / kMinSweepTile tiles, after one histogram read for all passes
+// (skipped for balanced partitions, whose digit starts are closed-form).
+template <int BITS, int THREADS, int IPT>
+static cudaError_t lookback_pass_t(const uint32_t* src_k, const void* src_v, uint32_t* dst_k,
+                                   void* dst_v, int64_t n, int vb, int shift, int w, bool balanced,
+                                   const uint32_t* digit_base, uint32_t* status, uint32_t* ticket,
+                                   cudaStream_t s) {
+  constexpr int T = THREADS * IPT;
+  const int64_t tiles = (n + T - 1) / T;
+  SweepParams sp{};
+  sp.keys_in = src_k;
+  sp.vals_in = src_v;
+  sp.keys_out = dst_k;
+  sp.vals_out = dst_v;
+  sp.n = n;
+  sp.shift = shift;
+  sp.nbits = BITS;
+  sp.w = w;
+  sp.balanced = balanced ? 1 : 0;
+  sp.digit_base = digit_base;
+  sp.lookback = status;
+  sp.lb_stride = (tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;
+  sp.ticket = ticket;
+  sp.status = status_word();
+  return sweep_dispatch<BITS, THREADS, IPT>(sp, tiles, vb, s);
+}
+
+template <int BITS>
+static cudaError_t lookback_pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                                 int64_t n, int vb, int shift, int w, bool balanced,
+                                 const uint32_t* digit_base, uint32_t* status, uint32_t* ticket,
+                                 cudaStream_t s, int cfg) {
+  switch (cfg) {
+#define BCF_LBP(C)                                                                                     \
+  case C:                                                                                              \
+    return lookback_pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C]>(src_k, src_v, dst_k, dst_v, n, vb, \
+                                                                       shift, w, balanced, digit_base,   \
+                                                                       status, ticket, s);
+    BCF_LBP(0)
+    BCF_LBP(1)
+    BCF_LBP(2)
+    BCF_LBP(3)
+#undef BCF_LBP
+  }
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t small_histogram(const uint32_t* keys, int64_t n, int passes, const int* shift,
+                                   int label_bits, unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
+  HistParams hp{};
+  hp.keys = keys;
+  hp.n = n;
+  hp.passes = passes;
+  for (int q = 0; q < 4; ++q) {
+    hp.shift[q] = q < passes ? shift[q] : 0;
+    hp.nbits[q] = 8;
+  }
+  hp.label_bits = label_bits;
+  hp.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
+  hp.digit_base = reinterpret_cast<uint32_t*>(ws + L.digit_base);
+  hp.done = reinterpret_cast<uint32_t*>(ws + L.counters) + 4;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n / 4 + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 2));
+  k_histogram<256><<<grid, 256, 0, s>>>(hp);
+  return cudaGetLastError();
+}
+
 cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n, int vb, const PassPlan& plan,
                        unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
+  const bool small = n <= kSmallSweepN;
+  if (small && (e = small_histogram(keys_in, n, plan.passes, plan.shift, 0, ws, L, s)) != cudaSuccess)
+    return e;
   uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);
   uint32_t* offsets = reinterpret_cast<uint32_t*>(ws + L.lookback);
 
@@ -161,8 +241,15 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
     const bool to_out = odd_in_place ? (q % 2 == 1) : (((P - 1 - q) % 2) == 0);
     uint32_t* dk = to_out ? keys_out : kt;
     void* dv = to_out ? vals_out : vt;
-    e = pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], plan.nbits[q], 0, false, totals + q * 256,
-                offsets, s, cfg);
+    if (small) {
+      e = lookback_pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], 0, false,
+                           reinterpret_cast<uint32_t*>(ws + L.digit_base) + q * 256,
+                           reinterpret_cast<uint32_t*>(ws + L.status) + (size_t)q * L.lb_stride * 256,
+                           reinterpret_cast<uint32_t*>(ws + L.counters) + q, s, cfg);
+    } else {
+      e = pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], plan.nbits[q], 0, false, totals + q * 256,
+                  offsets, s, cfg);
+    }
     if (e != cudaSuccess) return e;
     src_k = dk;
     src_v = dv;
@@ -197,6 +284,17 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
         return e;
       src_v = vt;
     }
+  }
+  if (n <= kSmallSweepN) {
+    const int bits = L.radix == 32 ? 5 : 8;
+    const int zero = 0;
+    if (!balanced && (e = small_histogram(src_k, n, 1, &zero, bits, ws, L, s)) != cudaSuccess) return e;
+    uint32_t* base = reinterpret_cast<uint32_t*>(ws + L.digit_base);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + L.status);
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + L.counters);
+    if (bits == 5)
+      return lookback_pass<5>(src_k, src_v, keys_out, vals_out, n, vb, 0, w, balanced, base, status, ticket, s, cfg);
+    return lookback_pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, w, balanced, base, status, ticket, s, cfg);
   }
   if (L.radix == 32)
     return pass<5>(src_k, src_v, keys_out, vals_out, n, vb, 0, 5, w, balanced, totals, offsets, s, cfg);

@@ -9,9 +9,11 @@
 //   2. k_seg_small  (sort only) persistent blocks pull small segments from the
 //                   queue and sort each whole in shared memory with the Lemma 1
 //                   schedule (tile_sort.cuh): one read and one write per key;
-//   3. k_seg_hist + k_seg_scan   per-segment digit counts -> absolute digit starts;
-//   4. k_sweep (segment mode)    one launch per digit pass covers the tiles of
-//                   every long segment; look-back chains stop at segment starts.
+//   3. per digit pass: k_tile_counts over the long segments' tiles, k_scan_offsets
+//                   (running sums over all tiles), k_seg_digit_base (each segment's
+//                   digit starts from those sums), then k_sweep in segment mode: a
+//                   tile's run start is its running sum minus the one at its
+//                   segment's first tile, plus the segment's digit start.
 // Launch grids are host-side upper bounds; blocks without work exit at once.
 #include "common.cuh"
 #include "internal.h"
@@ -99,63 +101,27 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
   }
 }
 
-// Per-segment digit counts of every pass (segments in sweep tiles).
-struct SegHistParams {
-  const uint32_t* keys;
-  const int64_t* offs;
-  const int32_t* tile_seg;
-  const int32_t* seg_tile0;
-  const int32_t* seg_slot;
-  const uint32_t* ctr;
-  int tile, passes, label_bits;
-  int shift[4], nbits[4];
-  uint32_t* seg_hist;  // slot x passes x 256
-};
-
-__global__ void __launch_bounds__(256) k_seg_hist(SegHistParams p) {
-  __shared__ uint32_t h[4 * 256];
-  const int tid = threadIdx.x;
-  const int64_t tile = blockIdx.x;
-  if (tile >= (int64_t)p.ctr[C_NTILES]) return;
-  const int seg = p.tile_seg[tile];
-  const int64_t lo = p.offs[seg], hi = p.offs[seg + 1];
-  const int64_t start = lo + (tile - p.seg_tile0[seg]) * (int64_t)p.tile;
-  const int64_t end = min(hi, start + p.tile);
-  for (int i = tid; i < 4 * 256; i += 256) h[i] = 0;
-  __syncthreads();
-  uint32_t mask[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    mask[q] = p.label_bits ? ((1u << p.label_bits) - 1u) : ((1u << p.nbits[q]) - 1u);
-  for (int64_t i = start + tid; i < end; i += 256) {
-    const uint32_t k = p.keys[i];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (q < p.passes) atomicAdd(&h[q * 256 + ((k >> p.shift[q]) & mask[q])], 1u);
-  }
-  __syncthreads();
-  uint32_t* dst = p.seg_hist + (size_t)p.seg_slot[seg] * p.passes * 256;
-  for (int i = tid; i < p.passes * 256; i += 256)
-    if (h[i]) atomicAdd(&dst[i], h[i]);
-}
-
-// Exclusive scan of each long segment's counts -> absolute digit starts.
-__global__ void __launch_bounds__(256) k_seg_scan(const uint32_t* __restrict__ seg_hist,
-                                                  uint32_t* __restrict__ seg_base,
-                                                  const int32_t* __restrict__ slot_seg,
-                                                  const int64_t* __restrict__ offs,
-                                                  const uint32_t* __restrict__ ctr, int passes,
-                                                  int64_t slots_cap) {
+// Digit starts of every long segment for one pass, from that pass's running
+// tile sums: the segment holds run[d][t0 + tiles] - run[d][t0] keys of digit d;
+// an exclusive scan over d, offset by the segment's start, gives the starts.
+__global__ void __launch_bounds__(256) k_seg_digit_base(const uint32_t* __restrict__ run,
+                                                        int64_t stride, uint32_t* __restrict__ seg_base,
+                                                        const int32_t* __restrict__ slot_seg,
+                                                        const int32_t* __restrict__ seg_tile0,
+                                                        const int64_t* __restrict__ offs,
+                                                        const uint32_t* __restrict__ ctr, int tile) {
   __shared__ uint32_t scratch[32];
   const int64_t slot = blockIdx.x;
   if (slot >= (int64_t)ctr[C_NLARGE]) return;
-  const uint32_t start = (uint32_t)offs[slot_seg[slot]];
-  for (int q = 0; q < passes; ++q) {
-    const uint32_t c = seg_hist[((size_t)slot * passes + q) * 256 + threadIdx.x];
-    uint32_t tot;
-    const uint32_t e = block_excl_scan<256>(c, scratch, &tot);
-    seg_base[((size_t)q * slots_cap + slot) * 256 + threadIdx.x] = start + e;
-  }
+  const int seg = slot_seg[slot];
+  const int64_t lo = offs[seg], len = offs[seg + 1] - lo;
+  const int t0 = seg_tile0[seg];
+  const int t1 = t0 + (int)((len + tile - 1) / tile);
+  const uint32_t* r = run + (size_t)threadIdx.x * stride;
+  const uint32_t c = r[t1] - r[t0];
+  uint32_t tot;
+  const uint32_t e = block_excl_scan<256>(c, scratch, &tot);
+  seg_base[(size_t)slot * 256 + threadIdx.x] = (uint32_t)lo + e;
 }
 
 // Persistent blocks: sort every small segment whole with the Lemma 1 schedule.
@@ -212,7 +178,7 @@ SegLayout seg_layout(int64_t n_total, int64_t nseg, int vb, int passes, bool sor
   const int64_t max_large = sort ? std::min<int64_t>(nseg, n_total / (L.small_max + 1) + 1) : nseg;
   L.slots_cap = max_large > 0 ? max_large : 1;
   L.tiles_cap = n_total / T + max_large + 1;
-  L.lb_stride = (L.tiles_cap + kLookbackWindow - 1) / kLookbackWindow * kLookbackWindow;
+  L.lb_stride = (L.tiles_cap + kLookbackWindow) / kLookbackWindow * kLookbackWindow;  // > tiles
   L.passes = passes;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -227,10 +193,9 @@ SegLayout seg_layout(int64_t n_total, int64_t nseg, int vb, int passes, bool sor
   L.seg_tile0 = take((size_t)std::max<int64_t>(nseg, 1) * 4);
   L.slot_seg = take((size_t)L.slots_cap * 4);
   L.tile_seg = take((size_t)L.tiles_cap * 4);
-  L.seg_base = take((size_t)passes * L.slots_cap * 256 * 4);
+  L.seg_base = take((size_t)L.slots_cap * 256 * 4);  // digit starts of the current pass
   L.zero_begin = off;
   L.ctr = take(16 * 4);
-  L.seg_hist = take((size_t)L.slots_cap * passes * 256 * 4);
   L.lookback = take((size_t)L.lb_stride * 256 * 4);  // tile counts -> running sums (one pass at a time)
   L.zero_bytes = off - L.zero_begin;
   L.total = off;
@@ -290,29 +255,6 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
   }
 
   const int P = plan.passes;
-  if (!balanced) {
-    SegHistParams hp{};
-    hp.keys = keys_in;
-    hp.offs = offs;
-    hp.tile_seg = I32(L.tile_seg);
-    hp.seg_tile0 = I32(L.seg_tile0);
-    hp.seg_slot = I32(L.seg_slot);
-    hp.ctr = ctr;
-    hp.tile = kSweepTile;
-    hp.passes = P;
-    hp.label_bits = label ? 8 : 0;
-    for (int q = 0; q < 4; ++q) {
-      hp.shift[q] = plan.shift[q];
-      hp.nbits[q] = plan.nbits[q] ? plan.nbits[q] : 1;
-    }
-    hp.seg_hist = U32(L.seg_hist);
-    k_seg_hist<<<(unsigned)L.tiles_cap, 256, 0, s>>>(hp);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_seg_scan<<<(unsigned)L.slots_cap, 256, 0, s>>>(U32(L.seg_hist), U32(L.seg_base), I32(L.slot_seg),
-                                                     offs, ctr, P, L.slots_cap);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-
   uint32_t* kt = U32(L.keys_tmp);
   void* vt = vb ? (void*)(ws + L.vals_tmp) : nullptr;
   const uint32_t* src_k = keys_in;
@@ -341,6 +283,11 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_scan_offsets<<<256, kScanThreads, 0, s>>>(offsets, L.tiles_cap, L.lb_stride, nullptr, 0, n_total, 1, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!balanced) {
+      k_seg_digit_base<<<(unsigned)L.slots_cap, 256, 0, s>>>(offsets, L.lb_stride, U32(L.seg_base), I32(L.slot_seg),
+                                                             I32(L.seg_tile0), offs, ctr, kSweepTile);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     SweepParams sp{};
     sp.tile_offsets = offsets;
     sp.keys_in = src_k;
@@ -360,7 +307,7 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
     sp.tile_seg = I32(L.tile_seg);
     sp.seg_tile0 = I32(L.seg_tile0);
     sp.seg_slot = I32(L.seg_slot);
-    sp.seg_base = U32(L.seg_base) + (size_t)q * L.slots_cap * 256;
+    sp.seg_base = U32(L.seg_base);
     sp.seg_w = seg_w;
     sp.num_tiles = ctr + C_NTILES;
     if ((e = sweep_dispatch<8>(sp, L.tiles_cap, vb, s)) != cudaSuccess) return e;

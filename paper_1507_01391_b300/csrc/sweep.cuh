@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
 
 // One block per digit: exclusive scan of the digit's tile counts, offset by the
 // digit's global start (sum of smaller digits' totals, or b*n/w for a balanced
-// partition, whose counts are checked here).
+// partition, whose counts are checked here).  Entry `tiles` receives the digit's
+// total run end, so stride must exceed tiles.
 constexpr int kScanThreads = 1024;
 constexpr int kScanPerThread = 16;
 
@@ -249,31 +250,41 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
   __shared__ uint32_t scratch[32];
   __shared__ uint32_t s_base;
   const int d = blockIdx.x;
-  if (threadIdx.x == 0) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {  // digit start: warp-wide sum of the smaller digits' totals
     uint32_t b = 0;
-    if (!totals) {
-      // segment mode: plain running sums (each segment subtracts its first tile's)
-    } else if (balanced) {
-      b = (uint32_t)min((int64_t)d * (n / w), n);
-      const uint32_t expect = d < w ? (uint32_t)(n / w) : 0u;
-      if (totals[d] != expect) set_status(status, DEV_NOT_BALANCED);
-    } else {
-      for (int e = 0; e < d; ++e) b += totals[e];
+    if (totals && !balanced)
+      for (int e = tid; e < d; e += 32) b += totals[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (tid == 0) {
+      if (balanced) {
+        b = (uint32_t)min((int64_t)d * (n / w), n);
+        const uint32_t expect = d < w ? (uint32_t)(n / w) : 0u;
+        if (totals && totals[d] != expect) set_status(status, DEV_NOT_BALANCED);
+      }
+      s_base = b;  // segment mode (no totals): plain running sums from 0
     }
-    s_base = b;
   }
   __syncthreads();
   uint32_t carry = s_base;
   uint32_t* row = counts + (size_t)d * stride;
   for (int64_t c0 = 0; c0 < tiles; c0 += (int64_t)kScanThreads * kScanPerThread) {
-    const int64_t i0 = c0 + (int64_t)threadIdx.x * kScanPerThread;
+    const int64_t i0 = c0 + (int64_t)tid * kScanPerThread;
     uint32_t v[kScanPerThread];
+    if (i0 + kScanPerThread <= tiles) {  // 64-byte aligned: four 16-byte loads
+#pragma unroll
+      for (int j = 0; j < kScanPerThread; j += 4) {
+        const uint4 x = *reinterpret_cast<const uint4*>(row + i0 + j);
+        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kScanPerThread; ++j) v[j] = (i0 + j < tiles) ? row[i0 + j] : 0u;
+    }
     uint32_t sum = 0;
 #pragma unroll
-    for (int j = 0; j < kScanPerThread; ++j) {
-      v[j] = (i0 + j < tiles) ? row[i0 + j] : 0u;
-      sum += v[j];
-    }
+    for (int j = 0; j < kScanPerThread; ++j) sum += v[j];
     uint32_t total;
     uint32_t run = carry + block_excl_scan<kScanThreads>(sum, scratch, &total);
 #pragma unroll
@@ -283,6 +294,7 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
     }
     carry += total;
   }
+  if (tid == 0 && tiles < stride) row[tiles] = carry;  // end of the digit's runs
 }
 
 // ------------------------------------------------------------- one sweep

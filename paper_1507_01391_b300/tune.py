@@ -52,20 +52,33 @@ def _device_key():
     return "%s/%dsm" % (p.name, p.multi_processor_count)
 
 
-def _time(fn, reps):
+def _time(fn, reps, inner):
+    """Median device time of one fn() call, in ms, from replays of a CUDA graph of
+    `inner` calls: small inputs would otherwise time the host's launch cost."""
     import torch
-    for _ in range(2):
-        fn()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            fn()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(inner):
+            fn()
+    g.replay()
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        fn()
+        g.replay()
         b.record()
         b.synchronize()
-        ts.append(a.elapsed_time(b))
+        ts.append(a.elapsed_time(b) / inner)
+    del g
     return statistics.median(ts)
 
 
@@ -97,9 +110,10 @@ def autotune(ops=("sort", "partition"), log2_sizes=range(12, 27, 2), w=256, reps
                 n -= n % w
             fn = _workload(op, n, w)
             times = {}
+            inner = max(1, min(32, (1 << 22) >> k))  # about 2^22 keys per replay
             for c in range(len(configs())):
-                set_config(op, k, c)
-                times[c] = _time(fn, reps)
+                set_config(op, k, c)  # read at capture time: each config gets its own graph
+                times[c] = _time(fn, reps, inner)
             best = min(times, key=times.get)
             set_config(op, k, best)
             result[op][k] = (best, times)

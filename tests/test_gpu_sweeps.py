@@ -12,6 +12,10 @@ pytestmark = pytest.mark.gpu
 
 TILE = 4096
 SIZES = [1, 2, 31, 32, 33, 1000, TILE - 1, TILE, TILE + 1, 3 * TILE + 5, 50_001]
+# Inputs up to 2^18 keys take the single-launch look-back sweeps, larger ones the
+# tile counts + scan + sweep passes: both sides of the boundary.
+SMALL_MAX = 1 << 18
+BOUNDARY = [SMALL_MAX - 1, SMALL_MAX, SMALL_MAX + 1, 700_001]
 
 
 @pytest.fixture(scope="module")
@@ -38,6 +42,13 @@ def _sort_case(bcf, keys, vals, key_bits=32, in_place=False):
 @pytest.mark.parametrize("n", SIZES)
 def test_sort_uniform_kv(bcf, n):
     _sort_case(bcf, synth.uniform_keys(n, seed=n), synth.index_payload(n))
+
+
+@pytest.mark.parametrize("n", BOUNDARY)
+@pytest.mark.parametrize("key_bits", [8, 32])
+def test_sort_small_large_boundary(bcf, n, key_bits):
+    _sort_case(bcf, synth.uniform_keys(n, seed=n + key_bits, bits=key_bits), synth.index_payload(n),
+               key_bits=key_bits)
 
 
 @pytest.mark.parametrize("kind", ["equal", "sorted", "reverse", "few", "zipf"])
@@ -128,6 +139,16 @@ def test_partition_ragged_and_widths(bcf, n, vb):
     keys = synth.random_labels(n, w, seed=n)
     vals = None if vb == 0 else synth.uniform_keys(2 * n, seed=1).view(np.uint64)
     _partition_case(bcf, keys, vals, w, False)
+
+
+@pytest.mark.parametrize("n", BOUNDARY)
+@pytest.mark.parametrize("w", [32, 256])
+@pytest.mark.parametrize("balanced", [True, False])
+def test_partition_small_large_boundary(bcf, n, w, balanced):
+    if balanced:
+        n -= n % w
+    keys = synth.partition_keys(n, w, seed=n + w) if balanced else synth.random_labels(n, w, seed=n + w)
+    _partition_case(bcf, keys, synth.index_payload(n), w, balanced)
 
 
 def test_partition_in_place(bcf):

@@ -45,8 +45,10 @@ FALLBACK_HBM_GBS = 6400.0
 # Per-launch DRAM traffic of the dominant kernel from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
 # it was taken on: if permute.cu changes, the figure is dropped (null).
-NCU_TRAFFIC = {"kernel": "k_permute<4,0> x2 (keys pass + payload pass)", "source_sha1": None, "bytes": None,
-               "summary": "profiles/k_permute_kv_2pow24.md"}
+NCU_TRAFFIC = {"kernel": "k_pb_bucket<4,512> + k_pb_place<4,0> (bucketed kv permute, both passes)",
+               "source": "permute_bucketed.cu", "source_sha1": "242b6917030cb3627d2443fbc824cd9b28421794",
+               "bytes": 576164864,
+               "summary": "profiles/k_pb_bucketed_permute_kv_2pow24.md"}
 
 
 def log(*a):
@@ -238,11 +240,12 @@ def run_headline(args, rank, world, local):
     ko = torch.empty_like(d["keys"])
     vo = torch.empty_like(d["vals"])
     to = torch.empty_like(d["tsrc"])
+    pws = bcf.workspace(bcf.permute_workspace_size(N_PERM, 4, bcf.PERMUTE_BUCKETED))
 
     def step(kev=None):
         if kev is not None:
             kev[0].record()
-        bcf.permute_kv(d["keys"], d["vals"], d["pi"], keys_out=ko, vals_out=vo)
+        bcf.permute_kv(d["keys"], d["vals"], d["pi"], keys_out=ko, vals_out=vo, bucketed=True, ws=pws)
         if kev is not None:
             kev[1].record()
         bcf.permute_tiles(d["tsrc"], d["lpi"], tile=TILE, dst=to)
@@ -296,11 +299,13 @@ def run_e2e(args, bcf, x):
     to = torch.empty(N_PERM, dtype=torch.int32, device="cuda")
     h2d = sum(v.numel() * v.element_size() for v in pin.values())
     d2h = 3 * N_PERM * 4
+    pws = bcf.workspace(bcf.permute_workspace_size(N_PERM, 4, bcf.PERMUTE_BUCKETED))
 
     def step():
         for k in pin:
             dev[k].copy_(pin[k], non_blocking=True)
-        bcf.permute_kv(dev["keys"], dev["vals"].view(torch.float32), dev["pi"], keys_out=ko, vals_out=vo)
+        bcf.permute_kv(dev["keys"], dev["vals"].view(torch.float32), dev["pi"], keys_out=ko, vals_out=vo,
+                       bucketed=True, ws=pws)
         bcf.permute_tiles(dev["tsrc"], dev["lpi"], tile=TILE, dst=to)
         outs_h[0].copy_(ko, non_blocking=True)
         outs_h[1].copy_(to, non_blocking=True)
@@ -381,6 +386,8 @@ def headline_config():
                         "4096-key tiles by per-tile uniform random uint16 permutations",
             "n": N_PERM, "tile": TILE, "keys_per_step": 2 * N_PERM,
             "l2": "every input larger than the 126 MB L2 (no flush between steps)",
+            "permute_form": "bucketed: group by destination block of 2^15 into a 10 B/key workspace, "
+                            "then place each block in shared memory (two coalesced passes)",
             "tile_schedule": "scatter"}
 
 
@@ -443,18 +450,29 @@ def run_rows(which, peak):
         ku = to_dev(synth.random_labels(n, w, seed=0x150701392))
         ms, _ = graph_ms(lambda: bcf.partition(ku, v, w, keys_out=ko, vals_out=vo, ws=ws), 3, 20, inner=20)
         add("partition_w32_n65536_unbalanced", n, 20 * n, ms, "histogram read + one sweep; graph replay")
-    if want("permute_kv_2pow24") or want("tile_permute_scatter_2pow24") or want("tile_permute_coloured_2pow24"):
+    if any(want(r) for r in ("permute_kv_2pow24", "permute_kv_scatter_2pow24", "permute_kv_fused_2pow24",
+                             "permute_keys_2pow24", "tile_permute_scatter_2pow24", "tile_permute_coloured_2pow24")):
         n = N_PERM
         k = to_dev(synth.uniform_keys(n, seed=1))
         v = to_dev(synth.float_bits_payload(n, seed=2))
         pi = to_dev(synth.random_perm(n, seed=3))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
+        pws = bcf.workspace(bcf.permute_workspace_size(n, 4, bcf.PERMUTE_BUCKETED))
         if want("permute_kv_2pow24"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo))
-            add("permute_kv_2pow24", n, 20 * n, ms, "keys pass + payload pass (chosen form)")
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=pws))
+            add("permute_kv_2pow24", n, 20 * n, ms, "bucketed: two coalesced passes (chosen form); model "
+                "charges the one-pass 20 B/key, the passes move about 42 B/key")
+        if want("permute_kv_scatter_2pow24"):
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False))
+            add("permute_kv_scatter_2pow24", n, 20 * n, ms, "scatter: keys pass + payload pass")
         if want("permute_kv_fused_2pow24"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, fused=True))
-            add("permute_kv_fused_2pow24", n, 20 * n, ms, "one fused pass (plain form)")
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, fused=True, bucketed=False))
+            add("permute_kv_fused_2pow24", n, 20 * n, ms, "scatter: one fused pass (plain form)")
+        if want("permute_keys_2pow24"):
+            ms, _ = ev_ms(lambda: bcf.permute(k, pi, dst=ko, bucketed=True, ws=pws))
+            add("permute_keys_2pow24", n, 12 * n, ms, "keys only, bucketed")
+            ms, _ = ev_ms(lambda: bcf.permute(k, pi, dst=ko, bucketed=False))
+            add("permute_keys_scatter_2pow24", n, 12 * n, ms, "keys only, one scatter pass")
         lpi = to_dev(synth.tile_local_perms(n, TILE, seed=4))
         for coloured in (False, True):
             name = "tile_permute_%s_2pow24" % ("coloured" if coloured else "scatter")
@@ -592,7 +610,13 @@ def _case_inputs(name):
         k, v, pi = (to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.float_bits_payload(n, seed=2)),
                     to_dev(synth.random_perm(n, seed=3)))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
-        return lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo)
+        ws = bcf.workspace(bcf.permute_workspace_size(n, 4, bcf.PERMUTE_BUCKETED))
+        return lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=ws)
+    if name == "permute_kv_scatter":
+        k, v, pi = (to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.float_bits_payload(n, seed=2)),
+                    to_dev(synth.random_perm(n, seed=3)))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        return lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False)
     if name in ("tile_scatter", "tile_coloured"):
         k, lpi = to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.tile_local_perms(n, TILE, seed=4))
         ko = torch.empty_like(k)
@@ -616,7 +640,7 @@ def _case_inputs(name):
     raise ValueError(name)
 
 
-CASES = ("permute_kv", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256",
+CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256",
          "tile_sort")
 
 
@@ -654,7 +678,7 @@ def main():
     value = world * keys_step / (ms_step * 1e-3) / 1e9
     bytes_launch = 20 * N_PERM
     achieved = bytes_launch / (h["kern_ms"] * 1e-3) / 1e9
-    src_sha = file_sha1(os.path.join(ROOT, "paper_1507_01391_b300", "csrc", "permute.cu"))
+    src_sha = file_sha1(os.path.join(ROOT, "paper_1507_01391_b300", "csrc", NCU_TRAFFIC["source"]))
     traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["source_sha1"] == src_sha else None
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
@@ -667,7 +691,7 @@ def main():
                      "kernel": NCU_TRAFFIC["kernel"], "bytes_per_launch": bytes_launch,
                      "kernel_ms": round(h["kern_ms"], 4), "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
                      "frac_of_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4)},
-        "gpu_launches": 3 * args.steps,  # keys pass + payload pass + tile permute
+        "gpu_launches": 3 * args.steps,  # bucket pass + place pass + tile permute
         "clocks": h["clocks"],
         "e2e": h["e2e"],
         "status_ok": h["status_ok"],

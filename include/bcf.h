@@ -59,6 +59,7 @@ typedef struct CUstream_st* bcf_stream_t;
 #define BCF_TILES_COLOURED 0x10   /* permute_tiles: randomized colouring schedule */
 #define BCF_PARTITION_LEMMA1 0x20 /* partition: Lemma 1 tile schedule */
 #define BCF_PERMUTE_FUSED 0x40    /* permute_kv: one pass for keys and payloads */
+#define BCF_PERMUTE_BUCKETED 0x80 /* permute: two coalesced passes through ws */
 
 /* Message for a status code (static string; never NULL). */
 const char* bcf_status_string(int status);
@@ -120,15 +121,29 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
  *              items and pi[i] is local to the row of i (a batch of independent
  *              permutations): dst[row(i)*row_len + pi[i]] = src[i].
  *  flags       BCF_CHECK_PERM: also verify that pi is a bijection (device status
- *              BCF_E_BAD_PERM otherwise); needs bcf_permute_workspace_size() of
- *              ws, else ws may be NULL.
+ *              BCF_E_BAD_PERM otherwise).
+ *              BCF_PERMUTE_BUCKETED: instead of one scattered store per element
+ *              (each costs an L2 sector operation), move the elements in two
+ *              coalesced passes: group them by destination block of 2^15
+ *              positions into ws (tiles of 8192 elements, one global atomic claim
+ *              per tile and block), then place each block in shared memory and
+ *              write it out in order.  Same result.  Applies to 4-byte elements
+ *              with payloads of 0 or 4 bytes and n <= 2^26; otherwise the
+ *              one-pass scatter runs.  With a pi that is not a bijection the
+ *              output is unspecified (nothing is written outside dst) and, when
+ *              the device can tell, BCF_E_BAD_PERM is set.
+ *  ws          bcf_permute_workspace_size(n, val_bytes, flags) bytes, 16-byte
+ *              aligned (val_bytes 0 for bcf_permute); NULL when that size is 0.
+ *              Caller-owned; contents need not be initialised.
  * An index outside its range is never written; it sets BCF_E_BAD_PERM. */
-int bcf_permute_workspace_size(int64_t n, int flags, size_t* bytes);
+int bcf_permute_workspace_size(int64_t n, int val_bytes, int flags, size_t* bytes);
 int bcf_permute(const void* src, void* dst, const uint32_t* pi, int64_t n, int64_t row_len,
                 int elem_bytes, int flags, void* ws, size_t ws_bytes, bcf_stream_t stream);
 /* Keys and values moved by one pi (val_bytes 0, 4 or 8).  By default the keys
  * and the payloads are scattered in two passes, each of whose outputs stays in
- * L2 while it fills; BCF_PERMUTE_FUSED scatters both in one pass. */
+ * L2 while it fills; BCF_PERMUTE_FUSED scatters both in one pass;
+ * BCF_PERMUTE_BUCKETED (which takes precedence) moves both through ws in two
+ * coalesced passes. */
 int bcf_permute_kv(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
                    const uint32_t* pi, int64_t n, int64_t row_len, int val_bytes, int flags,
                    void* ws, size_t ws_bytes, bcf_stream_t stream);

@@ -28,6 +28,10 @@ CHECK_PERM = 0x2
 TILES_COLOURED = 0x10
 PARTITION_LEMMA1 = 0x20
 PERMUTE_FUSED = 0x40
+PERMUTE_BUCKETED = 0x80
+# Sizes from which permute()/permute_kv() pick the bucketed form by default.
+BUCKETED_MIN_N = 1 << 20
+BUCKETED_MAX_N = 1 << 26
 
 
 class BcfError(RuntimeError):
@@ -48,7 +52,7 @@ _SIGS = {
     "bcf_sort": ([_P, _P, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_partition_workspace_size": ([_I64, _I, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_partition": ([_P, _P, _P, _P, _I64, _I, _I, _I, _P, _SZ, _P], _I),
-    "bcf_permute_workspace_size": ([_I64, _I, ctypes.POINTER(_SZ)], _I),
+    "bcf_permute_workspace_size": ([_I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_permute": ([_P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_kv": ([_P, _P, _P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_tiles": ([_P, _P, _P, _I64, _I, _I, _U64, _P], _I),
@@ -198,40 +202,55 @@ def partition(keys, vals, w, balanced=False, keys_out=None, vals_out=None, ws=No
     return keys_out, vals_out
 
 
-def permute(src, pi, dst=None, check=False, row_len=0, stream=None):
+def _permute_flags(n, elem_bytes, val_bytes, check, fused, bucketed):
+    if bucketed is None:  # default: the bucketed form where it applies and pays (keys with payloads;
+        # a single array of 2^24 keys measured faster as one scatter pass)
+        bucketed = (elem_bytes == 4 and val_bytes == 4 and BUCKETED_MIN_N <= n <= BUCKETED_MAX_N)
+    return (CHECK_PERM if check else 0) | (PERMUTE_FUSED if fused else 0) | (PERMUTE_BUCKETED if bucketed else 0)
+
+
+def permute_workspace_size(n, val_bytes=0, flags=0):
+    sz = ctypes.c_size_t(0)
+    _check(lib().bcf_permute_workspace_size(int(n), int(val_bytes), int(flags), ctypes.byref(sz)),
+           "bcf_permute_workspace_size")
+    return sz.value
+
+
+def permute(src, pi, dst=None, check=False, row_len=0, stream=None, bucketed=None, ws=None):
     """dst[pi[i]] = src[i] for 4- or 8-byte elements (bcf_permute); with row_len,
-    pi is local to rows of row_len items."""
+    pi is local to rows of row_len items.  bucketed: None (one scatter pass) or
+    True (two coalesced passes; 4-byte elements, n <= 2^26); ws: optional
+    preallocated workspace (uint8 tensor)."""
     torch = _torch()
     _dev_u32(pi, "pi")
     n = src.numel()
     dst = torch.empty_like(src) if dst is None else dst
-    flags = CHECK_PERM if check else 0
-    ws = None
-    if check:
-        sz = ctypes.c_size_t(0)
-        lib().bcf_permute_workspace_size(n, flags, ctypes.byref(sz))
-        ws = workspace(sz.value, src.device)
+    flags = _permute_flags(n, src.element_size(), 0, check, False, bucketed)
+    need = permute_workspace_size(n, 0, flags)
+    if need and (ws is None or ws.numel() < need):
+        ws = workspace(need, src.device)
     _check(lib().bcf_permute(_ptr(src), _ptr(dst), _ptr(pi), n, row_len, src.element_size(), flags, _ptr(ws),
                              0 if ws is None else ws.numel(), _stream(stream)), "bcf_permute")
     return dst
 
 
 def permute_kv(keys, vals, pi, keys_out=None, vals_out=None, check=False, row_len=0, stream=None,
-               fused=False):
-    """Keys and payloads moved by one permutation in one pass (bcf_permute_kv)."""
+               fused=False, bucketed=None, ws=None):
+    """Keys and payloads moved by one permutation (bcf_permute_kv).  Forms: two
+    scatter passes (default below 2^20 keys), one fused scatter (fused=True) or
+    two coalesced bucketed passes (bucketed; default from 2^20 to 2^26 keys)."""
     torch = _torch()
     n = keys.numel()
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
     if vals is not None and vals_out is None:
         vals_out = torch.empty_like(vals)
-    flags = (CHECK_PERM if check else 0) | (PERMUTE_FUSED if fused else 0)
-    ws = None
-    if check:
-        sz = ctypes.c_size_t(0)
-        lib().bcf_permute_workspace_size(n, flags, ctypes.byref(sz))
-        ws = workspace(sz.value, keys.device)
+    vb = _vb(vals)
+    flags = _permute_flags(n, 4, vb, check, fused, bucketed)
+    need = permute_workspace_size(n, vb, flags)
+    if need and (ws is None or ws.numel() < need):
+        ws = workspace(need, keys.device)
     _check(lib().bcf_permute_kv(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), _ptr(pi), n,
-                                row_len, _vb(vals), flags, _ptr(ws), 0 if ws is None else ws.numel(),
+                                row_len, vb, flags, _ptr(ws), 0 if ws is None else ws.numel(),
                                 _stream(stream)), "bcf_permute_kv")
     return keys_out, vals_out
 

@@ -178,9 +178,17 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
 }
 
 // ------------------------------------------------------------ permutations
-int bcf_permute_workspace_size(int64_t n, int flags, size_t* bytes) {
-  if (!bytes || n < 0) return BCF_E_INVAL;
-  *bytes = (flags & BCF_CHECK_PERM) ? bcf::align_up((size_t)((n + 31) / 32) * 4) : 0;
+// Workspace: [bucketed-form region (BCF_PERMUTE_BUCKETED)][seen bitmap (BCF_CHECK_PERM)].
+static size_t permute_bucket_bytes(int64_t n, int vb, int flags) {
+  return ((flags & BCF_PERMUTE_BUCKETED) && bcf::permute_bucketed_supported(n, 4, vb))
+             ? bcf::permute_bucketed_workspace(n, vb)
+             : 0;
+}
+
+int bcf_permute_workspace_size(int64_t n, int val_bytes, int flags, size_t* bytes) {
+  if (!bytes || n < 0 || !valid_vb(val_bytes)) return BCF_E_INVAL;
+  *bytes = permute_bucket_bytes(n, val_bytes, flags) +
+           ((flags & BCF_CHECK_PERM) ? bcf::align_up((size_t)((n + 31) / 32) * 4) : 0);
   return BCF_OK;
 }
 
@@ -194,15 +202,22 @@ static int permute_common(const void* sk, const void* sv, void* dk, void* dv, co
   if (vb && (!sv || !dv || !aligned16(sv) || !aligned16(dv))) return BCF_E_INVAL;
   if (!disjoint(sk, (size_t)n * kb, dk, (size_t)n * kb)) return BCF_E_INVAL;
   if (vb && !disjoint(sv, (size_t)n * vb, dv, (size_t)n * vb)) return BCF_E_INVAL;
-  uint32_t* seen = nullptr;
-  if (flags & BCF_CHECK_PERM) {
-    size_t need = 0;
-    bcf_permute_workspace_size(n, flags, &need);
+  // bcf_permute sizes its workspace with val_bytes 0 whatever its element size
+  const int ws_vb = sv ? vb : 0;
+  size_t need = 0;
+  bcf_permute_workspace_size(n, ws_vb, flags, &need);
+  if (need) {
     if (!ws || !aligned16(ws)) return BCF_E_INVAL;
     if (ws_bytes < need) return BCF_E_WORKSPACE;
-    seen = static_cast<uint32_t*>(ws);
   }
+  const size_t bucket_bytes = permute_bucket_bytes(n, ws_vb, flags);
+  const bool check = (flags & BCF_CHECK_PERM) != 0;
   if (!device_ready()) return BCF_E_CUDA;
+  if ((flags & BCF_PERMUTE_BUCKETED) && bcf::permute_bucketed_supported(n, kb, vb))
+    return cuda_rc(bcf::permute_bucketed(static_cast<const uint32_t*>(sk), static_cast<const uint32_t*>(sv),
+                                         static_cast<uint32_t*>(dk), static_cast<uint32_t*>(dv), pi, n,
+                                         row_len, vb, check, static_cast<unsigned char*>(ws), s));
+  uint32_t* seen = check ? reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + bucket_bytes) : nullptr;
   return cuda_rc(bcf::permute(sk, sv, dk, dv, pi, n, row_len, kb, vb, seen,
                               (flags & BCF_PERMUTE_FUSED) != 0, s));
 }

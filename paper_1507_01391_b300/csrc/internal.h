@@ -96,6 +96,12 @@ cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint3
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
                     const uint32_t* pi, int64_t n, int64_t row_len, int kbytes, int vbytes,
                     uint32_t* seen_bitmap, bool fused, cudaStream_t s);
+// Two-pass bucketed permutation (permute_bucketed.cu).
+bool permute_bucketed_supported(int64_t n, int kb, int vb);
+size_t permute_bucketed_workspace(int64_t n, int vb);
+cudaError_t permute_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
+                             const uint32_t* pi, int64_t n, int64_t row_len, int vb, bool check,
+                             unsigned char* ws, cudaStream_t s);
 cudaError_t gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
                    int64_t row_len, int elem_bytes, cudaStream_t s);
 cudaError_t permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,

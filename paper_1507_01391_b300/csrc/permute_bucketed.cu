@@ -1,0 +1,347 @@
+// permute_bucketed.cu -- the permutation dst[pi[i]] = src[i] (Sec. 1) in two
+// coalesced passes through a workspace, instead of one scattered store per element.
+//
+// A scattered 4-byte store costs one L2 sector operation however few bytes it
+// carries, and L2 accepts only so many of those per second; that rate, not HBM
+// bandwidth, bounds the one-pass scatter.  Here every store is part of a run:
+//
+//  Pass 1 (k_pb_bucket): persistent blocks take tiles of kPbTile elements; a tile's
+//    pi, keys and payloads stream into shared memory by bulk copies while the
+//    previous tile is processed.  Element i belongs to destination block
+//    b = pi[i] >> kPbBits (2^15 destinations each).  A tile is counted per block,
+//    reordered into block order in shared memory, and each run is written to the
+//    block's region of the workspace at an offset claimed with one global atomic
+//    per (tile, block).  Only pi's low 15 bits travel with the element.  The order
+//    inside a region is whatever the claims produced; pass 2 does not depend on it.
+//  Pass 2 (k_pb_place): one block per destination block reads the region in order,
+//    stores every element at its 15-bit offset in shared memory (128 KB), then
+//    writes the block of dst with 16-byte stores; payloads take a second round.
+//
+// Traffic per element: pass 1 reads 4 + 4 + vb bytes and writes 2 + 4 + vb, pass 2
+// reads them back (plus pi's low bits again for the payload round) and writes
+// 4 + vb -- about twice the one-pass bytes, but in whole sectors.
+#include "common.cuh"
+#include "internal.h"
+#include "sweep.cuh"
+
+namespace bcf {
+
+namespace {
+
+constexpr int kPbBits = 15;                 // destinations per block: 2^15
+constexpr int kPbBlock = 1 << kPbBits;
+constexpr int kPbThreads = 512, kPbIPT = 16;
+constexpr int kPbTile = kPbThreads * kPbIPT;  // 8192 elements per pass-1 tile
+constexpr int kPbMaxBlocks = 2048;          // n <= 2^26
+constexpr int kPlaceThreads = 1024;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+struct PbLayout {
+  size_t k1 = 0, v1 = 0, p1 = 0, fill = 0, total = 0;
+};
+
+PbLayout pb_layout(int64_t n, int vb) {
+  PbLayout L;
+  size_t off = 0;
+  L.k1 = off;
+  off = align_up(off + (size_t)n * 4);
+  L.v1 = off;
+  off = align_up(off + (size_t)n * vb);
+  L.p1 = off;
+  off = align_up(off + (size_t)n * 2 + 16);
+  L.fill = off;
+  off = align_up(off + (size_t)kPbMaxBlocks * 4);
+  L.total = off;
+  return L;
+}
+
+template <int NB>
+constexpr int pb_smem_bytes() {
+  // in: pi, keys, payloads; reordered: (key | payload << 32), (offset | block << 16);
+  // per-block counts and write offsets; scan scratch; mbarrier
+  return kPbTile * 4 * 3 + kPbTile * 8 + kPbTile * 4 + NB * 4 * 2 + 32 * 4 + 16;
+}
+
+template <int VB, int NB>
+__global__ void __launch_bounds__(kPbThreads, 1)
+    k_pb_bucket(const uint32_t* __restrict__ pi, const uint32_t* __restrict__ sk,
+                const uint32_t* __restrict__ sv, uint32_t* __restrict__ K1, uint32_t* __restrict__ V1,
+                uint16_t* __restrict__ P1, uint32_t* __restrict__ fill, int64_t n, int64_t row_len,
+                int ntiles, unsigned* status) {
+  constexpr int T = kPbTile;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t* in_p = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* in_k = in_p + T;
+  uint32_t* in_v = in_k + T;
+  unsigned long long* skv = reinterpret_cast<unsigned long long*>(in_v + T);
+  uint32_t* spb = reinterpret_cast<uint32_t*>(skv + T);
+  uint32_t* cur = spb + T;  // per-block count, then start, then cursor
+  uint32_t* gofs = cur + NB;
+  uint32_t* scratch = gofs + NB;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(scratch + 32);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  auto bulk_elems = [&](int t) { return (int)min((int64_t)T, n - (int64_t)t * T) & ~3; };
+  auto issue = [&](int t) {  // one thread: stream tile t into the in-buffers
+    const int e = bulk_elems(t);
+    const int64_t o = (int64_t)t * T;
+    if (e > 0) {
+      mbar_arrive_expect_tx(bar, (VB ? 3u : 2u) * (unsigned)e * 4u);
+      bulk_g2s(in_p, pi + o, e * 4, bar);
+      bulk_g2s(in_k, sk + o, e * 4, bar);
+      if (VB) bulk_g2s(in_v, sv + o, e * 4, bar);
+    } else {
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    }
+  };
+  if (tid == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+
+  int it = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    const int64_t base = (int64_t)t * T;
+    const int cnt = (int)min((int64_t)T, n - base);
+    const int be = bulk_elems(t);
+    if (!mbar_wait(bar, it & 1, status)) {
+      mbar_wait(bar, it & 1, status);  // give the copy in flight a last chance to land
+      return;
+    }
+    // Each warp takes 32 consecutive elements per step: conflict-free reads.
+    uint32_t d[kPbIPT], k[kPbIPT], v[kPbIPT];
+#pragma unroll
+    for (int j = 0; j < kPbIPT; ++j) {
+      const int li = warp * (kPbIPT * 32) + j * 32 + lane;
+      v[j] = 0;
+      if (li < be) {
+        d[j] = in_p[li];
+        k[j] = in_k[li];
+        if (VB) v[j] = in_v[li];
+      } else if (li < cnt) {  // ragged end of the last tile
+        d[j] = pi[base + li];
+        k[j] = sk[base + li];
+        if (VB) v[j] = sv[base + li];
+      } else {
+        d[j] = kNone;
+        continue;
+      }
+      if (row_len > 0) {  // pi local to rows of row_len elements
+        const int64_t i = base + li;
+        const int64_t g = (int64_t)d[j] < row_len ? (i / row_len) * row_len + d[j] : n;
+        d[j] = g < n ? (uint32_t)g : (uint32_t)n;
+      }
+      if ((int64_t)d[j] >= n) {
+        set_status(status, DEV_BAD_PERM);
+        d[j] = kNone;
+      }
+    }
+    __syncthreads();  // in-buffers read; the previous tile's write-out is done
+    for (int b = tid; b < NB; b += kPbThreads) cur[b] = 0;
+    if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPbIPT; ++j)
+      if (d[j] != kNone) atomicAdd(&cur[d[j] >> kPbBits], 1u);
+    __syncthreads();
+
+    // Block starts inside the tile; one claim per non-empty block, whose latency
+    // the shared-memory reorder below hides.
+    constexpr int PER = (NB + kPbThreads - 1) / kPbThreads;
+    uint32_t c[PER], sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int b = tid * PER + q;
+      c[q] = b < NB ? cur[b] : 0u;
+      sum += c[q];
+    }
+    uint32_t total;
+    uint32_t run = block_excl_scan<kPbThreads>(sum, scratch, &total);
+    uint32_t claim[PER], start[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int b = tid * PER + q;
+      claim[q] = 0;
+      start[q] = run;
+      if (b < NB) {
+        cur[b] = run;
+        if (c[q]) claim[q] = atomicAdd(&fill[b], c[q]);
+        run += c[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPbIPT; ++j) {
+      if (d[j] == kNone) continue;
+      const uint32_t b = d[j] >> kPbBits;
+      const uint32_t pos = atomicAdd(&cur[b], 1u);
+      skv[pos] = ((unsigned long long)v[j] << 32) | k[j];
+      spb[pos] = (d[j] & (kPbBlock - 1)) | (b << 16);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int b = tid * PER + q;
+      if (b < NB && c[q]) {
+        const int64_t lo = (int64_t)b << kPbBits;
+        const int64_t cap = min((int64_t)kPbBlock, n - lo);
+        if ((int64_t)claim[q] + c[q] > cap) {  // more elements than destinations: pi is no bijection
+          set_status(status, DEV_BAD_PERM);
+          gofs[b] = kNone;
+        } else {
+          gofs[b] = (uint32_t)(lo + claim[q]) - start[q];
+        }
+      }
+    }
+    __syncthreads();
+    // Write-out: consecutive threads take consecutive reordered elements, so the
+    // stores of one run are contiguous.  Only the `total` elements that passed the
+    // range check were reordered; entries past them are stale.
+    for (int i = tid; i < (int)total; i += kPbThreads) {
+      const uint32_t pb = spb[i];
+      const uint32_t g = gofs[pb >> 16];
+      if (g == kNone) continue;
+      const uint32_t dst = g + (uint32_t)i;
+      const unsigned long long kv = skv[i];
+      K1[dst] = (uint32_t)kv;
+      if (VB) V1[dst] = (uint32_t)(kv >> 32);
+      P1[dst] = (uint16_t)pb;
+    }
+  }
+}
+
+// Pass 2: destination block blockIdx.x.  CHECK: a bitmap of the block's offsets
+// finds a destination hit twice (with no block over-full, that is the only way pi
+// can fail to be a bijection).
+template <int VB, bool CHECK>
+__global__ void __launch_bounds__(kPlaceThreads, 1)
+    k_pb_place(const uint32_t* __restrict__ K1, const uint32_t* __restrict__ V1,
+               const uint16_t* __restrict__ P1, uint32_t* __restrict__ dk, uint32_t* __restrict__ dv,
+               int64_t n, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* xs = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* seen = xs + kPbBlock;  // CHECK only
+  const int tid = threadIdx.x;
+  const int64_t lo = (int64_t)blockIdx.x << kPbBits;
+  const int cap = (int)min((int64_t)kPbBlock, n - lo);
+  constexpr uint32_t M = kPbBlock - 1;
+  if (CHECK) {
+    for (int i = tid; i < kPbBlock / 32; i += kPlaceThreads) seen[i] = 0;
+    __syncthreads();
+  }
+  auto mark = [&](uint32_t o) {
+    const uint32_t bit = 1u << (o & 31);
+    if (atomicOr(&seen[o >> 5], bit) & bit) set_status(status, DEV_BAD_PERM);
+  };
+  const int nv = cap / 8;
+#pragma unroll 1
+  for (int round = 0; round < (VB ? 2 : 1); ++round) {
+    const uint32_t* X = round ? V1 : K1;
+    uint32_t* D = round ? dv : dk;
+    for (int t = tid; t < nv; t += kPlaceThreads) {
+      const int64_t i = lo + (int64_t)t * 8;
+      const uint4 p = __ldcs(reinterpret_cast<const uint4*>(P1 + i));
+      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(X + i));
+      const uint4 b = __ldcs(reinterpret_cast<const uint4*>(X + i + 4));
+      const uint32_t o[8] = {p.x & M, (p.x >> 16) & M, p.y & M, (p.y >> 16) & M,
+                             p.z & M, (p.z >> 16) & M, p.w & M, (p.w >> 16) & M};
+      const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        xs[o[c]] = x[c];
+        if (CHECK && round == 0) mark(o[c]);
+      }
+    }
+    for (int i = nv * 8 + tid; i < cap; i += kPlaceThreads) {
+      const uint32_t o = P1[lo + i] & M;
+      xs[o] = X[lo + i];
+      if (CHECK && round == 0) mark(o);
+    }
+    __syncthreads();
+    const int mv = cap / 4;
+    for (int t = tid; t < mv; t += kPlaceThreads)
+      __stcs(reinterpret_cast<uint4*>(D + lo) + t, reinterpret_cast<const uint4*>(xs)[t]);
+    for (int j = mv * 4 + tid; j < cap; j += kPlaceThreads) D[lo + j] = xs[j];
+    __syncthreads();
+  }
+}
+
+int sm_count_cached() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!sms[dev]) {
+    int c = 148;
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = c;
+  }
+  return sms[dev];
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, int bytes) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int VB, int NB>
+cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
+                         const uint32_t* pi, int64_t n, int64_t row_len, bool check,
+                         unsigned char* ws, cudaStream_t s) {
+  const PbLayout L = pb_layout(n, VB);
+  uint32_t* K1 = reinterpret_cast<uint32_t*>(ws + L.k1);
+  uint32_t* V1 = reinterpret_cast<uint32_t*>(ws + L.v1);
+  uint16_t* P1 = reinterpret_cast<uint16_t*>(ws + L.p1);
+  uint32_t* fill = reinterpret_cast<uint32_t*>(ws + L.fill);
+  const int blocks = (int)((n + kPbBlock - 1) >> kPbBits);
+  const int ntiles = (int)((n + kPbTile - 1) / kPbTile);
+  cudaError_t e = cudaMemsetAsync(fill, 0, (size_t)blocks * 4, s);
+  if (e != cudaSuccess) return e;
+  constexpr int sm1 = pb_smem_bytes<NB>();
+  static bool ready1 = false;
+  if (!ready1) {
+    if ((e = set_smem(k_pb_bucket<VB, NB>, sm1)) != cudaSuccess) return e;
+    ready1 = true;
+  }
+  const int grid = std::min(ntiles, sm_count_cached());
+  k_pb_bucket<VB, NB><<<grid, kPbThreads, sm1, s>>>(pi, sk, sv, K1, V1, P1, fill, n, row_len, ntiles,
+                                                    status_word());
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int sm2 = kPbBlock * 4 + (check ? kPbBlock / 8 : 0);
+  if (check) {
+    static bool ready2 = false;
+    if (!ready2) {
+      if ((e = set_smem(k_pb_place<VB, true>, sm2)) != cudaSuccess) return e;
+      ready2 = true;
+    }
+    k_pb_place<VB, true><<<blocks, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, status_word());
+  } else {
+    static bool ready2 = false;
+    if (!ready2) {
+      if ((e = set_smem(k_pb_place<VB, false>, sm2)) != cudaSuccess) return e;
+      ready2 = true;
+    }
+    k_pb_place<VB, false><<<blocks, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, status_word());
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool permute_bucketed_supported(int64_t n, int kb, int vb) {
+  return kb == 4 && (vb == 0 || vb == 4) && n > 0 && n <= (int64_t)kPbMaxBlocks * kPbBlock;
+}
+
+size_t permute_bucketed_workspace(int64_t n, int vb) { return pb_layout(n, vb).total; }
+
+cudaError_t permute_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
+                             const uint32_t* pi, int64_t n, int64_t row_len, int vb, bool check,
+                             unsigned char* ws, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const bool few = ((n + kPbBlock - 1) >> kPbBits) <= 512;
+  if (vb == 4)
+    return few ? run_bucketed<4, 512>(sk, sv, dk, dv, pi, n, row_len, check, ws, s)
+               : run_bucketed<4, 2048>(sk, sv, dk, dv, pi, n, row_len, check, ws, s);
+  return few ? run_bucketed<0, 512>(sk, sv, dk, dv, pi, n, row_len, check, ws, s)
+             : run_bucketed<0, 2048>(sk, sv, dk, dv, pi, n, row_len, check, ws, s);
+}
+
+}  // namespace bcf

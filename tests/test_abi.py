@@ -45,8 +45,19 @@ def test_workspace_queries():
     assert L.bcf_sort_workspace_size(1 << 30, 4, 32, ctypes.byref(sz)) == bcf.E_UNSUPPORTED
     assert L.bcf_partition_workspace_size(4096, 257, 4, 0, ctypes.byref(sz)) == bcf.E_UNSUPPORTED
     assert L.bcf_partition_workspace_size(4096, 0, 4, 0, ctypes.byref(sz)) == bcf.E_INVAL
-    assert L.bcf_permute_workspace_size(100, 0, ctypes.byref(sz)) == bcf.OK and sz.value == 0
-    assert L.bcf_permute_workspace_size(100, bcf.CHECK_PERM, ctypes.byref(sz)) == bcf.OK and sz.value >= 16
+    assert L.bcf_permute_workspace_size(100, 0, 0, ctypes.byref(sz)) == bcf.OK and sz.value == 0
+    assert L.bcf_permute_workspace_size(100, 0, bcf.CHECK_PERM, ctypes.byref(sz)) == bcf.OK and sz.value >= 16
+    # bucketed form: pi's low bits (2 B), keys (4 B) and payloads (vb) per element
+    assert L.bcf_permute_workspace_size(1 << 20, 4, bcf.PERMUTE_BUCKETED, ctypes.byref(sz)) == bcf.OK
+    assert sz.value >= 10 << 20
+    assert L.bcf_permute_workspace_size(1 << 20, 0, bcf.PERMUTE_BUCKETED, ctypes.byref(sz)) == bcf.OK
+    assert (6 << 20) <= sz.value < (10 << 20)
+    # beyond 2^26 elements, or with 8-byte payloads, the one-pass scatter runs: no bucketed region
+    assert L.bcf_permute_workspace_size((1 << 26) + 1, 4, bcf.PERMUTE_BUCKETED, ctypes.byref(sz)) == bcf.OK
+    assert sz.value == 0
+    assert L.bcf_permute_workspace_size(1 << 20, 8, bcf.PERMUTE_BUCKETED, ctypes.byref(sz)) == bcf.OK
+    assert sz.value == 0
+    assert L.bcf_permute_workspace_size(100, 3, 0, ctypes.byref(sz)) == bcf.E_INVAL
 
 
 def test_argument_checks_reject_without_launching():

@@ -129,3 +129,103 @@ def test_permute_tiles_reports_bad_label(bcf):
     for coloured in (False, True):
         bcf.permute_tiles(dev(synth.uniform_keys(tile + 100, seed=2)), dev(lpi), tile=tile, coloured=coloured)
         assert bcf.get_status() == bcf.E_BAD_PERM
+
+
+# ------------------------------------------------------------ bucketed form
+# Two coalesced passes: group by destination block of 2^15, then place each
+# block in shared memory.  Sizes span several 8192-element tiles and blocks and
+# end in ragged tails (n not a multiple of 4, 8192 or 2^15).
+BLOCK = 1 << 15
+
+
+@pytest.mark.parametrize("n", [1, 5, 8191, 8192, 8193, BLOCK - 3, BLOCK, BLOCK + 1, 3 * BLOCK + 4099, 300_001])
+@pytest.mark.parametrize("with_vals", [False, True])
+def test_permute_bucketed(bcf, n, with_vals):
+    keys = synth.uniform_keys(n, seed=n + 11)
+    vals = synth.float_bits_payload(n, seed=n + 12)
+    pi = synth.random_perm(n, seed=n + 13)
+    if with_vals:
+        ko, vo = bcf.permute_kv(dev(keys), dev(vals), dev(pi), bucketed=True)
+        assert bits_equal(host(vo, np.float32), oracle.permute(vals, pi))
+    else:
+        ko = bcf.permute(dev(keys), dev(pi), bucketed=True)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+
+
+@pytest.mark.parametrize("kind", ["identity", "reverse", "rotate", "transpose", "one_block_per_tile"])
+def test_permute_bucketed_structured(bcf, kind):
+    """Permutations that load blocks unevenly over time: the identity sends every
+    tile to one block, a transpose sends consecutive elements to far-apart blocks."""
+    n = 5 * BLOCK + 128
+    i = np.arange(n, dtype=np.int64)
+    if kind == "identity":
+        pi = i
+    elif kind == "reverse":
+        pi = n - 1 - i
+    elif kind == "rotate":
+        pi = (i + 12_345) % n
+    elif kind == "transpose":  # n = 64 * (n // 64): i = r * 64 + c -> c * (n // 64) + r
+        pi = (i % 64) * (n // 64) + i // 64
+    else:  # tile t of 8192 elements -> block (t * 7) mod blocks, shuffled inside
+        pi = synth.random_perm(n, seed=3).astype(np.int64)
+        pi = np.sort(pi)[np.argsort(np.argsort((i // 8192 * 7919 + i % 8192) % n, kind="stable"), kind="stable")]
+    pi = pi.astype(np.uint32)
+    assert len(np.unique(pi)) == n
+    keys = synth.uniform_keys(n, seed=4)
+    vals = synth.float_bits_payload(n, seed=5)
+    ko, vo = bcf.permute_kv(dev(keys), dev(vals), dev(pi), bucketed=True, check=True)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+    assert bits_equal(host(vo, np.float32), oracle.permute(vals, pi))
+
+
+def test_permute_bucketed_rows(bcf):
+    """Row-local permutations (row_len > 0) through the bucketed form."""
+    rows, row_len = 6, 70_001
+    n = rows * row_len
+    pi = np.concatenate([synth.random_perm(row_len, seed=r) for r in range(rows)])
+    keys = synth.uniform_keys(n, seed=7)
+    vals = synth.float_bits_payload(n, seed=8)
+    ko, vo = bcf.permute_kv(dev(keys), dev(vals), dev(pi), row_len=row_len, bucketed=True)
+    assert bcf.get_status() == bcf.OK
+    glob = (np.arange(n) // row_len * row_len + pi).astype(np.uint32)
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, glob))
+    assert bits_equal(host(vo, np.float32), oracle.permute(vals, glob))
+
+
+def test_permute_bucketed_more_than_512_blocks(bcf):
+    """Above 512 destination blocks the pass-1 kernel keeps 2048 block counters."""
+    n = 600 * BLOCK + 7
+    keys = synth.uniform_keys(n, seed=9)
+    pi = synth.random_perm(n, seed=10)
+    ko = bcf.permute(dev(keys), dev(pi), bucketed=True)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+
+
+def test_permute_bucketed_reports_non_bijection(bcf):
+    n = 3 * BLOCK + 5
+    keys = dev(synth.uniform_keys(n, seed=2))
+    for a, b in [(10, 11), (7, 3 * BLOCK)]:  # same block; different blocks (one over-full)
+        pi = synth.random_perm(n, seed=1)
+        pi[a] = pi[b]
+        bcf.permute(keys, dev(pi), check=True, bucketed=True)
+        assert bcf.get_status() == bcf.E_BAD_PERM
+    pi = synth.random_perm(n, seed=1)
+    pi[3] = n + 5  # out of range: never written, always reported
+    bcf.permute(keys, dev(pi), bucketed=True)
+    assert bcf.get_status() == bcf.E_BAD_PERM
+
+
+def test_permute_bucketed_not_applicable_runs_scatter(bcf):
+    """8-byte payloads are outside the bucketed form: the flag falls back to the
+    one-pass scatter and the result is the same."""
+    n = 50_000
+    keys = synth.uniform_keys(n, seed=1)
+    vals = synth.uniform_keys(2 * n, seed=2).view(np.uint64)
+    pi = synth.random_perm(n, seed=3)
+    ko, vo = bcf.permute_kv(dev(keys), dev(vals), dev(pi), bucketed=True)
+    assert bcf.get_status() == bcf.OK
+    assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
+    assert bits_equal(host(vo, np.uint64), oracle.permute(vals, pi))

@@ -561,20 +561,33 @@ def run_rows(which, peak):
                 vals.grad = None
                 _, y = autograd.sort_by_key(keys, vals, 20)
                 y.backward(g)
+
+            def fwd():
+                with torch.no_grad():
+                    autograd.sort_by_key(keys, vals, 20)
             ms_eager, _ = ev_ms(fb, 3, 10)
             ms, _ = graph_ms(fb, 3, 10)
-            # plain form: one key-value sort of the same 2^22 keys (20-bit keys)
+            ms_fwd, _ = graph_ms(fwd, 3, 10)
+            # plain forms: the same per-row sort of the float values as one segmented
+            # key-value sort (no autograd), and one flat kv sort of all 2^22 keys
             kf = keys.reshape(-1)
-            vf = to_dev(synth.index_payload(B * n))
+            vf = vals.detach().reshape(-1)
+            offs = autograd._row_offsets(B, n, kf.device)
             ko, vo = torch.empty_like(kf), torch.empty_like(vf)
+            wss = bcf.workspace(bcf.segmented_sort_workspace_size(B * n, B, 4, 20))
+            ms_rows, _ = graph_ms(lambda: bcf.segmented_sort(kf, vf, offs, key_bits=20, keys_out=ko, vals_out=vo,
+                                                             ws=wss), 3, 10)
             ws = bcf.workspace(bcf.sort_workspace_size(B * n, 4, 20))
             ms_plain, _ = graph_ms(lambda: bcf.sort(kf, vf, key_bits=20, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
             add("autograd_sort_by_key_64x65536", B * n, B * n * (3 * 16 + 12 + 12), ms,
-                "forward (3 digit passes + gather) and backward scatter, one CUDA-graph replay (eager "
-                "%.3f ms); plain kv sort of the same keys %.4f ms -> ratio %.2f" % (ms_eager, ms_plain, ms / ms_plain))
-            rows["autograd_sort_by_key_64x65536"]["plain_sort_ms"] = round(ms_plain, 4)
-            rows["autograd_sort_by_key_64x65536"]["ratio_vs_plain"] = round(ms / ms_plain, 3)
-            rows["autograd_sort_by_key_64x65536"]["eager_ms"] = round(ms_eager, 4)
+                "forward (per-row sort with index payload + gather) and backward scatter, one CUDA-graph "
+                "replay (eager %.3f ms); forward alone %.4f ms vs the plain per-row kv sort %.4f ms; "
+                "plain flat kv sort of all keys %.4f ms" % (ms_eager, ms_fwd, ms_rows, ms_plain))
+            r = rows["autograd_sort_by_key_64x65536"]
+            r.update({"fwd_ms": round(ms_fwd, 4), "plain_rows_sort_ms": round(ms_rows, 4),
+                      "ratio_fwd_vs_plain_rows_sort": round(ms_fwd / ms_rows, 3),
+                      "plain_flat_sort_ms": round(ms_plain, 4), "ratio_fwdbwd_vs_plain_flat_sort": round(ms / ms_plain, 3),
+                      "eager_ms": round(ms_eager, 4)})
         if want("autograd_permute_rows_64x65536"):
             pi = to_dev(np.concatenate([synth.random_perm(n, seed=100 + b) for b in range(B)])).view(B, n)
 
@@ -583,14 +596,24 @@ def run_rows(which, peak):
                 autograd.permute_rows(vals, pi).backward(g)
             ms_eager, _ = ev_ms(fb2, 3, 10)
             ms, _ = graph_ms(fb2, 3, 10)
-            # plain form: one permutation of the same 2^22 values
+            # plain forms: the forward permutation alone, and forward + inverse (gather)
             vflat = vals.detach().reshape(-1)
-            yo = torch.empty_like(vflat)
-            ms_plain, _ = graph_ms(lambda: bcf.permute(vflat, pi.reshape(-1), dst=yo, row_len=n), 3, 10)
+            gflat = g.reshape(-1)
+            yo, go = torch.empty_like(vflat), torch.empty_like(vflat)
+            pflat = pi.reshape(-1)
+            ms_plain, _ = graph_ms(lambda: bcf.permute(vflat, pflat, dst=yo, row_len=n), 3, 10)
+
+            def plain_fb():
+                bcf.permute(vflat, pflat, dst=yo, row_len=n)
+                bcf.gather(gflat, pflat, dst=go, row_len=n)
+            ms_plain_fb, _ = graph_ms(plain_fb, 3, 10)
             add("autograd_permute_rows_64x65536", B * n, B * n * 24, ms,
                 "forward scatter (12 B/key) + backward gather (12 B/key), one CUDA-graph replay (eager "
-                "%.3f ms); plain permutation %.4f ms" % (ms_eager, ms_plain))
-            rows["autograd_permute_rows_64x65536"]["ratio_vs_plain_fwd"] = round(ms / ms_plain, 3)
+                "%.3f ms); plain permutation %.4f ms, plain permutation + gather %.4f ms"
+                % (ms_eager, ms_plain, ms_plain_fb))
+            rows["autograd_permute_rows_64x65536"].update(
+                {"plain_fwd_ms": round(ms_plain, 4), "plain_fwdbwd_ms": round(ms_plain_fb, 4),
+                 "ratio_vs_plain_fwdbwd": round(ms / ms_plain_fb, 3), "eager_ms": round(ms_eager, 4)})
     if "segmented_sort_batched_10k" in plain_ns and "sort_kv_2pow26_uniform" in plain_ns:
         rows["segmented_sort_batched_10k"]["ratio_vs_plain_per_key"] = round(
             plain_ns["segmented_sort_batched_10k"] / plain_ns["sort_kv_2pow26_uniform"], 3)

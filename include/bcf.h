@@ -221,6 +221,15 @@ int bcf_tune_config_info(int config, int* threads, int* keys_per_thread);
 int bcf_tune_set(int op, int log2_n, int config);
 /* The configuration a call of n keys would use now. */
 int bcf_tune_get(int op, int64_t n, int* config);
+/* Tuning cache (the library's only persistent state): bcf_tune_save writes the
+ * explicit table entries of the current device (keyed "<device name>/<SMs>sm")
+ * to the text file `path`, keeping other devices' entries already there;
+ * bcf_tune_load applies the current device's entries from `path` (*applied, if
+ * not NULL, receives how many).  Host-only; BCF_E_INVAL for an unreadable /
+ * unwritable file or a malformed entry, BCF_E_CUDA if the device cannot be
+ * queried. */
+int bcf_tune_save(const char* path);
+int bcf_tune_load(const char* path, int* applied);
 
 /* ---------------------------------------------------------------------------
  * Partition without a workspace.  The paper has no counterpart: this is a
@@ -242,6 +251,18 @@ int bcf_tune_get(int op, int64_t n, int* config);
 int bcf_partition_noalloc(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                           void* vals_out, int64_t n, int w, int val_bytes, int flags,
                           bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Testing aid for failure detection (no counterpart in the paper).  Inputs of at
+ * most 2^18 keys run each sort / partition pass as one sweep launch in which a
+ * tile waits, with a bounded number of polls, for the status words its
+ * predecessors publish.  After bcf_debug_lookback(t, polls) with t >= 0, tile t of
+ * those sweeps publishes nothing and every wait gives up after `polls` polls, so
+ * the next call ends with device status BCF_E_TIMEOUT (its output is then
+ * unspecified; nothing is written outside the output arrays) instead of hanging.
+ * t < 0 restores normal operation.  Host state, not thread-safe; meant for tests.
+ * Returns BCF_E_INVAL for polls == 0 with t >= 0. */
+int bcf_debug_lookback(int silent_tile, unsigned spin_limit);
 
 #ifdef __cplusplus
 }

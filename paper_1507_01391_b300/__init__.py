@@ -67,6 +67,9 @@ _SIGS = {
     "bcf_tune_config_info": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "bcf_tune_set": ([_I, _I, _I], _I),
     "bcf_tune_get": ([_I, _I64, ctypes.POINTER(_I)], _I),
+    "bcf_debug_lookback": ([_I, ctypes.c_uint], _I),
+    "bcf_tune_save": ([ctypes.c_char_p], _I),
+    "bcf_tune_load": ([ctypes.c_char_p, ctypes.POINTER(_I)], _I),
 }
 OP_SORT, OP_PARTITION = 0, 1
 NOALLOC_MAX_N = 1 << 22
@@ -95,9 +98,12 @@ def lib() -> ctypes.CDLL:
     return _lib
 
 
-def __getattr__(name):  # raw entry points: bcf_sort, bcf_permute, ...
+def __getattr__(name):  # raw entry points: bcf_sort, bcf_permute, ...; the autograd forms
     if name.startswith("bcf_") and name in _SIGS:
         return getattr(lib(), name)
+    if name in ("SortByKey", "PermuteFn", "sort_by_key", "permute_rows"):
+        from . import autograd
+        return getattr(autograd, name)
     raise AttributeError(name)
 
 
@@ -181,6 +187,9 @@ def sort(keys, vals=None, key_bits=32, keys_out=None, vals_out=None, ws=None, st
     _check(lib().bcf_sort(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n, vb, key_bits,
                           _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)), "bcf_sort")
     return keys_out, vals_out
+
+
+sort_kv = sort  # the key-value sort under its other name
 
 
 def partition(keys, vals, w, balanced=False, keys_out=None, vals_out=None, ws=None, stream=None,

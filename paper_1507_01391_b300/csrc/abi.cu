@@ -5,6 +5,10 @@
 // segmented.cu.  No entry point allocates device memory.
 #include <cuda_runtime.h>
 
+#include <cstdio>
+#include <string>
+#include <vector>
+
 #include "bcf.h"
 #include "common.cuh"
 #include "internal.h"
@@ -359,6 +363,80 @@ int bcf_tune_set(int op, int log2_n, int config) {
 int bcf_tune_get(int op, int64_t n, int* config) {
   if ((op != BCF_OP_SORT && op != BCF_OP_PARTITION) || n < 0 || !config) return BCF_E_INVAL;
   *config = bcf::tuned_config(op, n);
+  return BCF_OK;
+}
+
+// Tuning cache file: a text header line, then one line per explicit entry:
+// "<device name>/<SMs>sm \t op \t log2_n \t config".  Entries of other devices are
+// kept when this device's entries are rewritten.
+static bool tune_device_key(std::string* key) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return false;
+  *key = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "sm";
+  return true;
+}
+
+static const char kTuneHeader[] = "bcf-tune 1";
+
+int bcf_tune_save(const char* path) {
+  if (!path) return BCF_E_INVAL;
+  std::string key;
+  if (!tune_device_key(&key)) return BCF_E_CUDA;
+  std::vector<std::string> keep;
+  if (FILE* f = std::fopen(path, "r")) {
+    char line[512];
+    bool first = true;
+    while (std::fgets(line, sizeof line, f)) {
+      std::string l(line);
+      if (first) {
+        first = false;
+        if (l.rfind(kTuneHeader, 0) == 0) continue;
+      }
+      if (l.rfind(key + "\t", 0) != 0 && !l.empty() && l != "\n") keep.push_back(l);
+    }
+    std::fclose(f);
+  }
+  FILE* f = std::fopen(path, "w");
+  if (!f) return BCF_E_INVAL;
+  std::fprintf(f, "%s\n", kTuneHeader);
+  for (const std::string& l : keep) std::fputs(l.c_str(), f);
+  for (int op = 0; op < 2; ++op)
+    for (int b = 0; b < 64; ++b) {
+      const int c = bcf::tune_entry(op, b);
+      if (c >= 0) std::fprintf(f, "%s\t%d\t%d\t%d\n", key.c_str(), op, b, c);
+    }
+  return std::fclose(f) == 0 ? BCF_OK : BCF_E_INVAL;
+}
+
+int bcf_tune_load(const char* path, int* applied) {
+  if (!path) return BCF_E_INVAL;
+  if (applied) *applied = 0;
+  std::string key;
+  if (!tune_device_key(&key)) return BCF_E_CUDA;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return BCF_E_INVAL;
+  char line[512];
+  int count = 0;
+  bool ok = std::fgets(line, sizeof line, f) && std::string(line).rfind(kTuneHeader, 0) == 0;
+  while (ok && std::fgets(line, sizeof line, f)) {
+    std::string l(line);
+    if (l.rfind(key + "\t", 0) != 0) continue;
+    int op = -1, b = -1, c = -2;
+    if (std::sscanf(l.c_str() + key.size() + 1, "%d\t%d\t%d", &op, &b, &c) != 3 || bcf::tune_set(op, b, c) != 0) {
+      ok = false;
+      break;
+    }
+    ++count;
+  }
+  std::fclose(f);
+  if (applied) *applied = count;
+  return ok ? BCF_OK : BCF_E_INVAL;
+}
+
+int bcf_debug_lookback(int silent_tile, unsigned spin_limit) {
+  if (silent_tile >= 0 && spin_limit == 0) return BCF_E_INVAL;
+  bcf::debug_lookback(silent_tile, spin_limit);
   return BCF_OK;
 }
 

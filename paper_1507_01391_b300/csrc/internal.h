@@ -53,6 +53,7 @@ inline int sweep_cfg_tile(int cfg) { return kSweepCfgThreads[cfg] * kSweepCfgIPT
 // (op 1) of n keys.  Entries of -1 fall back to a size rule.
 int tuned_config(int op, int64_t n);
 int tune_set(int op, int log2_n, int cfg);
+int tune_entry(int op, int log2_n);  // explicit table entry, -1 if none
 
 struct PassPlan {
   int passes = 0;
@@ -96,6 +97,8 @@ cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint3
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
                     const uint32_t* pi, int64_t n, int64_t row_len, int kbytes, int vbytes,
                     uint32_t* seen_bitmap, bool fused, cudaStream_t s);
+// Testing aid for the bounded look-back waits (radix.cu).
+void debug_lookback(int silent_tile, unsigned spin_limit);
 // Two-pass bucketed permutation (permute_bucketed.cu).
 bool permute_bucketed_supported(int64_t n, int kb, int vb);
 size_t permute_bucketed_workspace(int64_t n, int vb);

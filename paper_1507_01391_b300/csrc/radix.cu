@@ -55,6 +55,12 @@ int tune_set(int op, int log2_n, int cfg) {
   return 0;
 }
 
+int tune_entry(int op, int log2_n) {
+  tune_init();
+  if ((op != 0 && op != 1) || log2_n < 0 || log2_n >= 64) return -1;
+  return g_tune[op][log2_n];
+}
+
 SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp, int tile) {
   SweepLayout L;
   L.radix = radix;
@@ -144,6 +150,17 @@ static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_
   return cudaErrorInvalidValue;
 }
 
+// Testing aid (bcf_debug_lookback): the look-back sweeps leave one tile silent and
+// give up waiting after a short poll count.
+namespace {
+int g_silent_tile1 = 0;
+unsigned g_spin_limit = 0;
+}  // namespace
+void debug_lookback(int silent_tile, unsigned spin_limit) {
+  g_silent_tile1 = silent_tile >= 0 ? silent_tile + 1 : 0;
+  g_spin_limit = silent_tile >= 0 ? spin_limit : 0;
+}
+
 // Small inputs: one sweep launch per pass with a decoupled look-back over at most
 // kSmallSweepN / kMinSweepTile tiles, after one histogram read for all passes
 // (skipped for balanced partitions, whose digit starts are closed-form).
@@ -169,6 +186,8 @@ static cudaError_t lookback_pass_t(const uint32_t* src_k, const void* src_v, uin
   sp.lb_stride = (tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;
   sp.ticket = ticket;
   sp.status = status_word();
+  sp.spin_limit = g_spin_limit;
+  sp.silent_tile1 = g_silent_tile1;
   return sweep_dispatch<BITS, THREADS, IPT>(sp, tiles, vb, s);
 }
 

@@ -53,6 +53,11 @@ struct SweepParams {
   const uint32_t* seg_base;    // slot x RADIX absolute digit starts
   const int32_t* seg_w;        // partition: labels of segment s are < seg_w[s]
   const uint32_t* num_tiles;   // tiles of this launch (device count)
+  // look-back mode only: polls before a wait gives up (0: kSpinLimit), and 1 + the
+  // index of a tile that never publishes its status (0: none) -- a testing aid that
+  // makes a later tile's bounded wait run out
+  unsigned spin_limit;
+  int silent_tile1;
 };
 
 template <int BITS>
@@ -432,7 +437,8 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
     const uint32_t tile_excl = block_excl_scan<THREADS>(tid < RADIX ? count : 0u, scratch, &total);
     uint32_t* lbd = p.lookback + (size_t)tid * p.lb_stride;  // digit-major status words
     if (tid < RADIX) {
-      if (!p.tile_offsets) st_relaxed(lbd + tile, (t_in == 0 ? LB_INC : LB_AGG) | count);
+      if (!p.tile_offsets && tile + 1 != p.silent_tile1)
+        st_relaxed(lbd + tile, (t_in == 0 ? LB_INC : LB_AGG) | count);
       tstart[tid] = tile_excl;
       uint32_t run = tile_excl;
 #pragma unroll 4
@@ -545,13 +551,13 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
           if (f == LB_INC) done = true;
         }
         if (done) break;
-        if (stalled && ++spins > kSpinLimit) {
+        if (stalled && ++spins > (p.spin_limit ? p.spin_limit : kSpinLimit)) {
           set_status(p.status, DEV_TIMEOUT);
           break;
         }
         if (!stalled && j >= ws) j = ws - 1;  // window below `first`: finished
       }
-      st_relaxed(lbd + tile, LB_INC | (excl + count));
+      if (tile + 1 != p.silent_tile1) st_relaxed(lbd + tile, LB_INC | (excl + count));
     }
     uint32_t base;  // absolute start of this digit's block
     if (p.balanced) {

@@ -4,14 +4,13 @@ Every digit pass can run with one of ``configs()`` tile shapes (threads per bloc
 keys per thread, compiled into libbcf.so).  ``autotune()`` times each shape through
 the C ABI on random keys of each requested size, keeps the fastest in the library's
 host-side table (``bcf_tune_set``) and returns the choices; ``save()``/``load()``
-keep them in a JSON file keyed by device name and SM count, so a process can load
-the table at start-up instead of measuring again.  The inputs are random keys made
+keep the table in a text file keyed by device name and SM count (``bcf_tune_save``,
+``bcf_tune_load``), so a process can load it at start-up instead of measuring again.  The inputs are random keys made
 on the device with torch; they only exist to time the kernels.
 """
 from __future__ import annotations
 
 import ctypes
-import json
 import os
 import statistics
 
@@ -124,33 +123,31 @@ def autotune(ops=("sort", "partition"), log2_sizes=range(12, 27, 2), w=256, reps
 
 
 def cache_path():
-    return os.environ.get("BCF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "bcf", "tune.json"))
+    return os.environ.get("BCF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "bcf", "tune.txt"))
 
 
-def save(result, path=None):
+def save(result=None, path=None):
+    """Write the library's explicit table entries for this device to the cache
+    file (bcf_tune_save; other devices' entries are kept).  `result` (from
+    autotune) is accepted for convenience: its choices are already in the table."""
     path = path or cache_path()
-    os.makedirs(os.path.dirname(path), exist_ok=True)
-    data = {}
-    if os.path.exists(path):
-        with open(path) as f:
-            data = json.load(f)
-    data[_device_key()] = {op: {str(k): v[0] for k, v in tab.items()} for op, tab in result.items()}
-    with open(path, "w") as f:
-        json.dump(data, f, indent=1, sort_keys=True)
+    d = os.path.dirname(path)
+    if d:
+        os.makedirs(d, exist_ok=True)
+    rc = lib().bcf_tune_save(path.encode())
+    if rc != OK:
+        raise BcfError(rc, "bcf_tune_save")
     return path
 
 
 def load(path=None) -> bool:
-    """Apply the cached table of this device, if any; returns whether one was found."""
+    """Apply this device's cached entries (bcf_tune_load); returns whether any
+    were found."""
     path = path or cache_path()
     if not os.path.exists(path):
         return False
-    with open(path) as f:
-        data = json.load(f)
-    tab = data.get(_device_key())
-    if not tab:
-        return False
-    for op, entries in tab.items():
-        for k, c in entries.items():
-            set_config(op, int(k), int(c))
-    return True
+    applied = ctypes.c_int(0)
+    rc = lib().bcf_tune_load(path.encode(), ctypes.byref(applied))
+    if rc != OK:
+        raise BcfError(rc, "bcf_tune_load")
+    return applied.value > 0

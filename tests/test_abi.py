@@ -141,3 +141,14 @@ def test_tuning_table_on_the_host():
     assert L.bcf_tune_set(bcf.OP_SORT, 64, 0) == bcf.E_INVAL
     assert L.bcf_tune_set(bcf.OP_SORT, 3, nconf) == bcf.E_INVAL
     assert L.bcf_tune_set(7, 3, 0) == bcf.E_INVAL
+    # the cache file needs the device's name, so only the argument checks run here
+    applied = ctypes.c_int(-1)
+    assert L.bcf_tune_save(None) == bcf.E_INVAL
+    assert L.bcf_tune_load(None, ctypes.byref(applied)) == bcf.E_INVAL
+
+
+def test_lookback_testing_aid_arguments():
+    """bcf_debug_lookback is host state: a silent tile needs a poll limit."""
+    L = bcf.lib()
+    assert L.bcf_debug_lookback(3, 0) == bcf.E_INVAL
+    assert L.bcf_debug_lookback(-1, 0) == bcf.OK

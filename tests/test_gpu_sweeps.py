@@ -199,3 +199,29 @@ def test_partition_lemma1_reports_bad_label(bcf):
     keys[123] = 40
     bcf.partition(dev(keys), None, 16, flags=bcf.PARTITION_LEMMA1)
     assert bcf.get_status() == bcf.E_BAD_KEY
+
+
+# ------------------------------------------------------ bounded look-back waits
+@pytest.mark.parametrize("op", ["partition", "sort"])
+def test_lookback_wait_gives_up(bcf, op):
+    """A tile that never publishes its status makes the next tiles' waits run out:
+    the call ends with BCF_E_TIMEOUT after a bounded number of polls instead of
+    hanging, and the library works normally afterwards."""
+    n, w = 65536, 32  # <= 2^18 keys: one look-back sweep per pass, several tiles
+    keys = synth.partition_keys(n, w, seed=77) if op == "partition" else synth.uniform_keys(n, seed=78)
+    vals = synth.index_payload(n)
+    L = bcf.lib()
+    assert L.bcf_debug_lookback(3, 0) == bcf.E_INVAL
+    assert L.bcf_debug_lookback(3, 4096) == bcf.OK
+    try:
+        if op == "partition":
+            bcf.partition(dev(keys), dev(vals), w, balanced=True)
+        else:
+            bcf.sort(dev(keys), dev(vals))
+        assert bcf.get_status() == bcf.E_TIMEOUT
+    finally:
+        assert L.bcf_debug_lookback(-1, 0) == bcf.OK
+    if op == "partition":
+        _partition_case(bcf, keys, vals, w, True)
+    else:
+        _sort_case(bcf, keys, vals)

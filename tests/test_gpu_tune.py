@@ -50,8 +50,24 @@ def test_autotune_and_cache(bcf, tmp_path):
             best, times = res[op][k]
             assert best == min(times, key=times.get)
             assert tune.get_config(op, 1 << k) == best
-    path = tune.save(res, str(tmp_path / "tune.json"))
+    path = tune.save(res, str(tmp_path / "tune.txt"))
     for op in ("sort", "partition"):
         tune.set_config(op, 14, -1)
     assert tune.load(path)
     assert tune.get_config("sort", 1 << 14) == res["sort"][14][0]
+
+
+def test_tune_cache_keeps_other_devices(bcf, tmp_path):
+    """bcf_tune_save rewrites only this device's lines of the cache file."""
+    from paper_1507_01391_b300 import tune
+    path = tmp_path / "tune.txt"
+    path.write_text("bcf-tune 1\nOther GPU/7sm\t0\t20\t2\n")
+    tune.set_config("sort", 20, 3)
+    tune.save(path=str(path))
+    lines = path.read_text().splitlines()
+    assert lines[0] == "bcf-tune 1" and "Other GPU/7sm\t0\t20\t2" in lines
+    mine = [ln for ln in lines[1:] if not ln.startswith("Other GPU")]
+    assert any(ln.endswith("\t0\t20\t3") for ln in mine)
+    tune.set_config("sort", 20, -1)
+    assert tune.load(str(path)) and tune.get_config("sort", 1 << 20) == 3
+    tune.set_config("sort", 20, -1)

@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kPbBits = 15;                 // destinations per block: 2^15
 constexpr int kPbBlock = 1 << kPbBits;
-constexpr int kPbThreads = 512, kPbIPT = 16;
+constexpr int kPbThreads = 1024, kPbIPT = 8;
 constexpr int kPbTile = kPbThreads * kPbIPT;  // 8192 elements per pass-1 tile
 constexpr int kPbMaxBlocks = 2048;          // n <= 2^26
 constexpr int kPlaceThreads = 1024;
@@ -169,13 +169,17 @@ __global__ void __launch_bounds__(kPbThreads, 1)
       }
     }
     __syncthreads();
+    {
+      uint32_t pos[kPbIPT];
 #pragma unroll
-    for (int j = 0; j < kPbIPT; ++j) {
-      if (d[j] == kNone) continue;
-      const uint32_t b = d[j] >> kPbBits;
-      const uint32_t pos = atomicAdd(&cur[b], 1u);
-      skv[pos] = ((unsigned long long)v[j] << 32) | k[j];
-      spb[pos] = (d[j] & (kPbBlock - 1)) | (b << 16);
+      for (int j = 0; j < kPbIPT; ++j)  // every claim first, so none waits behind a store
+        pos[j] = d[j] != kNone ? atomicAdd(&cur[d[j] >> kPbBits], 1u) : 0u;
+#pragma unroll
+      for (int j = 0; j < kPbIPT; ++j) {
+        if (d[j] == kNone) continue;
+        skv[pos[j]] = ((unsigned long long)v[j] << 32) | k[j];
+        spb[pos[j]] = (d[j] & (kPbBlock - 1)) | ((d[j] >> kPbBits) << 16);
+      }
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
@@ -195,15 +199,28 @@ __global__ void __launch_bounds__(kPbThreads, 1)
     // Write-out: consecutive threads take consecutive reordered elements, so the
     // stores of one run are contiguous.  Only the `total` elements that passed the
     // range check were reordered; entries past them are stale.
-    for (int i = tid; i < (int)total; i += kPbThreads) {
-      const uint32_t pb = spb[i];
-      const uint32_t g = gofs[pb >> 16];
-      if (g == kNone) continue;
-      const uint32_t dst = g + (uint32_t)i;
-      const unsigned long long kv = skv[i];
-      K1[dst] = (uint32_t)kv;
-      if (VB) V1[dst] = (uint32_t)(kv >> 32);
-      P1[dst] = (uint16_t)pb;
+    const int tot = (int)total;
+    constexpr int U = 4;  // loads of U elements first, then their stores
+    for (int i0 = tid; i0 < tot; i0 += U * kPbThreads) {
+      uint32_t pb[U], g[U];
+      unsigned long long kv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * kPbThreads;
+        pb[u] = i < tot ? spb[i] : 0u;
+        kv[u] = i < tot ? skv[i] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) g[u] = gofs[pb[u] >> 16];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * kPbThreads;
+        if (i >= tot || g[u] == kNone) continue;
+        const uint32_t dst = g[u] + (uint32_t)i;
+        K1[dst] = (uint32_t)kv[u];
+        if (VB) V1[dst] = (uint32_t)(kv[u] >> 32);
+        P1[dst] = (uint16_t)pb[u];
+      }
     }
   }
 }
@@ -236,18 +253,28 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
   for (int round = 0; round < (VB ? 2 : 1); ++round) {
     const uint32_t* X = round ? V1 : K1;
     uint32_t* D = round ? dv : dk;
-    for (int t = tid; t < nv; t += kPlaceThreads) {
-      const int64_t i = lo + (int64_t)t * 8;
-      const uint4 p = __ldcs(reinterpret_cast<const uint4*>(P1 + i));
-      const uint4 a = __ldcs(reinterpret_cast<const uint4*>(X + i));
-      const uint4 b = __ldcs(reinterpret_cast<const uint4*>(X + i + 4));
-      const uint32_t o[8] = {p.x & M, (p.x >> 16) & M, p.y & M, (p.y >> 16) & M,
-                             p.z & M, (p.z >> 16) & M, p.w & M, (p.w >> 16) & M};
-      const uint32_t x[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    // Two groups of 8 per thread per step, every load issued before any store.
+    for (int t = tid; t < nv; t += 2 * kPlaceThreads) {
+      const bool two = t + kPlaceThreads < nv;
+      uint4 p[2], a[2], b[2];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        xs[o[c]] = x[c];
-        if (CHECK && round == 0) mark(o[c]);
+      for (int h = 0; h < 2; ++h) {
+        const int64_t i = lo + (int64_t)(h && two ? t + kPlaceThreads : t) * 8;
+        p[h] = __ldcs(reinterpret_cast<const uint4*>(P1 + i));
+        a[h] = __ldcs(reinterpret_cast<const uint4*>(X + i));
+        b[h] = __ldcs(reinterpret_cast<const uint4*>(X + i + 4));
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h && !two) break;
+        const uint32_t o[8] = {p[h].x & M, (p[h].x >> 16) & M, p[h].y & M, (p[h].y >> 16) & M,
+                               p[h].z & M, (p[h].z >> 16) & M, p[h].w & M, (p[h].w >> 16) & M};
+        const uint32_t x[8] = {a[h].x, a[h].y, a[h].z, a[h].w, b[h].x, b[h].y, b[h].z, b[h].w};
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          xs[o[c]] = x[c];
+          if (CHECK && round == 0) mark(o[c]);
+        }
       }
     }
     for (int i = nv * 8 + tid; i < cap; i += kPlaceThreads) {

@@ -451,7 +451,8 @@ def run_rows(which, peak):
         ms, _ = graph_ms(lambda: bcf.partition(ku, v, w, keys_out=ko, vals_out=vo, ws=ws), 3, 20, inner=20)
         add("partition_w32_n65536_unbalanced", n, 20 * n, ms, "histogram read + one sweep; graph replay")
     if any(want(r) for r in ("permute_kv_2pow24", "permute_kv_scatter_2pow24", "permute_kv_fused_2pow24",
-                             "permute_keys_2pow24", "tile_permute_scatter_2pow24", "tile_permute_coloured_2pow24")):
+                             "permute_keys_2pow24", "tile_permute_scatter_2pow24", "tile_permute_coloured_2pow24",
+                             "tile_permute_coloured_sorted_finish_2pow24")):
         n = N_PERM
         k = to_dev(synth.uniform_keys(n, seed=1))
         v = to_dev(synth.float_bits_payload(n, seed=2))
@@ -474,10 +475,11 @@ def run_rows(which, peak):
             ms, _ = ev_ms(lambda: bcf.permute(k, pi, dst=ko, bucketed=False))
             add("permute_keys_scatter_2pow24", n, 12 * n, ms, "keys only, one scatter pass")
         lpi = to_dev(synth.tile_local_perms(n, TILE, seed=4))
-        for coloured in (False, True):
-            name = "tile_permute_%s_2pow24" % ("coloured" if coloured else "scatter")
+        for coloured, finish in ((False, "greedy"), (True, "greedy"), (True, "sorted")):
+            name = "tile_permute_%s_2pow24" % ("scatter" if not coloured else
+                                               "coloured" if finish == "greedy" else "coloured_sorted_finish")
             if want(name):
-                ms, _ = ev_ms(lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=coloured, dst=ko))
+                ms, _ = ev_ms(lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=coloured, dst=ko, finish=finish))
                 add(name, n, 10 * n, ms)
         del k, v, pi, ko, vo, lpi
     for kind in ("uniform", "zipf"):

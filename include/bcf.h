@@ -60,6 +60,7 @@ typedef struct CUstream_st* bcf_stream_t;
 #define BCF_PARTITION_LEMMA1 0x20 /* partition: Lemma 1 tile schedule */
 #define BCF_PERMUTE_FUSED 0x40    /* permute_kv: one pass for keys and payloads */
 #define BCF_PERMUTE_BUCKETED 0x80 /* permute: two coalesced passes through ws */
+#define BCF_TILES_SORTED_FINISH 0x100 /* permute_tiles, coloured: Sec. 3 finishing step */
 
 /* Message for a status code (static string; never NULL). */
 const char* bcf_status_string(int status);
@@ -154,8 +155,13 @@ int bcf_permute_kv(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, vo
  * flags BCF_TILES_COLOURED selects the randomized colouring schedule of Sec. 3
  * (colour k = (j - h(i)) mod m; conflict-free sends; leftovers retried with a
  * fresh h, then sent one bank at a time), seeded by `seed`; otherwise a direct
- * scatter into shared memory.  Results are identical either way.  A local index
- * outside the tile sets BCF_E_BAD_PERM and is not written. */
+ * scatter into shared memory.  With BCF_TILES_COLOURED, BCF_TILES_SORTED_FINISH
+ * sends the leftovers as the finishing step of Sec. 3 does instead: sorted by
+ * destination (bank, slot), packed into ceil(L/32) columns, and sent in three
+ * conflict-free groups (labels whose bank is private to their row; each row's
+ * first and last destination banks, the label of slot j in step j).  Results are
+ * identical either way.  A local index outside the tile sets BCF_E_BAD_PERM and
+ * is not written. */
 int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
                       int tile, int flags, uint64_t seed, bcf_stream_t stream);
 

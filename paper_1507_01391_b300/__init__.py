@@ -29,6 +29,7 @@ TILES_COLOURED = 0x10
 PARTITION_LEMMA1 = 0x20
 PERMUTE_FUSED = 0x40
 PERMUTE_BUCKETED = 0x80
+TILES_SORTED_FINISH = 0x100
 # Sizes from which permute()/permute_kv() pick the bucketed form by default.
 BUCKETED_MIN_N = 1 << 20
 BUCKETED_MAX_N = 1 << 26
@@ -264,11 +265,16 @@ def permute_kv(keys, vals, pi, keys_out=None, vals_out=None, check=False, row_le
     return keys_out, vals_out
 
 
-def permute_tiles(src, lpi, tile=4096, coloured=False, seed=0x150701391, dst=None, stream=None):
-    """Tile-local permutation by uint16 local labels (bcf_permute_tiles)."""
+def permute_tiles(src, lpi, tile=4096, coloured=False, seed=0x150701391, dst=None, stream=None,
+                  finish="greedy"):
+    """Tile-local permutation by uint16 local labels (bcf_permute_tiles).  With
+    coloured=True, finish="sorted" sends the leftovers by the three-group
+    finishing step instead of greedily."""
     torch = _torch()
     dst = torch.empty_like(src) if dst is None else dst
-    flags = TILES_COLOURED if coloured else 0
+    if finish not in ("greedy", "sorted"):
+        raise ValueError("finish must be 'greedy' or 'sorted'")
+    flags = (TILES_COLOURED if coloured else 0) | (TILES_SORTED_FINISH if finish == "sorted" else 0)
     _check(lib().bcf_permute_tiles(_ptr(src), _ptr(dst), _ptr(lpi), src.numel(), tile, flags,
                                    seed & 0xFFFFFFFFFFFFFFFF, _stream(stream)), "bcf_permute_tiles")
     return dst

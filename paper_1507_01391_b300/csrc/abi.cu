@@ -249,6 +249,7 @@ int bcf_permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, i
   if (!disjoint(src, (size_t)n * 4, dst, (size_t)n * 4)) return BCF_E_INVAL;
   if (!device_ready()) return BCF_E_CUDA;
   return cuda_rc(bcf::permute_tiles(src, dst, lpi, n, tile, (flags & BCF_TILES_COLOURED) != 0,
+                                    (flags & BCF_TILES_SORTED_FINISH) != 0,
                                     seed, (cudaStream_t)stream));
 }
 

@@ -108,7 +108,7 @@ cudaError_t permute_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* d
 cudaError_t gather(const void* src, void* dst, const uint32_t* idx, int64_t n, int64_t n_src,
                    int64_t row_len, int elem_bytes, cudaStream_t s);
 cudaError_t permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
-                          int tile, bool coloured, uint64_t seed, cudaStream_t s);
+                          int tile, bool coloured, bool sorted_finish, uint64_t seed, cudaStream_t s);
 
 // ---------------------------------------------------------------- segments
 struct SegLayout {

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
     k_pb_place(const uint32_t* __restrict__ K1, const uint32_t* __restrict__ V1,
                const uint16_t* __restrict__ P1, uint32_t* __restrict__ dk, uint32_t* __restrict__ dv,
                int64_t n, unsigned* status) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   uint32_t* xs = reinterpret_cast<uint32_t*>(smem);
   uint32_t* seen = xs + kPbBlock;  // CHECK only
   const int tid = threadIdx.x;

@@ -15,8 +15,13 @@
 //                (the CAC argument of the Communication step).  Each row sends
 //                at most one item of each colour per round; items whose colour
 //                was already taken are retried next round with a fresh h (the
-//                Synchronization loop), and the few left after the last round
-//                are sent greedily, one item per destination bank per request.
+//                Synchronization loop).  The few left after the last round are
+//                either sent greedily, one item per destination bank per request,
+//                or (sorted finish) packed into a matrix sorted by destination and
+//                sent in the three groups of the paper's finishing step: labels
+//                whose destination bank is private to their row go first in any
+//                order, then a row's first and last destination banks, the label
+//                of slot j in step j.
 #include "common.cuh"
 #include "internal.h"
 #include "trace.cuh"
@@ -45,6 +50,11 @@ struct TPSmem {
   static constexpr size_t tbl = mbar + 16;
   static constexpr size_t lab = tbl + (size_t)T * 4;    // labels widened to one word each
   static constexpr size_t bytes_coloured = lab + (size_t)T * 4;
+  // sorted finish: bitmap of the (bank, slot) label space and scan scratch; the
+  // source positions reuse lpi, the packed labels lab and the packed keys tbl
+  static constexpr size_t bits = bytes_coloured;
+  static constexpr size_t scr = bits + (size_t)(T / 32) * 4;
+  static constexpr size_t bytes_sorted = scr + 8 * 4;
 };
 
 // Stage the tile's keys and local labels into shared memory.  Returns len.
@@ -115,12 +125,146 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_scatter(const uint32_t* __r
 // Coloured schedule.  Thread (warp g, lane l) owns row l's slots [g*M/4, (g+1)*M/4)
 // and, in the send phase, colours [g*M/4, (g+1)*M/4).  Table entry tbl[k*32 + l]
 // holds the item of colour k that row l sends this round: (label << 8) | slot.
+// Sorted finish for the items still pending after the colouring rounds (the
+// finishing step of Sec. 3).  The pending labels (i, j) -- destination bank i,
+// slot j -- are ordered lexicographically by counting over the label space (a
+// bitmap; labels are distinct integers below T), packed row-major into ceil(L/32)
+// columns with row r in bank r, and sent in three conflict-free phases:
+//  * middle labels of row r (bank neither r's first nor its last destination):
+//    no other row holds a label for that bank, so every row sends one per step;
+//  * first-group labels (bank = the row's first destination), label (i, j) in
+//    step j: two rows sending in one step would need the same (i, j);
+//  * last-group labels, likewise.
+// Returns nothing; every pending item is written to out_s.
+template <int T>
+__device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* in_s, uint32_t* out_s,
+                                              unsigned char* smem) {
+  using S = TPSmem<T>;
+  constexpr int M = S::M, WARPS = kTPThreads / 32, SPW = M / WARPS, NW = T / 32;
+  const uint32_t* lab = reinterpret_cast<const uint32_t*>(smem + S::lab);
+  uint16_t* src_of = reinterpret_cast<uint16_t*>(smem + S::lpi);  // staged labels no longer needed
+  uint32_t* bits = reinterpret_cast<uint32_t*>(smem + S::bits);
+  uint32_t* pkl = reinterpret_cast<uint32_t*>(smem + S::lab);     // filled after lab is read
+  uint32_t* pkk = reinterpret_cast<uint32_t*>(smem + S::tbl);     // colour table no longer needed
+  uint32_t* scr = reinterpret_cast<uint32_t*>(smem + S::scr);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int w = tid; w < NW; w += kTPThreads) {
+    BCF_TR(&bits[w], 4, 1, TS_COL_TABLE);
+    bits[w] = 0;
+  }
+  __syncthreads();
+  // Key of label p = j*32 + i in destination order: i*M + j.
+  for (uint32_t pend = pending; pend; pend &= pend - 1) {
+    const int s = warp * SPW + __ffs(pend) - 1, q = s * 32 + lane;
+    BCF_TR(&lab[q], 4, 0, TS_COL_READ);
+    const uint32_t p = lab[q];
+    const uint32_t key = (p & 31u) * M + (p >> 5);
+    BCF_TR(&bits[key >> 5], 4, 2, TS_COL_PACK);
+    atomicOr(&bits[key >> 5], 1u << (key & 31));
+    BCF_TR_WORD(&src_of[key], 1, TS_COL_PACK);
+    src_of[key] = (uint16_t)q;
+  }
+  __syncthreads();
+  // Ranks: exclusive scan of the words' popcounts (one word per thread).
+  uint32_t word = 0;
+  if (tid < NW) {
+    BCF_TR(&bits[tid], 4, 0, TS_COL_TABLE);
+    word = bits[tid];
+  }
+  const uint32_t c = __popc(word);
+  uint32_t x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scr[warp] = x;
+  __syncthreads();
+  uint32_t before = 0, total = 0;
+#pragma unroll
+  for (int g = 0; g < WARPS; ++g) {
+    const uint32_t t = scr[g];
+    if (g < warp) before += t;
+    total += t;
+  }
+  __syncthreads();
+  const int L = (int)total;
+  if (L == 0) return;
+  const int C = (L + 31) / 32;  // columns of the packed matrix
+  uint32_t rank = before + x - c;
+  for (uint32_t b = word; b; b &= b - 1, ++rank) {
+    const uint32_t key = (uint32_t)tid * 32 + (uint32_t)(__ffs(b) - 1);
+    const uint32_t p = (key % M) * 32 + key / M;  // back to the label
+    const int r = (int)rank / C, t = (int)rank % C;
+    BCF_TR_WORD(&src_of[key], 0, TS_COL_PACK);
+    const uint32_t q = src_of[key];
+    BCF_TR(&in_s[q], 4, 0, TS_COL_PACK);
+    BCF_TR(&pkl[t * 32 + r], 4, 1, TS_COL_PACK);
+    pkl[t * 32 + r] = p;
+    BCF_TR(&pkk[t * 32 + r], 4, 1, TS_COL_PACK);
+    pkk[t * 32 + r] = in_s[q];
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  // Row `lane` of the packed matrix lives in bank `lane`.
+  const int nr = max(0, min(C, L - lane * C));
+  uint32_t i_first = 32, i_last = 32;
+  if (nr > 0) {
+    BCF_TR(&pkl[lane], 4, 0, TS_COL_READ);
+    i_first = pkl[lane] & 31u;
+    BCF_TR(&pkl[(nr - 1) * 32 + lane], 4, 0, TS_COL_READ);
+    i_last = pkl[(nr - 1) * 32 + lane] & 31u;
+  }
+  auto send = [&](int t) {
+    BCF_TR(&pkl[t * 32 + lane], 4, 0, TS_COL_READ);
+    const uint32_t p = pkl[t * 32 + lane];
+    BCF_TR(&pkk[t * 32 + lane], 4, 0, TS_COL_READ);
+    const uint32_t v = pkk[t * 32 + lane];
+    BCF_TR(&out_s[p], 4, 1, TS_COL_FINISH);
+    out_s[p] = v;
+  };
+  for (int t = 0; t < C; ++t) {  // middle labels, one per row per step
+    bool go = false;
+    if (t < nr) {
+      BCF_TR(&pkl[t * 32 + lane], 4, 0, TS_COL_READ);
+      const uint32_t i = pkl[t * 32 + lane] & 31u;
+      go = i != i_first && i != i_last;
+    }
+    if (go) send(t);
+  }
+  // First group: a prefix sorted by slot; label (i_first, j) goes in step j.
+  // Steps past every row's last first-group label are skipped.
+  int nf = 0;
+  while (nf < nr && (pkl[nf * 32 + lane] & 31u) == i_first) ++nf;
+  int cur = 0;
+  for (int j = 0; j < M && __any_sync(0xffffffffu, cur < nf); ++j) {
+    bool go = false;
+    if (cur < nf) {
+      BCF_TR(&pkl[cur * 32 + lane], 4, 0, TS_COL_READ);
+      go = (int)(pkl[cur * 32 + lane] >> 5) == j;
+    }
+    if (go) send(cur++);
+  }
+  // Last group (when the row has a different last destination): a suffix.
+  int beg = nr;
+  if (i_last != i_first)
+    while (beg > 0 && (pkl[(beg - 1) * 32 + lane] & 31u) == i_last) --beg;
+  for (int j = 0; j < M && __any_sync(0xffffffffu, beg < nr); ++j) {
+    bool go = false;
+    if (beg < nr) {
+      BCF_TR(&pkl[beg * 32 + lane], 4, 0, TS_COL_READ);
+      go = (int)(pkl[beg * 32 + lane] >> 5) == j;
+    }
+    if (go) send(beg++);
+  }
+}
+
 template <int T>
 __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __restrict__ src,
                                                               uint32_t* __restrict__ dst,
                                                               const uint16_t* __restrict__ lpi,
                                                               int64_t n, uint64_t seed,
-                                                              int rounds, unsigned* status) {
+                                                              int rounds, int sorted, unsigned* status) {
   using S = TPSmem<T>;
   constexpr int M = S::M;          // columns (slots per bank) = colours
   constexpr int WARPS = kTPThreads / 32;
@@ -198,6 +342,10 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
     __syncthreads();
   }
 
+  if (sorted) {
+    sorted_finish<T>(pending, in_s, out_s, smem);
+    pending = 0;
+  }
   // Finish: greedy conflict-free sends.  Each lane offers its next pending item;
   // among lanes aiming at one destination bank only the lowest sends.
   while (__any_sync(0xffffffffu, pending != 0)) {
@@ -220,13 +368,14 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
 
 template <int T>
 static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi,
-                                int64_t n, bool coloured, uint64_t seed, cudaStream_t s) {
+                                int64_t n, bool coloured, bool sorted, uint64_t seed, cudaStream_t s) {
   using S = TPSmem<T>;
   const int64_t tiles = (n + T - 1) / T;
   if (coloured) {
     auto k = k_tile_coloured<T>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_coloured);
-    k<<<(unsigned)tiles, kTPThreads, S::bytes_coloured, s>>>(src, dst, lpi, n, seed, 3, status_word());
+    const int bytes = (int)(sorted ? S::bytes_sorted : S::bytes_coloured);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_sorted);
+    k<<<(unsigned)tiles, kTPThreads, bytes, s>>>(src, dst, lpi, n, seed, 3, sorted ? 1 : 0, status_word());
   } else {
     auto k = k_tile_scatter<T>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
@@ -236,12 +385,12 @@ static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16
 }
 
 cudaError_t permute_tiles(const uint32_t* src, uint32_t* dst, const uint16_t* lpi, int64_t n,
-                          int tile, bool coloured, uint64_t seed, cudaStream_t s) {
+                          int tile, bool coloured, bool sorted, uint64_t seed, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   switch (tile) {
-    case 1024: return launch_tiles<1024>(src, dst, lpi, n, coloured, seed, s);
-    case 2048: return launch_tiles<2048>(src, dst, lpi, n, coloured, seed, s);
-    case 4096: return launch_tiles<4096>(src, dst, lpi, n, coloured, seed, s);
+    case 1024: return launch_tiles<1024>(src, dst, lpi, n, coloured, sorted, seed, s);
+    case 2048: return launch_tiles<2048>(src, dst, lpi, n, coloured, sorted, seed, s);
+    case 4096: return launch_tiles<4096>(src, dst, lpi, n, coloured, sorted, seed, s);
   }
   return cudaErrorInvalidValue;
 }

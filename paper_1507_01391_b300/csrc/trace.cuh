@@ -28,7 +28,8 @@ enum TraceSite : uint32_t {
   TS_COL_TABLE = 20,    // colouring: table reset / claims
   TS_COL_SEND = 21,     // colouring: conflict-free sends
   TS_COL_READ = 22,     // colouring: reading own row (labels, items)
-  TS_COL_FINISH = 23,   // colouring: greedy finishing sends
+  TS_COL_FINISH = 23,   // colouring: finishing sends (greedy or sorted)
+  TS_COL_PACK = 24,     // colouring, sorted finish: ordering and packing the leftovers
 };
 
 #ifdef BCF_TRACE

@@ -82,20 +82,23 @@ def test_gather_reports_out_of_range(bcf):
 
 
 # ------------------------------------------------------------ tile-local
-@pytest.mark.parametrize("coloured", [False, True])
+SCHEDULES = [(False, "greedy"), (True, "greedy"), (True, "sorted")]
+
+
+@pytest.mark.parametrize("coloured,finish", SCHEDULES)
 @pytest.mark.parametrize("tile", [1024, 2048, 4096])
 @pytest.mark.parametrize("n_tiles,extra", [(1, 0), (3, 0), (5, 77), (0, 33)])
-def test_permute_tiles(bcf, coloured, tile, n_tiles, extra):
+def test_permute_tiles(bcf, coloured, finish, tile, n_tiles, extra):
     n = n_tiles * tile + extra
     src = synth.uniform_keys(n, seed=n + tile)
     lpi = synth.tile_local_perms(n, tile, seed=n)
-    out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured)
+    out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured, finish=finish)
     assert bcf.get_status() == bcf.OK
     assert bits_equal(host(out, np.uint32), oracle.permute_tiles(src, lpi, tile))
 
 
-@pytest.mark.parametrize("coloured", [False, True])
-def test_permute_tiles_structured(bcf, coloured):
+@pytest.mark.parametrize("coloured,finish", SCHEDULES)
+def test_permute_tiles_structured(bcf, coloured, finish):
     """Adversarial labels for the colouring: identity, reversal, a transpose of
     the 32 x 128 bank matrix (every row sends all its items to one bank), and all
     items of a row aimed at one slot column."""
@@ -106,18 +109,18 @@ def test_permute_tiles_structured(bcf, coloured):
         lpi = np.asarray(lab, dtype=np.uint16)
         assert len(np.unique(lpi)) == tile
         src = synth.uniform_keys(tile, seed=5)
-        out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured, seed=123)
+        out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured, seed=123, finish=finish)
         assert bits_equal(host(out, np.uint32), oracle.permute_tiles(src, lpi, tile))
     assert bcf.get_status() == bcf.OK
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("coloured", [False, True])
-def test_permute_tiles_full_size(bcf, coloured):
+@pytest.mark.parametrize("coloured,finish", SCHEDULES)
+def test_permute_tiles_full_size(bcf, coloured, finish):
     n, tile = 1 << 24, 4096
     src = synth.uniform_keys(n, seed=0x1D)
     lpi = synth.tile_local_perms(n, tile, seed=0x1E)
-    out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured)
+    out = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=coloured, finish=finish)
     assert bcf.get_status() == bcf.OK
     assert bits_equal(host(out, np.uint32), oracle.permute_tiles(src, lpi, tile))
 
@@ -126,8 +129,9 @@ def test_permute_tiles_reports_bad_label(bcf):
     tile = 1024
     lpi = synth.tile_local_perms(tile + 100, tile, seed=1)
     lpi[tile + 5] = 500  # outside the 100-item ragged tile
-    for coloured in (False, True):
-        bcf.permute_tiles(dev(synth.uniform_keys(tile + 100, seed=2)), dev(lpi), tile=tile, coloured=coloured)
+    for coloured, finish in SCHEDULES:
+        bcf.permute_tiles(dev(synth.uniform_keys(tile + 100, seed=2)), dev(lpi), tile=tile, coloured=coloured,
+                          finish=finish)
         assert bcf.get_status() == bcf.E_BAD_PERM
 
 

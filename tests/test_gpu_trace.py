@@ -82,6 +82,29 @@ def test_coloured_sends_meet_the_conflict_avoidance_condition(tr):
     assert _replay(tr, rec)["hw_conflicts"] == 0
 
 
+@pytest.mark.parametrize("tile", [1024, 4096])
+def test_sorted_finish_sends_meet_the_conflict_avoidance_condition(tr, tile):
+    """The finishing step of Sec. 3: leftovers sorted by destination and sent in
+    three groups.  Every finishing send request touches distinct banks (strict
+    rule); only the ordering/packing step may conflict."""
+    import paper_1507_01391_b300 as bcf
+    lpi = synth.tile_local_perms(4 * tile, tile, seed=5)
+    src = synth.uniform_keys(4 * tile, seed=6)
+    out = {}
+
+    def run():
+        out["y"] = bcf.permute_tiles(dev(src), dev(lpi), tile=tile, coloured=True, seed=11, finish="sorted")
+    rec, _ = tr.capture(run)
+    assert bits_equal(host(out["y"], np.uint32), oracle.permute_tiles(src, lpi, tile))
+    fin = _replay(tr, rec, "col_finish")  # random permutations leave a few items per tile
+    assert fin is not None and fin["requests"] > 0, "no leftovers reached the finishing step"
+    assert fin["hw_conflicts"] == 0 and fin["strict_conflicts"] == 0, fin
+    for site in ("col_send", "col_read"):
+        r = _replay(tr, rec, site)
+        assert r is None or r["hw_conflicts"] == 0, (site, r)
+    assert _replay(tr, rec, "col_pack") is not None
+
+
 def test_direct_scatter_shows_the_conflicts(tr):
     """The same permutation scattered directly: random banks within each request,
     so the replay must count conflicts (about 2-4 wavefronts per request)."""

@@ -183,8 +183,11 @@ constexpr int kCountTilesPerBlock = BCF_COUNT_TILES_PER_BLOCK;
 template <int BITS, int T>
 __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tiles) {
   constexpr int RADIX = 1 << BITS;
+  constexpr int NV = T / 1024;  // 16-byte loads per thread per tile
+  static_assert(kCountTilesPerBlock == 4, "fast path counts four tiles at once");
   __shared__ uint32_t h[RADIX];
   __shared__ uint32_t tot[RADIX];
+  __shared__ uint32_t h4[4][RADIX];
   const int tid = threadIdx.x;
   for (int i = tid; i < RADIX; i += 256) tot[i] = 0;
   const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
@@ -192,6 +195,37 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
   const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
   const bool segmented = p.seg_offs != nullptr;
   if (segmented) tiles = min(tiles, (int64_t)ld_relaxed(p.num_tiles));
+  if constexpr (NV <= 4) {
+    // Four full tiles: every load in flight before any count, one histogram per
+    // tile, and the four counts of a digit stored together (the count rows'
+    // stride is a multiple of 16 words and t0 a multiple of 4).
+    if (!segmented && (t0 + 4) * T <= p.n) {
+      for (int i = tid; i < 4 * RADIX; i += 256) h4[i / RADIX][i % RADIX] = 0;
+      uint4 x[4][NV];
+      const uint4* k4 = reinterpret_cast<const uint4*>(p.keys + t0 * T);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
+      __syncthreads();
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          atomicAdd(&h4[t][(x[t][q].x >> shift) & mask], 1u);
+          atomicAdd(&h4[t][(x[t][q].y >> shift) & mask], 1u);
+          atomicAdd(&h4[t][(x[t][q].z >> shift) & mask], 1u);
+          atomicAdd(&h4[t][(x[t][q].w >> shift) & mask], 1u);
+        }
+      __syncthreads();
+      for (int d = tid; d < RADIX; d += 256) {
+        const uint4 c = make_uint4(h4[0][d], h4[1][d], h4[2][d], h4[3][d]);
+        *reinterpret_cast<uint4*>(p.counts + (size_t)d * p.stride + t0) = c;
+        if (p.totals && (c.x | c.y | c.z | c.w)) atomicAdd(&p.totals[d], c.x + c.y + c.z + c.w);
+      }
+      return;
+    }
+  }
   for (int64_t tile = t0; tile < min(t0 + kCountTilesPerBlock, tiles); ++tile) {
     int64_t start = tile * T, hi = p.n;
     if (segmented) {

@@ -290,6 +290,23 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
   __shared__ uint32_t s_base;
   const int d = blockIdx.x;
   const int tid = threadIdx.x;
+  uint32_t* row = counts + (size_t)d * stride;
+  // The first chunk's counts are loaded before the digit start is summed, so
+  // that the two global reads overlap.
+  uint32_t v[kScanPerThread];
+  auto load = [&](int64_t i0) {
+    if (i0 + kScanPerThread <= tiles) {  // 64-byte aligned: four 16-byte loads
+#pragma unroll
+      for (int j = 0; j < kScanPerThread; j += 4) {
+        const uint4 x = *reinterpret_cast<const uint4*>(row + i0 + j);
+        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kScanPerThread; ++j) v[j] = (i0 + j < tiles) ? row[i0 + j] : 0u;
+    }
+  };
+  load((int64_t)tid * kScanPerThread);
   if (tid < 32) {  // digit start: warp-wide sum of the smaller digits' totals
     uint32_t b = 0;
     if (totals && !balanced)
@@ -307,20 +324,9 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
   }
   __syncthreads();
   uint32_t carry = s_base;
-  uint32_t* row = counts + (size_t)d * stride;
   for (int64_t c0 = 0; c0 < tiles; c0 += (int64_t)kScanThreads * kScanPerThread) {
     const int64_t i0 = c0 + (int64_t)tid * kScanPerThread;
-    uint32_t v[kScanPerThread];
-    if (i0 + kScanPerThread <= tiles) {  // 64-byte aligned: four 16-byte loads
-#pragma unroll
-      for (int j = 0; j < kScanPerThread; j += 4) {
-        const uint4 x = *reinterpret_cast<const uint4*>(row + i0 + j);
-        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kScanPerThread; ++j) v[j] = (i0 + j < tiles) ? row[i0 + j] : 0u;
-    }
+    if (c0 > 0) load(i0);
     uint32_t sum = 0;
 #pragma unroll
     for (int j = 0; j < kScanPerThread; ++j) sum += v[j];

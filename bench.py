@@ -497,6 +497,20 @@ def run_rows(which, peak):
             "(16 B/key); model charges 68 B/key")
         plain_ns[name] = ms * 1e6 / n
         del k, v, ko, vo, ws
+    if want("partition_splitters_255_2pow26"):
+        n = 1 << 26
+        keys = synth.uniform_keys(n, seed=0x2D)
+        g = synth.rng(7)
+        sample = np.sort(keys[g.integers(0, n, size=255 * 16)])
+        spl = sample[(np.arange(1, 256) * sample.size) // 256].astype(np.uint32)
+        k, v, sd = to_dev(keys), to_dev(synth.index_payload(n)), to_dev(spl)
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.partition_splitters_workspace_size(n, 255, 4))
+        ms, _ = ev_ms(lambda: bcf.partition_splitters(k, v, sd, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+        add("partition_splitters_255_2pow26", n, 16 * n, ms, "sample-sort bucketing: 256 buckets from 255 "
+            "sampled splitters (binary search per key in shared memory); tile counts (4 B/key) + sweep (16 B/key), "
+            "model charges 16 B/key")
+        del k, v, sd, ko, vo, ws
     if want("partition_w256_2pow26"):
         n, w = 1 << 26, 256
         k = to_dev(synth.partition_keys(n, w, seed=0x2C))

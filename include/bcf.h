@@ -116,6 +116,24 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
                   size_t ws_bytes, bcf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Partition by splitters (the pivot bucketing of the sorting problem, Sec. 1: a
+ * w-way partition whose labels come from w - 1 pivots): key k goes to bucket
+ * b(k) = number of splitters s with s <= k, so bucket b holds the keys in
+ * [s[b-1], s[b]).  Stable; keys (and payloads) move, labels are not stored.
+ *  splitters  device array of nsplit uint32 values in non-decreasing order
+ *             (equal splitters give empty buckets); 0 <= nsplit <= 255, w =
+ *             nsplit + 1.  Descending neighbours set device status BCF_E_BAD_KEY
+ *             (the output is then unspecified).
+ *  flags      BCF_ASSUME_BALANCED: exactly n/w keys per bucket (n % w == 0,
+ *             else BCF_E_INVAL; other counts -> BCF_E_NOT_BALANCED).
+ *  ws         bcf_partition_splitters_workspace_size() bytes.  In place allowed.
+ * n must be < 2^30. */
+int bcf_partition_splitters_workspace_size(int64_t n, int nsplit, int val_bytes, int flags, size_t* bytes);
+int bcf_partition_splitters(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                            void* vals_out, int64_t n, const uint32_t* splitters, int nsplit,
+                            int val_bytes, int flags, void* ws, size_t ws_bytes, bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Permutation (Sec. 1): dst[pi[i]] = src[i] for i in [0, n).
  *  elem_bytes  4 or 8 (bcf_permute); src and dst must not overlap.
  *  row_len     0: pi holds global indices.  > 0: the arrays are rows of row_len

@@ -56,6 +56,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "oracle_sort_kv": [P, P, P, P, I64, I],
         "oracle_stable_rank": [P, I64, I64],
         "oracle_partition_kv": [P, P, P, P, I64, I64, I, I],
+        "oracle_partition_splitters": [P, P, P, P, I64, P, I64, I, I],
         "oracle_permute": [P, P, P, I64, I],
         "oracle_permute_tiles": [P, P, P, I64, I64],
         "oracle_gather": [P, P, P, I64, I64, I],
@@ -124,6 +125,20 @@ def partition_kv(keys, vals, w, balanced=False, L=None):
     vo = None if vals is None else np.empty_like(vals)
     _check(L.oracle_partition_kv(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.size,
                                  int(w), int(bool(balanced)), _vb(vals)))
+    return ko, vo
+
+
+def partition_splitters(keys, vals, splitters, balanced=False, L=None):
+    """Stable partition of the keys (and payloads) into len(splitters) + 1 buckets,
+    bucket = number of splitters <= key."""
+    L = L or lib()
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    spl = np.ascontiguousarray(splitters, dtype=np.uint32)
+    vals = None if vals is None else np.ascontiguousarray(vals)
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(vals)
+    _check(L.oracle_partition_splitters(_ptr(keys), _ptr(vals), _ptr(ko), _ptr(vo), keys.size,
+                                        _ptr(spl), spl.size, int(bool(balanced)), _vb(vals)))
     return ko, vo
 
 

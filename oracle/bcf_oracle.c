@@ -154,6 +154,54 @@ int oracle_partition_kv(const uint32_t* keys, const void* vals, uint32_t* keys_o
     return ORACLE_OK;
 }
 
+/* Partition by splitters: each key's label is the count of splitters not above
+ * it (a linear count, no search), then the same counting partition as above but
+ * moving the original keys. */
+int oracle_partition_splitters(const uint32_t* keys, const void* vals, uint32_t* keys_out,
+                               void* vals_out, int64_t n, const uint32_t* splitters,
+                               int64_t nsplit, int balanced, int val_bytes) {
+    if (n < 0 || nsplit < 0 || !valid_val_bytes(val_bytes)) return ORACLE_E_ARG;
+    for (int64_t t = 1; t < nsplit; ++t)
+        if (splitters[t - 1] > splitters[t]) return ORACLE_E_ARG;
+    const int64_t w = nsplit + 1;
+    if (balanced && (n % w) != 0) return ORACLE_E_BALANCE;
+    uint32_t* label = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
+    int64_t* count = (int64_t*)calloc((size_t)w, sizeof(int64_t));
+    if (!label || !count) {
+        free(label);
+        free(count);
+        return ORACLE_E_NOMEM;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t b = 0;
+        for (int64_t t = 0; t < nsplit; ++t) b += splitters[t] <= keys[i];
+        label[i] = b;
+        count[b] += 1;
+    }
+    int rc = ORACLE_OK;
+    if (balanced)
+        for (int64_t b = 0; b < w; ++b)
+            if (count[b] != n / w) rc = ORACLE_E_BALANCE;
+    if (rc == ORACLE_OK) {
+        int64_t run = 0;
+        for (int64_t b = 0; b < w; ++b) {
+            int64_t c = count[b];
+            count[b] = run;
+            run += c;
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t p = count[label[i]]++;
+            keys_out[p] = keys[i];
+            if (val_bytes && vals && vals_out)
+                memcpy((char*)vals_out + p * val_bytes, (const char*)vals + i * val_bytes,
+                       (size_t)val_bytes);
+        }
+    }
+    free(label);
+    free(count);
+    return rc;
+}
+
 /* Permutation problem (Sec. 1): the item at position i goes to position pi[i].
  * pi must be a bijection on [0, n); this is checked with a seen-table first. */
 int oracle_permute(const void* src, void* dst, const uint32_t* pi, int64_t n,

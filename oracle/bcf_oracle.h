@@ -36,6 +36,13 @@ int64_t oracle_stable_rank(const uint32_t* keys, int64_t n, int64_t i);
 int oracle_partition_kv(const uint32_t* keys, const void* vals, uint32_t* keys_out,
                         void* vals_out, int64_t n, int64_t w, int balanced, int val_bytes);
 
+/* Partition by splitters (pivot bucketing, Sec. 1): label of key k = number of
+ * splitters s[t] <= k, then the stable counting partition by that label, moving
+ * the keys themselves.  Splitters must be non-decreasing (ORACLE_E_ARG otherwise). */
+int oracle_partition_splitters(const uint32_t* keys, const void* vals, uint32_t* keys_out,
+                               void* vals_out, int64_t n, const uint32_t* splitters,
+                               int64_t nsplit, int balanced, int val_bytes);
+
 /* Permutation problem (Sec. 1): out[pi[i]] = in[i] after a bijectivity check. */
 int oracle_permute(const void* src, void* dst, const uint32_t* pi, int64_t n,
                    int elem_bytes);

@@ -53,6 +53,8 @@ _SIGS = {
     "bcf_sort": ([_P, _P, _P, _P, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_partition_workspace_size": ([_I64, _I, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_partition": ([_P, _P, _P, _P, _I64, _I, _I, _I, _P, _SZ, _P], _I),
+    "bcf_partition_splitters_workspace_size": ([_I64, _I, _I, _I, ctypes.POINTER(_SZ)], _I),
+    "bcf_partition_splitters": ([_P, _P, _P, _P, _I64, _P, _I, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_workspace_size": ([_I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_permute": ([_P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_kv": ([_P, _P, _P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
@@ -209,6 +211,35 @@ def partition(keys, vals, w, balanced=False, keys_out=None, vals_out=None, ws=No
     _check(lib().bcf_partition(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n, w, vb,
                                flags, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "bcf_partition")
+    return keys_out, vals_out
+
+
+def partition_splitters_workspace_size(n, nsplit, val_bytes=4, flags=0) -> int:
+    sz = ctypes.c_size_t(0)
+    _check(lib().bcf_partition_splitters_workspace_size(int(n), int(nsplit), int(val_bytes), int(flags),
+                                                        ctypes.byref(sz)), "bcf_partition_splitters_workspace_size")
+    return sz.value
+
+
+def partition_splitters(keys, vals, splitters, balanced=False, keys_out=None, vals_out=None, ws=None,
+                        stream=None):
+    """Stable partition of keys (and payloads) into len(splitters) + 1 buckets, bucket =
+    number of splitters <= key (bcf_partition_splitters); splitters: ascending uint32
+    values in a 32-bit CUDA tensor."""
+    torch = _torch()
+    _dev_u32(splitters, "splitters")
+    n = keys.numel()
+    nsplit = splitters.numel()
+    vb = _vb(vals)
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    if vals is not None and vals_out is None:
+        vals_out = torch.empty_like(vals)
+    flags = ASSUME_BALANCED if balanced else 0
+    if ws is None:
+        ws = workspace(partition_splitters_workspace_size(n, nsplit, vb, flags), keys.device)
+    _check(lib().bcf_partition_splitters(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n,
+                                         _ptr(splitters), nsplit, vb, flags, _ptr(ws), ws.numel(),
+                                         _stream(stream)), "bcf_partition_splitters")
     return keys_out, vals_out
 
 

@@ -181,6 +181,38 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
                                 bcf::tuned_config(BCF_OP_PARTITION, n)));
 }
 
+// Splitter partition: the sweep layout of a 256-bucket partition, always with
+// room for an in-place copy and for the reduce-then-scan counts at any size.
+static bcf::SweepLayout splitter_layout(int64_t n, int val_bytes) {
+  return bcf::sweep_layout(n, val_bytes, 1, 256, true);
+}
+
+int bcf_partition_splitters_workspace_size(int64_t n, int nsplit, int val_bytes, int flags, size_t* bytes) {
+  (void)flags;
+  if (!bytes || n < 0 || nsplit < 0 || !valid_vb(val_bytes)) return BCF_E_INVAL;
+  if (nsplit > 255 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  *bytes = splitter_layout(n, val_bytes).total;
+  return BCF_OK;
+}
+
+int bcf_partition_splitters(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                            void* vals_out, int64_t n, const uint32_t* splitters, int nsplit,
+                            int val_bytes, int flags, void* ws, size_t ws_bytes, bcf_stream_t stream) {
+  int rc = check_kv(keys_in, vals_in, keys_out, vals_out, n, val_bytes);
+  if (rc) return rc;
+  if (nsplit < 0 || (nsplit > 0 && !splitters)) return BCF_E_INVAL;
+  if (nsplit > 255 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  const bool balanced = (flags & BCF_ASSUME_BALANCED) != 0;
+  if (balanced && n % (nsplit + 1)) return BCF_E_INVAL;
+  if (n == 0) return BCF_OK;
+  const bcf::SweepLayout L = splitter_layout(n, val_bytes);
+  if (!ws || !aligned16(ws)) return BCF_E_INVAL;
+  if (ws_bytes < L.total) return BCF_E_WORKSPACE;
+  if (!device_ready()) return BCF_E_CUDA;
+  return cuda_rc(bcf::partition_splitters(keys_in, vals_in, keys_out, vals_out, n, splitters, nsplit, val_bytes,
+                                          balanced, static_cast<unsigned char*>(ws), L, (cudaStream_t)stream));
+}
+
 // ------------------------------------------------------------ permutations
 // Workspace: [bucketed-form region (BCF_PERMUTE_BUCKETED)][seen bitmap (BCF_CHECK_PERM)].
 static size_t permute_bucket_bytes(int64_t n, int vb, int flags) {

@@ -97,6 +97,10 @@ cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint3
 cudaError_t permute(const void* src_k, const void* src_v, void* dst_k, void* dst_v,
                     const uint32_t* pi, int64_t n, int64_t row_len, int kbytes, int vbytes,
                     uint32_t* seen_bitmap, bool fused, cudaStream_t s);
+// w-way partition by w - 1 ascending splitters (radix.cu).
+cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                                void* vals_out, int64_t n, const uint32_t* splitters, int nsplit, int vb,
+                                bool balanced, unsigned char* ws, const SweepLayout& L, cudaStream_t s);
 // Testing aid for the bounded look-back waits (radix.cu).
 void debug_lookback(int silent_tile, unsigned spin_limit);
 // Two-pass bucketed permutation (permute_bucketed.cu).

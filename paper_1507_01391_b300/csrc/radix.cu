@@ -320,6 +320,63 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
   return pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, 8, w, balanced, totals, offsets, s, cfg);
 }
 
+// w-way partition by w - 1 splitters (sample-sort bucketing): one reduce-then-scan
+// pass whose digit is the number of splitters <= key, default tile configuration.
+cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
+                                void* vals_out, int64_t n, const uint32_t* splitters, int nsplit, int vb,
+                                bool balanced, unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  constexpr int THREADS = kSweepCfgThreads[0], IPT = kSweepCfgIPT[0], T = THREADS * IPT;
+  cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
+  if (e != cudaSuccess) return e;
+  uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);
+  uint32_t* offsets = reinterpret_cast<uint32_t*>(ws + L.lookback);
+  const uint32_t* src_k = keys_in;
+  const void* src_v = vals_in;
+  if (keys_in == keys_out) {  // in place: sweep from a copy of the input
+    uint32_t* kt = reinterpret_cast<uint32_t*>(ws + L.keys_tmp);
+    if ((e = cudaMemcpyAsync(kt, keys_in, (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+      return e;
+    src_k = kt;
+    if (vb && vals_in) {
+      void* vt = ws + L.vals_tmp;
+      if ((e = cudaMemcpyAsync(vt, vals_in, (size_t)n * vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return e;
+      src_v = vt;
+    }
+  }
+  const int64_t tiles = (n + T - 1) / T;
+  const int64_t stride = (tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;  // > tiles
+  CountParams cp{};
+  cp.keys = src_k;
+  cp.n = n;
+  cp.counts = offsets;
+  cp.stride = stride;
+  cp.totals = totals;
+  cp.splitters = splitters;
+  cp.nsplit = nsplit;
+  const int64_t count_blocks = (tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
+  k_tile_counts<8, T, true><<<(unsigned)count_blocks, 256, 0, s>>>(cp, tiles);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_scan_offsets<<<256, kScanThreads, 0, s>>>(offsets, tiles, stride, totals, balanced ? 1 : 0, n, nsplit + 1,
+                                               status_word());
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  SweepParams sp{};
+  sp.keys_in = src_k;
+  sp.vals_in = src_v;
+  sp.keys_out = keys_out;
+  sp.vals_out = vals_out;
+  sp.n = n;
+  sp.nbits = 8;
+  sp.balanced = balanced ? 1 : 0;
+  sp.lb_stride = stride;
+  sp.tile_offsets = offsets;
+  sp.status = status_word();
+  sp.splitters = splitters;
+  sp.nsplit = nsplit;
+  return sweep_dispatch<8, THREADS, IPT, true>(sp, tiles, vb, s);
+}
+
 BCF_TRACE_INSTALLER(radix)
 
 }  // namespace bcf

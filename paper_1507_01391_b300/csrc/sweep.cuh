@@ -58,6 +58,9 @@ struct SweepParams {
   // makes a later tile's bounded wait run out
   unsigned spin_limit;
   int silent_tile1;
+  // splitter mode (k_sweep<..., SPLIT = true>): digit = number of splitters <= key
+  const uint32_t* splitters;   // nsplit ascending values
+  int nsplit;                  // 0..255
 };
 
 template <int BITS>
@@ -159,6 +162,35 @@ __global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
   }
 }
 
+// Bucket of key k among nsplit ascending splitters: the number of splitters <= k.
+// The splitters, padded to 255 with 0xFFFFFFFF, sit in shared memory as a perfect
+// binary search tree in level order (node i at spl[i], children 2i and 2i+1): the
+// nodes of one level are consecutive words, so the first six levels of a warp's
+// searches never share a bank.  After eight steps i - 256 counts the tree's
+// values <= k; the clamp removes the padding (which only 0xFFFFFFFF reaches).
+__device__ __forceinline__ uint32_t split_bucket(const uint32_t* spl, int nsplit, uint32_t k) {
+  uint32_t i = 1;
+#pragma unroll
+  for (int l = 0; l < 8; ++l) i = 2 * i + (spl[i] <= k ? 1u : 0u);
+  return min(i - 256u, (uint32_t)nsplit);
+}
+
+// Build the search tree of split_bucket from the ascending splitters (every thread
+// of the block takes part; a barrier must follow) and, given a status word, flag
+// a descending pair.  Node i at level l (2^l <= i < 2^(l+1)) holds the sorted
+// value of rank (2 (i - 2^l) + 1) 2^(7-l) - 1.
+__device__ __forceinline__ void stage_splitters(const uint32_t* src, int nsplit, uint32_t* spl, int nthreads,
+                                                unsigned* status) {
+  for (int i = 1 + (int)threadIdx.x; i < 256; i += nthreads) {
+    const int l = 31 - __clz(i);
+    const int r = ((2 * (i - (1 << l)) + 1) << (7 - l)) - 1;
+    spl[i] = r < nsplit ? src[r] : 0xFFFFFFFFu;
+  }
+  if (status)
+    for (int i = 1 + (int)threadIdx.x; i < nsplit; i += nthreads)
+      if (src[i - 1] > src[i]) set_status(status, DEV_BAD_KEY);
+}
+
 // ------------------------------------------------------------- reduce-then-scan
 // Per-tile digit counts of one pass (digit-major), plus the pass's digit totals.
 struct CountParams {
@@ -173,6 +205,8 @@ struct CountParams {
   const int32_t* tile_seg;
   const int32_t* seg_tile0;
   const uint32_t* num_tiles;
+  const uint32_t* splitters;     // splitter mode: digit = number of splitters <= key
+  int nsplit;
 };
 
 #ifndef BCF_COUNT_TILES_PER_BLOCK
@@ -180,7 +214,7 @@ struct CountParams {
 #endif
 constexpr int kCountTilesPerBlock = BCF_COUNT_TILES_PER_BLOCK;
 
-template <int BITS, int T>
+template <int BITS, int T, bool SPLIT = false>
 __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tiles) {
   constexpr int RADIX = 1 << BITS;
   constexpr int NV = T / 1024;  // 16-byte loads per thread per tile
@@ -192,6 +226,12 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
   for (int i = tid; i < RADIX; i += 256) tot[i] = 0;
   const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
   const int shift = p.label_bits ? 0 : p.shift;
+  __shared__ uint32_t spl[SPLIT ? 256 : 1];
+  if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, 256, nullptr);  // read after a barrier below
+  auto dig = [&](uint32_t x) -> uint32_t {
+    if constexpr (SPLIT) return split_bucket(spl, p.nsplit, x);
+    else return (x >> shift) & mask;
+  };
   const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
   const bool segmented = p.seg_offs != nullptr;
   if (segmented) tiles = min(tiles, (int64_t)ld_relaxed(p.num_tiles));
@@ -212,10 +252,10 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
       for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          atomicAdd(&h4[t][(x[t][q].x >> shift) & mask], 1u);
-          atomicAdd(&h4[t][(x[t][q].y >> shift) & mask], 1u);
-          atomicAdd(&h4[t][(x[t][q].z >> shift) & mask], 1u);
-          atomicAdd(&h4[t][(x[t][q].w >> shift) & mask], 1u);
+          atomicAdd(&h4[t][dig(x[t][q].x)], 1u);
+          atomicAdd(&h4[t][dig(x[t][q].y)], 1u);
+          atomicAdd(&h4[t][dig(x[t][q].z)], 1u);
+          atomicAdd(&h4[t][dig(x[t][q].w)], 1u);
         }
       __syncthreads();
       for (int d = tid; d < RADIX; d += 256) {
@@ -238,7 +278,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     __syncthreads();
     const uint32_t* k = p.keys + start;
     if (segmented) {  // segment starts need not be 16-byte aligned: scalar loads
-      for (int i = tid; i < cnt; i += 256) atomicAdd(&h[(__ldcs(k + i) >> shift) & mask], 1u);
+      for (int i = tid; i < cnt; i += 256) atomicAdd(&h[dig(__ldcs(k + i))], 1u);
     } else if (cnt == T) {  // full tile: all T/1024 vector loads in flight before counting
       constexpr int NV = T / 1024;
       uint4 x[NV];
@@ -246,21 +286,21 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
       for (int q = 0; q < NV; ++q) x[q] = __ldcs(reinterpret_cast<const uint4*>(k) + tid + 256 * q);
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
-        atomicAdd(&h[(x[q].x >> shift) & mask], 1u);
-        atomicAdd(&h[(x[q].y >> shift) & mask], 1u);
-        atomicAdd(&h[(x[q].z >> shift) & mask], 1u);
-        atomicAdd(&h[(x[q].w >> shift) & mask], 1u);
+        atomicAdd(&h[dig(x[q].x)], 1u);
+        atomicAdd(&h[dig(x[q].y)], 1u);
+        atomicAdd(&h[dig(x[q].z)], 1u);
+        atomicAdd(&h[dig(x[q].w)], 1u);
       }
     } else {
       const int nv = cnt >> 2;
       for (int v = tid; v < nv; v += 256) {
         const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
-        atomicAdd(&h[(x.x >> shift) & mask], 1u);
-        atomicAdd(&h[(x.y >> shift) & mask], 1u);
-        atomicAdd(&h[(x.z >> shift) & mask], 1u);
-        atomicAdd(&h[(x.w >> shift) & mask], 1u);
+        atomicAdd(&h[dig(x.x)], 1u);
+        atomicAdd(&h[dig(x.y)], 1u);
+        atomicAdd(&h[dig(x.z)], 1u);
+        atomicAdd(&h[dig(x.w)], 1u);
       }
-      for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[(k[i] >> shift) & mask], 1u);
+      for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[dig(k[i])], 1u);
     }
     __syncthreads();
     for (int d = tid; d < RADIX; d += 256) {
@@ -343,7 +383,7 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
 }
 
 // ------------------------------------------------------------- one sweep
-template <int THREADS, int IPT, int BITS, int VB>
+template <int THREADS, int IPT, int BITS, int VB, bool SPLIT = false>
 struct SweepSmem {
   static constexpr int T = THREADS * IPT;
   static constexpr int WARPS = THREADS / 32;
@@ -356,15 +396,17 @@ struct SweepSmem {
   static constexpr size_t scratch = gofs + (size_t)RADIX * 4;
   static constexpr size_t mbar = scratch + 32 * 4;
   static constexpr size_t info = mbar + 8;                 // tile, seg
-  static constexpr size_t bytes = info + 16;
+  static constexpr size_t spl = info + 16;                 // splitter mode: splitters
+  static constexpr size_t sdig = spl + (SPLIT ? 256 * 4 : 0);  // splitter mode: digit of each ordered key
+  static constexpr size_t bytes = sdig + (SPLIT ? (size_t)T : 0);
 };
 
-template <int THREADS, int IPT, int BITS, int VB>
+template <int THREADS, int IPT, int BITS, int VB, bool SPLIT = false>
 __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) * 256 / THREADS > 0
                                                ? (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) * 256 / THREADS
                                                : 1) k_sweep(SweepParams p) {
   using VT = typename ValT<VB>::type;
-  using S = SweepSmem<THREADS, IPT, BITS, VB>;
+  using S = SweepSmem<THREADS, IPT, BITS, VB, SPLIT>;
   constexpr int T = S::T, RADIX = S::RADIX;
   constexpr uint32_t DMASK = RADIX - 1;
   static_assert(RADIX <= THREADS, "one thread per digit");
@@ -378,6 +420,8 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   uint32_t* scratch = reinterpret_cast<uint32_t*>(smem + S::scratch);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
   int* s_info = reinterpret_cast<int*>(smem + S::info);
+  uint32_t* spl = reinterpret_cast<uint32_t*>(smem + S::spl);
+  uint8_t* sdig = reinterpret_cast<uint8_t*>(smem + S::sdig);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool segmented = p.seg_offs != nullptr;
@@ -423,6 +467,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       bulk_g2s(vals_s, reinterpret_cast<const VT*>(p.vals_in) + start - vsh, (unsigned)(vfull * VB), mbar);
   }
   for (int i = tid; i < S::WARPS * RADIX; i += THREADS) whist[i] = 0;
+  if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, THREADS, p.status);
   for (int i = max(kfull - ksh, 0) + tid; i < cnt; i += THREADS) keys_s[ksh + i] = p.keys_in[start + i];
   if (VB && !iota) {
     for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
@@ -453,6 +498,17 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
       if (label_mode && valid && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
     }
+    // Splitter mode: every key's bucket once, four 8-bit digits per register.
+    uint32_t dg[SPLIT ? (IPT + 3) / 4 : 1] = {};
+    if constexpr (SPLIT) {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j)
+        if (in_tile(wbase + j * 32 + lane)) dg[j >> 2] |= split_bucket(spl, p.nsplit, key[j]) << (8 * (j & 3));
+    }
+    auto digit = [&](int j) -> uint32_t {
+      if constexpr (SPLIT) return (dg[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+      else return (key[j] >> shift) & DMASK;
+    };
 
     // Phase A -- counts: every warp histograms its own keys (the row "radix sort"
     // count of Corollary 1, one histogram per warp).
@@ -460,8 +516,8 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
 #pragma unroll
     for (int j = 0; j < IPT; ++j)
       if (in_tile(wbase + j * 32 + lane)) {
-        BCF_TR(&wh[(key[j] >> shift) & DMASK], 4, 2, TS_COUNT_ATOM);
-        atomicAdd(&wh[(key[j] >> shift) & DMASK], 1u);
+        BCF_TR(&wh[digit(j)], 4, 2, TS_COUNT_ATOM);
+        atomicAdd(&wh[digit(j)], 1u);
       }
     __syncthreads();
 
@@ -497,7 +553,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
       const bool valid = in_tile(wbase + j * 32 + lane);
-      const uint32_t d = (key[j] >> shift) & DMASK;
+      const uint32_t d = digit(j);
       unsigned peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
 #if BCF_PEERS_MATCH
       peers &= __match_any_sync(0xffffffffu, valid ? d : 0xFFFFFFFFu);
@@ -517,6 +573,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       old = __shfl_sync(0xffffffffu, old, leader);
       if (valid) {
         const uint32_t pos = old + __popc(peers & lt);
+        if constexpr (SPLIT) sdig[pos] = (uint8_t)d;
         if constexpr (VB == 4) {
           BCF_TR(&kv_s[pos], 8, 1, TS_SCATTER);
           kv_s[pos] = ((unsigned long long)val[j] << 32) | key[j];
@@ -637,8 +694,11 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       if (VB) BCF_TR(&vals_s[i], VB, 0, TS_WRITEOUT_READ);
       if (VB) v = vals_s[i];
     }
-    BCF_TR(&gofs[(k >> shift) & DMASK], 4, 0, TS_OFFSET_READ);
-    const uint32_t dst = gofs[(k >> shift) & DMASK] + (uint32_t)i;
+    uint32_t dk;
+    if constexpr (SPLIT) dk = sdig[i];
+    else dk = (k >> shift) & DMASK;
+    BCF_TR(&gofs[dk], 4, 0, TS_OFFSET_READ);
+    const uint32_t dst = gofs[dk] + (uint32_t)i;
     if (dst - lo32 < len32) {
       p.keys_out[dst] = k;
       if (VB) vout[dst] = v;
@@ -646,10 +706,10 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   }
 }
 
-template <int BITS, int VB, int THREADS = kSweepThreads, int IPT = kSweepIPT>
+template <int BITS, int VB, int THREADS = kSweepThreads, int IPT = kSweepIPT, bool SPLIT = false>
 inline cudaError_t launch_sweep(const SweepParams& p, int64_t grid, cudaStream_t s) {
-  using S = SweepSmem<THREADS, IPT, BITS, VB>;
-  auto kern = k_sweep<THREADS, IPT, BITS, VB>;
+  using S = SweepSmem<THREADS, IPT, BITS, VB, SPLIT>;
+  auto kern = k_sweep<THREADS, IPT, BITS, VB, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
   if (e != cudaSuccess) return e;
   if (grid <= 0) return cudaSuccess;
@@ -657,12 +717,12 @@ inline cudaError_t launch_sweep(const SweepParams& p, int64_t grid, cudaStream_t
   return cudaGetLastError();
 }
 
-template <int BITS, int THREADS = kSweepThreads, int IPT = kSweepIPT>
+template <int BITS, int THREADS = kSweepThreads, int IPT = kSweepIPT, bool SPLIT = false>
 inline cudaError_t sweep_dispatch(const SweepParams& p, int64_t grid, int vb, cudaStream_t s) {
   switch (vb) {
-    case 0: return launch_sweep<BITS, 0, THREADS, IPT>(p, grid, s);
-    case 4: return launch_sweep<BITS, 4, THREADS, IPT>(p, grid, s);
-    case 8: return launch_sweep<BITS, 8, THREADS, IPT>(p, grid, s);
+    case 0: return launch_sweep<BITS, 0, THREADS, IPT, SPLIT>(p, grid, s);
+    case 4: return launch_sweep<BITS, 4, THREADS, IPT, SPLIT>(p, grid, s);
+    case 8: return launch_sweep<BITS, 8, THREADS, IPT, SPLIT>(p, grid, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -58,6 +58,9 @@ def test_workspace_queries():
     assert L.bcf_permute_workspace_size(1 << 20, 8, bcf.PERMUTE_BUCKETED, ctypes.byref(sz)) == bcf.OK
     assert sz.value == 0
     assert L.bcf_permute_workspace_size(100, 3, 0, ctypes.byref(sz)) == bcf.E_INVAL
+    assert L.bcf_partition_splitters_workspace_size(1 << 20, 255, 4, 0, ctypes.byref(sz)) == bcf.OK
+    assert sz.value >= 8 << 20  # room for an in-place copy of keys and payloads
+    assert L.bcf_partition_splitters_workspace_size(100, 256, 4, 0, ctypes.byref(sz)) == bcf.E_UNSUPPORTED
 
 
 def test_argument_checks_reject_without_launching():

@@ -41,6 +41,12 @@ def _partition_pins(L):
         assert np.array_equal(vo[16 * b:16 * b + 16], np.flatnonzero(keys == b).astype(np.uint32))
 
 
+def _splitter_pins(L):
+    keys = np.array([5, 1, 9, 5, 3, 7, 5, 2], dtype=np.uint32)
+    ko, vo = oracle.partition_splitters(keys, synth.index_payload(8), np.array([5, 5, 8], dtype=np.uint32), L=L)
+    assert ko.tolist() == [1, 3, 2, 5, 5, 7, 5, 9] and vo.tolist() == [1, 4, 7, 0, 3, 5, 6, 2]
+
+
 def _permute_pins(L):
     pi = synth.random_perm(50, seed=4)
     inv = oracle.permute(synth.index_payload(50), pi, L=L)
@@ -74,6 +80,8 @@ MUTANTS = [
     ("merge copies a wrong right tail", "while (j < hi) dst[k++] = src[j++];", "while (j < hi) { dst[k++] = src[mid - 1]; j++; }", _sort_pins),
     ("partition scans backwards", "for (int64_t i = 0; i < n; ++i) {\n        int64_t p = count[keys[i]]++;",
      "for (int64_t i = n - 1; i >= 0; --i) {\n        int64_t p = count[keys[i]]++;", _partition_pins),
+    ("splitter bucket counts splitters below, not at or below", "for (int64_t t = 0; t < nsplit; ++t) b += splitters[t] <= keys[i];",
+     "for (int64_t t = 0; t < nsplit; ++t) b += splitters[t] < keys[i];", _splitter_pins),
     ("permute writes gather-style", "memcpy((char*)dst + (int64_t)pi[i] * elem_bytes, (const char*)src + i * elem_bytes,",
      "memcpy((char*)dst + i * elem_bytes, (const char*)src + (int64_t)pi[i] * elem_bytes,", _permute_pins),
     ("row->col conversion transposed", "for (int64_t r = 0; r < w; ++r) M[r * m + c] = seq[c * w + r];",
@@ -93,5 +101,5 @@ def test_pins_catch_mutant(tmp_path, name, old, new, pins):
 
 def test_unmutated_copy_passes_the_same_pins(tmp_path):
     L = _mutant(tmp_path, "#include <stdlib.h>", "#include <stdlib.h>")
-    for pins in (_sort_pins, _partition_pins, _permute_pins, _lemma1_pins, _bank_pins):
+    for pins in (_sort_pins, _partition_pins, _splitter_pins, _permute_pins, _lemma1_pins, _bank_pins):
         pins(L)

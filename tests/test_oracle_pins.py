@@ -142,6 +142,62 @@ def test_partition_unbalanced_and_errors(orc):
         orc.partition_kv(keys[:100], None, 37, balanced=True)  # n % w != 0
 
 
+# ------------------------------------------------------ splitter partition ----
+def _bisect_order(keys, spl):
+    # bucket = number of splitters <= key (bisect_right, a library routine), then
+    # Python's stable sort by bucket
+    import bisect
+    lab = [bisect.bisect_right(list(spl), int(k)) for k in keys]
+    return sorted(range(len(keys)), key=lambda i: lab[i]), lab
+
+
+@pytest.mark.parametrize("nsplit", [0, 1, 5, 255])
+def test_partition_splitters_against_bisect(orc, nsplit):
+    n = 3000
+    g = synth.rng(nsplit + 7)
+    keys = g.integers(0, 1 << 12, size=n, dtype=np.uint32)
+    spl = np.sort(g.integers(0, 1 << 12, size=nsplit, dtype=np.uint32))
+    if nsplit:
+        keys[:nsplit] = spl  # keys equal to splitters sit in the upper bucket
+    order, lab = _bisect_order(keys, spl)
+    ko, vo = orc.partition_splitters(keys, synth.index_payload(n), spl)
+    assert np.array_equal(vo, np.asarray(order, dtype=np.uint32))
+    assert np.array_equal(ko, keys[order])
+    # every key lies in its bucket's range [s[b-1], s[b])
+    labs = np.asarray(lab)[order]
+    assert np.all(np.diff(labs) >= 0)
+    for b in np.unique(labs):
+        kb = ko[labs == b].astype(np.int64)
+        if b > 0:
+            assert kb.min() >= int(spl[b - 1])
+        if b < nsplit:
+            assert kb.max() < int(spl[b])
+
+
+def test_partition_splitters_reduces_to_label_partition(orc):
+    """Splitters 1..w-1 on keys in [0, w): the bucket is the key itself."""
+    w, n = 37, 5000
+    keys = synth.random_labels(n, w, seed=9)
+    spl = np.arange(1, w, dtype=np.uint32)
+    ko, vo = orc.partition_splitters(keys, synth.index_payload(n), spl)
+    rk, rv = orc.partition_kv(keys, synth.index_payload(n), w)
+    assert np.array_equal(ko, rk) and np.array_equal(vo, rv)
+
+
+def test_partition_splitters_duplicates_balanced_and_errors(orc):
+    keys = np.array([5, 1, 9, 5, 3, 7, 5, 2], dtype=np.uint32)
+    ko, vo = orc.partition_splitters(keys, synth.index_payload(8), np.array([5, 5, 8], dtype=np.uint32))
+    # buckets: [<5] = 1,3,2 ; [5,5) empty ; [5,8) = 5,5,7,5 ; [>=8] = 9
+    assert ko.tolist() == [1, 3, 2, 5, 5, 7, 5, 9] and vo.tolist() == [1, 4, 7, 0, 3, 5, 6, 2]
+    bal = np.array([8, 1, 9, 2, 7, 3, 6, 0], dtype=np.uint32)
+    ko, _ = orc.partition_splitters(bal, None, np.array([5], dtype=np.uint32), balanced=True)
+    assert ko.tolist() == [1, 2, 3, 0, 8, 9, 7, 6]
+    with pytest.raises(orc.OracleError):
+        orc.partition_splitters(bal, None, np.array([3], dtype=np.uint32), balanced=True)  # 3 vs 5
+    with pytest.raises(orc.OracleError):
+        orc.partition_splitters(keys, None, np.array([6, 2], dtype=np.uint32))  # descending
+
+
 # ------------------------------------------------------------- permutation ----
 def test_permute_all_permutations_n8(orc):
     """For every pi of [8]: permuting the index array yields pi^-1, which numpy's

@@ -73,6 +73,24 @@ def env_rank():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (the slowest rank's time): an all-reduce MAX
+    over the default process group (NCCL on the GPU, gloo on the CPU)."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(ms_total, steps, world, keys_step):
+    """Whole-job throughput (Gkeys/s) and ms per step: every rank moved keys_step
+    keys per step (weak scaling) in the slowest rank's time."""
+    ms_step = ms_total / steps
+    return world * keys_step / (ms_step * 1e-3) / 1e9, ms_step
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -284,10 +302,7 @@ def run_headline(args, rank, world, local):
     clocks = sampler.stop() if rank == 0 else None
     ms_total = t0.elapsed_time(t1)
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in kevs)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world, "cuda")
     st = bcf.get_status()
     # correctness of the timed outputs (cheap spot check on the device)
     ok = bool(st == bcf.OK)
@@ -745,9 +760,7 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     peak, peak_kind = measured_peaks()
     h = run_headline(args, rank, world, local)
-    ms_step = h["ms_total"] / args.steps
-    keys_step = 2 * N_PERM
-    value = world * keys_step / (ms_step * 1e-3) / 1e9
+    value, ms_step = aggregate(h["ms_total"], args.steps, world, 2 * N_PERM)
     bytes_launch = 20 * N_PERM
     achieved = bytes_launch / (h["kern_ms"] * 1e-3) / 1e9
     src_sha = file_sha1(os.path.join(ROOT, "paper_1507_01391_b300", "csrc", NCU_TRAFFIC["source"]))

@@ -99,8 +99,7 @@ cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint3
   const int64_t count_blocks = (tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
   k_tile_counts<8, kL1Tile><<<(unsigned)count_blocks, 256, 0, s>>>(cp, tiles);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_scan_offsets<<<256, kScanThreads, 0, s>>>(offsets, tiles, stride, totals, balanced ? 1 : 0, n, w,
-                                              status_word());
+  launch_scan_offsets(256, offsets, tiles, stride, totals, balanced ? 1 : 0, n, w, status_word(), s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   switch (vb) {
 #define BCF_PL1(VB)                                                                                  \

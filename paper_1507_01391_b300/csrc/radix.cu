@@ -113,8 +113,8 @@ static cudaError_t pass_t(const uint32_t* src_k, const void* src_v, uint32_t* ds
   k_tile_counts<BITS, T><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_scan_offsets<<<RADIX, kScanThreads, 0, s>>>(offsets, L.tiles, L.lb_stride, totals, balanced ? 1 : 0, n,
-                                                w > 0 ? w : 1, status_word());
+  launch_scan_offsets(RADIX, offsets, L.tiles, L.lb_stride, totals, balanced ? 1 : 0, n, w > 0 ? w : 1,
+                      status_word(), s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   SweepParams sp{};
   sp.keys_in = src_k;
@@ -358,8 +358,7 @@ cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, ui
   const int64_t count_blocks = (tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
   k_tile_counts<8, T, true><<<(unsigned)count_blocks, 256, 0, s>>>(cp, tiles);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_scan_offsets<<<256, kScanThreads, 0, s>>>(offsets, tiles, stride, totals, balanced ? 1 : 0, n, nsplit + 1,
-                                               status_word());
+  launch_scan_offsets(256, offsets, tiles, stride, totals, balanced ? 1 : 0, n, nsplit + 1, status_word(), s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   SweepParams sp{};
   sp.keys_in = src_k;

@@ -279,9 +279,9 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
     cp.seg_tile0 = I32(L.seg_tile0);
     cp.num_tiles = ctr + C_NTILES;
     const int64_t count_blocks = (L.tiles_cap + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
-    k_tile_counts<8, kSweepTile><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles_cap);
+    k_tile_counts<8, kSweepTile, false, false><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles_cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_scan_offsets<<<256, kScanThreads, 0, s>>>(offsets, L.tiles_cap, L.lb_stride, nullptr, 0, n_total, 1, st);
+    launch_scan_offsets(256, offsets, L.tiles_cap, L.lb_stride, nullptr, 0, n_total, 1, st, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (!balanced) {
       k_seg_digit_base<<<(unsigned)L.slots_cap, 256, 0, s>>>(offsets, L.lb_stride, U32(L.seg_base), I32(L.slot_seg),

@@ -214,14 +214,17 @@ struct CountParams {
 #endif
 constexpr int kCountTilesPerBlock = BCF_COUNT_TILES_PER_BLOCK;
 
-template <int BITS, int T, bool SPLIT = false>
+// FAST: the four-tiles-at-once path for unsegmented inputs (its 16 vector loads in
+// flight take registers; the segment-mode instance leaves it out and keeps its
+// occupancy for the scalar loads of unaligned segments).
+template <int BITS, int T, bool SPLIT = false, bool FAST = true>
 __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tiles) {
   constexpr int RADIX = 1 << BITS;
   constexpr int NV = T / 1024;  // 16-byte loads per thread per tile
   static_assert(kCountTilesPerBlock == 4, "fast path counts four tiles at once");
   __shared__ uint32_t h[RADIX];
   __shared__ uint32_t tot[RADIX];
-  __shared__ uint32_t h4[4][RADIX];
+  __shared__ uint32_t h4[FAST ? 4 : 1][RADIX];
   const int tid = threadIdx.x;
   for (int i = tid; i < RADIX; i += 256) tot[i] = 0;
   const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
   const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
   const bool segmented = p.seg_offs != nullptr;
   if (segmented) tiles = min(tiles, (int64_t)ld_relaxed(p.num_tiles));
-  if constexpr (NV <= 4) {
+  if constexpr (FAST && NV <= 4) {
     // Four full tiles: every load in flight before any count, one histogram per
     // tile, and the four counts of a digit stored together (the count rows'
     // stride is a multiple of 16 words and t0 a multiple of 4).
@@ -319,13 +322,13 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
 // digit's global start (sum of smaller digits' totals, or b*n/w for a balanced
 // partition, whose counts are checked here).  Entry `tiles` receives the digit's
 // total run end, so stride must exceed tiles.
-constexpr int kScanThreads = 1024;
 constexpr int kScanPerThread = 16;
 
-static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* counts, int64_t tiles,
-                                                               int64_t stride, const uint32_t* totals,
-                                                               int balanced, int64_t n, int w,
-                                                               unsigned* status) {
+template <int kScanThreads>
+__global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* counts, int64_t tiles,
+                                                                 int64_t stride, const uint32_t* totals,
+                                                                 int balanced, int64_t n, int w,
+                                                                 unsigned* status) {
   __shared__ uint32_t scratch[32];
   __shared__ uint32_t s_base;
   const int d = blockIdx.x;
@@ -380,6 +383,18 @@ static __global__ void __launch_bounds__(kScanThreads) k_scan_offsets(uint32_t* 
     carry += total;
   }
   if (tid == 0 && tiles < stride) row[tiles] = carry;  // end of the digit's runs
+}
+
+// One block per digit; a block of 256 threads covers 4096 tiles in one step, so
+// only larger tile counts take 1024 (fewer idle threads at every barrier).
+static inline cudaError_t launch_scan_offsets(int radix, uint32_t* counts, int64_t tiles, int64_t stride,
+                                              const uint32_t* totals, int balanced, int64_t n, int w,
+                                              unsigned* status, cudaStream_t s) {
+  if (tiles <= 256 * kScanPerThread)
+    k_scan_offsets_t<256><<<radix, 256, 0, s>>>(counts, tiles, stride, totals, balanced, n, w, status);
+  else
+    k_scan_offsets_t<1024><<<radix, 1024, 0, s>>>(counts, tiles, stride, totals, balanced, n, w, status);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------- one sweep

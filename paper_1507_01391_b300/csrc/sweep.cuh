@@ -280,8 +280,28 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     for (int i = tid; i < RADIX; i += 256) h[i] = 0;
     __syncthreads();
     const uint32_t* k = p.keys + start;
-    if (segmented) {  // segment starts need not be 16-byte aligned: scalar loads
-      for (int i = tid; i < cnt; i += 256) atomicAdd(&h[dig(__ldcs(k + i))], 1u);
+    if (segmented) {
+      // Segment starts need not be 16-byte aligned: 16-byte loads of the aligned
+      // window around the tile, counting only the tile's own elements; a vector
+      // that would pass the array's end is read element by element.
+      const int mis = (int)((reinterpret_cast<uintptr_t>(k) & 15u) >> 2);
+      const int64_t a0 = start - mis;  // element index of the window's first word
+      const uint4* k4 = reinterpret_cast<const uint4*>(p.keys + a0);
+      const int nv = (cnt + mis + 3) >> 2;
+      for (int v = tid; v < nv; v += 256) {
+        const int e0 = v * 4 - mis;  // tile-relative index of the vector's first element
+        uint32_t x[4];
+        if (a0 + (int64_t)v * 4 + 4 <= p.n) {
+          const uint4 q = __ldcs(k4 + v);
+          x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) x[c] = (e0 + c >= 0 && e0 + c < cnt) ? k[e0 + c] : 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (e0 + c >= 0 && e0 + c < cnt) atomicAdd(&h[dig(x[c])], 1u);
+      }
     } else if (cnt == T) {  // full tile: all T/1024 vector loads in flight before counting
       constexpr int NV = T / 1024;
       uint4 x[NV];

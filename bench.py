@@ -395,7 +395,7 @@ def oracle_step(inp):
 def cpu_baseline(budget_s=12.0, n=1 << 22):
     inp = oracle_inputs(n)
     total, reps = 0.0, 0
-    while total < budget_s and reps < 20:
+    while total < budget_s and reps < 400:
         total += oracle_step(inp)
         reps += 1
     return {"value": round(2 * n * reps / total / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -122,6 +122,7 @@ struct SegLayout {
   int64_t lb_stride = 0;    // look-back status words per digit
   int passes = 0;
   size_t keys_tmp = 0, vals_tmp = 0, small_ids = 0, seg_slot = 0, seg_tile0 = 0, slot_seg = 0;
+  size_t tiny_ids = 0, bin_first = 0;  // tiny segments packed several to a tile
   size_t tile_seg = 0, seg_base = 0, ctr = 0, lookback = 0;
   size_t zero_begin = 0, zero_bytes = 0, total = 0;
 };

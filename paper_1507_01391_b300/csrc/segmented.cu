@@ -8,7 +8,13 @@
 //                   the small-segment queue, longer ones get a run of sweep tiles;
 //   2. k_seg_small  (sort only) persistent blocks pull small segments from the
 //                   queue and sort each whole in shared memory with the Lemma 1
-//                   schedule (tile_sort.cuh): one read and one write per key;
+//                   schedule (tile_sort.cuh): one read and one write per key.
+//                   Segments of more than kTinyMax keys take a tile each; tiny ones
+//                   are packed, in order, into bins of consecutive tiny segments
+//                   whose key counts sum to less than a tile (a bin holds the
+//                   segments whose running key offset lies in one kTinyMax-wide
+//                   interval), and a bin is sorted as one tile of items ordered by
+//                   (segment in the bin, key, position);
 //   3. per digit pass: k_tile_counts over the long segments' tiles, k_scan_offsets
 //                   (running sums over all tiles), k_seg_digit_base (each segment's
 //                   digit starts from those sums), then k_sweep in segment mode: a
@@ -22,7 +28,12 @@
 
 namespace bcf {
 
-enum : int { C_NSMALL = 0, C_NLARGE = 1, C_NTILES = 2, C_QUEUE = 3, C_TICKET = 4 /* +pass */ };
+enum : int { C_NSMALL = 0, C_NLARGE = 1, C_NTILES = 2, C_QUEUE = 3, C_TICKET = 4 /* +pass */,
+             C_NTINY = 8, C_NBINS = 9 };
+
+// Tiny segments (1..kTinyMax keys) share tiles: a bin's keys sum to at most
+// 2 * kTinyMax - 1 < kL1Tile.
+constexpr int kTinyMax = kL1Tile / 2;
 
 struct PlanParams {
   const int64_t* offs;
@@ -32,7 +43,10 @@ struct PlanParams {
   int64_t tiles_cap;    // capacity of tile_seg
   int64_t slots_cap;    // capacity of slot_seg
   const int32_t* seg_w; // partition widths (checked when given)
-  int32_t* small_ids;
+  int32_t* small_ids;   // segments of kTinyMax + 1 .. small_max keys (a tile each)
+  int32_t* tiny_ids;    // segments of 1 .. kTinyMax keys, in order
+  uint32_t* bin_first;  // per bin: ~(index in tiny_ids of its first segment), max-reduced
+  int64_t bins_cap;
   int32_t* seg_slot;
   int32_t* seg_tile0;
   int32_t* tile_seg;
@@ -49,7 +63,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
   const int tid = threadIdx.x;
   if (tid == 0) bad = (p.nseg > 0 && (p.offs[0] != 0 || p.offs[p.nseg] != p.n_total)) ? 1 : 0;
   __syncthreads();
-  uint32_t run_small = 0, run_large = 0, run_tiles = 0;
+  uint32_t run_small = 0, run_large = 0, run_tiles = 0, run_tiny = 0, run_tiny_keys = 0;
   for (int64_t base = 0; base < p.nseg; base += kPlanThreads) {
     const int64_t s = base + tid;
     int64_t len = 0;
@@ -62,12 +76,17 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
         len = 0;
       }
     }
-    const bool small = len > 0 && len <= p.small_max;
+    const bool tiny = len > 0 && len <= kTinyMax && p.small_max > 0;
+    const bool small = len > kTinyMax && len <= p.small_max;
     const bool large = len > p.small_max;
     const uint32_t tiles = large ? (uint32_t)((len + p.tile - 1) / p.tile) : 0u;
     uint32_t tot;
     const uint32_t es = block_excl_scan<kPlanThreads>(small ? 1u : 0u, scratch, &tot);
     const uint32_t add_small = tot;
+    const uint32_t ey = block_excl_scan<kPlanThreads>(tiny ? 1u : 0u, scratch, &tot);
+    const uint32_t add_tiny = tot;
+    const uint32_t ek = block_excl_scan<kPlanThreads>(tiny ? (uint32_t)len : 0u, scratch, &tot);
+    const uint32_t add_tiny_keys = tot;
     const uint32_t el = block_excl_scan<kPlanThreads>(large ? 1u : 0u, scratch, &tot);
     const uint32_t add_large = tot;
     const uint32_t et = block_excl_scan<kPlanThreads>(tiles, scratch, &tot);
@@ -76,6 +95,16 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
       p.seg_slot[s] = -1;
       p.seg_tile0[s] = -1;
       if (small) p.small_ids[run_small + es] = (int32_t)s;
+      if (tiny) {
+        // bin = running key offset / kTinyMax; offsets grow by at most kTinyMax per
+        // segment, so bins are consecutive and each bin's first segment is the
+        // smallest index mapped to it
+        const uint32_t idx = run_tiny + ey;
+        const uint32_t bin = (run_tiny_keys + ek) / kTinyMax;
+        p.tiny_ids[idx] = (int32_t)s;
+        if ((int64_t)bin < p.bins_cap) atomicMax(&p.bin_first[bin], ~idx);
+        else bad = 1;
+      }
       if (large) {
         const uint32_t slot = run_large + el, t0 = run_tiles + et;
         if ((int64_t)slot < p.slots_cap && (int64_t)(t0 + tiles) <= p.tiles_cap) {
@@ -91,9 +120,21 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
     run_small += add_small;
     run_large += add_large;
     run_tiles += add_tiles;
+    run_tiny += add_tiny;
+    run_tiny_keys += add_tiny_keys;
   }
   __syncthreads();
   if (tid == 0) {
+    // Bins in use: every id up to the last tiny segment's bin is taken (ids grow
+    // by at most one per segment).  The total key count can reach one bin past
+    // it; that bin has no first segment (its word is still zero).
+    uint32_t nbins = 0;
+    if (run_tiny > 0) {
+      nbins = (uint32_t)min((int64_t)(run_tiny_keys / kTinyMax) + 1, p.bins_cap);
+      while (nbins > 0 && p.bin_first[nbins - 1] == 0u) --nbins;
+    }
+    p.ctr[C_NTINY] = run_tiny;
+    p.ctr[C_NBINS] = nbins;
     p.ctr[C_NSMALL] = run_small;
     p.ctr[C_NLARGE] = (int64_t)run_large <= p.slots_cap ? run_large : (uint32_t)p.slots_cap;
     p.ctr[C_NTILES] = (int64_t)run_tiles <= p.tiles_cap ? run_tiles : (uint32_t)p.tiles_cap;
@@ -124,7 +165,68 @@ __global__ void __launch_bounds__(256) k_seg_digit_base(const uint32_t* __restri
   seg_base[(size_t)slot * 256 + threadIdx.x] = (uint32_t)lo + e;
 }
 
-// Persistent blocks: sort every small segment whole with the Lemma 1 schedule.
+// One bin of tiny segments as one Lemma 1 tile.  Segment j of the bin (j < cnt)
+// occupies packed positions [cum[j], cum[j+1]); its keys become items
+// (j << 44 | key << 12 | packed position), whose order is (segment, key, input
+// order), so sorted position t of segment j is its rank t - cum[j].
+template <int VB>
+__device__ __forceinline__ void sort_bin(const uint32_t* __restrict__ keys_in, const void* __restrict__ vals_in,
+                                         uint32_t* __restrict__ keys_out, void* __restrict__ vals_out,
+                                         const int64_t* __restrict__ offs, const int32_t* __restrict__ ids,
+                                         int cnt, unsigned long long* X, unsigned long long* Y, uint16_t* cum,
+                                         uint32_t* scratch) {
+  using VT = typename ValT<VB>::type;
+  constexpr int PER = kL1Tile / kL1Threads;  // bin segments per thread in the scan
+  const int tid = threadIdx.x;
+  uint32_t len[PER], sum = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = tid * PER + q;
+    len[q] = j < cnt ? (uint32_t)(offs[ids[j] + 1] - offs[ids[j]]) : 0u;
+    sum += len[q];
+  }
+  uint32_t total;
+  uint32_t run = block_excl_scan<kL1Threads>(sum, scratch, &total);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int j = tid * PER + q;
+    if (j <= cnt) cum[j] = (uint16_t)run;  // cum[cnt] = total
+    run += len[q];
+  }
+  __syncthreads();
+  for (int q = tid; q < kL1Tile; q += kL1Threads) {
+    unsigned long long it = ~0ull;  // padding sorts last
+    if (q < (int)total) {
+      int lo = 0, hi = cnt - 1;  // last j with cum[j] <= q
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)cum[mid] <= q) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint32_t key = keys_in[offs[ids[lo]] + (q - (int)cum[lo])];
+      it = ((unsigned long long)lo << 44) | ((unsigned long long)key << 12) | (unsigned)q;
+    }
+    BCF_TR(&X[q], 8, 1, TS_L1_IO);
+    X[q] = it;
+  }
+  __syncthreads();
+  lemma1_schedule(X, Y);
+  const VT* vin = reinterpret_cast<const VT*>(vals_in);
+  VT* vout = reinterpret_cast<VT*>(vals_out);
+  for (int t = tid; t < (int)total; t += kL1Threads) {
+    BCF_TR(&Y[t], 8, 0, TS_L1_IO);
+    const unsigned long long it = Y[t];
+    const int j = (int)(it >> 44), q = (int)(it & 0xFFFu);
+    const int64_t lo = offs[ids[j]];
+    const int c = (int)cum[j];
+    keys_out[lo + (t - c)] = (uint32_t)(it >> 12);
+    if (VB) vout[lo + (t - c)] = vin ? vin[lo + (q - c)] : VT(lo + (q - c));
+  }
+  __syncthreads();
+}
+
+// Persistent blocks: sort every small segment whole with the Lemma 1 schedule --
+// first the segments that take a tile each, then the bins of tiny segments.
 template <int VB>
 __global__ void __launch_bounds__(kL1Threads) k_seg_small(const uint32_t* __restrict__ keys_in,
                                                           const void* __restrict__ vals_in,
@@ -132,20 +234,33 @@ __global__ void __launch_bounds__(kL1Threads) k_seg_small(const uint32_t* __rest
                                                           void* __restrict__ vals_out,
                                                           const int64_t* __restrict__ offs,
                                                           const int32_t* __restrict__ small_ids,
+                                                          const int32_t* __restrict__ tiny_ids,
+                                                          const uint32_t* __restrict__ bin_first,
                                                           uint32_t* ctr) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* X = reinterpret_cast<unsigned long long*>(smem);
   unsigned long long* Y = X + kL1Tile;
+  uint16_t* cum = reinterpret_cast<uint16_t*>(Y + kL1Tile);  // kL1Tile + 1 entries
   __shared__ int item;
+  __shared__ uint32_t scratch[32];
+  const int nsmall = (int)ctr[C_NSMALL], nbins = (int)ctr[C_NBINS], ntiny = (int)ctr[C_NTINY];
   while (true) {
     if (threadIdx.x == 0) item = (int)atomicAdd(&ctr[C_QUEUE], 1u);
     __syncthreads();
     const int i = item;
     __syncthreads();
-    if (i >= (int)ctr[C_NSMALL]) break;
-    const int seg = small_ids[i];
-    const int64_t lo = offs[seg];
-    lemma1_tile<VB>(keys_in, vals_in, keys_out, vals_out, lo, (int)(offs[seg + 1] - lo), X, Y);
+    if (i >= nsmall + nbins) break;
+    if (i < nsmall) {
+      const int seg = small_ids[i];
+      const int64_t lo = offs[seg];
+      lemma1_tile<VB>(keys_in, vals_in, keys_out, vals_out, lo, (int)(offs[seg + 1] - lo), X, Y);
+    } else {
+      const int b = i - nsmall;
+      const int first = (int)~bin_first[b];
+      const int last = b + 1 < nbins ? (int)~bin_first[b + 1] : ntiny;
+      sort_bin<VB>(keys_in, vals_in, keys_out, vals_out, offs, tiny_ids + first, last - first, X, Y, cum,
+                   scratch);
+    }
   }
 }
 
@@ -189,6 +304,7 @@ SegLayout seg_layout(int64_t n_total, int64_t nseg, int vb, int passes, bool sor
   L.keys_tmp = take((size_t)n_total * 4);
   L.vals_tmp = take((size_t)n_total * vb);
   L.small_ids = take((size_t)std::max<int64_t>(nseg, 1) * 4);
+  L.tiny_ids = take((size_t)std::max<int64_t>(nseg, 1) * 4);
   L.seg_slot = take((size_t)std::max<int64_t>(nseg, 1) * 4);
   L.seg_tile0 = take((size_t)std::max<int64_t>(nseg, 1) * 4);
   L.slot_seg = take((size_t)L.slots_cap * 4);
@@ -196,22 +312,25 @@ SegLayout seg_layout(int64_t n_total, int64_t nseg, int vb, int passes, bool sor
   L.seg_base = take((size_t)L.slots_cap * 256 * 4);  // digit starts of the current pass
   L.zero_begin = off;
   L.ctr = take(16 * 4);
+  L.bin_first = take((size_t)(n_total / kTinyMax + 2) * 4);  // zeroed: 0 = bin not started
   L.lookback = take((size_t)L.lb_stride * 256 * 4);  // tile counts -> running sums (one pass at a time)
   L.zero_bytes = off - L.zero_begin;
   L.total = off;
   return L;
 }
 
+constexpr size_t kSegSmallSmem = kL1SmemBytes + (kL1Tile + 8) * 2;  // items + packed offsets
+
 template <int VB>
 static cudaError_t small_sort(const uint32_t* ki, const void* vi, uint32_t* ko, void* vo,
-                              const int64_t* offs, const int32_t* ids, uint32_t* ctr, int64_t nseg,
-                              cudaStream_t s) {
+                              const int64_t* offs, const int32_t* ids, const int32_t* tiny_ids,
+                              const uint32_t* bin_first, uint32_t* ctr, int64_t nseg, cudaStream_t s) {
   auto k = k_seg_small<VB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kL1SmemBytes);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmallSmem);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(nseg, (int64_t)sms() * 3);
   if (grid <= 0) return cudaSuccess;
-  k<<<(unsigned)grid, kL1Threads, kL1SmemBytes, s>>>(ki, vi, ko, vo, offs, ids, ctr);
+  k<<<(unsigned)grid, kL1Threads, kSegSmallSmem, s>>>(ki, vi, ko, vo, offs, ids, tiny_ids, bin_first, ctr);
   return cudaGetLastError();
 }
 
@@ -236,6 +355,9 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
   pp.slots_cap = L.slots_cap;
   pp.seg_w = seg_w;
   pp.small_ids = I32(L.small_ids);
+  pp.tiny_ids = I32(L.tiny_ids);
+  pp.bin_first = U32(L.bin_first);
+  pp.bins_cap = n_total / kTinyMax + 2;
   pp.seg_slot = I32(L.seg_slot);
   pp.seg_tile0 = I32(L.seg_tile0);
   pp.tile_seg = I32(L.tile_seg);
@@ -247,9 +369,18 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
 
   if (L.small_max > 0) {
     switch (vb) {
-      case 0: e = small_sort<0>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), ctr, nseg, s); break;
-      case 4: e = small_sort<4>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), ctr, nseg, s); break;
-      case 8: e = small_sort<8>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), ctr, nseg, s); break;
+      case 0:
+        e = small_sort<0>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), I32(L.tiny_ids),
+                          U32(L.bin_first), ctr, nseg, s);
+        break;
+      case 4:
+        e = small_sort<4>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), I32(L.tiny_ids),
+                          U32(L.bin_first), ctr, nseg, s);
+        break;
+      case 8:
+        e = small_sort<8>(keys_in, vals_in, keys_out, vals_out, offs, I32(L.small_ids), I32(L.tiny_ids),
+                          U32(L.bin_first), ctr, nseg, s);
+        break;
     }
     if (e != cudaSuccess) return e;
   }

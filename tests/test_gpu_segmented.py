@@ -63,6 +63,11 @@ def _seg_sort_case(bcf, keys, vals, offs, key_bits=32):
     [1, 10_000, 3, 8193, 5, 70_001],               # misaligned long segments
     [4096 * 3],                                     # one long segment
     [17] * 50,                                      # many small ones
+    # tiny segments (<= 2048 keys) share tiles: bins cut at running offsets 2048,
+    # 4096, ...; 2048/2049 and 4096/4097 are the tiny/one-tile/long boundaries
+    [2048, 1, 2047, 2, 2048, 0, 2049, 1, 1, 4096, 30, 5000, 7, 2048, 2048, 1],
+    [1] * 3000 + [2048] + [3] * 700,                # thousands of one-key segments in a bin
+    [1000, 9000, 1000, 1500, 0, 600, 4097, 2000, 47],  # tiny ones separated by long ones
 ])
 @pytest.mark.parametrize("vb", [0, 4, 8])
 def test_segmented_sort_sizes(bcf, sizes, vb):

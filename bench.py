@@ -46,7 +46,7 @@ FALLBACK_HBM_GBS = 6400.0
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
 # it was taken on: if permute.cu changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "k_pb_bucket<4,512> + k_pb_place<4,0> (bucketed kv permute, both passes)",
-               "source": "permute_bucketed.cu", "source_sha1": "95299345f7b51aa4242a2162732e1f2377c81c2e",
+               "source": "permute_bucketed.cu", "source_sha1": "1572774d5465c73fed0316240453e3f0cf367cd5",
                "bytes": 578021632,
                "summary": "profiles/k_pb_bucketed_permute_kv_2pow24.md"}
 

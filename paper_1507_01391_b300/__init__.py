@@ -111,10 +111,16 @@ def __getattr__(name):  # raw entry points: bcf_sort, bcf_permute, ...; the auto
 
 
 # ------------------------------------------------------------------ helpers
+_cuda_ok = False
+
+
 def _torch():
+    global _cuda_ok
     import torch
-    if not torch.cuda.is_available():
-        raise RuntimeError("bcf needs a CUDA device; there is no CPU path")
+    if not _cuda_ok:  # checked once per process
+        if not torch.cuda.is_available():
+            raise RuntimeError("bcf needs a CUDA device; there is no CPU path")
+        _cuda_ok = True
     return torch
 
 
@@ -206,8 +212,8 @@ def partition(keys, vals, w, balanced=False, keys_out=None, vals_out=None, ws=No
     keys_out = torch.empty_like(keys) if keys_out is None else keys_out
     if vals is not None and vals_out is None:
         vals_out = torch.empty_like(vals)
-    need = partition_workspace_size(n, w, vb, flags)
-    ws = workspace(need, keys.device) if ws is None else ws
+    if ws is None:  # a caller's workspace is checked against the size by the library
+        ws = workspace(partition_workspace_size(n, w, vb, flags), keys.device)
     _check(lib().bcf_partition(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), n, w, vb,
                                flags, _ptr(ws), ws.numel() * ws.element_size(), _stream(stream)),
            "bcf_partition")

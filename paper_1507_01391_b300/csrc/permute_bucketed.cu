@@ -304,9 +304,17 @@ int sm_count_cached() {
   return sms[dev];
 }
 
+// Raise a kernel's dynamic shared-memory limit once per device (`done` is the
+// caller's per-kernel flag array).
 template <typename K>
-cudaError_t set_smem(K kernel, int bytes) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+cudaError_t set_smem(K kernel, int bytes, bool (&done)[64]) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (done[dev]) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
 }
 
 template <int VB, int NB>
@@ -323,29 +331,20 @@ cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, u
   cudaError_t e = cudaMemsetAsync(fill, 0, (size_t)blocks * 4, s);
   if (e != cudaSuccess) return e;
   constexpr int sm1 = pb_smem_bytes<NB>();
-  static bool ready1 = false;
-  if (!ready1) {
-    if ((e = set_smem(k_pb_bucket<VB, NB>, sm1)) != cudaSuccess) return e;
-    ready1 = true;
-  }
+  static bool ready1[64] = {};
+  if ((e = set_smem(k_pb_bucket<VB, NB>, sm1, ready1)) != cudaSuccess) return e;
   const int grid = std::min(ntiles, sm_count_cached());
   k_pb_bucket<VB, NB><<<grid, kPbThreads, sm1, s>>>(pi, sk, sv, K1, V1, P1, fill, n, row_len, ntiles,
                                                     status_word());
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int sm2 = kPbBlock * 4 + (check ? kPbBlock / 8 : 0);
   if (check) {
-    static bool ready2 = false;
-    if (!ready2) {
-      if ((e = set_smem(k_pb_place<VB, true>, sm2)) != cudaSuccess) return e;
-      ready2 = true;
-    }
+    static bool ready2[64] = {};
+    if ((e = set_smem(k_pb_place<VB, true>, sm2, ready2)) != cudaSuccess) return e;
     k_pb_place<VB, true><<<blocks, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, status_word());
   } else {
-    static bool ready2 = false;
-    if (!ready2) {
-      if ((e = set_smem(k_pb_place<VB, false>, sm2)) != cudaSuccess) return e;
-      ready2 = true;
-    }
+    static bool ready2[64] = {};
+    if ((e = set_smem(k_pb_place<VB, false>, sm2, ready2)) != cudaSuccess) return e;
     k_pb_place<VB, false><<<blocks, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, status_word());
   }
   return cudaGetLastError();

@@ -223,6 +223,44 @@ def lemma1_sort(M, L=None):
     return M
 
 
+def theorem1_sort(M, record=None, L=None):
+    """Theorem 1 (Sec. 2) on an m x m matrix, m a perfect square: super-rows of
+    sqrt(m) adjacent rows each sorted by Lemma 1; columns sorted ascending; super-
+    rows sorted again in alternating order (super-row 0 ascending); columns sorted;
+    rows sorted.  Returns the matrix, sorted in row-major order.  `record`, if
+    given, receives a copy of the matrix after each of the five steps."""
+    L = L or lib()
+    M = np.array(M, dtype=np.uint32, order="C", copy=True)
+    m = M.shape[0]
+    r = int(round(m ** 0.5))
+    if M.shape != (m, m) or r * r != m:
+        raise OracleError("Theorem 1 needs a square matrix whose side is a perfect square")
+
+    def sort_super_rows(alternating):
+        for g in range(r):
+            blk = np.ascontiguousarray(M[g * r:(g + 1) * r])
+            _check(L.oracle_lemma1_sort(_ptr(blk), r, m))  # ascending, row-major
+            if alternating and g % 2 == 1:
+                blk = blk.reshape(-1)[::-1].reshape(r, m)  # descending order
+            M[g * r:(g + 1) * r] = blk
+
+    def note():
+        if record is not None:
+            record.append(M.copy())
+
+    sort_super_rows(False)
+    note()
+    M[:] = np.sort(M, axis=0)  # columns ascending (top to bottom)
+    note()
+    sort_super_rows(True)
+    note()
+    M[:] = np.sort(M, axis=0)
+    note()
+    M[:] = np.sort(M, axis=1)  # rows ascending
+    note()
+    return M
+
+
 def bank_count(req, lane, addr, width, L=None):
     """Return (hw_wavefronts, hw_conflicts, strict_conflicts) for a trace."""
     L = L or lib()

@@ -390,3 +390,71 @@ def test_bank_broadcast_and_wide_accesses(orc):
     res = orc.bank_count(req2, np.concatenate([lane, lane]),
                          np.concatenate([addr, addr]), np.concatenate([width, width]))
     assert res == (64, 62, 62)
+
+
+# ------------------------------------------------------- Theorem 1 (Sec. 2) ----
+def _contiguous(rows):
+    return len(rows) == 0 or rows[-1] - rows[0] + 1 == len(rows)
+
+
+def _theorem1_steps_hold(orc, M):
+    """Dirty-row bounds of the proof of Theorem 1 on a 0-1 matrix: at most one
+    dirty row per super-row after the first step; dirty rows contiguous once the
+    columns are sorted; at most two after the alternating super-row sorts; one
+    after the next column sort; none at the end."""
+    m = M.shape[0]
+    r = int(round(m ** 0.5))
+    rec = []
+    out = orc.theorem1_sort(M, record=rec)
+    s1, s2, s3, s4, s5 = rec
+    for g in range(r):
+        assert _dirty_rows(s1[g * r:(g + 1) * r]) <= 1
+    assert _dirty_rows(s1) <= r
+    assert _contiguous(_dirty_row_indices(s2))
+    assert _dirty_rows(s3) <= 2
+    assert _dirty_rows(s4) <= 1
+    assert np.all(np.diff(s5.reshape(-1).astype(np.int64)) >= 0)
+    return out
+
+
+def test_theorem1_zero_one_exhaustive_4x4(orc):
+    for bits in range(1 << 16):
+        M = ((bits >> np.arange(16)) & 1).astype(np.uint32).reshape(4, 4)
+        _theorem1_steps_hold(orc, M)
+
+
+def test_theorem1_zero_one_sampled_9x9(orc):
+    g = synth.rng(91)
+    for _ in range(3000):
+        M = (g.random((9, 9)) < g.random()).astype(np.uint32)
+        _theorem1_steps_hold(orc, M)
+
+
+@pytest.mark.parametrize("m", [4, 9, 16])
+def test_theorem1_sorts_random_matrices(orc, m):
+    g = synth.rng(m)
+    for _ in range(200):
+        M = g.integers(0, 1000, size=(m, m), dtype=np.uint32)
+        out = orc.theorem1_sort(M)
+        assert np.array_equal(out.reshape(-1), np.sort(M.reshape(-1)))
+
+
+def test_theorem1_rejects_other_shapes(orc):
+    with pytest.raises(orc.OracleError):
+        orc.theorem1_sort(np.zeros((4, 8), np.uint32))
+    with pytest.raises(orc.OracleError):
+        orc.theorem1_sort(np.zeros((5, 5), np.uint32))
+
+
+def test_corollary1_partition_small_alphabets(orc):
+    """Corollary 1: with w <= sqrt(m), Lemma 1 partitions a matrix of labels (the
+    row sorts then only order labels, the radix-sort case).  Every 2 x 4 matrix
+    over labels {0, 1, 2} and sampled 3 x 9 ones end partitioned."""
+    for code in range(3 ** 8):
+        M = np.array([(code // 3 ** k) % 3 for k in range(8)], dtype=np.uint32).reshape(2, 4)
+        out = orc.lemma1_sort(M)
+        assert np.array_equal(out.reshape(-1), np.sort(M.reshape(-1)))
+    g = synth.rng(39)
+    for _ in range(2000):
+        M = g.integers(0, 3, size=(3, 9), dtype=np.uint32)
+        assert np.array_equal(orc.lemma1_sort(M).reshape(-1), np.sort(M.reshape(-1)))

@@ -12,10 +12,14 @@
  * Buffer layout (device memory, 16-byte aligned, owned by the caller): a 64-bit
  * record counter, 8 bytes of padding, then records of four uint32:
  *   [0] request id  -- shared by the lanes of one warp-wide access
- *   [1] lane        -- 0..31
+ *   [1] thread index in the block (lane = low 5 bits) | block index << 16
  *   [2] address     -- byte offset in the block's shared-memory window
- *   [3] width | store << 8 | site << 16   (store: 0 load, 1 store, 2 atomic;
- *                    width 4, 8 or 16 bytes; site: the access site, see trace.cuh)
+ *   [3] width | store << 8 | site << 16   (store: 0 load, 1 store, 2 atomic,
+ *                    3 barrier; width 4, 8 or 16 bytes, 0 for a barrier; site:
+ *                    the access site, see trace.cuh)
+ * After every block-wide barrier of a traced kernel each warp appends one barrier
+ * record (store 3), so a replay can tell which accesses may race: those of
+ * different threads to one word between the same two barriers, one a store.
  * The counter keeps counting past the buffer's capacity; records beyond it are
  * dropped.  One trace at a time per process; kernels of other calls that run while
  * it is active are traced too.

@@ -66,6 +66,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "oracle_l1_row_to_col": [P, I64, I64],
         "oracle_l1_col_to_row": [P, I64, I64],
         "oracle_lemma1_sort": [P, I64, I64],
+        "oracle_race_check": [P, I64, P, P],
         "oracle_bank_count": [P, P, P, P, I64, P, P, P],
     }
     for name, args in sig.items():
@@ -259,6 +260,17 @@ def theorem1_sort(M, record=None, L=None):
     M[:] = np.sort(M, axis=1)  # rows ascending
     note()
     return M
+
+
+def race_check(rec, L=None):
+    """(racing words, words checked) of a shared-memory trace: records (N, 4) of
+    uint32 as the trace build writes them (request, thread | block << 16, address,
+    width | kind << 8 | site << 16)."""
+    L = L or lib()
+    rec = np.ascontiguousarray(rec, dtype=np.uint32)
+    races, words = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(L.oracle_race_check(_ptr(rec), rec.shape[0], ctypes.byref(races), ctypes.byref(words)))
+    return races.value, words.value
 
 
 def bank_count(req, lane, addr, width, L=None):

@@ -357,6 +357,82 @@ int oracle_lemma1_sort(uint32_t* M, int64_t w, int64_t m) {
     return ORACLE_OK;
 }
 
+/* ---- Race check of a trace (between block-wide barriers) ---- */
+typedef struct {
+    uint32_t block, epoch, word, thread;
+    int store;
+} race_entry;
+
+static int race_cmp(const void* a, const void* b) {
+    const race_entry* x = (const race_entry*)a;
+    const race_entry* y = (const race_entry*)b;
+    if (x->block != y->block) return x->block < y->block ? -1 : 1;
+    if (x->epoch != y->epoch) return x->epoch < y->epoch ? -1 : 1;
+    if (x->word != y->word) return x->word < y->word ? -1 : 1;
+    return 0;
+}
+
+int oracle_race_check(const uint32_t* rec, int64_t nrec, int64_t* races, int64_t* words) {
+    if (nrec < 0 || !races || !words) return ORACLE_E_ARG;
+    /* barriers seen so far by each (block, warp) */
+    uint32_t* seen = (uint32_t*)calloc((size_t)65536 * 32, sizeof(uint32_t));
+    int64_t cap = 0;
+    for (int64_t r = 0; r < nrec; ++r) {
+        const uint32_t kind = (rec[4 * r + 3] >> 8) & 0xFF, width = rec[4 * r + 3] & 0xFF;
+        if (kind == 0 || kind == 1) cap += (width + 3) / 4;
+    }
+    race_entry* e = (race_entry*)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(race_entry));
+    if (!seen || !e) {
+        free(seen);
+        free(e);
+        return ORACLE_E_NOMEM;
+    }
+    int64_t ne = 0;
+    for (int64_t r = 0; r < nrec; ++r) {
+        const uint32_t thread = rec[4 * r + 1] & 0xFFFF, block = rec[4 * r + 1] >> 16;
+        const uint32_t kind = (rec[4 * r + 3] >> 8) & 0xFF, width = rec[4 * r + 3] & 0xFF;
+        uint32_t* count = &seen[(size_t)block * 32 + ((thread >> 5) & 31)];
+        if (kind == 3) {
+            *count += 1;
+            continue;
+        }
+        if (kind != 0 && kind != 1) continue;
+        for (uint32_t q = 0; q < (width + 3) / 4; ++q) {
+            e[ne].block = block;
+            e[ne].epoch = *count;
+            e[ne].word = rec[4 * r + 2] / 4 + q;
+            e[ne].thread = thread;
+            e[ne].store = (int)kind;
+            ++ne;
+        }
+    }
+    qsort(e, (size_t)ne, sizeof(race_entry), race_cmp);
+    int64_t nr = 0, nw = 0;
+    for (int64_t a = 0; a < ne;) {
+        int64_t b = a;
+        while (b < ne && race_cmp(&e[a], &e[b]) == 0) ++b;
+        /* one group: the accesses of one word in one segment of one block */
+        int64_t writer = -1;
+        int race = 0;
+        for (int64_t i = a; i < b; ++i) {
+            if (!e[i].store) continue;
+            if (writer < 0) writer = e[i].thread;
+            else if ((uint32_t)writer != e[i].thread) race = 1;
+        }
+        if (writer >= 0)
+            for (int64_t i = a; i < b; ++i)
+                if (!e[i].store && e[i].thread != (uint32_t)writer) race = 1;
+        nr += race;
+        ++nw;
+        a = b;
+    }
+    free(seen);
+    free(e);
+    *races = nr;
+    *words = nw;
+    return ORACLE_OK;
+}
+
 /* ---- Bank model (Sec. 1, "Model of Computation") ----
  * Shared memory is w = 32 banks of 4-byte words; the word at byte address a is in
  * bank (a/4) mod 32.  Hardware rule: a request is split into phases by access

@@ -78,6 +78,15 @@ int oracle_lemma1_sort(uint32_t* M, int64_t w, int64_t m);
  * (4, 8 or 16 bytes).  Outputs: total hardware wavefronts, hardware conflicts
  * (wavefronts above one per phase), and conflicts under the strict model in
  * which two lanes may never touch the same bank in one request. */
+/* Race check of a shared-memory trace (records of four uint32: request id,
+ * thread | block << 16, byte address, width | kind << 8 | site << 16, kind 0 load,
+ * 1 store, 2 atomic, 3 barrier).  Each warp's accesses are split by its barrier
+ * records into segments; accesses of different threads of one block to one 4-byte
+ * word in the same segment race when at least one is a store (atomics are not
+ * checked).  *races receives the number of racing words, *words the number of
+ * (block, segment, word) groups checked. */
+int oracle_race_check(const uint32_t* rec, int64_t nrec, int64_t* races, int64_t* words);
+
 int oracle_bank_count(const int64_t* req, const int32_t* lane, const uint32_t* addr,
                       const int32_t* width, int64_t nrec, int64_t* hw_wavefronts,
                       int64_t* hw_conflicts, int64_t* dmm_conflicts);

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kL1Threads) k_partition_l1(const uint32_t* __r
   const int64_t start = tile * kL1Tile;
   const int len = (int)min((int64_t)kL1Tile, n - start);
   tstart[tid] = 0;  // kL1Threads == 256 labels
-  __syncthreads();
+  BCF_SYNC();
   for (int q = tid; q < kL1Tile; q += kL1Threads) {
     unsigned long long d = 0x100ull;  // padding sorts after every label
     if (q < len) {
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kL1Threads) k_partition_l1(const uint32_t* __r
     BCF_TR(&X[q], 8, 1, TS_L1_IO);
     X[q] = (d << 32) | (unsigned)q;
   }
-  __syncthreads();
+  BCF_SYNC();
   uint32_t total;
   const uint32_t c = tstart[tid];
   const uint32_t e = block_excl_scan<kL1Threads>(c, scratch, &total);

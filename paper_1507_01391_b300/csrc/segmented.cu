@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = (p.nseg > 0 && (p.offs[0] != 0 || p.offs[p.nseg] != p.n_total)) ? 1 : 0;
-  __syncthreads();
+  BCF_SYNC();
   uint32_t run_small = 0, run_large = 0, run_tiles = 0, run_tiny = 0, run_tiny_keys = 0;
   for (int64_t base = 0; base < p.nseg; base += kPlanThreads) {
     const int64_t s = base + tid;
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
     run_tiny += add_tiny;
     run_tiny_keys += add_tiny_keys;
   }
-  __syncthreads();
+  BCF_SYNC();
   if (tid == 0) {
     // Bins in use: every id up to the last tiny segment's bin is taken (ids grow
     // by at most one per segment).  The total key count can reach one bin past
@@ -193,7 +193,7 @@ __device__ __forceinline__ void sort_bin(const uint32_t* __restrict__ keys_in, c
     if (j <= cnt) cum[j] = (uint16_t)run;  // cum[cnt] = total
     run += len[q];
   }
-  __syncthreads();
+  BCF_SYNC();
   for (int q = tid; q < kL1Tile; q += kL1Threads) {
     unsigned long long it = ~0ull;  // padding sorts last
     if (q < (int)total) {
@@ -209,7 +209,7 @@ __device__ __forceinline__ void sort_bin(const uint32_t* __restrict__ keys_in, c
     BCF_TR(&X[q], 8, 1, TS_L1_IO);
     X[q] = it;
   }
-  __syncthreads();
+  BCF_SYNC();
   lemma1_schedule(X, Y);
   const VT* vin = reinterpret_cast<const VT*>(vals_in);
   VT* vout = reinterpret_cast<VT*>(vals_out);
@@ -222,7 +222,7 @@ __device__ __forceinline__ void sort_bin(const uint32_t* __restrict__ keys_in, c
     keys_out[lo + (t - c)] = (uint32_t)(it >> 12);
     if (VB) vout[lo + (t - c)] = vin ? vin[lo + (q - c)] : VT(lo + (q - c));
   }
-  __syncthreads();
+  BCF_SYNC();
 }
 
 // Persistent blocks: sort every small segment whole with the Lemma 1 schedule --
@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(kL1Threads) k_seg_small(const uint32_t* __rest
   const int nsmall = (int)ctr[C_NSMALL], nbins = (int)ctr[C_NBINS], ntiny = (int)ctr[C_NTINY];
   while (true) {
     if (threadIdx.x == 0) item = (int)atomicAdd(&ctr[C_QUEUE], 1u);
-    __syncthreads();
+    BCF_SYNC();
     const int i = item;
-    __syncthreads();
+    BCF_SYNC();
     if (i >= nsmall + nbins) break;
     if (i < nsmall) {
       const int seg = small_ids[i];

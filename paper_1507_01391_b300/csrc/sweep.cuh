@@ -82,7 +82,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
     if (lane >= o) x += y;
   }
   if (lane == 31) scratch[warp] = x;
-  __syncthreads();
+  BCF_SYNC();
   if (warp == 0) {
     uint32_t s = lane < WARPS ? scratch[lane] : 0u;
 #pragma unroll
@@ -92,10 +92,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
     }
     if (lane < WARPS) scratch[lane] = s;
   }
-  __syncthreads();
+  BCF_SYNC();
   const uint32_t before = warp ? scratch[warp - 1] : 0u;
   *total = scratch[WARPS - 1];
-  __syncthreads();
+  BCF_SYNC();
   return before + x - v;
 }
 
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
   __shared__ int is_last;
   const int tid = threadIdx.x;
   for (int i = tid; i < 4 * 256; i += THREADS) h[i] = 0;
-  __syncthreads();
+  BCF_SYNC();
   uint32_t mask[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -145,13 +145,13 @@ __global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
     for (int q = 0; q < 4; ++q)
       if (q < p.passes) atomicAdd(&h[q * 256 + ((k >> p.shift[q]) & mask[q])], 1u);
   }
-  __syncthreads();
+  BCF_SYNC();
   for (int i = tid; i < p.passes * 256; i += THREADS)
     if (h[i]) atomicAdd(&p.hist[i], h[i]);
   __threadfence();
-  __syncthreads();
+  BCF_SYNC();
   if (tid == 0) is_last = (atomicAdd(p.done, 1u) == gridDim.x - 1);
-  __syncthreads();
+  BCF_SYNC();
   if (!is_last) return;
   __threadfence();
   for (int q = 0; q < p.passes; ++q) {
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
       for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
-      __syncthreads();
+      BCF_SYNC();
 #pragma unroll
       for (int t = 0; t < 4; ++t)
 #pragma unroll
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
           atomicAdd(&h4[t][dig(x[t][q].z)], 1u);
           atomicAdd(&h4[t][dig(x[t][q].w)], 1u);
         }
-      __syncthreads();
+      BCF_SYNC();
       for (int d = tid; d < RADIX; d += 256) {
         const uint4 c = make_uint4(h4[0][d], h4[1][d], h4[2][d], h4[3][d]);
         *reinterpret_cast<uint4*>(p.counts + (size_t)d * p.stride + t0) = c;
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     }
     const int cnt = (int)min((int64_t)T, hi - start);
     for (int i = tid; i < RADIX; i += 256) h[i] = 0;
-    __syncthreads();
+    BCF_SYNC();
     const uint32_t* k = p.keys + start;
     if (segmented) {
       // Segment starts need not be 16-byte aligned: 16-byte loads of the aligned
@@ -325,13 +325,13 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
       }
       for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[dig(k[i])], 1u);
     }
-    __syncthreads();
+    BCF_SYNC();
     for (int d = tid; d < RADIX; d += 256) {
       const uint32_t c = h[d];
       p.counts[(size_t)d * p.stride + tile] = c;
       tot[d] += c;
     }
-    __syncthreads();
+    BCF_SYNC();
   }
   if (p.totals)
     for (int d = tid; d < RADIX; d += 256)
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* count
       s_base = b;  // segment mode (no totals): plain running sums from 0
     }
   }
-  __syncthreads();
+  BCF_SYNC();
   uint32_t carry = s_base;
   for (int64_t c0 = 0; c0 < tiles; c0 += (int64_t)kScanThreads * kScanPerThread) {
     const int64_t i0 = c0 + (int64_t)tid * kScanPerThread;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
     s_info[0] = tile;
     s_info[1] = (segmented && (uint32_t)tile < ld_relaxed(p.num_tiles)) ? p.tile_seg[tile] : -1;
   }
-  __syncthreads();
+  BCF_SYNC();
   const int tile = s_info[0];
   if (segmented && s_info[1] < 0) return;  // more blocks than tiles this time
   const int seg = s_info[1];
@@ -508,9 +508,9 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
     for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
       vals_s[vsh + i] = reinterpret_cast<const VT*>(p.vals_in)[start + i];
   }
-  __syncthreads();  // mbarrier initialised before anyone waits on it
+  BCF_SYNC();  // mbarrier initialised before anyone waits on it
   mbar_wait(mbar, 0, p.status);
-  __syncthreads();
+  BCF_SYNC();
 
   // The rest is written once for full tiles (no per-key bounds tests) and once
   // for the ragged last tile.
@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
         BCF_TR(&wh[digit(j)], 4, 2, TS_COUNT_ATOM);
         atomicAdd(&wh[digit(j)], 1u);
       }
-    __syncthreads();
+    BCF_SYNC();
 
     // Phase B -- per digit: tile count, tile-exclusive start, and each warp's base
     // (tile start + counts of earlier warps).  In look-back mode the tile count is
@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
         run += c;
       }
     }
-    __syncthreads();
+    BCF_SYNC();
 
     // Phase C -- rank and scatter into shared memory in digit order.  Peers with
     // the same digit come from one ballot per digit bit; the lowest peer claims the
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
     }
     gofs[tid] = base + excl - tstart[tid];
   }
-  __syncthreads();
+  BCF_SYNC();
 
   // Write out: consecutive threads take consecutive sorted positions, so the
   // stores of one digit's run are contiguous in global memory.  Positions are

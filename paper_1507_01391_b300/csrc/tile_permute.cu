@@ -72,11 +72,11 @@ __device__ __forceinline__ int stage_tile(const uint32_t* src, const uint16_t* l
     if (bk) bulk_g2s(in_s, src + start, bk, mbar);
     if (bl) bulk_g2s(lpi_s, lpi + start, bl, mbar);
   }
-  __syncthreads();
+  BCF_SYNC();
   for (int i = (((len * 4) & ~15) >> 2) + threadIdx.x; i < len; i += blockDim.x) in_s[i] = src[start + i];
   for (int i = (((len * 2) & ~15) >> 1) + threadIdx.x; i < len; i += blockDim.x) lpi_s[i] = lpi[start + i];
   mbar_wait(mbar, 0, status);
-  __syncthreads();
+  BCF_SYNC();
   return len;
 }
 
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_scatter(const uint32_t* __r
       set_status(status, DEV_BAD_PERM);
     }
   }
-  __syncthreads();
+  BCF_SYNC();
   write_tile<T>(dst, (int64_t)blockIdx.x * T, len, out_s);
 }
 
@@ -152,7 +152,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
     BCF_TR(&bits[w], 4, 1, TS_COL_TABLE);
     bits[w] = 0;
   }
-  __syncthreads();
+  BCF_SYNC();
   // Key of label p = j*32 + i in destination order: i*M + j.
   for (uint32_t pend = pending; pend; pend &= pend - 1) {
     const int s = warp * SPW + __ffs(pend) - 1, q = s * 32 + lane;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
     BCF_TR_WORD(&src_of[key], 1, TS_COL_PACK);
     src_of[key] = (uint16_t)q;
   }
-  __syncthreads();
+  BCF_SYNC();
   // Ranks: exclusive scan of the words' popcounts (one word per thread).
   uint32_t word = 0;
   if (tid < NW) {
@@ -179,7 +179,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
     if (lane >= o) x += y;
   }
   if (lane == 31) scr[warp] = x;
-  __syncthreads();
+  BCF_SYNC();
   uint32_t before = 0, total = 0;
 #pragma unroll
   for (int g = 0; g < WARPS; ++g) {
@@ -187,7 +187,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
     if (g < warp) before += t;
     total += t;
   }
-  __syncthreads();
+  BCF_SYNC();
   const int L = (int)total;
   if (L == 0) return;
   const int C = (L + 31) / 32;  // columns of the packed matrix
@@ -204,7 +204,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
     BCF_TR(&pkk[t * 32 + r], 4, 1, TS_COL_PACK);
     pkk[t * 32 + r] = in_s[q];
   }
-  __syncthreads();
+  BCF_SYNC();
   if (warp != 0) return;
   // Row `lane` of the packed matrix lives in bank `lane`.
   const int nr = max(0, min(C, L - lane * C));
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
     BCF_TR(&lab[q], 4, 1, TS_COL_READ);
     lab[q] = q < len ? (uint32_t)lpi_s[q] : 0u;
   }
-  __syncthreads();
+  BCF_SYNC();
 
   // Pending slots of this thread; labels outside the tile are dropped (and flagged).
   uint32_t pending = 0;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
       BCF_TR(&tbl[k * 32 + lane], 4, 1, TS_COL_TABLE);
       tbl[k * 32 + lane] = EMPTY;
     }
-    __syncthreads();
+    BCF_SYNC();
     // Claim the first free entry of each colour in this row; an item whose colour
     // is already taken stays pending for the next round.
     uint32_t todo = pending;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
           pending &= ~(1u << c);
       }
     }
-    __syncthreads();
+    BCF_SYNC();
     // Communication: in step k every row sends its colour-k item (if any); the
     // destination banks of one step are distinct.
 #pragma unroll 4
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
         out_s[e >> 8] = in_s[(e & 0xFFu) * 32 + lane];
       }
     }
-    __syncthreads();
+    BCF_SYNC();
   }
 
   if (sorted) {
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __
       pending &= ~(1u << c);
     }
   }
-  __syncthreads();
+  BCF_SYNC();
   write_tile<T>(dst, tile * T, len, out_s);
 }
 

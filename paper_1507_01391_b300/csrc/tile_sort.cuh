@@ -76,7 +76,7 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
     BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 1, TS_L1_ROW_ST);
     S[(t * 16 + i) * kL1Rows + r] = v[i];
   }
-  __syncthreads();
+  BCF_SYNC();
   unsigned long long* src = S;
   unsigned long long* dst = D;
 #pragma unroll 1
@@ -112,7 +112,7 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
       i += take_a;
       j += !take_a;
     }
-    __syncthreads();
+    BCF_SYNC();
     unsigned long long* tmp = src;
     src = dst;
     dst = tmp;
@@ -134,7 +134,7 @@ __device__ __forceinline__ void l1_row_to_col(const unsigned long long* M, unsig
     BCF_TR(&N[c * kL1Rows + p], 8, 1, TS_L1_CONVERT);
     N[c * kL1Rows + p] = M[(j * 16 + p) * kL1Rows + R];
   }
-  __syncthreads();
+  BCF_SYNC();
 }
 
 // Column-major -> row-major: M(R, C) = N(C % 16, R * 16 + C / 16).
@@ -149,7 +149,7 @@ __device__ __forceinline__ void l1_col_to_row(const unsigned long long* N, unsig
     BCF_TR(&M[C * kL1Rows + p], 8, 1, TS_L1_CONVERT);
     M[C * kL1Rows + p] = N[(p * 16 + j) * kL1Rows + r];
   }
-  __syncthreads();
+  BCF_SYNC();
 }
 
 // The Lemma 1 schedule on items already built in X; afterwards Y[t] holds the
@@ -181,7 +181,7 @@ __device__ __forceinline__ void lemma1_tile(const uint32_t* __restrict__ keys_in
     BCF_TR(&X[q], 8, 1, TS_L1_IO);
     X[q] = (key << 32) | (unsigned)q;  // padding sorts last (position >= len)
   }
-  __syncthreads();
+  BCF_SYNC();
   lemma1_schedule(X, Y);  // Y[t] = item of sorted position t
   const VT* vin = reinterpret_cast<const VT*>(vals_in);
   VT* vout = reinterpret_cast<VT*>(vals_out);
@@ -191,7 +191,7 @@ __device__ __forceinline__ void lemma1_tile(const uint32_t* __restrict__ keys_in
     keys_out[start + t] = (uint32_t)(it >> 32);
     if (VB) vout[start + t] = vin ? vin[start + (uint32_t)it] : VT(start + (uint32_t)it);
   }
-  __syncthreads();
+  BCF_SYNC();
 }
 
 }  // namespace bcf

@@ -1,8 +1,9 @@
 // trace.cuh -- optional shared-memory access tracing (builds with -DBCF_TRACE).
 //
 // In a trace build every instrumented shared-memory access appends one record per
-// active lane to a caller-provided device buffer: (request id, lane, shared-window
-// byte address, width | store << 8 | site << 16).  All lanes of one warp-wide
+// active lane to a caller-provided device buffer: (request id, thread index |
+// block index << 16, shared-window byte address, width | store << 8 | site << 16),
+// and every block-wide barrier taken through BCF_SYNC() one record per warp.  All lanes of one warp-wide
 // access share the request id, so the trace can be replayed through the bank model
 // of Sec. 1 (32 banks of 4-byte words; a request conflicts when two of its lanes
 // need different words of one bank).  Without BCF_TRACE the macro is empty and the
@@ -30,6 +31,7 @@ enum TraceSite : uint32_t {
   TS_COL_READ = 22,     // colouring: reading own row (labels, items)
   TS_COL_FINISH = 23,   // colouring: finishing sends (greedy or sorted)
   TS_COL_PACK = 24,     // colouring, sorted finish: ordering and packing the leftovers
+  TS_BARRIER = 30,      // a block-wide barrier (one record per warp; store field 3)
 };
 
 #ifdef BCF_TRACE
@@ -60,15 +62,36 @@ __device__ __forceinline__ void trace_access(const void* p, uint32_t width, uint
   if (r < t.cap) {
     uint32_t* o = t.rec + 4 * r;
     o[0] = (uint32_t)base;
-    o[1] = (uint32_t)lane;
+    o[1] = (uint32_t)threadIdx.x | ((uint32_t)blockIdx.x << 16);
     o[2] = smem_u32(p);
     o[3] = width | (store << 8) | (site << 16);
   }
 }
+
+// After a block-wide barrier every warp appends one barrier record, so a replay
+// can split each warp's accesses into the segments between barriers.
+__device__ __forceinline__ void trace_barrier() {
+  const TraceState t = g_bcf_trace;
+  if (!t.count || (threadIdx.x & 31u) != (uint32_t)(__ffs(__activemask()) - 1)) return;
+  const unsigned long long r = atomicAdd(t.count, 1ull);
+  if (r < t.cap) {
+    uint32_t* o = t.rec + 4 * r;
+    o[0] = (uint32_t)r;
+    o[1] = (uint32_t)threadIdx.x | ((uint32_t)blockIdx.x << 16);
+    o[2] = 0;
+    o[3] = 0u | (3u << 8) | ((uint32_t)TS_BARRIER << 16);
+  }
+}
 #define BCF_TR(ptr, width, store, site) ::bcf::trace_access((ptr), (width), (store), (site))
+#define BCF_SYNC()               \
+  do {                           \
+    __syncthreads();             \
+    ::bcf::trace_barrier();      \
+  } while (0)
 #else
 #define BCF_TR(ptr, width, store, site) ((void)0)
 #define BCF_TRACE_INSTALLER(name)
+#define BCF_SYNC() __syncthreads()
 #endif
 // Sub-word accesses are traced as the 4-byte word that holds them.
 #define BCF_TR_WORD(ptr, store, site) \

@@ -23,6 +23,7 @@ SITES = {
     "stage_read": 1, "count_atom": 2, "claim_atom": 3, "scatter": 4, "writeout_read": 5,
     "offset_read": 6, "l1_row_ld": 10, "l1_row_st": 11, "l1_convert": 12, "l1_io": 13,
     "col_table": 20, "col_send": 21, "col_read": 22, "col_finish": 23, "col_pack": 24,
+    "barrier": 30,
 }
 
 _trace_lib = None
@@ -80,7 +81,13 @@ def capture(fn, max_records: int = 1 << 22):
 
 
 def fields(rec):
-    """Split records into (request, lane, address, width, store, site) arrays."""
-    return (rec[:, 0].astype(np.int64), rec[:, 1].astype(np.int32), rec[:, 2].astype(np.uint32),
+    """Split records into (request, lane, address, width, store, site) arrays
+    (barrier records have store 3 and width 0)."""
+    return (rec[:, 0].astype(np.int64), (rec[:, 1] & 31).astype(np.int32), rec[:, 2].astype(np.uint32),
             (rec[:, 3] & 0xFF).astype(np.int32), ((rec[:, 3] >> 8) & 0xFF).astype(np.int32),
             (rec[:, 3] >> 16).astype(np.int32))
+
+
+def accesses(rec):
+    """The records without the barrier ones."""
+    return rec[((rec[:, 3] >> 8) & 0xFF) != 3]

@@ -28,7 +28,7 @@ def tr():
 
 
 def _replay(tr, rec, site=None):
-    req, lane, addr, width, store, s = tr.fields(rec)
+    req, lane, addr, width, store, s = tr.fields(tr.accesses(rec))
     if site is not None:
         keep = s == tr.SITES[site]
         req, lane, addr, width = req[keep], lane[keep], addr[keep], width[keep]
@@ -58,6 +58,15 @@ def test_lemma1_tile_sort_replays_conflict_free(tr):
         r = _replay(tr, rec, site)
         assert r is not None and r["hw_conflicts"] == 0, (site, r)
     assert _replay(tr, rec)["hw_conflicts"] == 0
+    _no_races(rec)
+
+
+def _no_races(rec):
+    """No two threads touch one word between the same two barriers with a store
+    among them (the trace's barrier records split each warp's accesses)."""
+    races, words = oracle.race_check(rec)
+    print("race check: %d racing words of %d checked" % (races, words))
+    assert words > 0 and races == 0
 
 
 def test_coloured_sends_meet_the_conflict_avoidance_condition(tr):
@@ -80,6 +89,7 @@ def test_coloured_sends_meet_the_conflict_avoidance_condition(tr):
         if r is not None:
             assert r["hw_conflicts"] == 0, (site, r)
     assert _replay(tr, rec)["hw_conflicts"] == 0
+    _no_races(rec)
 
 
 @pytest.mark.parametrize("tile", [1024, 4096])
@@ -103,6 +113,7 @@ def test_sorted_finish_sends_meet_the_conflict_avoidance_condition(tr, tile):
         r = _replay(tr, rec, site)
         assert r is None or r["hw_conflicts"] == 0, (site, r)
     assert _replay(tr, rec, "col_pack") is not None
+    _no_races(rec)
 
 
 def test_direct_scatter_shows_the_conflicts(tr):
@@ -117,6 +128,7 @@ def test_direct_scatter_shows_the_conflicts(tr):
     per_req = sc["wavefronts"] / sc["requests"]
     assert sc["hw_conflicts"] > 0 and 2.0 < per_req < 5.0, sc
     assert _replay(tr, rec, "stage_read")["hw_conflicts"] == 0
+    _no_races(rec)
 
 
 def test_sweep_strided_reads_are_conflict_free(tr):
@@ -137,6 +149,7 @@ def test_sweep_strided_reads_are_conflict_free(tr):
     assert _replay(tr, rec, "writeout_read")["hw_conflicts"] == 0
     sc = _replay(tr, rec, "scatter")
     assert sc is not None and sc["requests"] == n // 32
+    _no_races(rec)
 
 
 def test_lemma1_partition_replays_conflict_free(tr):
@@ -156,3 +169,25 @@ def test_lemma1_partition_replays_conflict_free(tr):
     for site in ("l1_row_ld", "l1_row_st", "l1_convert", "l1_io"):
         r = _replay(tr, rec, site)
         assert r is not None and r["hw_conflicts"] == 0, (site, r)
+    _no_races(rec)
+
+
+def test_segmented_small_path_has_no_races(tr):
+    """The batched sort's small-segment path (one tile per segment and packed bins
+    of tiny segments) keeps every shared word private between barriers."""
+    import torch
+
+    import paper_1507_01391_b300 as bcf
+    sizes = [3000, 17, 1, 2048, 900, 5, 4000]
+    offs = synth.offsets_from_sizes(sizes)
+    n = int(offs[-1])
+    keys = synth.uniform_keys(n, seed=12)
+    vals = synth.index_payload(n)
+    out = {}
+
+    def run():
+        out["k"], out["v"] = bcf.segmented_sort(dev(keys), dev(vals), torch.from_numpy(offs).cuda())
+    rec, _ = tr.capture(run)
+    rk, rv = oracle.segmented_sort_kv(keys, vals, offs)
+    assert bits_equal(host(out["k"], np.uint32), rk) and bits_equal(host(out["v"], np.uint32), rv)
+    _no_races(rec)

@@ -458,3 +458,31 @@ def test_corollary1_partition_small_alphabets(orc):
     for _ in range(2000):
         M = g.integers(0, 3, size=(3, 9), dtype=np.uint32)
         assert np.array_equal(orc.lemma1_sort(M).reshape(-1), np.sort(M.reshape(-1)))
+
+
+# ------------------------------------------------------------ race check ----
+def _rec(thread, addr, kind, width=4, block=0):
+    return [0, thread | (block << 16), addr, width | (kind << 8) | (1 << 16)]
+
+
+def _bar(thread, block=0):
+    return [0, thread | (block << 16), 0, (3 << 8) | (30 << 16)]
+
+
+def test_race_check_rules(orc):
+    """Different threads, one word, no barrier between, a store among them: a race.
+    A barrier in every warp between them, one thread, loads only, atomics, or
+    different blocks: none."""
+    R = lambda rows: orc.race_check(np.array(rows, dtype=np.uint32))[0]
+    assert R([_rec(0, 64, 1), _rec(33, 64, 1)]) == 1                     # two writers
+    assert R([_rec(0, 64, 1), _rec(5, 64, 0)]) == 1                      # write, other thread reads
+    assert R([_rec(0, 64, 1), _rec(0, 64, 0), _rec(0, 64, 1)]) == 0      # one thread
+    assert R([_rec(0, 64, 0), _rec(40, 64, 0)]) == 0                     # loads only
+    assert R([_rec(0, 64, 2), _rec(40, 64, 2)]) == 0                     # atomics
+    assert R([_rec(0, 64, 1, block=0), _rec(40, 64, 1, block=1)]) == 0  # other block
+    assert R([_rec(0, 64, 1), _bar(0), _bar(32), _rec(40, 64, 0)]) == 0  # barrier between
+    assert R([_rec(0, 64, 1), _bar(0), _rec(40, 64, 0)]) == 1            # warp 1 not past it yet
+    assert R([_rec(0, 60, 1, width=8), _rec(3, 64, 0)]) == 1             # wide store covers the word
+    assert R([_rec(0, 56, 1, width=8), _rec(3, 64, 0)]) == 0
+    races, words = orc.race_check(np.array([_rec(0, 0, 1, width=16), _rec(1, 16, 1)], dtype=np.uint32))
+    assert (races, words) == (0, 5)

@@ -434,7 +434,7 @@ def headline_config():
                         "4096-key tiles by per-tile uniform random uint16 permutations",
             "n": N_PERM, "tile": TILE, "keys_per_step": 2 * N_PERM,
             "l2": "every input larger than the 126 MB L2 (no flush between steps)",
-            "permute_form": "bucketed: group by destination block of 2^15 into a 10 B/key workspace, "
+            "permute_form": "bucketed: group by destination block (blocks sized to fill whole waves of SMs) into a 10 B/key workspace, "
                             "then place each block in shared memory (two coalesced passes)",
             "tile_schedule": "scatter"}
 

@@ -143,10 +143,11 @@ int bcf_partition_splitters(const uint32_t* keys_in, const void* vals_in, uint32
  *              BCF_E_BAD_PERM otherwise).
  *              BCF_PERMUTE_BUCKETED: instead of one scattered store per element
  *              (each costs an L2 sector operation), move the elements in two
- *              coalesced passes: group them by destination block of 2^15
- *              positions into ws (tiles of 8192 elements, one global atomic claim
- *              per tile and block), then place each block in shared memory and
- *              write it out in order.  Same result.  Applies to 4-byte elements
+ *              coalesced passes: group them by destination block into ws
+ *              (blocks of 4096 to 53248 positions, as many as fill whole waves
+ *              of one block per SM; tiles of 8192 elements, one global atomic
+ *              claim per tile and block), then place each block in shared
+ *              memory and write it out in order.  Same result.  Applies to 4-byte elements
  *              with payloads of 0 or 4 bytes and n <= 2^26; otherwise the
  *              one-pass scatter runs.  With a pi that is not a bijection the
  *              output is unspecified (nothing is written outside dst) and, when

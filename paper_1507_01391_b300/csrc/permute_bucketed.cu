@@ -8,17 +8,22 @@
 //  Pass 1 (k_pb_bucket): persistent blocks take tiles of kPbTile elements; a tile's
 //    pi, keys and payloads stream into shared memory by bulk copies while the
 //    previous tile is processed.  Element i belongs to destination block
-//    b = pi[i] >> kPbBits (2^15 destinations each).  A tile is counted per block,
-//    reordered into block order in shared memory, and each run is written to the
-//    block's region of the workspace at an offset claimed with one global atomic
-//    per (tile, block).  Only pi's low 15 bits travel with the element.  The order
-//    inside a region is whatever the claims produced; pass 2 does not depend on it.
-//  Pass 2 (k_pb_place): one block per destination block reads the region in order,
-//    stores every element at its 15-bit offset in shared memory (128 KB), then
-//    writes the block of dst with 16-byte stores; payloads take a second round.
+//    b = pi[i] / len (len destinations each, len <= kPbMaxLen).  A tile is counted
+//    per block, reordered into block order in shared memory, and each run is
+//    written to the block's region of the workspace at an offset claimed with one
+//    global atomic per (tile, block).  Only the offset pi[i] - b * len (16 bits)
+//    travels with the element.  The order inside a region is whatever the claims
+//    produced; pass 2 does not depend on it.
+//  Pass 2 (k_pb_place): one thread block per destination block reads the region in
+//    order, stores every element at its offset in shared memory (len x 4 bytes),
+//    then writes the block of dst with 16-byte stores; payloads take a second round.
+//
+// The block length is chosen so that the number of destination blocks is a
+// multiple of the SM count: pass 2 then runs in whole waves of one block per SM,
+// with no partly filled last wave.
 //
 // Traffic per element: pass 1 reads 4 + 4 + vb bytes and writes 2 + 4 + vb, pass 2
-// reads them back (plus pi's low bits again for the payload round) and writes
+// reads them back (plus the offsets again for the payload round) and writes
 // 4 + vb -- about twice the one-pass bytes, but in whole sectors.
 #include "common.cuh"
 #include "internal.h"
@@ -28,13 +33,38 @@ namespace bcf {
 
 namespace {
 
-constexpr int kPbBits = 15;                 // destinations per block: 2^15
-constexpr int kPbBlock = 1 << kPbBits;
+constexpr int kPbMaxLen = 53248;   // destinations per block at most (shared memory of pass 2)
+constexpr int kPbMinLen = 4096;    // ... and at least
+constexpr int kPbMagicShift = 42;  // b = (pi * magic) >> 42 is pi / len for pi < 2^26, len < 2^16
 constexpr int kPbThreads = 1024, kPbIPT = 8;
 constexpr int kPbTile = kPbThreads * kPbIPT;  // 8192 elements per pass-1 tile
-constexpr int kPbMaxBlocks = 2048;          // n <= 2^26
+constexpr int kPbMaxBlocks = 2048;
+constexpr int64_t kPbMaxN = (int64_t)1 << 26;
 constexpr int kPlaceThreads = 1024;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+// Destination blocks: nb blocks of len positions (len a multiple of 8, so every
+// block's region starts 16-byte aligned in all three workspace arrays).
+struct PbGeom {
+  int nb = 0;
+  uint32_t len = 0;
+  unsigned long long magic = 0;  // ceil(2^42 / len)
+};
+
+int sm_count_cached();
+
+PbGeom pb_geometry(int64_t n) {
+  const int64_t sms = std::max(1, sm_count_cached());
+  const int64_t waves = std::max<int64_t>(1, (n + sms * kPbMaxLen - 1) / (sms * kPbMaxLen));
+  int64_t len = (n + sms * waves - 1) / (sms * waves);
+  len = std::max<int64_t>((len + 7) / 8 * 8, kPbMinLen);
+  if ((n + len - 1) / len > kPbMaxBlocks) len = ((n + kPbMaxBlocks - 1) / kPbMaxBlocks + 7) / 8 * 8;
+  PbGeom g;
+  g.len = (uint32_t)len;
+  g.nb = (int)((n + len - 1) / len);
+  g.magic = ((1ull << kPbMagicShift) + (unsigned long long)len - 1) / (unsigned long long)len;
+  return g;
+}
 
 struct PbLayout {
   size_t k1 = 0, v1 = 0, p1 = 0, fill = 0, total = 0;
@@ -67,7 +97,7 @@ __global__ void __launch_bounds__(kPbThreads, 1)
     k_pb_bucket(const uint32_t* __restrict__ pi, const uint32_t* __restrict__ sk,
                 const uint32_t* __restrict__ sv, uint32_t* __restrict__ K1, uint32_t* __restrict__ V1,
                 uint16_t* __restrict__ P1, uint32_t* __restrict__ fill, int64_t n, int64_t row_len,
-                int ntiles, unsigned* status) {
+                int ntiles, uint32_t len, unsigned long long magic, unsigned* status) {
   constexpr int T = kPbTile;
   extern __shared__ __align__(128) unsigned char smem[];
   uint32_t* in_p = reinterpret_cast<uint32_t*>(smem);
@@ -133,7 +163,11 @@ __global__ void __launch_bounds__(kPbThreads, 1)
       if ((int64_t)d[j] >= n) {
         set_status(status, DEV_BAD_PERM);
         d[j] = kNone;
+        continue;
       }
+      // (offset | block << 16): block = d / len, offset = d - block * len
+      const uint32_t b = (uint32_t)(((unsigned long long)d[j] * magic) >> kPbMagicShift);
+      d[j] = (d[j] - b * len) | (b << 16);
     }
     __syncthreads();  // in-buffers read; the previous tile's write-out is done
     for (int b = tid; b < NB; b += kPbThreads) cur[b] = 0;
@@ -141,7 +175,7 @@ __global__ void __launch_bounds__(kPbThreads, 1)
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < kPbIPT; ++j)
-      if (d[j] != kNone) atomicAdd(&cur[d[j] >> kPbBits], 1u);
+      if (d[j] != kNone) atomicAdd(&cur[d[j] >> 16], 1u);
     __syncthreads();
 
     // Block starts inside the tile; one claim per non-empty block, whose latency
@@ -173,20 +207,20 @@ __global__ void __launch_bounds__(kPbThreads, 1)
       uint32_t pos[kPbIPT];
 #pragma unroll
       for (int j = 0; j < kPbIPT; ++j)  // every claim first, so none waits behind a store
-        pos[j] = d[j] != kNone ? atomicAdd(&cur[d[j] >> kPbBits], 1u) : 0u;
+        pos[j] = d[j] != kNone ? atomicAdd(&cur[d[j] >> 16], 1u) : 0u;
 #pragma unroll
       for (int j = 0; j < kPbIPT; ++j) {
         if (d[j] == kNone) continue;
         skv[pos[j]] = ((unsigned long long)v[j] << 32) | k[j];
-        spb[pos[j]] = (d[j] & (kPbBlock - 1)) | ((d[j] >> kPbBits) << 16);
+        spb[pos[j]] = d[j];
       }
     }
 #pragma unroll
     for (int q = 0; q < PER; ++q) {
       const int b = tid * PER + q;
       if (b < NB && c[q]) {
-        const int64_t lo = (int64_t)b << kPbBits;
-        const int64_t cap = min((int64_t)kPbBlock, n - lo);
+        const int64_t lo = (int64_t)b * len;
+        const int64_t cap = min((int64_t)len, n - lo);
         if ((int64_t)claim[q] + c[q] > cap) {  // more elements than destinations: pi is no bijection
           set_status(status, DEV_BAD_PERM);
           gofs[b] = kNone;
@@ -227,21 +261,23 @@ __global__ void __launch_bounds__(kPbThreads, 1)
 
 // Pass 2: destination block blockIdx.x.  CHECK: a bitmap of the block's offsets
 // finds a destination hit twice (with no block over-full, that is the only way pi
-// can fail to be a bijection).
+// can fail to be a bijection).  Offsets are clamped below len: with a pi that is
+// no bijection a region can hold entries no claim wrote, and those must not
+// reach outside the shared buffer.
 template <int VB, bool CHECK>
 __global__ void __launch_bounds__(kPlaceThreads, 1)
     k_pb_place(const uint32_t* __restrict__ K1, const uint32_t* __restrict__ V1,
                const uint16_t* __restrict__ P1, uint32_t* __restrict__ dk, uint32_t* __restrict__ dv,
-               int64_t n, unsigned* status) {
+               int64_t n, uint32_t len, unsigned* status) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint32_t* xs = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* seen = xs + kPbBlock;  // CHECK only
+  uint32_t* seen = xs + len;  // CHECK only
   const int tid = threadIdx.x;
-  const int64_t lo = (int64_t)blockIdx.x << kPbBits;
-  const int cap = (int)min((int64_t)kPbBlock, n - lo);
-  constexpr uint32_t M = kPbBlock - 1;
+  const int64_t lo = (int64_t)blockIdx.x * len;
+  const int cap = (int)min((int64_t)len, n - lo);
+  const uint32_t top = len - 1;
   if (CHECK) {
-    for (int i = tid; i < kPbBlock / 32; i += kPlaceThreads) seen[i] = 0;
+    for (int i = tid; i < (int)(len + 31) / 32; i += kPlaceThreads) seen[i] = 0;
     __syncthreads();
   }
   auto mark = [&](uint32_t o) {
@@ -267,8 +303,10 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (h && !two) break;
-        const uint32_t o[8] = {p[h].x & M, (p[h].x >> 16) & M, p[h].y & M, (p[h].y >> 16) & M,
-                               p[h].z & M, (p[h].z >> 16) & M, p[h].w & M, (p[h].w >> 16) & M};
+        const uint32_t o[8] = {min(p[h].x & 0xFFFFu, top), min(p[h].x >> 16, top),
+                               min(p[h].y & 0xFFFFu, top), min(p[h].y >> 16, top),
+                               min(p[h].z & 0xFFFFu, top), min(p[h].z >> 16, top),
+                               min(p[h].w & 0xFFFFu, top), min(p[h].w >> 16, top)};
         const uint32_t x[8] = {a[h].x, a[h].y, a[h].z, a[h].w, b[h].x, b[h].y, b[h].z, b[h].w};
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
@@ -278,7 +316,7 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
       }
     }
     for (int i = nv * 8 + tid; i < cap; i += kPlaceThreads) {
-      const uint32_t o = P1[lo + i] & M;
+      const uint32_t o = min((uint32_t)P1[lo + i], top);
       xs[o] = X[lo + i];
       if (CHECK && round == 0) mark(o);
     }
@@ -319,33 +357,34 @@ cudaError_t set_smem(K kernel, int bytes, bool (&done)[64]) {
 
 template <int VB, int NB>
 cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
-                         const uint32_t* pi, int64_t n, int64_t row_len, bool check,
+                         const uint32_t* pi, int64_t n, int64_t row_len, bool check, const PbGeom& g,
                          unsigned char* ws, cudaStream_t s) {
   const PbLayout L = pb_layout(n, VB);
   uint32_t* K1 = reinterpret_cast<uint32_t*>(ws + L.k1);
   uint32_t* V1 = reinterpret_cast<uint32_t*>(ws + L.v1);
   uint16_t* P1 = reinterpret_cast<uint16_t*>(ws + L.p1);
   uint32_t* fill = reinterpret_cast<uint32_t*>(ws + L.fill);
-  const int blocks = (int)((n + kPbBlock - 1) >> kPbBits);
   const int ntiles = (int)((n + kPbTile - 1) / kPbTile);
-  cudaError_t e = cudaMemsetAsync(fill, 0, (size_t)blocks * 4, s);
+  cudaError_t e = cudaMemsetAsync(fill, 0, (size_t)g.nb * 4, s);
   if (e != cudaSuccess) return e;
   constexpr int sm1 = pb_smem_bytes<NB>();
   static bool ready1[64] = {};
   if ((e = set_smem(k_pb_bucket<VB, NB>, sm1, ready1)) != cudaSuccess) return e;
   const int grid = std::min(ntiles, sm_count_cached());
-  k_pb_bucket<VB, NB><<<grid, kPbThreads, sm1, s>>>(pi, sk, sv, K1, V1, P1, fill, n, row_len, ntiles,
-                                                    status_word());
+  k_pb_bucket<VB, NB><<<grid, kPbThreads, sm1, s>>>(pi, sk, sv, K1, V1, P1, fill, n, row_len, ntiles, g.len,
+                                                    g.magic, status_word());
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int sm2 = kPbBlock * 4 + (check ? kPbBlock / 8 : 0);
+  // the limit is raised once, to the largest block; a launch takes what its block needs
+  constexpr int sm2_max = kPbMaxLen * 4 + kPbMaxLen / 8;
+  const int sm2 = (int)g.len * 4 + (check ? (int)(g.len + 31) / 32 * 4 : 0);
   if (check) {
     static bool ready2[64] = {};
-    if ((e = set_smem(k_pb_place<VB, true>, sm2, ready2)) != cudaSuccess) return e;
-    k_pb_place<VB, true><<<blocks, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, status_word());
+    if ((e = set_smem(k_pb_place<VB, true>, sm2_max, ready2)) != cudaSuccess) return e;
+    k_pb_place<VB, true><<<g.nb, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, g.len, status_word());
   } else {
     static bool ready2[64] = {};
-    if ((e = set_smem(k_pb_place<VB, false>, sm2, ready2)) != cudaSuccess) return e;
-    k_pb_place<VB, false><<<blocks, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, status_word());
+    if ((e = set_smem(k_pb_place<VB, false>, sm2_max, ready2)) != cudaSuccess) return e;
+    k_pb_place<VB, false><<<g.nb, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, g.len, status_word());
   }
   return cudaGetLastError();
 }
@@ -353,7 +392,7 @@ cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, u
 }  // namespace
 
 bool permute_bucketed_supported(int64_t n, int kb, int vb) {
-  return kb == 4 && (vb == 0 || vb == 4) && n > 0 && n <= (int64_t)kPbMaxBlocks * kPbBlock;
+  return kb == 4 && (vb == 0 || vb == 4) && n > 0 && n <= kPbMaxN;
 }
 
 size_t permute_bucketed_workspace(int64_t n, int vb) { return pb_layout(n, vb).total; }
@@ -362,12 +401,13 @@ cudaError_t permute_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* d
                              const uint32_t* pi, int64_t n, int64_t row_len, int vb, bool check,
                              unsigned char* ws, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const bool few = ((n + kPbBlock - 1) >> kPbBits) <= 512;
+  const PbGeom g = pb_geometry(n);
+  const bool few = g.nb <= 512;
   if (vb == 4)
-    return few ? run_bucketed<4, 512>(sk, sv, dk, dv, pi, n, row_len, check, ws, s)
-               : run_bucketed<4, 2048>(sk, sv, dk, dv, pi, n, row_len, check, ws, s);
-  return few ? run_bucketed<0, 512>(sk, sv, dk, dv, pi, n, row_len, check, ws, s)
-             : run_bucketed<0, 2048>(sk, sv, dk, dv, pi, n, row_len, check, ws, s);
+    return few ? run_bucketed<4, 512>(sk, sv, dk, dv, pi, n, row_len, check, g, ws, s)
+               : run_bucketed<4, 2048>(sk, sv, dk, dv, pi, n, row_len, check, g, ws, s);
+  return few ? run_bucketed<0, 512>(sk, sv, dk, dv, pi, n, row_len, check, g, ws, s)
+             : run_bucketed<0, 2048>(sk, sv, dk, dv, pi, n, row_len, check, g, ws, s);
 }
 
 }  // namespace bcf

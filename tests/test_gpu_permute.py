@@ -136,9 +136,10 @@ def test_permute_tiles_reports_bad_label(bcf):
 
 
 # ------------------------------------------------------------ bucketed form
-# Two coalesced passes: group by destination block of 2^15, then place each
-# block in shared memory.  Sizes span several 8192-element tiles and blocks and
-# end in ragged tails (n not a multiple of 4, 8192 or 2^15).
+# Two coalesced passes: group by destination block (4096 to 53248 positions,
+# sized so that the blocks fill whole waves of SMs), then place each block in
+# shared memory.  Sizes span several 8192-element tiles and blocks and end in
+# ragged tails (n not a multiple of 4, 8 or 8192).
 BLOCK = 1 << 15
 
 
@@ -199,8 +200,9 @@ def test_permute_bucketed_rows(bcf):
 
 
 def test_permute_bucketed_more_than_512_blocks(bcf):
-    """Above 512 destination blocks the pass-1 kernel keeps 2048 block counters."""
-    n = 600 * BLOCK + 7
+    """Above 512 destination blocks (740 blocks of 45344 on 148 SMs) the pass-1
+    kernel keeps 2048 block counters."""
+    n = (1 << 25) + 7
     keys = synth.uniform_keys(n, seed=9)
     pi = synth.random_perm(n, seed=10)
     ko = bcf.permute(dev(keys), dev(pi), bucketed=True)

@@ -41,6 +41,10 @@ constexpr int kPbTile = kPbThreads * kPbIPT;  // 8192 elements per pass-1 tile
 constexpr int kPbMaxBlocks = 2048;
 constexpr int64_t kPbMaxN = (int64_t)1 << 26;
 constexpr int kPlaceThreads = 1024;
+constexpr int kBulkChunk = 1 << 16;  // bytes per bulk store of the pass-2 write-out
+#ifndef BCF_PB_EVICT_FIRST
+#define BCF_PB_EVICT_FIRST 1
+#endif
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 // Destination blocks: nb blocks of len positions (len a multiple of 8, so every
@@ -285,48 +289,72 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
     if (atomicOr(&seen[o >> 5], bit) & bit) set_status(status, DEV_BAD_PERM);
   };
   const int nv = cap / 8;
+  const int mv = cap / 4;
+  // Two groups of 8 per thread per step, every load issued before any store.
+  uint4 p[2], a[2], b[2];
+  auto load = [&](const uint32_t* X, int t) {
+    const bool two = t + kPlaceThreads < nv;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t i = lo + (int64_t)(h && two ? t + kPlaceThreads : t) * 8;
+      p[h] = __ldcs(reinterpret_cast<const uint4*>(P1 + i));
+      a[h] = __ldcs(reinterpret_cast<const uint4*>(X + i));
+      b[h] = __ldcs(reinterpret_cast<const uint4*>(X + i + 4));
+    }
+  };
+  auto place = [&](int t, bool marking) {
+    const bool two = t + kPlaceThreads < nv;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h && !two) break;
+      const uint32_t o[8] = {min(p[h].x & 0xFFFFu, top), min(p[h].x >> 16, top),
+                             min(p[h].y & 0xFFFFu, top), min(p[h].y >> 16, top),
+                             min(p[h].z & 0xFFFFu, top), min(p[h].z >> 16, top),
+                             min(p[h].w & 0xFFFFu, top), min(p[h].w >> 16, top)};
+      const uint32_t x[8] = {a[h].x, a[h].y, a[h].z, a[h].w, b[h].x, b[h].y, b[h].z, b[h].w};
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        xs[o[c]] = x[c];
+        if (CHECK && marking) mark(o[c]);
+      }
+    }
+  };
 #pragma unroll 1
   for (int round = 0; round < (VB ? 2 : 1); ++round) {
     const uint32_t* X = round ? V1 : K1;
     uint32_t* D = round ? dv : dk;
-    // Two groups of 8 per thread per step, every load issued before any store.
-    for (int t = tid; t < nv; t += 2 * kPlaceThreads) {
-      const bool two = t + kPlaceThreads < nv;
-      uint4 p[2], a[2], b[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t i = lo + (int64_t)(h && two ? t + kPlaceThreads : t) * 8;
-        p[h] = __ldcs(reinterpret_cast<const uint4*>(P1 + i));
-        a[h] = __ldcs(reinterpret_cast<const uint4*>(X + i));
-        b[h] = __ldcs(reinterpret_cast<const uint4*>(X + i + 4));
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (h && !two) break;
-        const uint32_t o[8] = {min(p[h].x & 0xFFFFu, top), min(p[h].x >> 16, top),
-                               min(p[h].y & 0xFFFFu, top), min(p[h].y >> 16, top),
-                               min(p[h].z & 0xFFFFu, top), min(p[h].z >> 16, top),
-                               min(p[h].w & 0xFFFFu, top), min(p[h].w >> 16, top)};
-        const uint32_t x[8] = {a[h].x, a[h].y, a[h].z, a[h].w, b[h].x, b[h].y, b[h].z, b[h].w};
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          xs[o[c]] = x[c];
-          if (CHECK && round == 0) mark(o[c]);
-        }
-      }
+    int t = tid;
+    if (t < nv) load(X, t);
+    if (round > 0) {  // the previous round's bulk write-out must have read xs
+      if (tid == 0) bulk_s2g_wait_read();
+      __syncthreads();
+    }
+    while (t < nv) {
+      place(t, round == 0);
+      t += 2 * kPlaceThreads;
+      if (t < nv) load(X, t);
     }
     for (int i = nv * 8 + tid; i < cap; i += kPlaceThreads) {
       const uint32_t o = min((uint32_t)P1[lo + i], top);
       xs[o] = X[lo + i];
       if (CHECK && round == 0) mark(o);
     }
+    // Write-out: one thread hands the block to the bulk-copy engine, which writes
+    // it while the next round's first loads are in flight.
+    fence_proxy_async_smem();
     __syncthreads();
-    const int mv = cap / 4;
-    for (int t = tid; t < mv; t += kPlaceThreads)
-      __stcs(reinterpret_cast<uint4*>(D + lo) + t, reinterpret_cast<const uint4*>(xs)[t]);
+    if (tid == 0 && mv > 0) {
+      for (int c = 0; c < mv; c += kBulkChunk / 16)
+#if BCF_PB_EVICT_FIRST
+        bulk_s2g_evict_first(D + lo + (int64_t)c * 4, xs + c * 4, (unsigned)min(kBulkChunk, (mv - c) * 16));
+#else
+        bulk_s2g(D + lo + (int64_t)c * 4, xs + c * 4, (unsigned)min(kBulkChunk, (mv - c) * 16));
+#endif
+      bulk_s2g_commit();
+    }
     for (int j = mv * 4 + tid; j < cap; j += kPlaceThreads) D[lo + j] = xs[j];
-    __syncthreads();
   }
+  if (tid == 0) bulk_s2g_wait_read();  // shared memory stays valid until read out
 }
 
 int sm_count_cached() {

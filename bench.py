@@ -46,8 +46,8 @@ FALLBACK_HBM_GBS = 6400.0
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
 # it was taken on: if permute.cu changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "k_pb_bucket<4,512> + k_pb_place<4,0> (bucketed kv permute, both passes)",
-               "source": "permute_bucketed.cu", "source_sha1": "1572774d5465c73fed0316240453e3f0cf367cd5",
-               "bytes": 578021632,
+               "source": "permute_bucketed.cu", "source_sha1": "71cce08f113fdf81865033b8aca3c430d55308cb",
+               "bytes": 577893888,
                "summary": "profiles/k_pb_bucketed_permute_kv_2pow24.md"}
 
 
@@ -187,7 +187,108 @@ class ClockSampler:
         reasons = sorted({self.NAMES[k] for r in inside for k in range(4) if r[4 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(inside), "period_ms": self.period}
+                "samples": len(inside), "period_ms": self.period, "source": "nvidia-smi"}
+
+
+class NvmlSampler:
+    """Clock and throttle-reason polling through NVML (the library nvidia-smi reads,
+    called through ctypes) every millisecond, so that a timed region of a few
+    milliseconds still gets several samples.  Same report as ClockSampler, to which
+    it falls back when NVML cannot be loaded."""
+
+    # clock-event reason bits of NVML's public API
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
+    NVML_CLOCK_SM = 1
+
+    def __init__(self, gpu_index, period_ms=1):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.t0 = self.t1 = None
+        self.rows = []
+        self.thread = None
+        self.fallback = None
+        self.error = ""
+
+    def _open(self):
+        import ctypes
+
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        pr = torch.cuda.get_device_properties(self.gpu)
+        bus = b"%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle for GPU %d" % self.gpu)
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx)) != 0:
+            raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
+        self.max_mhz = mx.value
+
+        def read():
+            if lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(clk)) != 0:
+                return None
+            if reasons(h, ctypes.byref(rs)) != 0:
+                return None
+            return clk.value, rs.value
+        return read
+
+    def start(self):
+        try:
+            import threading
+            read = self._open()
+            if read() is None:
+                raise RuntimeError("NVML clock query failed")
+            self.stop_flag = False
+
+            def poll():
+                while not self.stop_flag:
+                    r = read()
+                    if r is not None:
+                        self.rows.append((time.time(), r[0], r[1]))
+                    time.sleep(self.period / 1000.0)
+            self.thread = threading.Thread(target=poll, daemon=True)
+            self.thread.start()
+        except Exception as e:
+            self.thread = None
+            self.error = "%s: %s" % (type(e).__name__, e)
+            self.fallback = ClockSampler(self.gpu)
+            self.fallback.start()
+
+    def mark(self, which):
+        if self.fallback is not None:
+            return self.fallback.mark(which)
+        if which == 0:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.fallback is not None:
+            out = self.fallback.stop()
+            if out is not None:
+                out["nvml_unavailable"] = self.error[:120]
+            return out
+        if self.thread is None:
+            return None
+        time.sleep(3 * self.period / 1000.0)
+        self.stop_flag = True
+        self.thread.join(timeout=1)
+        rows = list(self.rows)
+        inside = [r for r in rows if self.t0 is not None and self.t0 <= r[0] <= (self.t1 or r[0])]
+        if not inside:
+            after = [r for r in rows if self.t0 is not None and r[0] >= self.t0]
+            inside = after[:1] or rows[-1:]
+        if not inside:
+            return None
+        reasons = sorted({name for _, _, mask in inside for name, bit in self.REASONS if mask & bit})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(inside), "period_ms": self.period, "source": "nvml"}
 
 
 # ------------------------------------------------------------------ inputs
@@ -268,7 +369,7 @@ def run_headline(args, rank, world, local):
             kev[1].record()
         bcf.permute_tiles(d["tsrc"], d["lpi"], tile=TILE, dst=to)
 
-    sampler = ClockSampler(local)
+    sampler = NvmlSampler(local)
     if rank == 0:
         sampler.start()
     for _ in range(max(args.warmup, 3)):
@@ -367,9 +468,42 @@ def run_e2e(args, bcf, x):
         step(k)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t) / steps
+    link = link_bandwidth()
+    # the step's copies at the measured link rates: both directions at once until
+    # the smaller side is done, then the rest of the larger side alone
+    lo_b, hi_b = min(h2d, d2h), max(h2d, d2h)
+    alone = link["h2d"] if h2d >= d2h else link["d2h"]
+    bound_s = lo_b / (link["both_each_way"] * 1e9) + (hi_b - lo_b) / (alone * 1e9)
     return {"value": round(2 * N_PERM / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3),
-            "pipelined": "two buffer sets; copies in, permutations and copies out on three streams"}
+            "pipelined": "two buffer sets; copies in, permutations and copies out on three streams",
+            "link_gbs": link, "link_bound_ms": round(bound_s * 1e3, 3),
+            "frac_of_link": round(bound_s / dt, 3)}
+
+
+def link_bandwidth(mb=256, reps=4):
+    """Host<->device copy rates (GB/s) of pinned buffers: each direction alone and
+    both at once (per direction), the ceiling of the end-to-end step."""
+    import torch
+    n = mb << 18
+    h = [torch.empty(n, dtype=torch.int32).pin_memory() for _ in range(2)]
+    d = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(2)]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def run(up, down):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            if up:
+                with torch.cuda.stream(s1):
+                    d[0].copy_(h[0], non_blocking=True)
+            if down:
+                with torch.cuda.stream(s2):
+                    h[1].copy_(d[1], non_blocking=True)
+        torch.cuda.synchronize()
+        return round(n * 4 * reps / (time.perf_counter() - t) / 1e9, 1)
+    run(True, True)  # first touch of the pinned pages
+    return {"h2d": run(True, False), "d2h": run(False, True), "both_each_way": run(True, True)}
 
 
 # ------------------------------------------------------------------ CPU leg

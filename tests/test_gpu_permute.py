@@ -210,8 +210,8 @@ def test_permute_bucketed_more_than_512_blocks(bcf):
     assert bits_equal(host(ko, np.uint32), oracle.permute(keys, pi))
 
 
-def test_permute_bucketed_reports_non_bijection(bcf):
-    n = 3 * BLOCK + 5
+@pytest.mark.parametrize("n", [3 * BLOCK + 5, (1 << 22) + 3])  # blocks of 4096; of 28,344 (148 SMs)
+def test_permute_bucketed_reports_non_bijection(bcf, n):
     keys = dev(synth.uniform_keys(n, seed=2))
     for a, b in [(10, 11), (7, 3 * BLOCK)]:  # same block; different blocks (one over-full)
         pi = synth.random_perm(n, seed=1)

@@ -664,19 +664,27 @@ def run_rows(which, peak):
                 ms, _ = ev_ms(lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=coloured, dst=ko, finish=finish))
                 add(name, n, 10 * n, ms)
         del k, v, pi, ko, vo, lpi
-    for kind in ("uniform", "zipf"):
+    for kind in ("uniform", "zipf", "24bit"):
         name = "sort_kv_2pow26_%s" % kind
         if not want(name):
             continue
         n = 1 << 26
-        keys = synth.uniform_keys(n, seed=0x2A) if kind == "uniform" else synth.zipf_keys(n, seed=0x2B)
+        if kind == "uniform":
+            keys = synth.uniform_keys(n, seed=0x2A)
+        elif kind == "zipf":
+            keys = synth.zipf_keys(n, seed=0x2B)
+        else:  # keys below 2^24 sorted as 32-bit keys: the top digit never varies
+            keys = synth.uniform_keys(n, seed=0x2C, bits=24)
         k = to_dev(keys)
         v = to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
         ms, _ = ev_ms(lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
-        add(name, n, (4 + 4 * 16) * n, ms, "4 passes of 8 bits; per pass: tile counts (4 B/key) + sweep "
-            "(16 B/key); model charges 68 B/key")
+        runs = bcf.sort_passes_run(ws, n, 4, 32)
+        add(name, n, (4 + runs * 16) * n, ms, "%d of 4 passes of 8 bits run (a pass whose digit is the same in "
+            "every key is skipped); per pass: tile counts (4 B/key) + sweep (16 B/key); model charges "
+            "%d B/key" % (runs, 4 + runs * 16))
+        rows[name]["passes_run"] = runs
         plain_ns[name] = ms * 1e6 / n
         del k, v, ko, vo, ws
     if want("partition_splitters_255_2pow26"):

@@ -88,12 +88,21 @@ int bcf_get_status(bcf_stream_t stream, int* out);
  *  key_bits          1..32; every key must be < 2^key_bits (fewer digit passes)
  *  ws, ws_bytes      workspace of at least bcf_sort_workspace_size() bytes
  * Method: least-significant-digit radix passes of at most 8 bits; each pass ranks
- * and scatters tiles in shared memory and finds each tile's global offsets by a
- * bounded decoupled look-back.  n must be < 2^30. */
+ * and scatters tiles in shared memory and finds each tile's global offsets (per-
+ * tile counts and a scan, or for n <= 2^18 a bounded decoupled look-back).  A pass
+ * whose digit is the same in every key moves nothing and is skipped; the device
+ * decides this from the first pass's read of the keys, with no host round trip,
+ * so the call stays capturable in a CUDA graph.  n must be < 2^30. */
 int bcf_sort_workspace_size(int64_t n, int val_bytes, int key_bits, size_t* bytes);
 int bcf_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
              void* vals_out, int64_t n, int val_bytes, int key_bits, void* ws,
              size_t ws_bytes, bcf_stream_t stream);
+/* Digit passes that the last bcf_sort with this workspace ran (the others were
+ * skipped: their digit is the same in every key).  n, val_bytes and key_bits are
+ * those of that call; `stream` is its stream, which this synchronises before it
+ * reads two words of ws.  BCF_E_CUDA if the read fails. */
+int bcf_sort_passes_run(const void* ws, int64_t n, int val_bytes, int key_bits, int* passes,
+                        bcf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * w-way partition (Sec. 1 and abstract; Corollary 1 and Theorem 1 solve it in

@@ -60,6 +60,7 @@ _SIGS = {
     "bcf_permute_kv": ([_P, _P, _P, _P, _P, _I64, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_permute_tiles": ([_P, _P, _P, _I64, _I, _I, _U64, _P], _I),
     "bcf_gather": ([_P, _P, _P, _I64, _I64, _I64, _I, _P], _I),
+    "bcf_sort_passes_run": ([_P, _I64, _I, _I, ctypes.POINTER(_I), _P], _I),
     "bcf_sort_tiles": ([_P, _P, _P, _P, _I64, _I, _I, _P], _I),
     "bcf_segmented_sort_workspace_size": ([_I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_segmented_sort": ([_P, _P, _P, _P, _I64, _P, _I64, _I, _I, _P, _SZ, _P], _I),
@@ -199,6 +200,15 @@ def sort(keys, vals=None, key_bits=32, keys_out=None, vals_out=None, ws=None, st
 
 
 sort_kv = sort  # the key-value sort under its other name
+
+
+def sort_passes_run(ws, n, val_bytes=4, key_bits=32, stream=None) -> int:
+    """Digit passes the last sort that used workspace ws ran; the others were
+    skipped because their digit is the same in every key (syncs the stream)."""
+    out = ctypes.c_int(0)
+    _check(lib().bcf_sort_passes_run(_ptr(ws), int(n), int(val_bytes), int(key_bits), ctypes.byref(out),
+                                     _stream(stream)), "bcf_sort_passes_run")
+    return out.value
 
 
 def partition(keys, vals, w, balanced=False, keys_out=None, vals_out=None, ws=None, stream=None,

@@ -138,6 +138,20 @@ int bcf_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out, v
                                  bcf::tuned_config(BCF_OP_SORT, n)));
 }
 
+int bcf_sort_passes_run(const void* ws, int64_t n, int val_bytes, int key_bits, int* passes,
+                        bcf_stream_t stream) {
+  if (!ws || !passes || n < 0 || !valid_vb(val_bytes) || key_bits < 1 || key_bits > 32) return BCF_E_INVAL;
+  if (n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  *passes = 0;
+  if (n == 0) return BCF_OK;
+  if (!device_ready()) return BCF_E_CUDA;
+  const bcf::PassPlan pl = bcf::plan_passes(key_bits);
+  const bcf::SweepLayout L = bcf::sweep_layout(n, val_bytes, pl.passes, 256, true);
+  return bcf::sort_passes_run(static_cast<const unsigned char*>(ws), L, pl, (cudaStream_t)stream, passes) == 0
+             ? BCF_OK
+             : BCF_E_CUDA;
+}
+
 // ------------------------------------------------------------- partition
 static bcf::SweepLayout partition_layout(int64_t n, int w, int vb) {
   return bcf::sweep_layout(n, vb, 1, w <= 32 ? 32 : 256, true);

@@ -77,6 +77,15 @@ struct SweepLayout {
 SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp,
                          int tile = kMinSweepTile);
 
+// Three words of a sort's workspace, in the zeroed counter block: which key bits
+// vary (OR of the keys, OR of their complements), then the mask of passes that ran.
+inline uint32_t* sort_vary_words(unsigned char* ws, const SweepLayout& L) {
+  return reinterpret_cast<uint32_t*>(ws + L.counters) + 5;
+}
+// Passes the last sort in ws ran; syncs the stream.  Returns a cudaError_t value.
+int sort_passes_run(const unsigned char* ws, const SweepLayout& L, const PassPlan& plan, cudaStream_t s,
+                    int* out);
+
 // Radix sort launch sequence (see bcf_sort in include/bcf.h).
 // `cfg` is a sweep configuration whose tiles fit the layout's count buffer.
 cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,

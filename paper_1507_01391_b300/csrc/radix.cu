@@ -94,7 +94,7 @@ SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool n
 template <int BITS, int THREADS, int IPT>
 static cudaError_t pass_t(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
                           int64_t n, int vb, int shift, int nbits, int w, bool balanced,
-                          uint32_t* totals, uint32_t* offsets, cudaStream_t s) {
+                          uint32_t* totals, uint32_t* offsets, cudaStream_t s, const PassSel& sel) {
   constexpr int RADIX = 1 << BITS;
   constexpr int T = THREADS * IPT;
   SweepLayout L;  // this configuration's tile count and status stride
@@ -109,12 +109,13 @@ static cudaError_t pass_t(const uint32_t* src_k, const void* src_v, uint32_t* ds
   cp.counts = offsets;
   cp.stride = L.lb_stride;
   cp.totals = totals;
+  cp.sel = sel;
   const int64_t count_blocks = (L.tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
   k_tile_counts<BITS, T><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   launch_scan_offsets(RADIX, offsets, L.tiles, L.lb_stride, totals, balanced ? 1 : 0, n, w > 0 ? w : 1,
-                      status_word(), s);
+                      status_word(), s, sel);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   SweepParams sp{};
   sp.keys_in = src_k;
@@ -129,18 +130,20 @@ static cudaError_t pass_t(const uint32_t* src_k, const void* src_v, uint32_t* ds
   sp.lb_stride = L.lb_stride;
   sp.tile_offsets = offsets;
   sp.status = status_word();
+  sp.sel = sel;
   return sweep_dispatch<BITS, THREADS, IPT>(sp, L.tiles, vb, s);
 }
 
 template <int BITS>
 static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
-                        int64_t n, int vb, int shift, int nbits, int w, bool balanced,
-                        uint32_t* totals, uint32_t* offsets, cudaStream_t s, int cfg) {
+                       int64_t n, int vb, int shift, int nbits, int w, bool balanced,
+                       uint32_t* totals, uint32_t* offsets, cudaStream_t s, int cfg,
+                       const PassSel& sel = PassSel{}) {
   switch (cfg) {
 #define BCF_PASS(C)                                                                                  \
   case C:                                                                                            \
     return pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C]>(src_k, src_v, dst_k, dst_v, n, vb, shift, \
-                                                              nbits, w, balanced, totals, offsets, s);
+                                                              nbits, w, balanced, totals, offsets, s, sel);
     BCF_PASS(0)
     BCF_PASS(1)
     BCF_PASS(2)
@@ -168,7 +171,7 @@ template <int BITS, int THREADS, int IPT>
 static cudaError_t lookback_pass_t(const uint32_t* src_k, const void* src_v, uint32_t* dst_k,
                                    void* dst_v, int64_t n, int vb, int shift, int w, bool balanced,
                                    const uint32_t* digit_base, uint32_t* status, uint32_t* ticket,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, const PassSel& sel) {
   constexpr int T = THREADS * IPT;
   const int64_t tiles = (n + T - 1) / T;
   SweepParams sp{};
@@ -188,6 +191,7 @@ static cudaError_t lookback_pass_t(const uint32_t* src_k, const void* src_v, uin
   sp.status = status_word();
   sp.spin_limit = g_spin_limit;
   sp.silent_tile1 = g_silent_tile1;
+  sp.sel = sel;
   return sweep_dispatch<BITS, THREADS, IPT>(sp, tiles, vb, s);
 }
 
@@ -195,13 +199,13 @@ template <int BITS>
 static cudaError_t lookback_pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
                                  int64_t n, int vb, int shift, int w, bool balanced,
                                  const uint32_t* digit_base, uint32_t* status, uint32_t* ticket,
-                                 cudaStream_t s, int cfg) {
+                                 cudaStream_t s, int cfg, const PassSel& sel = PassSel{}) {
   switch (cfg) {
 #define BCF_LBP(C)                                                                                     \
   case C:                                                                                              \
     return lookback_pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C]>(src_k, src_v, dst_k, dst_v, n, vb, \
                                                                        shift, w, balanced, digit_base,   \
-                                                                       status, ticket, s);
+                                                                       status, ticket, s, sel);
     BCF_LBP(0)
     BCF_LBP(1)
     BCF_LBP(2)
@@ -212,8 +216,10 @@ static cudaError_t lookback_pass(const uint32_t* src_k, const void* src_v, uint3
 }
 
 static cudaError_t small_histogram(const uint32_t* keys, int64_t n, int passes, const int* shift,
-                                   int label_bits, unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
+                                   int label_bits, unsigned char* ws, const SweepLayout& L, cudaStream_t s,
+                                   uint32_t* vary = nullptr) {
   HistParams hp{};
+  hp.vary = vary;
   hp.keys = keys;
   hp.n = n;
   hp.passes = passes;
@@ -234,29 +240,80 @@ static cudaError_t small_histogram(const uint32_t* keys, int64_t n, int passes, 
   return cudaGetLastError();
 }
 
+// Brings a sorted result home when the passes that ran left it elsewhere: in the
+// temporary (in place, an odd number of runs), or still in the input (no pass ran,
+// out of place).  With no pass run and positions as the payload, writes them.
+__global__ void __launch_bounds__(256) k_pass_copy(PassSel sel, int64_t n, int vb) {
+  const int k = __popc(passes_run_mask(sel, vary_bits(sel)));
+  const uint32_t* sk = nullptr;
+  const unsigned char* sv = nullptr;
+  bool iota = false;
+  if (k == 0) {
+    sk = sel.k_in == sel.k_out ? nullptr : sel.k_in;
+    iota = vb == 4 && sel.v_in == nullptr;
+    sv = sel.v_in == sel.v_out ? nullptr : static_cast<const unsigned char*>(sel.v_in);
+  } else if (sel.in_place && (k & 1)) {
+    sk = sel.k_tmp;
+    sv = static_cast<const unsigned char*>(sel.v_tmp);
+  } else {
+    return;
+  }
+  unsigned char* dv = static_cast<unsigned char*>(sel.v_out);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n4 = n / 4;  // groups of four elements: 16-byte keys, 16 or 32 bytes of payload
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n4; g += stride) {
+    if (sk) reinterpret_cast<uint4*>(sel.k_out)[g] = reinterpret_cast<const uint4*>(sk)[g];
+    if (vb == 0) continue;
+    if (iota) {
+      const uint32_t i = (uint32_t)(g * 4);
+      reinterpret_cast<uint4*>(dv)[g] = make_uint4(i, i + 1, i + 2, i + 3);
+    } else if (sv) {
+      for (int h = 0; h < vb / 4; ++h)
+        reinterpret_cast<uint4*>(dv)[g * (vb / 4) + h] = reinterpret_cast<const uint4*>(sv)[g * (vb / 4) + h];
+    }
+  }
+  for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (sk) sel.k_out[i] = sk[i];
+    if (vb == 4 && iota) reinterpret_cast<uint32_t*>(dv)[i] = (uint32_t)i;
+    else if (vb == 4 && sv) reinterpret_cast<uint32_t*>(dv)[i] = reinterpret_cast<const uint32_t*>(sv)[i];
+    else if (vb == 8 && sv)
+      reinterpret_cast<unsigned long long*>(dv)[i] = reinterpret_cast<const unsigned long long*>(sv)[i];
+  }
+}
+
 cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n, int vb, const PassPlan& plan,
                        unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg) {
   if (n == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
-  const bool small = n <= kSmallSweepN;
-  if (small && (e = small_histogram(keys_in, n, plan.passes, plan.shift, 0, ws, L, s)) != cudaSuccess)
-    return e;
-  uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);
-  uint32_t* offsets = reinterpret_cast<uint32_t*>(ws + L.lookback);
-
-  // Ping-pong so that the last pass lands in keys_out.  When sorting in place
-  // with an odd pass count, every pass alternates tmp/out starting from tmp and
-  // a final copy brings the result home.
   uint32_t* kt = reinterpret_cast<uint32_t*>(ws + L.keys_tmp);
   void* vt = vb ? (void*)(ws + L.vals_tmp) : nullptr;
-  const bool in_place = (keys_in == keys_out);
   const int P = plan.passes;
+  // Which passes run, and the buffers of each, are settled on the device (PassSel).
+  PassSel sel;
+  sel.vary = sort_vary_words(ws, L);
+  sel.ran = sort_vary_words(ws, L) + 2;
+  sel.passes = P;
+  sel.in_place = keys_in == keys_out;
+  for (int q = 0; q < P; ++q) sel.shift[q] = plan.shift[q];
+  sel.k_in = keys_in;
+  sel.v_in = vals_in;
+  sel.k_out = keys_out;
+  sel.v_out = vals_out;
+  sel.k_tmp = kt;
+  sel.v_tmp = vt;
+  const bool small = n <= kSmallSweepN;
+  if (small && (e = small_histogram(keys_in, n, P, plan.shift, 0, ws, L, s, sel.vary)) != cudaSuccess) return e;
+  uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);
+  uint32_t* offsets = reinterpret_cast<uint32_t*>(ws + L.lookback);
+  // The buffers passed down are those of the case in which every pass runs (the
+  // kernels switch only when the device finds a skipped pass before theirs).
+  const bool odd_in_place = sel.in_place && (P % 2 == 1);
   const uint32_t* src_k = keys_in;
   const void* src_v = vals_in;
-  const bool odd_in_place = in_place && (P % 2 == 1);
   for (int q = 0; q < P; ++q) {
+    sel.q = q;
     const bool to_out = odd_in_place ? (q % 2 == 1) : (((P - 1 - q) % 2) == 0);
     uint32_t* dk = to_out ? keys_out : kt;
     void* dv = to_out ? vals_out : vt;
@@ -264,22 +321,36 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
       e = lookback_pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], 0, false,
                            reinterpret_cast<uint32_t*>(ws + L.digit_base) + q * 256,
                            reinterpret_cast<uint32_t*>(ws + L.status) + (size_t)q * L.lb_stride * 256,
-                           reinterpret_cast<uint32_t*>(ws + L.counters) + q, s, cfg);
+                           reinterpret_cast<uint32_t*>(ws + L.counters) + q, s, cfg, sel);
     } else {
       e = pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], plan.nbits[q], 0, false, totals + q * 256,
-                  offsets, s, cfg);
+                  offsets, s, cfg, sel);
     }
     if (e != cudaSuccess) return e;
     src_k = dk;
     src_v = dv;
   }
-  if (odd_in_place) {
-    if ((e = cudaMemcpyAsync(keys_out, kt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-      return e;
-    if (vb && (e = cudaMemcpyAsync(vals_out, vt, (size_t)n * vb, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-      return e;
-  }
-  return cudaSuccess;
+  if (!sel.in_place) return cudaSuccess;  // out of place the last pass that runs writes the output
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n / 4 + 255) / 256;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 8));
+  k_pass_copy<<<grid, 256, 0, s>>>(sel, n, vb);
+  return cudaGetLastError();
+}
+
+int sort_passes_run(const unsigned char* ws, const SweepLayout& L, const PassPlan& plan, cudaStream_t s,
+                    int* out) {
+  uint32_t ran = 0;
+  cudaError_t e = cudaMemcpyAsync(&ran, sort_vary_words(const_cast<unsigned char*>(ws), L) + 2, sizeof ran,
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return (int)e;
+  int k = 0;
+  for (int q = 0; q < plan.passes; ++q) k += (ran >> q) & 1u;
+  *out = k;
+  return 0;
 }
 
 cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,

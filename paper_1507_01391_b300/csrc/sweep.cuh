@@ -28,6 +28,74 @@ constexpr uint32_t LB_AGG = 1u << 30;   // tile aggregate published
 constexpr uint32_t LB_INC = 2u << 30;   // inclusive prefix published
 constexpr uint32_t LB_MASK = (1u << 30) - 1;
 
+// Pass skipping of the LSD radix sort.  A digit pass in which every key has the
+// same digit moves nothing, so it is left out; which passes run is decided on the
+// device (no host round trip, so a sort stays capturable in a CUDA graph).  The
+// first pass's count kernel (or the histogram of small inputs) ORs every key into
+// vary[0] and every complement into vary[1]: key bit b varies iff it is set in
+// both.  Each kernel of pass q then finds from vary whether pass q runs and which
+// buffers it reads and writes: the runs alternate between the output and a
+// temporary so that the last one lands in the output (in place with an odd count:
+// in the temporary, and k_pass_copy brings it home).  The host passes the buffers
+// of the case in which every pass runs; a kernel starts its reads there and only
+// re-reads when the device's choice differs, so the check costs no latency.
+struct PassSel {
+  uint32_t* vary;        // [2], zero before the first pass; nullptr: no skipping
+  uint32_t* ran;         // zero before the first pass; bit q set when pass q ran
+  int q = 0, passes = 0, in_place = 0;
+  int shift[4] = {0, 0, 0, 0};
+  const uint32_t* k_in = nullptr;
+  const void* v_in = nullptr;  // nullptr with 4-byte payloads: payload = input position
+  uint32_t* k_out = nullptr;
+  void* v_out = nullptr;
+  uint32_t* k_tmp = nullptr;
+  void* v_tmp = nullptr;
+};
+
+// The varying key bits: AND of the two OR words.
+__device__ __forceinline__ uint32_t vary_bits(const PassSel& s) {
+  return ld_relaxed(s.vary) & ld_relaxed(s.vary + 1);
+}
+
+// Passes that run (bit q) given the varying bits.  Out of place, when no digit
+// varies the last pass still runs (a stable pass over equal digits is a copy),
+// so that the result reaches the output.
+__device__ __forceinline__ unsigned passes_run_mask(const PassSel& s, uint32_t v) {
+  unsigned m = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)  // constant indices: the shifts stay in parameter space
+    if (q < s.passes && ((v >> s.shift[q]) & 0xFFu)) m |= 1u << q;
+  if (!m && !s.in_place) m = 1u << (s.passes - 1);
+  return m;
+}
+
+// Buffers of pass s.q given the varying bits; false when the pass is skipped.
+__device__ __forceinline__ bool pass_buffers(const PassSel& s, uint32_t v, const uint32_t*& sk,
+                                             const void*& sv, uint32_t*& dk, void*& dv) {
+  const unsigned m = passes_run_mask(s, v);
+  if (!((m >> s.q) & 1u)) return false;
+  const int i = __popc(m & ((1u << s.q) - 1u)), k = __popc(m);
+  auto to_out = [&](int j) { return (s.in_place && (k & 1)) ? (j & 1) == 1 : ((k - 1 - j) & 1) == 0; };
+  if (i == 0) {
+    sk = s.k_in;
+    sv = s.v_in;
+  } else if (to_out(i - 1)) {
+    sk = s.k_out;
+    sv = s.v_out;
+  } else {
+    sk = s.k_tmp;
+    sv = s.v_tmp;
+  }
+  if (to_out(i)) {
+    dk = s.k_out;
+    dv = s.v_out;
+  } else {
+    dk = s.k_tmp;
+    dv = s.v_tmp;
+  }
+  return true;
+}
+
 struct SweepParams {
   const uint32_t* keys_in;
   const void* vals_in;         // nullptr with 4-byte payloads: payload = input position
@@ -61,6 +129,7 @@ struct SweepParams {
   // splitter mode (k_sweep<..., SPLIT = true>): digit = number of splitters <= key
   const uint32_t* splitters;   // nsplit ascending values
   int nsplit;                  // 0..255
+  PassSel sel;                 // sel.vary != nullptr: buffers (or a skip) decided on the device
 };
 
 template <int BITS>
@@ -110,7 +179,27 @@ struct HistParams {
   uint32_t* hist;        // passes x 256, zero on entry
   uint32_t* digit_base;  // passes x 256, written by the last block
   uint32_t* done;        // zero on entry
+  uint32_t* vary;        // nullptr, or [2] zero on entry: OR of the keys, OR of their complements
 };
+
+// Block-wide OR of (o1, o0) into vary[0], vary[1] (every thread of the block
+// takes part; ends with a barrier).
+__device__ __forceinline__ void or_into_vary(uint32_t o1, uint32_t o0, uint32_t* vary, uint32_t* scratch2) {
+  o1 = __reduce_or_sync(0xffffffffu, o1);
+  o0 = __reduce_or_sync(0xffffffffu, o0);
+  if (threadIdx.x == 0) scratch2[0] = scratch2[1] = 0u;
+  BCF_SYNC();
+  if ((threadIdx.x & 31) == 0) {
+    atomicOr(&scratch2[0], o1);
+    atomicOr(&scratch2[1], o0);
+  }
+  BCF_SYNC();
+  if (threadIdx.x == 0) {
+    if (scratch2[0]) atomicOr(&vary[0], scratch2[0]);
+    if (scratch2[1]) atomicOr(&vary[1], scratch2[1]);
+  }
+  BCF_SYNC();
+}
 
 // Counts every digit of every pass in one read of the keys; the last block to
 // finish turns the counts into exclusive starts.
@@ -129,11 +218,14 @@ __global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
   const int64_t nvec = p.n >> 2;
   const uint4* kv = reinterpret_cast<const uint4*>(p.keys);
   const int64_t stride = (int64_t)gridDim.x * THREADS;
+  uint32_t o1 = 0, o0 = 0;  // OR of the keys and of their complements
   for (int64_t i = (int64_t)blockIdx.x * THREADS + tid; i < nvec; i += stride) {
     uint4 k4 = __ldcs(kv + i);
     uint32_t k[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
+      o1 |= k[c];
+      o0 |= ~k[c];
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (q < p.passes) atomicAdd(&h[q * 256 + ((k[c] >> p.shift[q]) & mask[q])], 1u);
@@ -141,10 +233,13 @@ __global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
   }
   for (int64_t i = nvec * 4 + (int64_t)blockIdx.x * THREADS + tid; i < p.n; i += stride) {
     uint32_t k = p.keys[i];
+    o1 |= k;
+    o0 |= ~k;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       if (q < p.passes) atomicAdd(&h[q * 256 + ((k >> p.shift[q]) & mask[q])], 1u);
   }
+  if (p.vary) or_into_vary(o1, o0, p.vary, scratch);
   BCF_SYNC();
   for (int i = tid; i < p.passes * 256; i += THREADS)
     if (h[i]) atomicAdd(&p.hist[i], h[i]);
@@ -207,6 +302,7 @@ struct CountParams {
   const uint32_t* num_tiles;
   const uint32_t* splitters;     // splitter mode: digit = number of splitters <= key
   int nsplit;
+  PassSel sel;                   // sel.vary != nullptr: pass 0 fills vary, later passes may skip
 };
 
 #ifndef BCF_COUNT_TILES_PER_BLOCK
@@ -238,6 +334,31 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
   const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
   const bool segmented = p.seg_offs != nullptr;
   if (segmented) tiles = min(tiles, (int64_t)ld_relaxed(p.num_tiles));
+  // Sort passes: pass 0 ORs the keys into sel.vary; a later pass reads the buffer
+  // the previous run wrote, or returns if its digit never varies.
+  const bool fill_vary = p.sel.vary && p.sel.q == 0;
+  const bool sel_later = p.sel.vary && p.sel.q > 0;
+  __shared__ const uint32_t* s_keys;  // the device's choice of input, or nullptr: pass skipped
+  auto resolve = [&]() -> bool {      // false: this pass is skipped; ends with a barrier
+    if (!sel_later) return true;
+    if (tid == 0) {
+      const uint32_t* sk;
+      const void* sv;
+      uint32_t* dk;
+      void* dv;
+      s_keys = pass_buffers(p.sel, vary_bits(p.sel), sk, sv, dk, dv) ? sk : nullptr;
+    }
+    BCF_SYNC();
+    if (!s_keys) return false;
+    p.keys = s_keys;
+    return true;
+  };
+  __shared__ uint32_t orw[2];
+  uint32_t o1 = 0, o0 = 0;
+  auto or4 = [&](const uint4& x) {
+    o1 |= x.x | x.y | x.z | x.w;
+    o0 |= ~x.x | ~x.y | ~x.z | ~x.w;
+  };
   if constexpr (FAST && NV <= 4) {
     // Four full tiles: every load in flight before any count, one histogram per
     // tile, and the four counts of a digit stored together (the count rows'
@@ -245,11 +366,20 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     if (!segmented && (t0 + 4) * T <= p.n) {
       for (int i = tid; i < 4 * RADIX; i += 256) h4[i / RADIX][i % RADIX] = 0;
       uint4 x[4][NV];
+      const uint32_t* k_first = p.keys;
       const uint4* k4 = reinterpret_cast<const uint4*>(p.keys + t0 * T);
 #pragma unroll
       for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
+      if (!resolve()) return;
+      if (p.keys != k_first) {  // an earlier pass was skipped: the keys are elsewhere
+        k4 = reinterpret_cast<const uint4*>(p.keys + t0 * T);
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
+      }
       BCF_SYNC();
 #pragma unroll
       for (int t = 0; t < 4; ++t)
@@ -259,6 +389,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
           atomicAdd(&h4[t][dig(x[t][q].y)], 1u);
           atomicAdd(&h4[t][dig(x[t][q].z)], 1u);
           atomicAdd(&h4[t][dig(x[t][q].w)], 1u);
+          if (fill_vary) or4(x[t][q]);
         }
       BCF_SYNC();
       for (int d = tid; d < RADIX; d += 256) {
@@ -266,9 +397,11 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
         *reinterpret_cast<uint4*>(p.counts + (size_t)d * p.stride + t0) = c;
         if (p.totals && (c.x | c.y | c.z | c.w)) atomicAdd(&p.totals[d], c.x + c.y + c.z + c.w);
       }
+      if (fill_vary) or_into_vary(o1, o0, p.sel.vary, orw);
       return;
     }
   }
+  if (!resolve()) return;
   for (int64_t tile = t0; tile < min(t0 + kCountTilesPerBlock, tiles); ++tile) {
     int64_t start = tile * T, hi = p.n;
     if (segmented) {
@@ -313,6 +446,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
         atomicAdd(&h[dig(x[q].y)], 1u);
         atomicAdd(&h[dig(x[q].z)], 1u);
         atomicAdd(&h[dig(x[q].w)], 1u);
+        if (fill_vary) or4(x[q]);
       }
     } else {
       const int nv = cnt >> 2;
@@ -322,8 +456,15 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
         atomicAdd(&h[dig(x.y)], 1u);
         atomicAdd(&h[dig(x.z)], 1u);
         atomicAdd(&h[dig(x.w)], 1u);
+        if (fill_vary) or4(x);
       }
-      for (int i = nv * 4 + tid; i < cnt; i += 256) atomicAdd(&h[dig(k[i])], 1u);
+      for (int i = nv * 4 + tid; i < cnt; i += 256) {
+        atomicAdd(&h[dig(k[i])], 1u);
+        if (fill_vary) {
+          o1 |= k[i];
+          o0 |= ~k[i];
+        }
+      }
     }
     BCF_SYNC();
     for (int d = tid; d < RADIX; d += 256) {
@@ -336,6 +477,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
   if (p.totals)
     for (int d = tid; d < RADIX; d += 256)
       if (tot[d]) atomicAdd(&p.totals[d], tot[d]);
+  if (fill_vary) or_into_vary(o1, o0, p.sel.vary, orw);
 }
 
 // One block per digit: exclusive scan of the digit's tile counts, offset by the
@@ -348,7 +490,7 @@ template <int kScanThreads>
 __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* counts, int64_t tiles,
                                                                  int64_t stride, const uint32_t* totals,
                                                                  int balanced, int64_t n, int w,
-                                                                 unsigned* status) {
+                                                                 unsigned* status, PassSel sel) {
   __shared__ uint32_t scratch[32];
   __shared__ uint32_t s_base;
   const int d = blockIdx.x;
@@ -370,6 +512,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* count
     }
   };
   load((int64_t)tid * kScanPerThread);
+  __shared__ int s_skip;
   if (tid < 32) {  // digit start: warp-wide sum of the smaller digits' totals
     uint32_t b = 0;
     if (totals && !balanced)
@@ -383,9 +526,12 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* count
         if (totals && totals[d] != expect) set_status(status, DEV_NOT_BALANCED);
       }
       s_base = b;  // segment mode (no totals): plain running sums from 0
+      // a skipped sort pass: nothing to scan (its counts were never written)
+      s_skip = sel.vary && !((passes_run_mask(sel, vary_bits(sel)) >> sel.q) & 1u);
     }
   }
   BCF_SYNC();
+  if (s_skip) return;
   uint32_t carry = s_base;
   for (int64_t c0 = 0; c0 < tiles; c0 += (int64_t)kScanThreads * kScanPerThread) {
     const int64_t i0 = c0 + (int64_t)tid * kScanPerThread;
@@ -407,13 +553,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* count
 
 // One block per digit; a block of 256 threads covers 4096 tiles in one step, so
 // only larger tile counts take 1024 (fewer idle threads at every barrier).
+// sel.vary != nullptr: a sort pass that may be skipped.
 static inline cudaError_t launch_scan_offsets(int radix, uint32_t* counts, int64_t tiles, int64_t stride,
                                               const uint32_t* totals, int balanced, int64_t n, int w,
-                                              unsigned* status, cudaStream_t s) {
+                                              unsigned* status, cudaStream_t s, const PassSel& sel = PassSel{}) {
   if (tiles <= 256 * kScanPerThread)
-    k_scan_offsets_t<256><<<radix, 256, 0, s>>>(counts, tiles, stride, totals, balanced, n, w, status);
+    k_scan_offsets_t<256><<<radix, 256, 0, s>>>(counts, tiles, stride, totals, balanced, n, w, status, sel);
   else
-    k_scan_offsets_t<1024><<<radix, 1024, 0, s>>>(counts, tiles, stride, totals, balanced, n, w, status);
+    k_scan_offsets_t<1024><<<radix, 1024, 0, s>>>(counts, tiles, stride, totals, balanced, n, w, status, sel);
   return cudaGetLastError();
 }
 
@@ -434,6 +581,7 @@ struct SweepSmem {
   static constexpr size_t spl = info + 16;                 // splitter mode: splitters
   static constexpr size_t sdig = spl + (SPLIT ? 256 * 4 : 0);  // splitter mode: digit of each ordered key
   static constexpr size_t bytes = sdig + (SPLIT ? (size_t)T : 0);
+  static_assert(scratch % 8 == 0, "scratch also carries pointers; mbar needs 8-byte alignment");
 };
 
 template <int THREADS, int IPT, int BITS, int VB, bool SPLIT = false>
@@ -487,29 +635,68 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   const bool label_mode = w > 0;
 
   // Stage the tile: bulk copy of the 16-byte-aligned window, plain loads for the
-  // ragged end.  Element i of the tile is keys_s[ksh + i].
-  const int ksh = (int)((reinterpret_cast<uintptr_t>(p.keys_in + start) & 15u) >> 2);
-  // vals_in == nullptr with 4-byte payloads: the payload is the input position
-  const bool iota = VB == 4 && p.vals_in == nullptr;
-  const int vsh = (VB && !iota) ? (int)((reinterpret_cast<uintptr_t>(reinterpret_cast<const VT*>(p.vals_in) + start) & 15u) / VB) : 0;
-  const int kfull = ((ksh + cnt) * 4 & ~15) / 4;  // elements covered by the bulk copy
-  const int vfull = (VB && !iota) ? (((vsh + cnt) * VB) & ~15) / VB : 0;
-  if (tid == 0) {
-    mbar_init(mbar, 1);
-    mbar_arrive_expect_tx(mbar, (unsigned)(kfull * 4 + vfull * VB));
-    if (kfull) bulk_g2s(keys_s, p.keys_in + start - ksh, (unsigned)kfull * 4, mbar);
-    if (VB && vfull)
-      bulk_g2s(vals_s, reinterpret_cast<const VT*>(p.vals_in) + start - vsh, (unsigned)(vfull * VB), mbar);
-  }
+  // ragged end.  Element i of the tile is keys_s[ksh + i].  vals_in == nullptr
+  // with 4-byte payloads: the payload is the input position.
+  int ksh = 0, vsh = 0, kfull = 0, vfull = 0;
+  bool iota = false;
+  auto stage = [&](bool first) {
+    ksh = (int)((reinterpret_cast<uintptr_t>(p.keys_in + start) & 15u) >> 2);
+    iota = VB == 4 && p.vals_in == nullptr;
+    vsh = (VB && !iota) ? (int)((reinterpret_cast<uintptr_t>(reinterpret_cast<const VT*>(p.vals_in) + start) & 15u) / VB) : 0;
+    kfull = ((ksh + cnt) * 4 & ~15) / 4;  // elements covered by the bulk copy
+    vfull = (VB && !iota) ? (((vsh + cnt) * VB) & ~15) / VB : 0;
+    if (tid == 0) {
+      if (first) mbar_init(mbar, 1);
+      mbar_arrive_expect_tx(mbar, (unsigned)(kfull * 4 + vfull * VB));
+      if (kfull) bulk_g2s(keys_s, p.keys_in + start - ksh, (unsigned)kfull * 4, mbar);
+      if (VB && vfull)
+        bulk_g2s(vals_s, reinterpret_cast<const VT*>(p.vals_in) + start - vsh, (unsigned)(vfull * VB), mbar);
+    }
+  };
+  stage(true);
   for (int i = tid; i < S::WARPS * RADIX; i += THREADS) whist[i] = 0;
   if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, THREADS, p.status);
+  unsigned parity = 0;
+  if (p.sel.vary) {
+    // Sort pass with device-side skipping: the tile's copy from the host's
+    // (every-pass-runs) buffers is already under way; one thread reads the
+    // device's choice and hands it to the block through `scratch`.
+    struct Choice {
+      const uint32_t* sk;
+      const void* sv;
+      uint32_t* dk;
+      void* dv;
+      int runs, moved;
+    };
+    Choice* ch = reinterpret_cast<Choice*>(scratch);
+    if (tid == 0) {
+      Choice c;
+      c.runs = pass_buffers(p.sel, vary_bits(p.sel), c.sk, c.sv, c.dk, c.dv);
+      c.moved = c.runs && (c.sk != p.keys_in || c.sv != p.vals_in);
+      *ch = c;
+      if (c.runs && blockIdx.x == 0) atomicOr(p.sel.ran, 1u << p.sel.q);
+    }
+    BCF_SYNC();
+    const Choice c = *ch;
+    if (!c.runs || c.moved) {
+      mbar_wait(mbar, 0, p.status);  // the copy already issued has landed
+      if (!c.runs) return;           // skipped pass: nothing to move
+      BCF_SYNC();
+      p.keys_in = c.sk;  // an earlier pass was skipped: stage from where its input is
+      p.vals_in = c.sv;
+      stage(false);
+      parity = 1;
+    }
+    p.keys_out = c.dk;
+    p.vals_out = c.dv;
+  }
   for (int i = max(kfull - ksh, 0) + tid; i < cnt; i += THREADS) keys_s[ksh + i] = p.keys_in[start + i];
   if (VB && !iota) {
     for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
       vals_s[vsh + i] = reinterpret_cast<const VT*>(p.vals_in)[start + i];
   }
   BCF_SYNC();  // mbarrier initialised before anyone waits on it
-  mbar_wait(mbar, 0, p.status);
+  mbar_wait(mbar, parity, p.status);
   BCF_SYNC();
 
   // The rest is written once for full tiles (no per-key bounds tests) and once

@@ -36,9 +36,8 @@ constexpr uint32_t LB_MASK = (1u << 30) - 1;
 // both.  Each kernel of pass q then finds from vary whether pass q runs and which
 // buffers it reads and writes: the runs alternate between the output and a
 // temporary so that the last one lands in the output (in place with an odd count:
-// in the temporary, and k_pass_copy brings it home).  The host passes the buffers
-// of the case in which every pass runs; a kernel starts its reads there and only
-// re-reads when the device's choice differs, so the check costs no latency.
+// in the temporary, and k_pass_copy brings it home).  One thread per block reads
+// the choice and hands it to the others.
 struct PassSel {
   uint32_t* vary;        // [2], zero before the first pass; nullptr: no skipping
   uint32_t* ran;         // zero before the first pass; bit q set when pass q ran
@@ -52,9 +51,11 @@ struct PassSel {
   void* v_tmp = nullptr;
 };
 
-// The varying key bits: AND of the two OR words.
+// The varying key bits: AND of the two OR words.  The words are final before the
+// kernel that reads them starts, so the read may go through the SM's read-only
+// cache: of the many blocks an SM runs, only the first waits on L2.
 __device__ __forceinline__ uint32_t vary_bits(const PassSel& s) {
-  return ld_relaxed(s.vary) & ld_relaxed(s.vary + 1);
+  return __ldg(s.vary) & __ldg(s.vary + 1);
 }
 
 // Passes that run (bit q) given the varying bits.  Out of place, when no digit
@@ -314,7 +315,7 @@ constexpr int kCountTilesPerBlock = BCF_COUNT_TILES_PER_BLOCK;
 // flight take registers; the segment-mode instance leaves it out and keeps its
 // occupancy for the scalar loads of unaligned segments).
 template <int BITS, int T, bool SPLIT = false, bool FAST = true>
-__global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tiles) {
+__global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t tiles) {
   constexpr int RADIX = 1 << BITS;
   constexpr int NV = T / 1024;  // 16-byte loads per thread per tile
   static_assert(kCountTilesPerBlock == 4, "fast path counts four tiles at once");
@@ -353,6 +354,7 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     p.keys = s_keys;
     return true;
   };
+  if (!resolve()) return;
   __shared__ uint32_t orw[2];
   uint32_t o1 = 0, o0 = 0;
   auto or4 = [&](const uint4& x) {
@@ -366,20 +368,11 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
     if (!segmented && (t0 + 4) * T <= p.n) {
       for (int i = tid; i < 4 * RADIX; i += 256) h4[i / RADIX][i % RADIX] = 0;
       uint4 x[4][NV];
-      const uint32_t* k_first = p.keys;
       const uint4* k4 = reinterpret_cast<const uint4*>(p.keys + t0 * T);
 #pragma unroll
       for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
-      if (!resolve()) return;
-      if (p.keys != k_first) {  // an earlier pass was skipped: the keys are elsewhere
-        k4 = reinterpret_cast<const uint4*>(p.keys + t0 * T);
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-#pragma unroll
-          for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
-      }
       BCF_SYNC();
 #pragma unroll
       for (int t = 0; t < 4; ++t)
@@ -401,7 +394,6 @@ __global__ void __launch_bounds__(256) k_tile_counts(CountParams p, int64_t tile
       return;
     }
   }
-  if (!resolve()) return;
   for (int64_t tile = t0; tile < min(t0 + kCountTilesPerBlock, tiles); ++tile) {
     int64_t start = tile * T, hi = p.n;
     if (segmented) {
@@ -609,14 +601,38 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool segmented = p.seg_offs != nullptr;
 
+  // Sort pass with device-side skipping: one thread finds whether the pass runs
+  // and which buffers it reads and writes, and hands that to the block.
+  struct Choice {
+    const uint32_t* sk;
+    const void* sv;
+    uint32_t* dk;
+    void* dv;
+    int runs;
+  };
+  Choice* ch = reinterpret_cast<Choice*>(scratch);
   // Look-back mode takes tiles in launch order (atomic ticket) so that every tile
   // a look-back waits on belongs to a block that is already running.
   if (tid == 0) {
+    if (p.sel.vary) {
+      Choice c;
+      c.runs = pass_buffers(p.sel, vary_bits(p.sel), c.sk, c.sv, c.dk, c.dv);
+      *ch = c;
+      if (c.runs && blockIdx.x == 0) atomicOr(p.sel.ran, 1u << p.sel.q);
+    }
     const int tile = p.tile_offsets ? (int)blockIdx.x : (int)atomicAdd(p.ticket, 1u);
     s_info[0] = tile;
     s_info[1] = (segmented && (uint32_t)tile < ld_relaxed(p.num_tiles)) ? p.tile_seg[tile] : -1;
   }
   BCF_SYNC();
+  if (p.sel.vary) {
+    const Choice c = *ch;
+    if (!c.runs) return;  // skipped pass: nothing to move
+    p.keys_in = c.sk;
+    p.vals_in = c.sv;
+    p.keys_out = c.dk;
+    p.vals_out = c.dv;
+  }
   const int tile = s_info[0];
   if (segmented && s_info[1] < 0) return;  // more blocks than tiles this time
   const int seg = s_info[1];
@@ -639,64 +655,30 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   // with 4-byte payloads: the payload is the input position.
   int ksh = 0, vsh = 0, kfull = 0, vfull = 0;
   bool iota = false;
-  auto stage = [&](bool first) {
+  auto stage = [&]() {
     ksh = (int)((reinterpret_cast<uintptr_t>(p.keys_in + start) & 15u) >> 2);
     iota = VB == 4 && p.vals_in == nullptr;
     vsh = (VB && !iota) ? (int)((reinterpret_cast<uintptr_t>(reinterpret_cast<const VT*>(p.vals_in) + start) & 15u) / VB) : 0;
     kfull = ((ksh + cnt) * 4 & ~15) / 4;  // elements covered by the bulk copy
     vfull = (VB && !iota) ? (((vsh + cnt) * VB) & ~15) / VB : 0;
     if (tid == 0) {
-      if (first) mbar_init(mbar, 1);
+      mbar_init(mbar, 1);
       mbar_arrive_expect_tx(mbar, (unsigned)(kfull * 4 + vfull * VB));
       if (kfull) bulk_g2s(keys_s, p.keys_in + start - ksh, (unsigned)kfull * 4, mbar);
       if (VB && vfull)
         bulk_g2s(vals_s, reinterpret_cast<const VT*>(p.vals_in) + start - vsh, (unsigned)(vfull * VB), mbar);
     }
   };
-  stage(true);
+  stage();
   for (int i = tid; i < S::WARPS * RADIX; i += THREADS) whist[i] = 0;
   if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, THREADS, p.status);
-  unsigned parity = 0;
-  if (p.sel.vary) {
-    // Sort pass with device-side skipping: the tile's copy from the host's
-    // (every-pass-runs) buffers is already under way; one thread reads the
-    // device's choice and hands it to the block through `scratch`.
-    struct Choice {
-      const uint32_t* sk;
-      const void* sv;
-      uint32_t* dk;
-      void* dv;
-      int runs, moved;
-    };
-    Choice* ch = reinterpret_cast<Choice*>(scratch);
-    if (tid == 0) {
-      Choice c;
-      c.runs = pass_buffers(p.sel, vary_bits(p.sel), c.sk, c.sv, c.dk, c.dv);
-      c.moved = c.runs && (c.sk != p.keys_in || c.sv != p.vals_in);
-      *ch = c;
-      if (c.runs && blockIdx.x == 0) atomicOr(p.sel.ran, 1u << p.sel.q);
-    }
-    BCF_SYNC();
-    const Choice c = *ch;
-    if (!c.runs || c.moved) {
-      mbar_wait(mbar, 0, p.status);  // the copy already issued has landed
-      if (!c.runs) return;           // skipped pass: nothing to move
-      BCF_SYNC();
-      p.keys_in = c.sk;  // an earlier pass was skipped: stage from where its input is
-      p.vals_in = c.sv;
-      stage(false);
-      parity = 1;
-    }
-    p.keys_out = c.dk;
-    p.vals_out = c.dv;
-  }
   for (int i = max(kfull - ksh, 0) + tid; i < cnt; i += THREADS) keys_s[ksh + i] = p.keys_in[start + i];
   if (VB && !iota) {
     for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
       vals_s[vsh + i] = reinterpret_cast<const VT*>(p.vals_in)[start + i];
   }
   BCF_SYNC();  // mbarrier initialised before anyone waits on it
-  mbar_wait(mbar, parity, p.status);
+  mbar_wait(mbar, 0, p.status);
   BCF_SYNC();
 
   // The rest is written once for full tiles (no per-key bounds tests) and once

@@ -5,7 +5,8 @@
 // and its label p = lpi[q] names bank p mod 32 ("row i") and slot p/32 ("j").
 //
 // Two schedules, same result:
-//  * scatter  -- every thread writes out_s[p] = in_s[q]; a warp's 32 stores land
+//  * scatter  -- every thread writes out_s[p] = in_s[q] (k_tile_scatter_stream,
+//                persistent blocks over many tiles); a warp's 32 stores land
 //                in arbitrary banks, so they conflict (about 3.5 wavefronts each
 //                for a random permutation).
 //  * coloured -- the randomized algorithm of Sec. 3.  A random hash h: [32] -> [m]
@@ -95,31 +96,92 @@ __device__ __forceinline__ void write_tile(uint32_t* dst, int64_t start, int len
   }
 }
 
+// Direct scatter, streamed: persistent blocks take tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ...; the keys and labels of the next kTSBuffers - 1 tiles arrive by
+// bulk copies into a ring of buffers while this one is scattered, and each
+// finished tile leaves by a bulk store from shared memory that the block only
+// waits on before it scatters the next tile.
+constexpr int kTSThreads = 256;
+#ifndef BCF_TS_BUFFERS
+#define BCF_TS_BUFFERS 3
+#endif
+constexpr int kTSBuffers = BCF_TS_BUFFERS;  // tiles in flight per block: kTSBuffers - 1 ahead
+
 template <int T>
-__global__ void __launch_bounds__(kTPThreads) k_tile_scatter(const uint32_t* __restrict__ src,
-                                                             uint32_t* __restrict__ dst,
-                                                             const uint16_t* __restrict__ lpi,
-                                                             int64_t n, unsigned* status) {
-  using S = TPSmem<T>;
+struct TSSmem {
+  static constexpr size_t in = 0;                                     // [kTSBuffers][T] keys
+  static constexpr size_t lpi = in + kTSBuffers * (size_t)T * 4;      // [kTSBuffers][T] labels
+  static constexpr size_t out = lpi + kTSBuffers * (size_t)T * 2;     // [T] scattered tile
+  static constexpr size_t mbar = out + (size_t)T * 4;                 // [kTSBuffers]
+  static constexpr size_t bytes = mbar + 8 * kTSBuffers;
+};
+
+template <int T>
+__global__ void __launch_bounds__(kTSThreads) k_tile_scatter_stream(const uint32_t* __restrict__ src,
+                                                                    uint32_t* __restrict__ dst,
+                                                                    const uint16_t* __restrict__ lpi,
+                                                                    int64_t n, int64_t tiles,
+                                                                    unsigned* status) {
+  using S = TSSmem<T>;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint32_t* in_s = reinterpret_cast<uint32_t*>(smem + S::in);
-  uint16_t* lpi_s = reinterpret_cast<uint16_t*>(smem + S::lpi);
   uint32_t* out_s = reinterpret_cast<uint32_t*>(smem + S::out);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
-  const int len = stage_tile<T>(src, lpi, n, blockIdx.x, in_s, lpi_s, mbar, status);
-  for (int q = threadIdx.x; q < len; q += kTPThreads) {
-    BCF_TR_WORD(&lpi_s[q], 0, TS_STAGE_READ);
-    const uint32_t p = lpi_s[q];
-    BCF_TR(&in_s[q], 4, 0, TS_STAGE_READ);
-    if ((int)p < len) {
-      BCF_TR(&out_s[p], 4, 1, TS_SCATTER);
-      out_s[p] = in_s[q];
-    } else {
-      set_status(status, DEV_BAD_PERM);
-    }
+  auto in_set = [&](int b) { return reinterpret_cast<uint32_t*>(smem + S::in) + b * T; };
+  auto lpi_set = [&](int b) { return reinterpret_cast<uint16_t*>(smem + S::lpi) + b * T; };
+  const int tid = threadIdx.x;
+  auto issue = [&](int64_t t, int b) {  // one thread: bulk copies of tile t into buffer b
+    const int len = (int)min((int64_t)T, n - t * T);
+    const unsigned bk = (unsigned)(len * 4) & ~15u, bl = (unsigned)(len * 2) & ~15u;
+    mbar_arrive_expect_tx(&mbar[b], bk + bl);
+    if (bk) bulk_g2s(in_set(b), src + t * T, bk, &mbar[b]);
+    if (bl) bulk_g2s(lpi_set(b), lpi + t * T, bl, &mbar[b]);
+  };
+  if (tid == 0) {
+    for (int b = 0; b < kTSBuffers; ++b) mbar_init(&mbar[b], 1);
+    for (int b = 0; b < kTSBuffers - 1; ++b)
+      if ((int64_t)blockIdx.x + (int64_t)b * gridDim.x < tiles) issue(blockIdx.x + (int64_t)b * gridDim.x, b);
   }
   BCF_SYNC();
-  write_tile<T>(dst, (int64_t)blockIdx.x * T, len, out_s);
+  int it = 0;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
+    const int b = it % kTSBuffers;
+    uint32_t* in_s = in_set(b);
+    uint16_t* lpi_s = lpi_set(b);
+    const int len = (int)min((int64_t)T, n - t * T);
+    if (len < T) {  // ragged last tile: the words past the bulk copies by plain loads
+      for (int i = (((len * 4) & ~15) >> 2) + tid; i < len; i += kTSThreads) in_s[i] = src[t * T + i];
+      for (int i = (((len * 2) & ~15) >> 1) + tid; i < len; i += kTSThreads) lpi_s[i] = lpi[t * T + i];
+    }
+    mbar_wait(&mbar[b], (it / kTSBuffers) & 1, status);  // bounded: a lost copy is recorded, not waited on
+    if (tid == 0) {
+      bulk_s2g_wait_read();  // the previous tile's store has read out_s
+      // the buffer of the previous round is free again: refill it kTSBuffers - 1 tiles ahead
+      const int64_t ahead = t + (int64_t)(kTSBuffers - 1) * gridDim.x;
+      if (ahead < tiles) issue(ahead, (it + kTSBuffers - 1) % kTSBuffers);
+    }
+    BCF_SYNC();
+#pragma unroll 4
+    for (int q = tid; q < len; q += kTSThreads) {
+      BCF_TR_WORD(&lpi_s[q], 0, TS_STAGE_READ);
+      const uint32_t p = lpi_s[q];
+      BCF_TR(&in_s[q], 4, 0, TS_STAGE_READ);
+      if ((int)p < len) {
+        BCF_TR(&out_s[p], 4, 1, TS_SCATTER);
+        out_s[p] = in_s[q];
+      } else {
+        set_status(status, DEV_BAD_PERM);
+      }
+    }
+    fence_proxy_async_smem();
+    BCF_SYNC();
+    const unsigned bo = (unsigned)(len * 4) & ~15u;
+    if (tid == 0 && bo) {
+      bulk_s2g(dst + t * T, out_s, bo);
+      bulk_s2g_commit();
+    }
+    for (int i = (int)(bo >> 2) + tid; i < len; i += kTSThreads) dst[t * T + i] = out_s[i];
+  }
+  if (tid == 0) bulk_s2g_wait_read();  // shared memory stays valid until read out
 }
 
 // Coloured schedule.  Thread (warp g, lane l) owns row l's slots [g*M/4, (g+1)*M/4)
@@ -377,9 +439,22 @@ static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_sorted);
     k<<<(unsigned)tiles, kTPThreads, bytes, s>>>(src, dst, lpi, n, seed, 3, sorted ? 1 : 0, status_word());
   } else {
-    auto k = k_tile_scatter<T>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
-    k<<<(unsigned)tiles, kTPThreads, S::bytes, s>>>(src, dst, lpi, n, status_word());
+    using SS = TSSmem<T>;
+    auto k = k_tile_scatter_stream<T>;
+    static int resident[64] = {0};  // per device: blocks resident at once (shared-memory limit set)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!resident[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SS::bytes);
+      if (e != cudaSuccess) return e;
+      int sms = 148, per_sm = 1;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kTSThreads, SS::bytes);
+      resident[dev] = sms * std::max(per_sm, 1);
+    }
+    const int64_t grid = std::min<int64_t>(tiles, resident[dev]);
+    k<<<(unsigned)grid, kTSThreads, SS::bytes, s>>>(src, dst, lpi, n, tiles, status_word());
   }
   return cudaGetLastError();
 }

@@ -407,22 +407,34 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
     const uint32_t* k = p.keys + start;
     if (segmented) {
       // Segment starts need not be 16-byte aligned: 16-byte loads of the aligned
-      // window around the tile, counting only the tile's own elements; a vector
-      // that would pass the array's end is read element by element.
+      // window around the tile (at most T/1024 + 1 per thread, all in flight
+      // before any count), counting only the tile's own elements; a vector that
+      // would pass the array's end is read element by element.
       const int mis = (int)((reinterpret_cast<uintptr_t>(k) & 15u) >> 2);
       const int64_t a0 = start - mis;  // element index of the window's first word
       const uint4* k4 = reinterpret_cast<const uint4*>(p.keys + a0);
       const int nv = (cnt + mis + 3) >> 2;
-      for (int v = tid; v < nv; v += 256) {
+      constexpr int NVS = T / 1024 + 1;
+      uint4 xv[NVS];
+#pragma unroll
+      for (int j = 0; j < NVS; ++j) {
+        const int v = tid + 256 * j;
         const int e0 = v * 4 - mis;  // tile-relative index of the vector's first element
-        uint32_t x[4];
-        if (a0 + (int64_t)v * 4 + 4 <= p.n) {
-          const uint4 q = __ldcs(k4 + v);
-          x[0] = q.x; x[1] = q.y; x[2] = q.z; x[3] = q.w;
-        } else {
+        if (v < nv && a0 + (int64_t)v * 4 + 4 <= p.n) {
+          xv[j] = __ldcs(k4 + v);
+        } else if (v < nv) {
+          uint32_t x[4];
 #pragma unroll
           for (int c = 0; c < 4; ++c) x[c] = (e0 + c >= 0 && e0 + c < cnt) ? k[e0 + c] : 0u;
+          xv[j] = make_uint4(x[0], x[1], x[2], x[3]);
         }
+      }
+#pragma unroll
+      for (int j = 0; j < NVS; ++j) {
+        const int v = tid + 256 * j;
+        if (v >= nv) continue;
+        const int e0 = v * 4 - mis;
+        const uint32_t x[4] = {xv[j].x, xv[j].y, xv[j].z, xv[j].w};
 #pragma unroll
         for (int c = 0; c < 4; ++c)
           if (e0 + c >= 0 && e0 + c < cnt) atomicAdd(&h[dig(x[c])], 1u);

@@ -828,6 +828,70 @@ def run_rows(which, peak):
     return rows
 
 
+def _ag_sort_oracle(oracle, L, keys, idx, vals, rowoffs):
+    """SortByKey forward (per-row sort with the position as payload, then a gather)
+    and backward (the scatter by the same order), on the oracle."""
+    perm = oracle.segmented_sort_kv(keys, idx, rowoffs, L=L)[1]
+    y = oracle.gather(vals, perm, L=L)
+    return oracle.permute(y, perm, L=L)
+
+
+def oracle_rows(rows):
+    """The CPU oracle (single-threaded plain C, as it stands) timed beside each row on
+    a sample of the row's operation of about 2^20 keys: its rate in the row's unit and
+    the GPU's speed-up over it."""
+    import oracle
+    import synth
+    L = oracle.lib()
+    m = 1 << 20
+    k, v = synth.uniform_keys(m, seed=0x51), synth.index_payload(m)
+    f = synth.float_bits_payload(m, seed=0x52)
+    pi = synth.random_perm(m, seed=0x53)
+    lpi = synth.tile_local_perms(m, TILE, seed=0x54)
+    pk256 = synth.partition_keys(m, 256, seed=0x55)
+    pk32 = synth.partition_keys(65536, 32, seed=0x56)
+    spl = np.sort(k[synth.rng(9).integers(0, m, size=255 * 16)])[(np.arange(1, 256) * 255 * 16) // 256].astype(np.uint32)
+    tiles = np.arange(0, m + 1, TILE, dtype=np.int64)
+    seg_sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
+    seg_offs = synth.offsets_from_sizes(seg_sizes[:np.searchsorted(np.cumsum(seg_sizes), m) + 1])
+    sk = synth.uniform_keys(int(seg_offs[-1]), seed=0x57)
+    pkeys, poffs, pw = synth.segmented_partition_input(80, seed=0x58)
+    rowoffs = np.arange(0, m + 1, 65536, dtype=np.int64)
+    z = synth.zipf_keys(m, seed=0x59)
+    k24 = synth.uniform_keys(m, seed=0x5A, bits=24)
+    cases = {  # row prefix -> (keys the sample processes, call)
+        "partition_w32_n65536": (65536, lambda: oracle.partition_kv(pk32, v[:65536], 32, True, L=L)),
+        "permute_kv": (m, lambda: (oracle.permute(k, pi, L=L), oracle.permute(f, pi, L=L))),
+        "permute_keys": (m, lambda: oracle.permute(k, pi, L=L)),
+        "tile_permute": (m, lambda: oracle.permute_tiles(k, lpi, TILE, L=L)),
+        "sort_kv_2pow26_uniform": (m, lambda: oracle.sort_kv(k, v, L=L)),
+        "sort_kv_2pow26_zipf": (m, lambda: oracle.sort_kv(z, v, L=L)),
+        "sort_kv_2pow26_24bit": (m, lambda: oracle.sort_kv(k24, v, L=L)),
+        "partition_splitters": (m, lambda: oracle.partition_splitters(k, v, spl, L=L)),
+        "partition_w256": (m, lambda: oracle.partition_kv(pk256, v, 256, True, L=L)),
+        "tile_sort": (m, lambda: oracle.segmented_sort_kv(k, v, tiles, L=L)),
+        "segmented_sort": (sk.size, lambda: oracle.segmented_sort_kv(sk, synth.index_payload(sk.size), seg_offs, L=L)),
+        "segmented_partition": (pkeys.size, lambda: oracle.segmented_partition_kv(
+            pkeys, synth.index_payload(pkeys.size), poffs, pw, True, L=L)),
+        "autograd_sort_by_key": (m, lambda: _ag_sort_oracle(oracle, L, k >> np.uint32(12), v, f, rowoffs)),
+        "autograd_permute_rows": (m, lambda: (oracle.permute(f, pi, L=L), oracle.gather(f, pi, L=L))),
+    }
+    for name, row in rows.items():
+        key = next((c for c in cases if name.startswith(c)), None)
+        if key is None:
+            continue
+        nk, fn = cases[key]
+        t = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t
+        rate = nk / dt / 1e9
+        row["oracle_gkeys_s"] = round(rate, 4)
+        row["gpu_vs_oracle"] = round(row["gkeys_s"] / rate, 1) if rate > 0 else None
+    return {"sample_keys": m, "cores": 1, "kind": "oracle",
+            "note": "per row: the oracle's plain C on a sample of about 2^20 keys of the row's operation, "
+                    "single-threaded; oracle_gkeys_s in the row's unit, gpu_vs_oracle = gkeys_s / oracle_gkeys_s"}
+
+
 # ------------------------------------------------------------------ cases
 def _case_inputs(name):
     import torch
@@ -930,6 +994,7 @@ def main():
             which = set(filter(None, args.rows_only.split(",")))
             line["tuning"] = run_tuning()
             line["rows"] = run_rows(which, peak)
+            line["rows_oracle"] = oracle_rows(line["rows"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -116,3 +116,21 @@ def test_sort_skip_in_a_cuda_graph(bcf):
         rk, rv = oracle.sort_kv(keys, synth.index_payload(n))
         assert bits_equal(host(ko, np.uint32), rk)
         assert bits_equal(host(vo, np.uint32), rv)
+
+
+@pytest.mark.parametrize("n", [5000, 300_001])
+@pytest.mark.parametrize("kind", ["top_byte_constant", "second_byte_only", "all_equal"])
+def test_sort_skip_in_place_8_byte_payloads(bcf, n, kind):
+    """In place with 8-byte payloads: 3 or 1 passes run (odd), so the result is
+    copied home from the temporary, payload words included; with none, nothing
+    moves."""
+    keys = _keys(n, kind, seed=n + 3)
+    vals = synth.uniform_keys(2 * n, seed=n + 4).view(np.uint64)
+    kd, vd = dev(keys), dev(vals)
+    ws = bcf.workspace(bcf.sort_workspace_size(n, 8, 32))
+    ko, vo = bcf.sort(kd, vd, keys_out=kd, vals_out=vd, ws=ws)
+    assert bcf.get_status() == bcf.OK
+    assert bcf.sort_passes_run(ws, n, 8, 32) == _expected_passes(kind, True)
+    rk, rv = oracle.sort_kv(keys, vals)
+    assert bits_equal(host(ko, np.uint32), rk)
+    assert bits_equal(host(vo, np.uint64), rv)

@@ -930,11 +930,20 @@ def _case_inputs(name):
         k, v = to_dev(synth.uniform_keys(n, seed=7)), to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         return lambda: bcf.sort_tiles(k, v, keys_out=ko, vals_out=vo)
+    if name == "segmented_sort":  # the batched workload: 10,000 log-uniform segments
+        sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
+        offs_np = synth.offsets_from_sizes(sizes)
+        m = int(offs_np[-1])
+        offs = torch.from_numpy(offs_np).cuda()
+        k, v = to_dev(synth.uniform_keys(m, seed=0x4B)), to_dev(synth.index_payload(m))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.segmented_sort_workspace_size(m, 10_000, 4, 32))
+        return lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws)
     raise ValueError(name)
 
 
 CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256",
-         "tile_sort")
+         "tile_sort", "segmented_sort")
 
 
 def run_case(args):

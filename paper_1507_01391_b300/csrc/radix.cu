@@ -240,24 +240,16 @@ static cudaError_t small_histogram(const uint32_t* keys, int64_t n, int passes, 
   return cudaGetLastError();
 }
 
-// Brings a sorted result home when the passes that ran left it elsewhere: in the
-// temporary (in place, an odd number of runs), or still in the input (no pass ran,
-// out of place).  With no pass run and positions as the payload, writes them.
+// In-place sorts only.  An odd number of passes that ran leaves the result in the
+// temporary: copy it home.  With no pass run the keys are already in place, and
+// only a position payload (no payload input) remains to be written.
 __global__ void __launch_bounds__(256) k_pass_copy(PassSel sel, int64_t n, int vb) {
   const int k = __popc(passes_run_mask(sel, vary_bits(sel)));
-  const uint32_t* sk = nullptr;
-  const unsigned char* sv = nullptr;
-  bool iota = false;
-  if (k == 0) {
-    sk = sel.k_in == sel.k_out ? nullptr : sel.k_in;
-    iota = vb == 4 && sel.v_in == nullptr;
-    sv = sel.v_in == sel.v_out ? nullptr : static_cast<const unsigned char*>(sel.v_in);
-  } else if (sel.in_place && (k & 1)) {
-    sk = sel.k_tmp;
-    sv = static_cast<const unsigned char*>(sel.v_tmp);
-  } else {
-    return;
-  }
+  const bool from_tmp = (k & 1) != 0;
+  const bool iota = k == 0 && vb == 4 && sel.v_in == nullptr;
+  if (!from_tmp && !iota) return;
+  const uint32_t* sk = from_tmp ? sel.k_tmp : nullptr;
+  const unsigned char* sv = from_tmp ? static_cast<const unsigned char*>(sel.v_tmp) : nullptr;
   unsigned char* dv = static_cast<unsigned char*>(sel.v_out);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t n4 = n / 4;  // groups of four elements: 16-byte keys, 16 or 32 bytes of payload

@@ -664,6 +664,22 @@ def run_rows(which, peak):
                 ms, _ = ev_ms(lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=coloured, dst=ko, finish=finish))
                 add(name, n, 10 * n, ms)
         del k, v, pi, ko, vo, lpi
+    if want("permute_kv_2pow26") or want("permute_kv_scatter_2pow26"):
+        # the same key-value permutation at 2^26 keys: 2^26 / 8192 tiles against 1332
+        # destination blocks leaves pass 1 runs of about 6 elements
+        n = 1 << 26
+        k, v, pi = to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.float_bits_payload(n, seed=2)), \
+            to_dev(synth.random_perm(n, seed=3))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        pws = bcf.workspace(bcf.permute_workspace_size(n, 4, bcf.PERMUTE_BUCKETED))
+        if want("permute_kv_2pow26"):
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=pws))
+            add("permute_kv_2pow26", n, 20 * n, ms, "bucketed: two coalesced passes; model charges the one-pass "
+                "20 B/key")
+        if want("permute_kv_scatter_2pow26"):
+            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False))
+            add("permute_kv_scatter_2pow26", n, 20 * n, ms, "scatter: keys pass + payload pass")
+        del k, v, pi, ko, vo, pws
     for kind in ("uniform", "zipf", "24bit"):
         name = "sort_kv_2pow26_%s" % kind
         if not want(name):
@@ -861,7 +877,7 @@ def oracle_rows(rows):
     k24 = synth.uniform_keys(m, seed=0x5A, bits=24)
     cases = {  # row prefix -> (keys the sample processes, call)
         "partition_w32_n65536": (65536, lambda: oracle.partition_kv(pk32, v[:65536], 32, True, L=L)),
-        "permute_kv": (m, lambda: (oracle.permute(k, pi, L=L), oracle.permute(f, pi, L=L))),
+        "permute_kv": (m, lambda: (oracle.permute(k, pi, L=L), oracle.permute(f, pi, L=L))),  # any size
         "permute_keys": (m, lambda: oracle.permute(k, pi, L=L)),
         "tile_permute": (m, lambda: oracle.permute_tiles(k, lpi, TILE, L=L)),
         "sort_kv_2pow26_uniform": (m, lambda: oracle.sort_kv(k, v, L=L)),

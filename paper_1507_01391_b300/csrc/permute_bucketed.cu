@@ -42,6 +42,9 @@ constexpr int kPbMaxBlocks = 2048;
 constexpr int64_t kPbMaxN = (int64_t)1 << 26;
 constexpr int kPlaceThreads = 1024;
 constexpr int kBulkChunk = 1 << 16;  // bytes per bulk store of the pass-2 write-out
+#ifndef BCF_PB_UNROLL
+#define BCF_PB_UNROLL 2
+#endif
 #ifndef BCF_PB_EVICT_FIRST
 #define BCF_PB_EVICT_FIRST 1
 #endif
@@ -238,7 +241,7 @@ __global__ void __launch_bounds__(kPbThreads, 1)
     // stores of one run are contiguous.  Only the `total` elements that passed the
     // range check were reordered; entries past them are stale.
     const int tot = (int)total;
-    constexpr int U = 4;  // loads of U elements first, then their stores
+    constexpr int U = BCF_PB_UNROLL;  // loads of U elements first, then their stores
     for (int i0 = tid; i0 < tot; i0 += U * kPbThreads) {
       uint32_t pb[U], g[U];
       unsigned long long kv[U];

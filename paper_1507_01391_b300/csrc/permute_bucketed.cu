@@ -45,6 +45,10 @@ constexpr int kBulkChunk = 1 << 16;  // bytes per bulk store of the pass-2 write
 #ifndef BCF_PB_UNROLL
 #define BCF_PB_UNROLL 2
 #endif
+#ifndef BCF_PB_GROUPS
+#define BCF_PB_GROUPS 1
+#endif
+constexpr int kPlaceGroups = BCF_PB_GROUPS;  // pass 2: groups of 8 elements in flight per thread
 #ifndef BCF_PB_EVICT_FIRST
 #define BCF_PB_EVICT_FIRST 1
 #endif
@@ -293,23 +297,23 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
   };
   const int nv = cap / 8;
   const int mv = cap / 4;
-  // Two groups of 8 per thread per step, every load issued before any store.
-  uint4 p[2], a[2], b[2];
+  // kPlaceGroups groups of 8 per thread per step, every load issued before any store.
+  constexpr int G = kPlaceGroups;
+  uint4 p[G], a[G], b[G];
   auto load = [&](const uint32_t* X, int t) {
-    const bool two = t + kPlaceThreads < nv;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t i = lo + (int64_t)(h && two ? t + kPlaceThreads : t) * 8;
+    for (int h = 0; h < G; ++h) {
+      const int th = t + h * kPlaceThreads;
+      const int64_t i = lo + (int64_t)(th < nv ? th : t) * 8;
       p[h] = __ldcs(reinterpret_cast<const uint4*>(P1 + i));
       a[h] = __ldcs(reinterpret_cast<const uint4*>(X + i));
       b[h] = __ldcs(reinterpret_cast<const uint4*>(X + i + 4));
     }
   };
   auto place = [&](int t, bool marking) {
-    const bool two = t + kPlaceThreads < nv;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      if (h && !two) break;
+    for (int h = 0; h < G; ++h) {
+      if (t + h * kPlaceThreads >= nv) break;
       const uint32_t o[8] = {min(p[h].x & 0xFFFFu, top), min(p[h].x >> 16, top),
                              min(p[h].y & 0xFFFFu, top), min(p[h].y >> 16, top),
                              min(p[h].z & 0xFFFFu, top), min(p[h].z >> 16, top),
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
     }
     while (t < nv) {
       place(t, round == 0);
-      t += 2 * kPlaceThreads;
+      t += G * kPlaceThreads;
       if (t < nv) load(X, t);
     }
     for (int i = nv * 8 + tid; i < cap; i += kPlaceThreads) {

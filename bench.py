@@ -199,7 +199,7 @@ class NvmlSampler:
     # clock-event reason bits of NVML's public API
     REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
                ("sw_power_cap", 0x4))
-    NVML_CLOCK_SM = 1
+    NVML_CLOCK_SM, NVML_CLOCK_MEM = 1, 2
 
     def __init__(self, gpu_index, period_ms=1):
         self.gpu = gpu_index
@@ -225,7 +225,7 @@ class NvmlSampler:
                 raise RuntimeError("no NVML handle for GPU %d" % self.gpu)
         reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
             lib.nvmlDeviceGetCurrentClocksThrottleReasons
-        clk, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        clk, mem, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
         if lib.nvmlDeviceGetMaxClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(mx)) != 0:
             raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
         self.max_mhz = mx.value
@@ -233,9 +233,11 @@ class NvmlSampler:
         def read():
             if lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_SM, ctypes.byref(clk)) != 0:
                 return None
+            if lib.nvmlDeviceGetClockInfo(h, self.NVML_CLOCK_MEM, ctypes.byref(mem)) != 0:
+                mem.value = 0
             if reasons(h, ctypes.byref(rs)) != 0:
                 return None
-            return clk.value, rs.value
+            return clk.value, rs.value, mem.value
         return read
 
     def start(self):
@@ -250,7 +252,7 @@ class NvmlSampler:
                 while not self.stop_flag:
                     r = read()
                     if r is not None:
-                        self.rows.append((time.time(), r[0], r[1]))
+                        self.rows.append((time.time(), r[0], r[1], r[2]))
                     time.sleep(self.period / 1000.0)
             self.thread = threading.Thread(target=poll, daemon=True)
             self.thread.start()
@@ -286,8 +288,9 @@ class NvmlSampler:
             inside = after[:1] or rows[-1:]
         if not inside:
             return None
-        reasons = sorted({name for _, _, mask in inside for name, bit in self.REASONS if mask & bit})
+        reasons = sorted({name for _, _, mask, _ in inside for name, bit in self.REASONS if mask & bit})
         return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": self.max_mhz,
+                "mem_mhz": statistics.median(r[3] for r in inside),
                 "reasons": reasons, "samples": len(inside), "period_ms": self.period, "source": "nvml"}
 
 
@@ -376,14 +379,25 @@ def run_headline(args, rank, world, local):
         step()
     torch.cuda.synchronize()
     # An idle GPU takes tens of milliseconds to raise its clocks: keep stepping
-    # (untimed) until 250 ms have passed, so that short timed runs see steady clocks.
+    # (untimed) for at least 250 ms and until two consecutive batches of 10 steps
+    # take the same time within 2% (at most 3 s), so that the short timed run sees
+    # the GPU in its steady state.
     t_settle = time.perf_counter()
     settle_steps = 0
-    while time.perf_counter() - t_settle < 0.25:
+    prev = None
+    while True:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
         for _ in range(10):
             step()
+        b.record()
+        b.synchronize()
         settle_steps += 10
-        torch.cuda.synchronize()
+        cur = a.elapsed_time(b)
+        elapsed = time.perf_counter() - t_settle
+        if (elapsed >= 0.25 and prev is not None and abs(cur - prev) <= 0.02 * prev) or elapsed >= 3.0:
+            break
+        prev = cur
     if world > 1:
         torch.distributed.barrier()
     kevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

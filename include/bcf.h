@@ -45,7 +45,7 @@ typedef struct CUstream_st* bcf_stream_t;
 #define BCF_OK 0
 #define BCF_E_INVAL 1          /* bad argument: null pointer, size, alignment, width */
 #define BCF_E_WORKSPACE 2      /* workspace smaller than *_workspace_size() */
-#define BCF_E_UNSUPPORTED 3    /* valid request outside what this build handles */
+#define BCF_E_UNSUPPORTED 3    /* valid request outside what the library handles */
 #define BCF_E_CUDA 4           /* a CUDA launch or copy failed */
 #define BCF_E_TIMEOUT 5        /* device: a bounded inter-block wait gave up */
 #define BCF_E_NOT_BALANCED 6   /* device: balanced partition saw a count != n/w */

@@ -82,7 +82,7 @@ const char* bcf_status_string(int status) {
     case BCF_OK: return "ok";
     case BCF_E_INVAL: return "invalid argument (null pointer, size, width, alignment or overlap)";
     case BCF_E_WORKSPACE: return "workspace smaller than the *_workspace_size() result";
-    case BCF_E_UNSUPPORTED: return "request outside what this build supports";
+    case BCF_E_UNSUPPORTED: return "request outside what the library supports";
     case BCF_E_CUDA: return "a CUDA launch or copy failed";
     case BCF_E_TIMEOUT: return "a bounded inter-block wait gave up on the device";
     case BCF_E_NOT_BALANCED: return "balanced partition: a label count differs from n/w";

@@ -62,3 +62,42 @@ def test_reference_arm_prints_on_rank_zero_only(monkeypatch, capsys):
     args = bench.parse()
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_has_the_contract_keys(monkeypatch, capsys):
+    """Rank 0 of the reference arm prints one JSON line with the bench contract's
+    keys, its CPU baseline and an end-to-end block that moves no bytes."""
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"])
+    args = bench.parse()
+    assert bench.run_reference(args) == 0
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and "workload" in line["config"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_every_bench_row_has_an_oracle_case():
+    """Each row the bench can report finds its oracle sample (a renamed row would
+    otherwise lose the timing beside it)."""
+    names = ["partition_w32_n65536", "partition_w32_n65536_eager", "partition_w32_n65536_lemma1",
+             "partition_w32_n65536_unbalanced", "permute_kv_2pow24", "permute_kv_scatter_2pow24",
+             "permute_kv_fused_2pow24", "permute_keys_2pow24", "permute_keys_scatter_2pow24",
+             "tile_permute_scatter_2pow24", "tile_permute_coloured_2pow24",
+             "tile_permute_coloured_sorted_finish_2pow24", "permute_kv_2pow26", "permute_kv_scatter_2pow26",
+             "sort_kv_2pow26_uniform", "sort_kv_2pow26_zipf", "sort_kv_2pow26_24bit",
+             "partition_splitters_255_2pow26", "partition_w256_2pow26", "partition_w256_2pow26_lemma1",
+             "tile_sort_lemma1_2pow24", "segmented_sort_batched_10k", "segmented_partition_batched_10k",
+             "autograd_sort_by_key_64x65536", "autograd_permute_rows_64x65536"]
+    rows = {n: {"gkeys_s": 1.0} for n in names}
+    info = bench.oracle_rows(rows)
+    assert info["kind"] == "oracle"
+    for n in names:
+        assert rows[n]["oracle_gkeys_s"] > 0 and rows[n]["gpu_vs_oracle"] > 0, n

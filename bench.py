@@ -333,6 +333,18 @@ def graph_ms(fn, warmup=3, iters=10, inner=1):
     return ms / inner, [t / inner for t in ts]
 
 
+def rotating(fns):
+    """A call that cycles through `fns`: a captured run of inner calls then reads a
+    different input set each call, so that inputs smaller than L2 do not stay
+    resident from one call to the next."""
+    state = [0]
+
+    def call():
+        fns[state[0] % len(fns)]()
+        state[0] += 1
+    return call
+
+
 def ev_ms(fn, warmup=3, iters=10):
     """Median CUDA-event time of fn() on the current stream, in ms."""
     import torch
@@ -667,28 +679,41 @@ def run_rows(which, peak):
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         pws = bcf.workspace(bcf.permute_workspace_size(n, 4, bcf.PERMUTE_BUCKETED))
         if want("permute_kv_2pow24"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=pws))
+            ms, _ = graph_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=pws), 3, 10, inner=10)
             add("permute_kv_2pow24", n, 20 * n, ms, "bucketed: two coalesced passes (chosen form); model "
                 "charges the one-pass 20 B/key, the passes move about 42 B/key")
         if want("permute_kv_scatter_2pow24"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False))
+            ms, _ = graph_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False), 3, 10, inner=10)
             add("permute_kv_scatter_2pow24", n, 20 * n, ms, "scatter: keys pass + payload pass")
         if want("permute_kv_fused_2pow24"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, fused=True, bucketed=False))
+            ms, _ = graph_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, fused=True, bucketed=False), 3, 10, inner=10)
             add("permute_kv_fused_2pow24", n, 20 * n, ms, "scatter: one fused pass (plain form)")
+        # keys (64 MB), pi (64 MB) and the output (64 MB) about fill L2: two sets of
+        # inputs and outputs, rotated
+        k2, pi2 = to_dev(synth.uniform_keys(n, seed=11)), to_dev(synth.random_perm(n, seed=13))
+        ko2 = torch.empty_like(k)
         if want("permute_keys_2pow24"):
-            ms, _ = ev_ms(lambda: bcf.permute(k, pi, dst=ko, bucketed=True, ws=pws))
-            add("permute_keys_2pow24", n, 12 * n, ms, "keys only, bucketed")
-            ms, _ = ev_ms(lambda: bcf.permute(k, pi, dst=ko, bucketed=False))
-            add("permute_keys_scatter_2pow24", n, 12 * n, ms, "keys only, one scatter pass")
-        lpi = to_dev(synth.tile_local_perms(n, TILE, seed=4))
+            ms, _ = graph_ms(rotating([lambda: bcf.permute(k, pi, dst=ko, bucketed=True, ws=pws),
+                                       lambda: bcf.permute(k2, pi2, dst=ko2, bucketed=True, ws=pws)]), 3, 10, inner=10)
+            add("permute_keys_2pow24", n, 12 * n, ms, "keys only, bucketed; two input/output sets rotated")
+            ms, _ = graph_ms(rotating([lambda: bcf.permute(k, pi, dst=ko, bucketed=False),
+                                       lambda: bcf.permute(k2, pi2, dst=ko2, bucketed=False)]), 3, 10, inner=10)
+            add("permute_keys_scatter_2pow24", n, 12 * n, ms,
+                "keys only, one scatter pass; two input/output sets rotated")
+        # keys (64 MB), tile labels (32 MB) and the output (64 MB) fit in L2 together:
+        # three sets of inputs and outputs, rotated
+        lpis = [to_dev(synth.tile_local_perms(n, TILE, seed=4 + i)) for i in range(3)]
+        ks = [k, k2, to_dev(synth.uniform_keys(n, seed=21))]
+        kos = [ko, ko2, torch.empty_like(k)]
         for coloured, finish in ((False, "greedy"), (True, "greedy"), (True, "sorted")):
             name = "tile_permute_%s_2pow24" % ("scatter" if not coloured else
                                                "coloured" if finish == "greedy" else "coloured_sorted_finish")
             if want(name):
-                ms, _ = ev_ms(lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=coloured, dst=ko, finish=finish))
-                add(name, n, 10 * n, ms)
-        del k, v, pi, ko, vo, lpi
+                calls = [(lambda kk=kk, ll=ll, oo=oo: bcf.permute_tiles(kk, ll, tile=TILE, coloured=coloured, dst=oo,
+                                                                        finish=finish)) for kk, ll, oo in zip(ks, lpis, kos)]
+                ms, _ = graph_ms(rotating(calls), 3, 10, inner=9)
+                add(name, n, 10 * n, ms, "three input/output sets rotated (each 160 MB)")
+        del k, v, pi, ko, vo, lpis, ks, kos, k2, pi2, ko2
     if want("permute_kv_2pow26") or want("permute_kv_scatter_2pow26"):
         # the same key-value permutation at 2^26 keys: 2^26 / 8192 tiles against 1332
         # destination blocks leaves pass 1 runs of about 6 elements
@@ -698,11 +723,11 @@ def run_rows(which, peak):
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         pws = bcf.workspace(bcf.permute_workspace_size(n, 4, bcf.PERMUTE_BUCKETED))
         if want("permute_kv_2pow26"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=pws))
+            ms, _ = graph_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=True, ws=pws), 3, 10, inner=2)
             add("permute_kv_2pow26", n, 20 * n, ms, "bucketed: two coalesced passes; model charges the one-pass "
                 "20 B/key")
         if want("permute_kv_scatter_2pow26"):
-            ms, _ = ev_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False))
+            ms, _ = graph_ms(lambda: bcf.permute_kv(k, v, pi, keys_out=ko, vals_out=vo, bucketed=False), 3, 10, inner=2)
             add("permute_kv_scatter_2pow26", n, 20 * n, ms, "scatter: keys pass + payload pass")
         del k, v, pi, ko, vo, pws
     for kind in ("uniform", "zipf", "24bit"):
@@ -720,7 +745,7 @@ def run_rows(which, peak):
         v = to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
-        ms, _ = ev_ms(lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+        ms, _ = graph_ms(lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws), 3, 10, inner=2)
         runs = bcf.sort_passes_run(ws, n, 4, 32)
         add(name, n, (4 + runs * 16) * n, ms, "%d of 4 passes of 8 bits run (a pass whose digit is the same in "
             "every key is skipped); per pass: tile counts (4 B/key) + sweep (16 B/key); model charges "
@@ -737,7 +762,7 @@ def run_rows(which, peak):
         k, v, sd = to_dev(keys), to_dev(synth.index_payload(n)), to_dev(spl)
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.partition_splitters_workspace_size(n, 255, 4))
-        ms, _ = ev_ms(lambda: bcf.partition_splitters(k, v, sd, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+        ms, _ = graph_ms(lambda: bcf.partition_splitters(k, v, sd, keys_out=ko, vals_out=vo, ws=ws), 3, 10, inner=2)
         add("partition_splitters_255_2pow26", n, 16 * n, ms, "sample-sort bucketing: 256 buckets from 255 "
             "sampled splitters (binary search per key in shared memory); tile counts (4 B/key) + sweep (16 B/key), "
             "model charges 16 B/key")
@@ -748,10 +773,10 @@ def run_rows(which, peak):
         v = to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED))
-        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+        ms, _ = graph_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws), 3, 10, inner=2)
         add("partition_w256_2pow26", n, 16 * n, ms)
         wsl = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.ASSUME_BALANCED | bcf.PARTITION_LEMMA1))
-        ms, _ = ev_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
+        ms, _ = graph_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
                                             flags=bcf.PARTITION_LEMMA1), 2, 5)
         add("partition_w256_2pow26_lemma1", n, 16 * n, ms, "Lemma 1 tile schedule (conflict-free), plain form")
         del wsl
@@ -761,9 +786,13 @@ def run_rows(which, peak):
         k = to_dev(synth.uniform_keys(n, seed=7))
         v = to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
-        ms, _ = ev_ms(lambda: bcf.sort_tiles(k, v, keys_out=ko, vals_out=vo))
+        k2, ko2, vo2 = to_dev(synth.uniform_keys(n, seed=8)), torch.empty_like(k), torch.empty_like(v)
+        ms, _ = graph_ms(rotating([lambda: bcf.sort_tiles(k, v, keys_out=ko, vals_out=vo),
+                                   lambda: bcf.sort_tiles(k2, v, keys_out=ko2, vals_out=vo2)]), 3, 10, inner=4)
         add("tile_sort_lemma1_2pow24", n, 16 * n, ms,
-            "4096-key tiles, Lemma 1 comparison sort (ALU bound); bytes: key r/w + payload gather r/w")
+            "4096-key tiles, Lemma 1 comparison sort (ALU bound); bytes: key r/w + payload gather r/w; "
+            "two input/output sets rotated")
+        del k2, ko2, vo2
         del k, v, ko, vo
     if want("segmented_sort_batched_10k") or want("segmented_partition_batched_10k"):
         sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
@@ -829,7 +858,8 @@ def run_rows(which, peak):
             add("autograd_sort_by_key_64x65536", B * n, B * n * (3 * 16 + 12 + 12), ms,
                 "forward (per-row sort with index payload + gather) and backward scatter, one CUDA-graph "
                 "replay (eager %.3f ms); forward alone %.4f ms vs the plain per-row kv sort %.4f ms; "
-                "plain flat kv sort of all keys %.4f ms" % (ms_eager, ms_fwd, ms_rows, ms_plain))
+                "plain flat kv sort of all keys %.4f ms; the 2^22-key working set stays in L2, so the HBM "
+                "fraction is nominal" % (ms_eager, ms_fwd, ms_rows, ms_plain))
             r = rows["autograd_sort_by_key_64x65536"]
             r.update({"fwd_ms": round(ms_fwd, 4), "plain_rows_sort_ms": round(ms_rows, 4),
                       "ratio_fwd_vs_plain_rows_sort": round(ms_fwd / ms_rows, 3),
@@ -856,8 +886,8 @@ def run_rows(which, peak):
             ms_plain_fb, _ = graph_ms(plain_fb, 3, 10)
             add("autograd_permute_rows_64x65536", B * n, B * n * 24, ms,
                 "forward scatter (12 B/key) + backward gather (12 B/key), one CUDA-graph replay (eager "
-                "%.3f ms); plain permutation %.4f ms, plain permutation + gather %.4f ms"
-                % (ms_eager, ms_plain, ms_plain_fb))
+                "%.3f ms); plain permutation %.4f ms, plain permutation + gather %.4f ms; the 2^22-key "
+                "working set stays in L2, so the HBM fraction is nominal" % (ms_eager, ms_plain, ms_plain_fb))
             rows["autograd_permute_rows_64x65536"].update(
                 {"plain_fwd_ms": round(ms_plain, 4), "plain_fwdbwd_ms": round(ms_plain_fb, 4),
                  "ratio_vs_plain_fwdbwd": round(ms / ms_plain_fb, 3), "eager_ms": round(ms_eager, 4)})

@@ -47,7 +47,7 @@ FALLBACK_HBM_GBS = 6400.0
 # it was taken on: if permute.cu changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "k_pb_bucket<4,512> + k_pb_place<4,0> (bucketed kv permute, both passes)",
                "source": "permute_bucketed.cu", "source_sha1": "9b9b6694d7c8c746e21acc7d0fb7dae6de12650c",
-               "bytes": 575105280,
+               "bytes": 575275264,
                "summary": "profiles/k_pb_bucketed_permute_kv_2pow24.md"}
 
 

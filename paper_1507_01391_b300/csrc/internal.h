@@ -13,6 +13,19 @@ namespace bcf {
 // Device status word of the current device (a module variable in abi.cu).
 unsigned* status_word();
 
+// Raise a kernel's dynamic shared-memory limit once per device; `done` is the
+// caller's per-kernel flag array (one static array per kernel instance).
+template <typename K>
+inline cudaError_t set_smem_once(K kernel, int bytes, bool (&done)[64]) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (done[dev]) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[dev] = true;
+  return e;
+}
+
 constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
 

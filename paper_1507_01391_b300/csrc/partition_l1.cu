@@ -103,13 +103,13 @@ cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint3
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   switch (vb) {
 #define BCF_PL1(VB)                                                                                  \
-  case VB:                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_partition_l1<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                  (int)kL1SmemBytes)) != cudaSuccess)                                \
-      return e;                                                                                      \
+  case VB: {                                                                                         \
+    static bool ready[64] = {};                                                                      \
+    if ((e = set_smem_once(k_partition_l1<VB>, (int)kL1SmemBytes, ready)) != cudaSuccess) return e;  \
     k_partition_l1<VB><<<(unsigned)tiles, kL1Threads, kL1SmemBytes, s>>>(                            \
         src_k, src_v, keys_out, vals_out, n, w, offsets, stride, status_word());                     \
-    break;
+    break;                                                                                           \
+  }
     BCF_PL1(0)
     BCF_PL1(4)
     BCF_PL1(8)

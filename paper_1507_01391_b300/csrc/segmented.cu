@@ -326,7 +326,8 @@ static cudaError_t small_sort(const uint32_t* ki, const void* vi, uint32_t* ko, 
                               const int64_t* offs, const int32_t* ids, const int32_t* tiny_ids,
                               const uint32_t* bin_first, uint32_t* ctr, int64_t nseg, cudaStream_t s) {
   auto k = k_seg_small<VB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmallSmem);
+  static bool ready[64] = {};
+  cudaError_t e = set_smem_once(k, (int)kSegSmallSmem, ready);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(nseg, (int64_t)sms() * 3);
   if (grid <= 0) return cudaSuccess;
@@ -477,13 +478,14 @@ cudaError_t sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* k
   cudaError_t e = cudaSuccess;
   switch (vb) {
 #define BCF_TS(VB)                                                                                 \
-  case VB:                                                                                         \
-    e = cudaFuncSetAttribute(k_sort_tiles<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                             (int)kL1SmemBytes);                                                   \
+  case VB: {                                                                                       \
+    static bool ready[64] = {};                                                                    \
+    e = set_smem_once(k_sort_tiles<VB>, (int)kL1SmemBytes, ready);                                 \
     if (e != cudaSuccess) return e;                                                                \
     k_sort_tiles<VB><<<(unsigned)tiles, kL1Threads, kL1SmemBytes, s>>>(keys_in, vals_in, keys_out, \
                                                                        vals_out, n);               \
-    break;
+    break;                                                                                         \
+  }
     BCF_TS(0)
     BCF_TS(4)
     BCF_TS(8)

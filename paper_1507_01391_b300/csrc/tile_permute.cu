@@ -436,15 +436,9 @@ static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16
   if (coloured) {
     auto k = k_tile_coloured<T>;
     const int bytes = (int)(sorted ? S::bytes_sorted : S::bytes_coloured);
-    static bool ready[64] = {};  // per device: the shared-memory limit is raised once
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (!ready[dev]) {
-      const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes_sorted);
-      if (e != cudaSuccess) return e;
-      ready[dev] = true;
-    }
+    static bool ready[64] = {};
+    const cudaError_t e = set_smem_once(k, (int)S::bytes_sorted, ready);
+    if (e != cudaSuccess) return e;
     k<<<(unsigned)tiles, kTPThreads, bytes, s>>>(src, dst, lpi, n, seed, 3, sorted ? 1 : 0, status_word());
   } else {
     using SS = TSSmem<T>;

@@ -3,8 +3,8 @@
 Plain, slow and obviously correct definitions of what the bank-conflict-free
 library computes (Afshani & Sitchinava, "Sorting and Permuting without Bank
 Conflicts on GPUs"): stable sort, stable counting partition, permutation scatter,
-tile-local permutation and gather, their segmented forms, a model of the Lemma 1
-schedule (Sec. 2) and of the bank model (Sec. 1, "Model of Computation").
+tile-local permutation and gather, their segmented forms, models of the Lemma 1
+schedule and of Lemma 2's 0-1 partition (Sec. 2) and of the bank model (Sec. 1, "Model of Computation").
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs may import
 this package.  It is written in plain C (``bcf_oracle.c``) and shares no code with
@@ -66,6 +66,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "oracle_l1_row_to_col": [P, I64, I64],
         "oracle_l1_col_to_row": [P, I64, I64],
         "oracle_lemma1_sort": [P, I64, I64],
+        "oracle_lemma2_partition": [P, P, I64, I64, I],
+        "oracle_l2_sort_colmajor": [P, P, I64, P, I64],
+        "oracle_l2_sort_rowmajor": [P, P, I64, I64, I64],
         "oracle_race_check": [P, I64, P, P],
         "oracle_bank_count": [P, P, P, P, I64, P, P, P],
     }
@@ -214,6 +217,30 @@ def l1_row_to_col(M, L=None):
 def l1_col_to_row(M, L=None):
     L = L or lib()
     L.oracle_l1_col_to_row(_ptr(M), M.shape[0], M.shape[1])
+
+
+def lemma2_partition(lab, pay, stage=4, L=None):
+    """Lemma 2's 0-1 partition of a w x m matrix (labels and payloads as (w, m)
+    arrays); returns new (labels, payloads) after the given stage (4: all)."""
+    L = L or lib()
+    lab = np.array(lab, dtype=np.uint32, order="C", copy=True)
+    pay = np.array(pay, dtype=np.uint32, order="C", copy=True)
+    assert lab.shape == pay.shape and lab.ndim == 2
+    _check(L.oracle_lemma2_partition(_ptr(lab), _ptr(pay), lab.shape[0], lab.shape[1], stage))
+    return lab, pay
+
+
+def l2_sort_colmajor(lab, pay, rows, L=None):
+    """One step of Lemma 2: the rows listed, as a matrix, sorted in column-major order (in place)."""
+    L = L or lib()
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    _check(L.oracle_l2_sort_colmajor(_ptr(lab), _ptr(pay), lab.shape[1], _ptr(rows), rows.size))
+
+
+def l2_sort_rowmajor(lab, pay, r0, h, L=None):
+    """One step of Lemma 2: rows [r0, r0 + h) sorted in row-major order (in place)."""
+    L = L or lib()
+    _check(L.oracle_l2_sort_rowmajor(_ptr(lab), _ptr(pay), lab.shape[1], r0, h))
 
 
 def lemma1_sort(M, L=None):

@@ -6,7 +6,8 @@
  * Every algorithm the paper gives reaches the exact sorted / partitioned /
  * permuted result (correctness of Lemma 1, Theorem 1 and the randomized
  * permutation of Sec. 3), so each oracle function is the plain definition written
- * out.  Only the Lemma 1 model and the bank model follow the paper's steps.
+ * out.  Only the Lemma 1 and Lemma 2 models and the bank model follow the paper's
+ * steps (Lemma 2's 0-1 partition leaves the order of equal labels to its steps).
  *
  * No blocking, no fusion, no library sort: insertion sort and a bottom-up merge
  * sort, a counting partition, and a direct out[pi[i]] = in[i] loop.  Shares no
@@ -355,6 +356,135 @@ int oracle_lemma1_sort(uint32_t* M, int64_t w, int64_t m) {
     }
     oracle_l1_sort_rows(M, w, m, 0);
     return ORACLE_OK;
+}
+
+/* ---- Lemma 2 model (Sec. 2): 0-1 partition of a w x m matrix, w = m or m^2 ----
+ *
+ * lab holds the 0/1 labels and pay the payloads of the w x m matrix, rows stored
+ * one after another (cell r*m + c).  Every "sort" of the proof is a 0-1 sort of
+ * a sequence of cells; the proof does not say which of the equal items goes
+ * where, so each one here is stable: the 0-items fill the first cells of the
+ * sequence in the order they were met, then the 1-items. */
+
+/* Stable 0-1 partition of the items in cells cell[0..s), taken in that order. */
+static int l2_partition_cells(uint32_t* lab, uint32_t* pay, const int64_t* cell, int64_t s) {
+    uint32_t* tl = (uint32_t*)malloc((size_t)s * sizeof(uint32_t));
+    uint32_t* tp = (uint32_t*)malloc((size_t)s * sizeof(uint32_t));
+    if (!tl || !tp) {
+        free(tl);
+        free(tp);
+        return ORACLE_E_NOMEM;
+    }
+    int64_t o = 0;
+    for (int label = 0; label <= 1; ++label)
+        for (int64_t i = 0; i < s; ++i)
+            if (lab[cell[i]] == (uint32_t)label) {
+                tl[o] = lab[cell[i]];
+                tp[o] = pay[cell[i]];
+                ++o;
+            }
+    for (int64_t i = 0; i < s; ++i) {
+        lab[cell[i]] = tl[i];
+        pay[cell[i]] = tp[i];
+    }
+    free(tl);
+    free(tp);
+    return ORACLE_OK;
+}
+
+/* Sort the matrix made of rows rows[0..h) (all m columns) in column-major order:
+ * its column 0 top to bottom, then column 1, and so on. */
+int oracle_l2_sort_colmajor(uint32_t* lab, uint32_t* pay, int64_t m, const int64_t* rows, int64_t h) {
+    int64_t* cell = (int64_t*)malloc((size_t)(h * m) * sizeof(int64_t));
+    if (!cell) return ORACLE_E_NOMEM;
+    for (int64_t c = 0; c < m; ++c)
+        for (int64_t j = 0; j < h; ++j) cell[c * h + j] = rows[j] * m + c;
+    int rc = l2_partition_cells(lab, pay, cell, h * m);
+    free(cell);
+    return rc;
+}
+
+/* Sort the contiguous rows [r0, r0 + h) in row-major order. */
+int oracle_l2_sort_rowmajor(uint32_t* lab, uint32_t* pay, int64_t m, int64_t r0, int64_t h) {
+    int64_t* cell = (int64_t*)malloc((size_t)(h * m) * sizeof(int64_t));
+    if (!cell) return ORACLE_E_NOMEM;
+    for (int64_t i = 0; i < h * m; ++i) cell[i] = r0 * m + i;
+    int rc = l2_partition_cells(lab, pay, cell, h * m);
+    free(cell);
+    return rc;
+}
+
+/* Balancing on w = m^k rows: round i works on sub-matrices of m^i contiguous
+ * rows, m of them to a group; square j of a group takes row j of each of the
+ * group's sub-matrices, and every square is sorted in column-major order.  Round
+ * 0 (sub-matrices of one row) therefore sorts squares of m contiguous rows. */
+static int l2_balance(uint32_t* lab, uint32_t* pay, int64_t w, int64_t m) {
+    int64_t* rows = (int64_t*)malloc((size_t)m * sizeof(int64_t));
+    if (!rows) return ORACLE_E_NOMEM;
+    int rc = ORACLE_OK;
+    for (int64_t sub = 1; sub < w && rc == ORACLE_OK; sub *= m) {
+        int64_t group = sub * m;
+        for (int64_t g = 0; g < w / group && rc == ORACLE_OK; ++g)
+            for (int64_t j = 0; j < sub && rc == ORACLE_OK; ++j) {
+                for (int64_t t = 0; t < m; ++t) rows[t] = g * group + t * sub + j;
+                rc = oracle_l2_sort_colmajor(lab, pay, m, rows, m);
+            }
+    }
+    free(rows);
+    return rc;
+}
+
+/* Convert: read the w x m matrix column by column and refill it row by row. */
+static int l2_col_to_row(uint32_t* a, int64_t w, int64_t m) {
+    uint32_t* seq = (uint32_t*)malloc((size_t)(w * m) * sizeof(uint32_t));
+    if (!seq) return ORACLE_E_NOMEM;
+    for (int64_t c = 0; c < m; ++c)
+        for (int64_t r = 0; r < w; ++r) seq[c * w + r] = a[r * m + c];
+    memcpy(a, seq, (size_t)(w * m) * sizeof(uint32_t));
+    free(seq);
+    return ORACLE_OK;
+}
+
+/* Lemma 2's algorithm on a w x m matrix, w = m (sorted directly, row-major) or
+ * w = m^2 (k = log_m w = 2, d = 2k dirty columns at most).  stage limits how
+ * far it runs: 1 balancing; 2 then convert and divide into m*d sub-problems of
+ * w/(m*d) <= m rows, each sorted directly in row-major order; 3 then every column
+ * sorted (the column, read top to bottom, refilled row by row into a w/m x m
+ * matrix that this function sorts, and read back); 4 (all) then the squares of m
+ * contiguous rows sorted in row-major order, and again with the decomposition
+ * shifted down by m/2 rows.  The w rows are the banks.  Labels must be 0 or 1. */
+int oracle_lemma2_partition(uint32_t* lab, uint32_t* pay, int64_t w, int64_t m, int stage) {
+    if (m < 4 || m % 4 != 0 || !(w == m || w == m * m) || stage < 1) return ORACLE_E_ARG;
+    for (int64_t i = 0; i < w * m; ++i)
+        if (lab[i] > 1) return ORACLE_E_KEY;
+    if (w == m) return oracle_l2_sort_rowmajor(lab, pay, m, 0, w);
+    int rc = l2_balance(lab, pay, w, m);
+    if (rc != ORACLE_OK || stage < 2) return rc;
+    if ((rc = l2_col_to_row(lab, w, m)) != ORACLE_OK) return rc;
+    if ((rc = l2_col_to_row(pay, w, m)) != ORACLE_OK) return rc;
+    const int64_t d = 4, chunk = w / (m * d);
+    for (int64_t r0 = 0; r0 < w && rc == ORACLE_OK; r0 += chunk) rc = oracle_l2_sort_rowmajor(lab, pay, m, r0, chunk);
+    if (rc != ORACLE_OK || stage < 3) return rc;
+    uint32_t* cl = (uint32_t*)malloc((size_t)w * sizeof(uint32_t));
+    uint32_t* cp = (uint32_t*)malloc((size_t)w * sizeof(uint32_t));
+    if (!cl || !cp) rc = ORACLE_E_NOMEM;
+    for (int64_t c = 0; c < m && rc == ORACLE_OK; ++c) {
+        for (int64_t r = 0; r < w; ++r) {
+            cl[r] = lab[r * m + c];
+            cp[r] = pay[r * m + c];
+        }
+        rc = oracle_lemma2_partition(cl, cp, w / m, m, 4);
+        for (int64_t r = 0; r < w && rc == ORACLE_OK; ++r) {
+            lab[r * m + c] = cl[r];
+            pay[r * m + c] = cp[r];
+        }
+    }
+    free(cl);
+    free(cp);
+    if (rc != ORACLE_OK || stage < 4) return rc;
+    for (int64_t r0 = 0; r0 + m <= w && rc == ORACLE_OK; r0 += m) rc = oracle_l2_sort_rowmajor(lab, pay, m, r0, m);
+    for (int64_t r0 = m / 2; r0 + m <= w && rc == ORACLE_OK; r0 += m) rc = oracle_l2_sort_rowmajor(lab, pay, m, r0, m);
+    return rc;
 }
 
 /* ---- Race check of a trace (between block-wide barriers) ---- */

@@ -72,6 +72,16 @@ void oracle_l1_row_to_col(uint32_t* M, int64_t w, int64_t m);
 void oracle_l1_col_to_row(uint32_t* M, int64_t w, int64_t m);
 int oracle_lemma1_sort(uint32_t* M, int64_t w, int64_t m);
 
+/* Lemma 2 model (Sec. 2): 0-1 partition of a w x m matrix (labels in lab, 0 or 1;
+ * payloads in pay; rows stored one after another), w = m or w = m*m, m a multiple
+ * of 4.  stage 1..4 stops after balancing / convert-and-divide / column sorts /
+ * shifted squares (4 = the whole algorithm).  The two step sorts are exported for
+ * the pins: a column-major sort of the matrix made of rows[0..h), and a row-major
+ * sort of rows [r0, r0 + h).  All sorts are stable 0-1 sorts. */
+int oracle_lemma2_partition(uint32_t* lab, uint32_t* pay, int64_t w, int64_t m, int stage);
+int oracle_l2_sort_colmajor(uint32_t* lab, uint32_t* pay, int64_t m, const int64_t* rows, int64_t h);
+int oracle_l2_sort_rowmajor(uint32_t* lab, uint32_t* pay, int64_t m, int64_t r0, int64_t h);
+
 /* The paper's bank model (Sec. 1, "Model of Computation") applied to a trace of
  * shared-memory accesses.  Record r: request id req[r] (records of one request
  * are contiguous), lane lane[r], byte address addr[r], access width width[r]

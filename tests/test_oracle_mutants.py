@@ -74,6 +74,26 @@ def _bank_pins(L):
     assert oracle.bank_count(req, lane, same, np.full(n, 4, np.int32), L=L)[:2] == (1, 0)
 
 
+def _lemma2_pins(L):
+    g = synth.rng(7)
+    w, m = 1024, 32
+    pay = np.arange(w * m, dtype=np.uint32).reshape(w, m)
+    cases = [(g.random((w, m)) < 0.3).astype(np.uint32), (np.arange(w)[:, None] >= w // 2).repeat(m, 1).astype(np.uint32)]
+    for _ in range(6):  # exactly half zeros: the dirty rows sit at row w/2, a square boundary
+        cases.append(g.permutation(np.arange(w * m) % 2).reshape(w, m).astype(np.uint32))
+    for lab in cases:
+        lo, po = oracle.lemma2_partition(lab, pay, L=L)
+        assert np.all(np.diff(lo.ravel().astype(np.int64)) >= 0)
+        assert sorted(zip(lab.ravel().tolist(), pay.ravel().tolist())) == sorted(zip(lo.ravel().tolist(), po.ravel().tolist()))
+        l1, _ = oracle.lemma2_partition(lab, pay, stage=1, L=L)
+        zeros = m - l1.sum(axis=1).astype(np.int64)
+        w0 = int((lab == 0).sum())
+        assert np.all(np.abs(zeros - w0 / w) <= 2)
+    cm = np.arange(w * m, dtype=np.uint32).reshape(m, w).T.copy()
+    _, po = oracle.lemma2_partition(np.zeros((w, m), np.uint32), cm, L=L)
+    assert np.array_equal(po.ravel(), np.arange(w * m, dtype=np.uint32))
+
+
 MUTANTS = [
     ("merge takes right run on ties", "if (src[j].key < src[i].key)", "if (src[j].key <= src[i].key)", _sort_pins),
     ("insertion sort moves past equal keys", "while (j >= 0 && a[j].key > x.key)", "while (j >= 0 && a[j].key >= x.key)", _sort_pins),
@@ -87,6 +107,12 @@ MUTANTS = [
     ("row->col conversion transposed", "for (int64_t r = 0; r < w; ++r) M[r * m + c] = seq[c * w + r];",
      "for (int64_t r = 0; r < w; ++r) M[r * m + c] = seq[r * m + c];", _lemma1_pins),
     ("Lemma 1 runs its loop once", "for (int rep = 0; rep < 2; ++rep) {", "for (int rep = 0; rep < 1; ++rep) {", _lemma1_pins),
+    ("Lemma 2 balancing squares take contiguous rows", "for (int64_t t = 0; t < m; ++t) rows[t] = g * group + t * sub + j;",
+     "for (int64_t t = 0; t < m; ++t) rows[t] = g * group + j * m + t;", _lemma2_pins),
+    ("Lemma 2 skips the shifted squares", "for (int64_t r0 = m / 2; r0 + m <= w", "for (int64_t r0 = w; r0 + m <= w", _lemma2_pins),
+    ("Lemma 2 step sort puts 1s first", "for (int label = 0; label <= 1; ++label)", "for (int label = 1; label >= 0; --label)", _lemma2_pins),
+    ("Lemma 2 converts row to column", "for (int64_t r = 0; r < w; ++r) seq[c * w + r] = a[r * m + c];\n    memcpy(a, seq",
+     "for (int64_t r = 0; r < w; ++r) seq[r * m + c] = a[c * w + r];\n    memcpy(a, seq", _lemma2_pins),
     ("bank model ignores phases", "int lanes_per_phase = 32 / words_per_lane;", "int lanes_per_phase = 32;", _bank_pins),
     ("bank model counts lanes not words", "if (words[bank][q] == word) dup = 1;", "if (0) dup = 1;", _bank_pins),
 ]
@@ -101,5 +127,5 @@ def test_pins_catch_mutant(tmp_path, name, old, new, pins):
 
 def test_unmutated_copy_passes_the_same_pins(tmp_path):
     L = _mutant(tmp_path, "#include <stdlib.h>", "#include <stdlib.h>")
-    for pins in (_sort_pins, _partition_pins, _splitter_pins, _permute_pins, _lemma1_pins, _bank_pins):
+    for pins in (_sort_pins, _partition_pins, _splitter_pins, _permute_pins, _lemma1_pins, _lemma2_pins, _bank_pins):
         pins(L)

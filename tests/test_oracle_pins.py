@@ -486,3 +486,128 @@ def test_race_check_rules(orc):
     assert R([_rec(0, 56, 1, width=8), _rec(3, 64, 0)]) == 0
     races, words = orc.race_check(np.array([_rec(0, 0, 1, width=16), _rec(1, 16, 1)], dtype=np.uint32))
     assert (races, words) == (0, 5)
+
+
+# ------------------------------------------------- Lemma 2 (0-1 partition) ----
+def _l2_inputs(w, m, seed):
+    """Random labels at several densities and structured ones (all 0, all 1, one
+    1, alternating rows, alternating columns, one 0 per row, 0s in the top half,
+    random with exactly half 0s), payload = cell index."""
+    g = np.random.default_rng(seed)
+    pay = np.arange(w * m, dtype=np.uint32).reshape(w, m)
+    cases = [(g.random((w, m)) < p).astype(np.uint32) for p in (0.003, 0.3, 0.5, 0.7, 0.97)]
+    cases.append(np.zeros((w, m), np.uint32))
+    cases.append(np.ones((w, m), np.uint32))
+    one = np.zeros((w, m), np.uint32)
+    one[w // 3, m // 2] = 1
+    cases.append(one)
+    cases.append(np.tile((np.arange(w) % 2)[:, None], (1, m)).astype(np.uint32))
+    cases.append(np.tile((np.arange(m) % 2)[None, :], (w, 1)).astype(np.uint32))
+    lone = np.ones((w, m), np.uint32)
+    lone[np.arange(w), np.arange(w) % m] = 0
+    cases.append(lone)
+    cases.append((np.arange(w)[:, None] >= w // 2).repeat(m, 1).astype(np.uint32))  # zeros in the top half
+    for _ in range(4):  # exactly half zeros: the dirty rows sit at row w/2, a square boundary
+        cases.append(g.permutation(np.arange(w * m) % 2).reshape(w, m).astype(np.uint32))
+    return [(lab, pay) for lab in cases]
+
+
+def _is_partitioned(lab):
+    f = lab.ravel().astype(np.int64)
+    return bool(np.all(np.diff(f) >= 0))
+
+
+@pytest.mark.parametrize("w,m", [(1024, 32), (256, 16), (16, 4), (32, 32), (8, 8)])
+def test_lemma2_partitions_and_keeps_pairs(orc, w, m):
+    """The whole algorithm: read row by row, the labels are all 0s then all 1s
+    (the partition problem's definition), and every (label, payload) pair survives."""
+    for lab, pay in _l2_inputs(w, m, seed=w + m):
+        lo, po = orc.lemma2_partition(lab, pay)
+        assert _is_partitioned(lo)
+        assert int(lo.sum()) == int(lab.sum())
+        assert sorted(zip(lab.ravel().tolist(), pay.ravel().tolist())) == sorted(zip(lo.ravel().tolist(), po.ravel().tolist()))
+
+
+@pytest.mark.parametrize("w,m", [(1024, 32), (256, 16), (64, 8)])
+def test_lemma2_balancing_bounds(orc, w, m):
+    """After balancing (k = log_m w = 2 rounds) every row holds between w0/w - k
+    and w0/w + k zeros (w0 = all zeros), its 0s left of its 1s, so at most 2k
+    columns are dirty (Lemma 2's proof, "Convert and Divide")."""
+    k = 2
+    for lab, pay in _l2_inputs(w, m, seed=3 * w):
+        lo, _ = orc.lemma2_partition(lab, pay, stage=1)
+        zeros = m - lo.sum(axis=1).astype(np.int64)
+        w0 = int((lab == 0).sum())
+        assert np.all(zeros >= w0 / w - k) and np.all(zeros <= w0 / w + k)
+        for r in range(w):
+            assert np.all(np.diff(lo[r].astype(np.int64)) >= 0)
+        dirty_cols = sum(1 for c in range(m) if 0 < lo[:, c].sum() < w)
+        assert dirty_cols <= 2 * k
+
+
+@pytest.mark.parametrize("w,m", [(1024, 32), (256, 16)])
+def test_lemma2_leaves_columns_and_dirty_rows(orc, w, m):
+    """After convert-and-divide every sub-problem of w/(4m) rows is sorted row by row
+    (at most one dirty row each); after the column sorts every column is 0s above 1s,
+    and the dirty rows are contiguous and at most m/2 of them, so one of the two
+    square decompositions holds them all."""
+    chunk = w // (4 * m)
+    for lab, pay in _l2_inputs(w, m, seed=5 * w):
+        l2, _ = orc.lemma2_partition(lab, pay, stage=2)
+        for r0 in range(0, w, chunk):
+            assert _is_partitioned(l2[r0:r0 + chunk])
+        l3, _ = orc.lemma2_partition(lab, pay, stage=3)
+        for c in range(m):
+            assert np.all(np.diff(l3[:, c].astype(np.int64)) >= 0)
+        dirty = [r for r in range(w) if 0 < l3[r].sum() < m]
+        assert len(dirty) <= m // 2
+        if dirty:
+            assert dirty == list(range(dirty[0], dirty[-1] + 1))
+            assert np.all(l3[:dirty[0]] == 0) and np.all(l3[dirty[-1] + 1:] == 1)
+
+
+@pytest.mark.parametrize("label", [0, 1])
+def test_lemma2_uniform_labels_move_nothing(orc, label):
+    """With one label every sort is the identity, so the algorithm only converts:
+    the output read row by row is the input read column by column (the array's
+    column-major layout, Sec. 1)."""
+    w, m = 1024, 32
+    lab = np.full((w, m), label, np.uint32)
+    pay = np.arange(w * m, dtype=np.uint32).reshape(m, w).T.copy()  # A[k] in row k % w, column k // w
+    _, po = orc.lemma2_partition(lab, pay)
+    assert np.array_equal(po.ravel(), np.arange(w * m, dtype=np.uint32))
+
+
+def test_lemma2_step_sorts_against_stable_argsort(orc):
+    """The two step sorts are stable 0-1 sorts of a cell sequence: compared with
+    numpy's stable argsort of the labels gathered in that sequence."""
+    g = np.random.default_rng(11)
+    w, m = 64, 8
+    for _ in range(20):
+        lab = g.integers(0, 2, size=(w, m), dtype=np.uint32)
+        pay = np.arange(w * m, dtype=np.uint32).reshape(w, m)
+        rows = g.permutation(w)[:m]
+        seq = [(r, c) for c in range(m) for r in rows]  # column-major order of the square
+        l1, p1 = lab.copy(), pay.copy()
+        orc.l2_sort_colmajor(l1, p1, rows)
+        src = np.array([lab[r, c] for r, c in seq])
+        order = np.argsort(src, kind="stable")
+        assert [p1[r, c] for r, c in seq] == [pay[seq[i]] for i in order]
+        r0, h = int(g.integers(0, w - 8)), 8
+        l2, p2 = lab.copy(), pay.copy()
+        orc.l2_sort_rowmajor(l2, p2, r0, h)
+        flat = lab[r0:r0 + h].ravel()
+        order = np.argsort(flat, kind="stable")
+        assert np.array_equal(p2[r0:r0 + h].ravel(), pay[r0:r0 + h].ravel()[order])
+        assert np.array_equal(np.delete(p2, range(r0, r0 + h), 0), np.delete(pay, range(r0, r0 + h), 0))
+
+
+def test_lemma2_rejects_other_shapes_and_labels(orc):
+    with pytest.raises(orc.OracleError):
+        orc.lemma2_partition(np.zeros((512, 32), np.uint32), np.zeros((512, 32), np.uint32))
+    with pytest.raises(orc.OracleError):
+        orc.lemma2_partition(np.zeros((36, 6), np.uint32), np.zeros((36, 6), np.uint32))
+    lab = np.zeros((16, 4), np.uint32)
+    lab[3, 1] = 2
+    with pytest.raises(orc.OracleError):
+        orc.lemma2_partition(lab, np.zeros((16, 4), np.uint32))

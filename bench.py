@@ -794,6 +794,18 @@ def run_rows(which, peak):
             "two input/output sets rotated")
         del k2, ko2, vo2
         del k, v, ko, vo
+    if want("partition_lemma2_2pow24"):
+        n = N_PERM
+        k, v = to_dev(synth.bernoulli_labels(n, 0.5, seed=0x2D)), to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        k2, ko2, vo2 = to_dev(synth.bernoulli_labels(n, 0.5, seed=0x2E)), torch.empty_like(k), torch.empty_like(v)
+        ms, _ = graph_ms(rotating([lambda: bcf.partition_lemma2(k, v, keys_out=ko, vals_out=vo),
+                                   lambda: bcf.partition_lemma2(k2, v, keys_out=ko2, vals_out=vo2)]), 3, 10, inner=4)
+        add("partition_lemma2_2pow24", n, 16 * n, ms,
+            "Lemma 2 0-1 partition of 512 matrices of 1024 x 32 (one block each); bytes: labels and payloads "
+            "read and written once; two input/output sets rotated")
+        del k2, ko2, vo2
+        del k, v, ko, vo
     if want("segmented_sort_batched_10k") or want("segmented_partition_batched_10k"):
         sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
         offs_np = synth.offsets_from_sizes(sizes)
@@ -930,6 +942,7 @@ def oracle_rows(rows):
     rowoffs = np.arange(0, m + 1, 65536, dtype=np.int64)
     z = synth.zipf_keys(m, seed=0x59)
     k24 = synth.uniform_keys(m, seed=0x5A, bits=24)
+    l2k = synth.bernoulli_labels(m, 0.5, seed=0x5B)
     cases = {  # row prefix -> (keys the sample processes, call)
         "partition_w32_n65536": (65536, lambda: oracle.partition_kv(pk32, v[:65536], 32, True, L=L)),
         "permute_kv": (m, lambda: (oracle.permute(k, pi, L=L), oracle.permute(f, pi, L=L))),  # any size
@@ -941,6 +954,8 @@ def oracle_rows(rows):
         "partition_splitters": (m, lambda: oracle.partition_splitters(k, v, spl, L=L)),
         "partition_w256": (m, lambda: oracle.partition_kv(pk256, v, 256, True, L=L)),
         "tile_sort": (m, lambda: oracle.segmented_sort_kv(k, v, tiles, L=L)),
+        "partition_lemma2": (m, lambda: [oracle.lemma2_partition(
+            l2k[t:t + 32768].reshape(32, 1024).T, v[t:t + 32768].reshape(32, 1024).T, L=L) for t in range(0, m, 32768)]),
         "segmented_sort": (sk.size, lambda: oracle.segmented_sort_kv(sk, synth.index_payload(sk.size), seg_offs, L=L)),
         "segmented_partition": (pkeys.size, lambda: oracle.segmented_partition_kv(
             pkeys, synth.index_payload(pkeys.size), poffs, pw, True, L=L)),
@@ -1001,6 +1016,10 @@ def _case_inputs(name):
         k, v = to_dev(synth.uniform_keys(n, seed=7)), to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         return lambda: bcf.sort_tiles(k, v, keys_out=ko, vals_out=vo)
+    if name == "partition_lemma2":
+        k, v = to_dev(synth.bernoulli_labels(n, 0.5, seed=0x2D)), to_dev(synth.index_payload(n))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        return lambda: bcf.partition_lemma2(k, v, keys_out=ko, vals_out=vo)
     if name == "segmented_sort":  # the batched workload: 10,000 log-uniform segments
         sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
         offs_np = synth.offsets_from_sizes(sizes)
@@ -1014,7 +1033,7 @@ def _case_inputs(name):
 
 
 CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256",
-         "tile_sort", "segmented_sort")
+         "tile_sort", "segmented_sort", "partition_lemma2")
 
 
 def run_case(args):

@@ -211,6 +211,23 @@ int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_
                    void* vals_out, int64_t n, int tile, int val_bytes, bcf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Lemma 2 (Sec. 2): 0-1 partition of independent w x m matrices, m = 32 and
+ * w = m^2 = 1024 rows (the processors, one bank each), 32768 items per matrix.
+ * Matrix t holds items [32768 t, 32768 (t+1)); inside it, item k sits in row
+ * k mod 1024, column k / 1024 (the column-major layout of Sec. 1).  The output of
+ * matrix t is the partitioned matrix read row by row: its 0-labelled items, then
+ * its 1-labelled ones.  The order among equal labels is the one Lemma 2's steps
+ * produce (balancing, convert and divide, column sorts, shifted square sorts,
+ * every sort a stable 0-1 sort of its cells); it is not the input order.
+ *  keys_in   labels, 0 or 1 (another value sets BCF_E_BAD_KEY and counts as 1).
+ *  vals_in   uint32 payloads, or NULL: item k carries its input position k.
+ *  keys_out, vals_out  n entries each; in place allowed (every block reads its
+ *            whole matrix before writing it).
+ *  n         a multiple of 32768 (BCF_E_INVAL otherwise), below 2^32. */
+int bcf_partition_lemma2(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                         uint32_t* vals_out, int64_t n, bcf_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Segmented forms.  offs is a DEVICE array of nseg+1 int64 CSR offsets (offs[0]
  * = 0, nondecreasing, offs[nseg] = n_total).  Each segment is sorted (or
  * partitioned) on its own.  No host synchronisation and no allocation: the whole

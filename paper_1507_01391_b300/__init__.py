@@ -62,6 +62,7 @@ _SIGS = {
     "bcf_gather": ([_P, _P, _P, _I64, _I64, _I64, _I, _P], _I),
     "bcf_sort_passes_run": ([_P, _I64, _I, _I, ctypes.POINTER(_I), _P], _I),
     "bcf_sort_tiles": ([_P, _P, _P, _P, _I64, _I, _I, _P], _I),
+    "bcf_partition_lemma2": ([_P, _P, _P, _P, _I64, _P], _I),
     "bcf_segmented_sort_workspace_size": ([_I64, _I64, _I, _I, ctypes.POINTER(_SZ)], _I),
     "bcf_segmented_sort": ([_P, _P, _P, _P, _I64, _P, _I64, _I, _I, _P, _SZ, _P], _I),
     "bcf_segmented_partition_workspace_size": ([_I64, _I64, _I, ctypes.POINTER(_SZ)], _I),
@@ -335,6 +336,21 @@ def gather(src, idx, dst=None, row_len=0, stream=None):
     _check(lib().bcf_gather(_ptr(src), _ptr(dst), _ptr(idx), n, src.numel(), row_len,
                             src.element_size(), _stream(stream)), "bcf_gather")
     return dst
+
+
+LEMMA2_ITEMS = 32768  # items of one 1024 x 32 matrix
+
+
+def partition_lemma2(keys, vals=None, keys_out=None, vals_out=None, stream=None):
+    """Lemma 2's 0-1 partition of every 1024 x 32 matrix (32768 items, column-major
+    in, row-major out).  vals None: each item carries its input position."""
+    torch = _torch()
+    keys_out = torch.empty_like(keys) if keys_out is None else keys_out
+    if vals_out is None:
+        vals_out = torch.empty_like(keys) if vals is None else torch.empty_like(vals)
+    _check(lib().bcf_partition_lemma2(_ptr(keys), _ptr(vals), _ptr(keys_out), _ptr(vals_out), keys.numel(),
+                                      _stream(stream)), "bcf_partition_lemma2")
+    return keys_out, vals_out
 
 
 def sort_tiles(keys, vals=None, tile=4096, keys_out=None, vals_out=None, stream=None):

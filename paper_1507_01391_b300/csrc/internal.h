@@ -162,4 +162,10 @@ cudaError_t segmented_partition(const uint32_t* keys_in, const void* vals_in, ui
 cudaError_t sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                        void* vals_out, int64_t n, int val_bytes, cudaStream_t s);
 
+// Lemma 2's 0-1 partition of independent 1024 x 32 matrices (n a multiple of 32768).
+cudaError_t partition_lemma2(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out,
+                             int64_t n, cudaStream_t s);
+// Number of SMs of the current device (cached per device).
+int sm_count_cached();
+
 }  // namespace bcf

@@ -1,0 +1,243 @@
+// partition_l2.cu -- Lemma 2 (Sec. 2): 0-1 partition of w x m matrices with
+// w = m^2, m = 32 (bcf_partition_lemma2).
+//
+// One block of 1024 threads holds one 1024 x 32 matrix (32,768 items) in shared
+// memory; thread r is the processor of row r (the paper's bank r).  The steps are
+// the proof's: balancing (two rounds of column-major square sorts, the second on
+// squares made of every 32nd row), conversion from column-major to row-major,
+// division into 128 sub-problems of 8 rows sorted directly, a sort of every
+// column, and row-major sorts of the squares of 32 contiguous rows, then of the
+// same decomposition shifted down by 16 rows.  Every sort is a stable 0-1 sort of
+// the cells in the stated order, so the payload order is fully determined.
+//
+// Layout: payload (r, c) at c*1024 + (r & ~31) + ((r + r/32) mod 32).  A column
+// read by the 32 rows of any square of either balancing round -- rows 32g + t or
+// rows 32t + j, t = 0..31 -- touches 32 distinct banks; the conversion reads and
+// writes along a diagonal schedule that is conflict-free as well.  Labels live as
+// one 32-bit mask per row (bit c = label of column c); after each sort the new
+// masks follow from the zero counts alone.
+#include "common.cuh"
+#include "internal.h"
+
+namespace bcf {
+namespace {
+
+constexpr int kL2M = 32;                       // columns: items per row
+constexpr int kL2W = kL2M * kL2M;              // rows: w = m^2
+constexpr int kL2Items = kL2W * kL2M;          // items per matrix
+constexpr int kL2PayWords = kL2W * (kL2M + 1); // also holds the padded row-major write-out
+constexpr size_t kL2Smem = (size_t)(kL2PayWords + kL2W + 2 * 32 * 32 + 32) * 4;
+
+__device__ __forceinline__ int l2_addr(int r, int c) {
+  return c * kL2W + (r & ~31) + ((r + (r >> 5)) & 31);
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) { return __reduce_add_sync(0xffffffffu, x); }
+
+// Mask of a row that holds `zeros` 0-items followed by 1-items.
+__device__ __forceinline__ uint32_t ones_after(int zeros) {
+  return zeros >= 32 ? 0u : (zeros <= 0 ? 0xffffffffu : (0xffffffffu << zeros));
+}
+
+// The warp's square (its lane j holds row row_of(j), all 32 columns, in pay[] and
+// lab) sorted in column-major order: the 0-items, taken column by column and top
+// to bottom, fill the square's first cells in that order, then the 1-items.  The
+// square's cells have been read into registers before any of them is written.
+template <typename RowOf>
+__device__ __forceinline__ void square_colmajor(uint32_t* P, uint32_t* Lm, const uint32_t (&pay)[32],
+                                                uint32_t lab, RowOf row_of, unsigned lt, int lane) {
+  const uint32_t Z = (uint32_t)kL2W - warp_sum((uint32_t)__popc(lab));
+  uint32_t zb = 0;  // 0-items in earlier columns
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const uint32_t bit = (lab >> c) & 1u;
+    const uint32_t b = __ballot_sync(0xffffffffu, bit);
+    const uint32_t rho = bit ? Z + (32u * c - zb) + __popc(b & lt) : zb + __popc(~b & lt);
+    P[l2_addr(row_of((int)(rho & 31u)), (int)(rho >> 5))] = pay[c];
+    zb += 32u - __popc(b);
+  }
+  // Cell (j, c) of the sorted square holds a 0 iff 32c + j < Z.
+  const int zc = (int)Z > lane ? ((int)Z - lane + 31) / 32 : 0;
+  Lm[row_of(lane)] = ones_after(zc);
+}
+
+// Rows [row0, row0 + G) (lane j of the G-lane group holds row row0 + j) sorted in
+// row-major order.
+template <int G>
+__device__ __forceinline__ void rows_rowmajor(uint32_t* P, uint32_t* Lm, const uint32_t (&pay)[32],
+                                              uint32_t lab, int row0, int lane) {
+  const int j = lane & (G - 1);
+  const uint32_t zr = 32u - __popc(lab);
+  uint32_t incl = zr;
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o, G);
+    if (j >= o) incl += v;
+  }
+  const uint32_t zb = incl - zr;                                  // 0-items in earlier rows
+  const uint32_t Z = __shfl_sync(0xffffffffu, incl, G - 1, G);    // 0-items in the group
+  const uint32_t ob = 32u * j - zb;                               // 1-items in earlier rows
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    const uint32_t bit = (lab >> c) & 1u;
+    const uint32_t below = (1u << c) - 1u;
+    const uint32_t rho = bit ? Z + ob + __popc(lab & below) : zb + __popc(~lab & below);
+    P[l2_addr(row0 + (int)(rho >> 5), (int)(rho & 31u))] = pay[c];
+  }
+  Lm[row0 + j] = ones_after((int)Z - 32 * j);
+}
+
+__device__ __forceinline__ void load_row(const uint32_t* P, const uint32_t* Lm, int r, uint32_t (&pay)[32],
+                                         uint32_t& lab) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(r, c)];
+  lab = Lm[r];
+}
+
+__global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __restrict__ keys,
+                                                          const uint32_t* __restrict__ vals,
+                                                          uint32_t* keys_out, uint32_t* vals_out,
+                                                          int64_t tiles, unsigned* status) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  uint32_t* P = sm;                   // payloads
+  uint32_t* Lm = P + kL2PayWords;     // label mask of each row
+  uint32_t* zw = Lm + kL2W;           // column sort: zeros of warp g in column c at [g*32 + c]
+  uint32_t* zpre = zw + 32 * 32;      // ... and zeros of earlier warps
+  uint32_t* ztot = zpre + 32 * 32;    // ... and zeros of the whole column
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const unsigned lt = lanemask_lt();
+  uint32_t pay[32];
+  uint32_t lab;
+
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t base = tile * kL2Items;
+    // Input item c*w + r of the matrix sits in row r, column c (column-major
+    // layout, Sec. 1): thread r reads its row, one coalesced column at a time.
+    const uint32_t* kin = keys + base + t;
+    lab = 0;
+    uint32_t any = 0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const uint32_t k = __ldcs(kin + c * kL2W);
+      any |= k;
+      lab |= (k != 0u ? 1u : 0u) << c;
+    }
+    if (any > 1u) set_status(status, DEV_BAD_KEY);
+#pragma unroll
+    for (int c = 0; c < 32; ++c) pay[c] = vals ? __ldcs(vals + base + c * kL2W + t) : (uint32_t)(base + c * kL2W + t);
+
+    // Balancing, round 0: squares of 32 contiguous rows (one per warp).
+    square_colmajor(P, Lm, pay, lab, [&](int j) { return warp * 32 + j; }, lt, lane);
+    __syncthreads();
+    // Round 1: square j takes row j of each of the 32 round-0 squares.
+    load_row(P, Lm, lane * 32 + warp, pay, lab);
+    __syncwarp();
+    square_colmajor(P, Lm, pay, lab, [&](int j) { return j * 32 + warp; }, lt, lane);
+    __syncthreads();
+
+    // Convert: column-major reading order refilled row by row.  Item (32g + l, c)
+    // moves to (32c + g, l).  Thread (g, l) handles column (l + s) mod 32 at step s.
+#pragma unroll
+    for (int s = 0; s < 32; ++s) pay[s] = P[l2_addr(t, (lane + s) & 31)];
+    lab = Lm[t];
+    uint32_t mine = 0;  // labels of new row 32*lane + warp: old column `lane` of this warp
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const uint32_t b = __ballot_sync(0xffffffffu, (lab >> c) & 1u);
+      if (c == lane) mine = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < 32; ++s) P[l2_addr(((lane + s) & 31) * 32 + warp, lane)] = pay[s];
+    Lm[lane * 32 + warp] = mine;
+    __syncthreads();
+
+    // Divide: 128 sub-problems of 8 contiguous rows, each sorted row-major.
+    load_row(P, Lm, t, pay, lab);
+    __syncwarp();
+    rows_rowmajor<8>(P, Lm, pay, lab, warp * 32 + (lane & ~7), lane);
+    __syncthreads();
+
+    // Column sorts: each column, top to bottom, stably 0s then 1s.
+    load_row(P, Lm, t, pay, lab);
+    uint32_t myz = 0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const uint32_t b = __ballot_sync(0xffffffffu, (lab >> c) & 1u);
+      if (c == lane) myz = 32u - __popc(b);
+    }
+    zw[warp * 32 + lane] = myz;
+    __syncthreads();
+    {
+      uint32_t pre = 0, tot = 0;
+      for (int g = 0; g < 32; ++g) {
+        const uint32_t z = zw[g * 32 + lane];
+        pre += g < warp ? z : 0u;
+        tot += z;
+      }
+      zpre[warp * 32 + lane] = pre;
+      if (warp == 0) ztot[lane] = tot;
+    }
+    __syncthreads();
+    {
+      uint32_t nm = 0;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        const uint32_t bit = (lab >> c) & 1u;
+        const uint32_t b = __ballot_sync(0xffffffffu, bit);
+        const uint32_t zp = zpre[warp * 32 + c], zt = ztot[c];
+        const uint32_t rho = bit ? zt + (32u * warp - zp) + __popc(b & lt) : zp + __popc(~b & lt);
+        P[l2_addr((int)rho, c)] = pay[c];
+        nm |= ((uint32_t)t >= zt ? 1u : 0u) << c;
+      }
+      Lm[t] = nm;
+    }
+    __syncthreads();
+
+    // Squares of 32 contiguous rows sorted row-major, then the decomposition
+    // shifted down by 16 rows.
+    load_row(P, Lm, t, pay, lab);
+    __syncwarp();
+    rows_rowmajor<32>(P, Lm, pay, lab, warp * 32, lane);
+    __syncthreads();
+    if (warp < 31) {
+      load_row(P, Lm, warp * 32 + 16 + lane, pay, lab);
+      __syncwarp();
+      rows_rowmajor<32>(P, Lm, pay, lab, warp * 32 + 16, lane);
+    }
+    __syncthreads();
+
+    // Write-out in row-major order (output item r*m + c), staged through a
+    // padded row-major copy so that both sides are conflict-free and coalesced.
+    load_row(P, Lm, t, pay, lab);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 32; ++c) P[t * 33 + c] = pay[c];
+    __syncthreads();
+    uint32_t* vo = vals_out + base;
+    uint32_t* ko = keys_out + base;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const int q = i * kL2W + t, r = q >> 5, c = q & 31;
+      __stcs(vo + q, P[r * 33 + c]);
+      __stcs(ko + q, (Lm[r] >> c) & 1u);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t partition_lemma2(const uint32_t* keys, const uint32_t* vals, uint32_t* keys_out, uint32_t* vals_out,
+                             int64_t n, cudaStream_t s) {
+  const int64_t tiles = n / kL2Items;
+  if (tiles == 0) return cudaSuccess;
+  static bool ready[64] = {};
+  cudaError_t e = set_smem_once(k_partition_l2, (int)kL2Smem, ready);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(tiles, std::max(1, sm_count_cached()));
+  k_partition_l2<<<(unsigned)grid, 1024, kL2Smem, s>>>(keys, vals, keys_out, vals_out, tiles, status_word());
+  return cudaGetLastError();
+}
+
+}  // namespace bcf

@@ -31,6 +31,19 @@
 
 namespace bcf {
 
+int sm_count_cached() {
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!sms[dev]) {
+    int c = 148;
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = c;
+  }
+  return sms[dev];
+}
+
 namespace {
 
 constexpr int kPbMaxLen = 53248;   // destinations per block at most (shared memory of pass 2)
@@ -61,8 +74,6 @@ struct PbGeom {
   uint32_t len = 0;
   unsigned long long magic = 0;  // ceil(2^42 / len)
 };
-
-int sm_count_cached();
 
 PbGeom pb_geometry(int64_t n) {
   const int64_t sms = std::max(1, sm_count_cached());
@@ -364,32 +375,6 @@ __global__ void __launch_bounds__(kPlaceThreads, 1)
   if (tid == 0) bulk_s2g_wait_read();  // shared memory stays valid until read out
 }
 
-int sm_count_cached() {
-  static int sms[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!sms[dev]) {
-    int c = 148;
-    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-    sms[dev] = c;
-  }
-  return sms[dev];
-}
-
-// Raise a kernel's dynamic shared-memory limit once per device (`done` is the
-// caller's per-kernel flag array).
-template <typename K>
-cudaError_t set_smem(K kernel, int bytes, bool (&done)[64]) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (done[dev]) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done[dev] = true;
-  return e;
-}
-
 template <int VB, int NB>
 cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, uint32_t* dv,
                          const uint32_t* pi, int64_t n, int64_t row_len, bool check, const PbGeom& g,
@@ -404,7 +389,7 @@ cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, u
   if (e != cudaSuccess) return e;
   constexpr int sm1 = pb_smem_bytes<NB>();
   static bool ready1[64] = {};
-  if ((e = set_smem(k_pb_bucket<VB, NB>, sm1, ready1)) != cudaSuccess) return e;
+  if ((e = set_smem_once(k_pb_bucket<VB, NB>, sm1, ready1)) != cudaSuccess) return e;
   const int grid = std::min(ntiles, sm_count_cached());
   k_pb_bucket<VB, NB><<<grid, kPbThreads, sm1, s>>>(pi, sk, sv, K1, V1, P1, fill, n, row_len, ntiles, g.len,
                                                     g.magic, status_word());
@@ -414,11 +399,11 @@ cudaError_t run_bucketed(const uint32_t* sk, const uint32_t* sv, uint32_t* dk, u
   const int sm2 = (int)g.len * 4 + (check ? (int)(g.len + 31) / 32 * 4 : 0);
   if (check) {
     static bool ready2[64] = {};
-    if ((e = set_smem(k_pb_place<VB, true>, sm2_max, ready2)) != cudaSuccess) return e;
+    if ((e = set_smem_once(k_pb_place<VB, true>, sm2_max, ready2)) != cudaSuccess) return e;
     k_pb_place<VB, true><<<g.nb, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, g.len, status_word());
   } else {
     static bool ready2[64] = {};
-    if ((e = set_smem(k_pb_place<VB, false>, sm2_max, ready2)) != cudaSuccess) return e;
+    if ((e = set_smem_once(k_pb_place<VB, false>, sm2_max, ready2)) != cudaSuccess) return e;
     k_pb_place<VB, false><<<g.nb, kPlaceThreads, sm2, s>>>(K1, V1, P1, dk, dv, n, g.len, status_word());
   }
   return cudaGetLastError();

@@ -584,7 +584,8 @@ struct SweepSmem {
   static constexpr size_t info = mbar + 8;                 // tile, seg
   static constexpr size_t spl = info + 16;                 // splitter mode: splitters
   static constexpr size_t sdig = spl + (SPLIT ? 256 * 4 : 0);  // splitter mode: digit of each ordered key
-  static constexpr size_t bytes = sdig + (SPLIT ? (size_t)T : 0);
+  static constexpr size_t mbins = (sdig + (SPLIT ? (size_t)T : 0) + 15) / 16 * 16;  // peer masks
+  static constexpr size_t bytes = mbins + (BCF_PEERS_MATCH == 2 ? (size_t)WARPS * RADIX * 4 : 0);
   static_assert(scratch % 8 == 0, "scratch also carries pointers; mbar needs 8-byte alignment");
 };
 
@@ -609,6 +610,7 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   int* s_info = reinterpret_cast<int*>(smem + S::info);
   uint32_t* spl = reinterpret_cast<uint32_t*>(smem + S::spl);
   uint8_t* sdig = reinterpret_cast<uint8_t*>(smem + S::sdig);
+  uint32_t* mbins = reinterpret_cast<uint32_t*>(smem + S::mbins);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool segmented = p.seg_offs != nullptr;
@@ -683,6 +685,9 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   };
   stage();
   for (int i = tid; i < S::WARPS * RADIX; i += THREADS) whist[i] = 0;
+#if BCF_PEERS_MATCH == 2
+  for (int i = tid; i < S::WARPS * RADIX; i += THREADS) mbins[i] = 0;
+#endif
   if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, THREADS, p.status);
   for (int i = max(kfull - ksh, 0) + tid; i < cnt; i += THREADS) keys_s[ksh + i] = p.keys_in[start + i];
   if (VB && !iota) {
@@ -771,7 +776,13 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       const bool valid = in_tile(wbase + j * 32 + lane);
       const uint32_t d = digit(j);
       unsigned peers = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
-#if BCF_PEERS_MATCH
+#if BCF_PEERS_MATCH == 2
+      // Every lane sets its bit in its digit's word; the word then is the peer set.
+      uint32_t* mb = mbins + warp * RADIX + d;
+      if (valid) atomicOr(mb, 1u << lane);
+      __syncwarp();
+      peers = valid ? *mb : 0u;
+#elif BCF_PEERS_MATCH
       peers &= __match_any_sync(0xffffffffu, valid ? d : 0xFFFFFFFFu);
 #else
 #pragma unroll
@@ -787,6 +798,10 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
         old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
       }
       old = __shfl_sync(0xffffffffu, old, leader);
+#if BCF_PEERS_MATCH == 2
+      if (valid && lane == leader) *mb = 0u;  // every peer has read the word (shuffle above)
+      __syncwarp();
+#endif
       if (valid) {
         const uint32_t pos = old + __popc(peers & lt);
         if constexpr (SPLIT) sdig[pos] = (uint8_t)d;

@@ -43,6 +43,11 @@ def random_labels(n: int, w: int, seed: int) -> np.ndarray:
     return rng(seed).integers(0, w, size=n, dtype=np.uint32)
 
 
+def bernoulli_labels(n: int, p: float, seed: int) -> np.ndarray:
+    """0/1 labels, each 1 with probability p (uint32)."""
+    return (rng(seed).random(n) < p).astype(np.uint32)
+
+
 def uniform_keys(n: int, seed: int, bits: int = 32) -> np.ndarray:
     """Keys uniform on [0, 2^bits)."""
     return rng(seed).integers(0, 1 << bits, size=n, dtype=np.uint64).astype(np.uint32)

@@ -52,7 +52,8 @@ __device__ __forceinline__ void square_colmajor(uint32_t* P, uint32_t* Lm, const
   for (int c = 0; c < 32; ++c) {
     const uint32_t bit = (lab >> c) & 1u;
     const uint32_t b = __ballot_sync(0xffffffffu, bit);
-    const uint32_t rho = bit ? Z + (32u * c - zb) + __popc(b & lt) : zb + __popc(~b & lt);
+    const uint32_t x = __popc(b & lt);  // 1-items above in this column; lane - x 0-items
+    const uint32_t rho = bit ? Z + (32u * c - zb) + x : zb + (uint32_t)lane - x;
     P[l2_addr(row_of((int)(rho & 31u)), (int)(rho >> 5))] = pay[c];
     zb += 32u - __popc(b);
   }
@@ -80,8 +81,8 @@ __device__ __forceinline__ void rows_rowmajor(uint32_t* P, uint32_t* Lm, const u
 #pragma unroll
   for (int c = 0; c < 32; ++c) {
     const uint32_t bit = (lab >> c) & 1u;
-    const uint32_t below = (1u << c) - 1u;
-    const uint32_t rho = bit ? Z + ob + __popc(lab & below) : zb + __popc(~lab & below);
+    const uint32_t x = __popc(lab & ((1u << c) - 1u));  // 1-items left of c; c - x 0-items
+    const uint32_t rho = bit ? Z + ob + x : zb + (uint32_t)c - x;
     P[l2_addr(row0 + (int)(rho >> 5), (int)(rho & 31u))] = pay[c];
   }
   Lm[row0 + j] = ones_after((int)Z - 32 * j);
@@ -137,8 +138,6 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
 
     // Convert: column-major reading order refilled row by row.  Item (32g + l, c)
     // moves to (32c + g, l).  Thread (g, l) handles column (l + s) mod 32 at step s.
-#pragma unroll
-    for (int s = 0; s < 32; ++s) pay[s] = P[l2_addr(t, (lane + s) & 31)];
     lab = Lm[t];
     uint32_t mine = 0;  // labels of new row 32*lane + warp: old column `lane` of this warp
 #pragma unroll
@@ -146,6 +145,8 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
       const uint32_t b = __ballot_sync(0xffffffffu, (lab >> c) & 1u);
       if (c == lane) mine = b;
     }
+#pragma unroll
+    for (int s = 0; s < 32; ++s) pay[s] = P[l2_addr(t, (lane + s) & 31)];
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 32; ++s) P[l2_addr(((lane + s) & 31) * 32 + warp, lane)] = pay[s];
@@ -158,8 +159,10 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     rows_rowmajor<8>(P, Lm, pay, lab, warp * 32 + (lane & ~7), lane);
     __syncthreads();
 
-    // Column sorts: each column, top to bottom, stably 0s then 1s.
-    load_row(P, Lm, t, pay, lab);
+    // Column sorts: each column, top to bottom, stably 0s then 1s.  The row's
+    // payloads are read after the counts (and before the barrier that precedes
+    // any write).
+    lab = Lm[t];
     uint32_t myz = 0;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
@@ -170,6 +173,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     __syncthreads();
     {
       uint32_t pre = 0, tot = 0;
+#pragma unroll 4
       for (int g = 0; g < 32; ++g) {
         const uint32_t z = zw[g * 32 + lane];
         pre += g < warp ? z : 0u;
@@ -178,15 +182,20 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
       zpre[warp * 32 + lane] = pre;
       if (warp == 0) ztot[lane] = tot;
     }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(t, c)];
     __syncthreads();
     {
+      const uint32_t* vzp = zpre + warp * 32;
+      const uint32_t* vzt = ztot;
       uint32_t nm = 0;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
         const uint32_t bit = (lab >> c) & 1u;
         const uint32_t b = __ballot_sync(0xffffffffu, bit);
-        const uint32_t zp = zpre[warp * 32 + c], zt = ztot[c];
-        const uint32_t rho = bit ? zt + (32u * warp - zp) + __popc(b & lt) : zp + __popc(~b & lt);
+        const uint32_t zp = vzp[c], zt = vzt[c];
+        const uint32_t x = __popc(b & lt);
+        const uint32_t rho = bit ? zt + (32u * warp - zp) + x : zp + (uint32_t)lane - x;
         P[l2_addr((int)rho, c)] = pay[c];
         nm |= ((uint32_t)t >= zt ? 1u : 0u) << c;
       }

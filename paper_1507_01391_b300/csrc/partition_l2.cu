@@ -14,8 +14,8 @@
 // read by the 32 rows of any square of either balancing round -- rows 32g + t or
 // rows 32t + j, t = 0..31 -- touches 32 distinct banks; the conversion reads and
 // writes along a diagonal schedule that is conflict-free as well.  Labels live as
-// one 32-bit mask per row (bit c = label of column c); after each sort the new
-// masks follow from the zero counts alone.
+// one 32-bit mask per row (bit c = label of column c; rows rotated the same way);
+// after each sort the new masks follow from the zero counts alone.
 #include "common.cuh"
 #include "internal.h"
 
@@ -31,6 +31,10 @@ constexpr size_t kL2Smem = (size_t)(kL2PayWords + kL2W + 2 * 32 * 32 + 32) * 4;
 __device__ __forceinline__ int l2_addr(int r, int c) {
   return c * kL2W + (r & ~31) + ((r + (r >> 5)) & 31);
 }
+
+// Label mask of row r, with the same rotation inside each group of 32 rows, so
+// that rows 32t + j (t = 0..31) also fall into distinct banks.
+__device__ __forceinline__ int lm_idx(int r) { return (r & ~31) + ((r + (r >> 5)) & 31); }
 
 __device__ __forceinline__ uint32_t warp_sum(uint32_t x) { return __reduce_add_sync(0xffffffffu, x); }
 
@@ -59,7 +63,7 @@ __device__ __forceinline__ void square_colmajor(uint32_t* P, uint32_t* Lm, const
   }
   // Cell (j, c) of the sorted square holds a 0 iff 32c + j < Z.
   const int zc = (int)Z > lane ? ((int)Z - lane + 31) / 32 : 0;
-  Lm[row_of(lane)] = ones_after(zc);
+  Lm[lm_idx(row_of(lane))] = ones_after(zc);
 }
 
 // Rows [row0, row0 + G) (lane j of the G-lane group holds row row0 + j) sorted in
@@ -85,14 +89,14 @@ __device__ __forceinline__ void rows_rowmajor(uint32_t* P, uint32_t* Lm, const u
     const uint32_t rho = bit ? Z + ob + x : zb + (uint32_t)c - x;
     P[l2_addr(row0 + (int)(rho >> 5), (int)(rho & 31u))] = pay[c];
   }
-  Lm[row0 + j] = ones_after((int)Z - 32 * j);
+  Lm[lm_idx(row0 + j)] = ones_after((int)Z - 32 * j);
 }
 
 __device__ __forceinline__ void load_row(const uint32_t* P, const uint32_t* Lm, int r, uint32_t (&pay)[32],
                                          uint32_t& lab) {
 #pragma unroll
   for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(r, c)];
-  lab = Lm[r];
+  lab = Lm[lm_idx(r)];
 }
 
 __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __restrict__ keys,
@@ -138,7 +142,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
 
     // Convert: column-major reading order refilled row by row.  Item (32g + l, c)
     // moves to (32c + g, l).  Thread (g, l) handles column (l + s) mod 32 at step s.
-    lab = Lm[t];
+    lab = Lm[lm_idx(t)];
     uint32_t mine = 0;  // labels of new row 32*lane + warp: old column `lane` of this warp
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < 32; ++s) P[l2_addr(((lane + s) & 31) * 32 + warp, lane)] = pay[s];
-    Lm[lane * 32 + warp] = mine;
+    Lm[lm_idx(lane * 32 + warp)] = mine;
     __syncthreads();
 
     // Divide: 128 sub-problems of 8 contiguous rows, each sorted row-major.
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     // Column sorts: each column, top to bottom, stably 0s then 1s.  The row's
     // payloads are read after the counts (and before the barrier that precedes
     // any write).
-    lab = Lm[t];
+    lab = Lm[lm_idx(t)];
     uint32_t myz = 0;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
         P[l2_addr((int)rho, c)] = pay[c];
         nm |= ((uint32_t)t >= zt ? 1u : 0u) << c;
       }
-      Lm[t] = nm;
+      Lm[lm_idx(t)] = nm;
     }
     __syncthreads();
 
@@ -229,7 +233,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     for (int i = 0; i < 32; ++i) {
       const int q = i * kL2W + t, r = q >> 5, c = q & 31;
       __stcs(vo + q, P[r * 33 + c]);
-      __stcs(ko + q, (Lm[r] >> c) & 1u);
+      __stcs(ko + q, (Lm[lm_idx(r)] >> c) & 1u);
     }
     __syncthreads();
   }

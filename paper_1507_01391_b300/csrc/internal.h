@@ -44,7 +44,8 @@ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a
 #define BCF_LB_WINDOW 8       // look-back status words read per round trip (multiple of 4)
 #endif
 #ifndef BCF_PEERS_MATCH
-#define BCF_PEERS_MATCH 0     // 1: peers from __match_any_sync instead of per-bit ballots
+#define BCF_PEERS_MATCH 0     // 1: peers from __match_any_sync, 2: from one shared atomicOr of the
+                              // lane bit per key, instead of per-bit ballots (both slower here)
 #endif
 constexpr int kSweepThreads = BCF_SWEEP_THREADS;
 constexpr int kSweepIPT = BCF_SWEEP_IPT;

@@ -46,8 +46,8 @@ FALLBACK_HBM_GBS = 6400.0
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
 # it was taken on: if permute.cu changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "k_pb_bucket<4,512> + k_pb_place<4,0> (bucketed kv permute, both passes)",
-               "source": "permute_bucketed.cu", "source_sha1": "9b9b6694d7c8c746e21acc7d0fb7dae6de12650c",
-               "bytes": 575275264,
+               "source": "permute_bucketed.cu", "source_sha1": "f473b17f81f00f545e0e74e5836096846558ad25",
+               "bytes": 575516928,
                "summary": "profiles/k_pb_bucketed_permute_kv_2pow24.md"}
 
 

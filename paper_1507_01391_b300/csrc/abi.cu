@@ -328,10 +328,10 @@ int bcf_sort_tiles(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_
 
 int bcf_partition_lemma2(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
                          uint32_t* vals_out, int64_t n, bcf_stream_t stream) {
+  if (n < 0 || n % 32768 != 0) return BCF_E_INVAL;
+  if (n >= ((int64_t)1 << 32)) return BCF_E_UNSUPPORTED;
   int rc = check_kv(keys_in, vals_in, keys_out, vals_out, n, 4);
   if (rc) return rc;
-  if (n % 32768 != 0) return BCF_E_INVAL;
-  if (n >= ((int64_t)1 << 32)) return BCF_E_UNSUPPORTED;
   if (n == 0) return BCF_OK;
   if (!device_ready()) return BCF_E_CUDA;
   return cuda_rc(bcf::partition_lemma2(keys_in, vals_in, keys_out, vals_out, n, (cudaStream_t)stream));

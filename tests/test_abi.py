@@ -93,6 +93,14 @@ def test_argument_checks_reject_without_launching():
     assert L.bcf_segmented_sort(a, None, b, None, 10, ws, 1, 0, 32, ws, 8, None) == bcf.E_WORKSPACE
     assert L.bcf_sort_tiles(a, None, b, None, 10, 1024, 0, None) == bcf.E_INVAL
     assert L.bcf_sort_tiles(a, None, a, None, 10, 4096, 0, None) == bcf.E_INVAL
+    # Lemma 2 partition: whole 32768-item matrices, 16-byte aligned, below 2^32 items
+    c, d = P(0x1000000), P(0x2000000)
+    assert L.bcf_partition_lemma2(a, None, b, c, 32768 + 4, None) == bcf.E_INVAL
+    assert L.bcf_partition_lemma2(mis, None, b, c, 32768, None) == bcf.E_INVAL
+    assert L.bcf_partition_lemma2(a, None, b, None, 32768, None) == bcf.E_INVAL  # no payload output
+    assert L.bcf_partition_lemma2(a, c, b, c, 32768, None) == bcf.E_INVAL  # keys out of place, payloads in place
+    assert L.bcf_partition_lemma2(a, c, b, d, 1 << 32, None) == bcf.E_UNSUPPORTED
+    assert L.bcf_partition_lemma2(None, None, None, None, 0, None) == bcf.OK
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

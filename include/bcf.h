@@ -26,7 +26,9 @@
  *  - Index payload: for the sorts, vals_in == NULL with val_bytes == 4 means the
  *    payload of item i is i (its input position, counted from the start of the
  *    array), so vals_out receives the sorting permutation (an argsort).
- *  - Nothing here throws; no function keeps host state between calls.
+ *  - Nothing here throws.  The only host state kept between calls is the tuning
+ *    table (bcf_tune_*) and, per device, the SM count and each kernel's raised
+ *    shared-memory limit (set on first use).
  */
 #ifndef BCF_H
 #define BCF_H

@@ -92,6 +92,25 @@ __device__ __forceinline__ void rows_rowmajor(uint32_t* P, uint32_t* Lm, const u
   Lm[lm_idx(row0 + j)] = ones_after((int)Z - 32 * j);
 }
 
+// True when every G-lane group of the warp holds rows of one label only (each
+// lane passes its row's mask).  Sorting such a group moves nothing, so the warp
+// may leave it as it is; the answer is the same in every lane.
+template <int G>
+__device__ __forceinline__ bool groups_uniform(uint32_t lab) {
+  const unsigned z = __ballot_sync(0xffffffffu, lab == 0u);
+  const unsigned o = __ballot_sync(0xffffffffu, lab == 0xffffffffu);
+  const unsigned m = G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u);
+  bool all = true;
+#pragma unroll
+  for (int g = 0; g < 32; g += G) all &= ((z >> g) & m) == m || ((o >> g) & m) == m;
+  return all;
+}
+
+__device__ __forceinline__ void load_pay(const uint32_t* P, int r, uint32_t (&pay)[32]) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(r, c)];
+}
+
 __device__ __forceinline__ void load_row(const uint32_t* P, const uint32_t* Lm, int r, uint32_t (&pay)[32],
                                          uint32_t& lab) {
 #pragma unroll
@@ -157,10 +176,15 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     Lm[lm_idx(lane * 32 + warp)] = mine;
     __syncthreads();
 
-    // Divide: 128 sub-problems of 8 contiguous rows, each sorted row-major.
-    load_row(P, Lm, t, pay, lab);
-    __syncwarp();
-    rows_rowmajor<8>(P, Lm, pay, lab, warp * 32 + (lane & ~7), lane);
+    // Divide: 128 sub-problems of 8 contiguous rows, each sorted row-major.  Only
+    // the few that hold both labels move anything: a warp whose four are all
+    // single-label leaves them in place.
+    lab = Lm[lm_idx(t)];
+    if (!groups_uniform<8>(lab)) {
+      load_pay(P, t, pay);
+      __syncwarp();
+      rows_rowmajor<8>(P, Lm, pay, lab, warp * 32 + (lane & ~7), lane);
+    }
     __syncthreads();
 
     // Column sorts: each column, top to bottom, stably 0s then 1s.  The row's
@@ -175,8 +199,9 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     }
     zw[warp * 32 + lane] = myz;
     __syncthreads();
+    bool moves;  // does any item of this warp's rows change place?
     {
-      uint32_t pre = 0, tot = 0;
+      uint32_t pre = 0, tot = 0;  // of column `lane`
 #pragma unroll 4
       for (int g = 0; g < 32; ++g) {
         const uint32_t z = zw[g * 32 + lane];
@@ -185,11 +210,17 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
       }
       zpre[warp * 32 + lane] = pre;
       if (warp == 0) ztot[lane] = tot;
+      // Rows of 0s with only 0s above them in every column, or rows of 1s with
+      // only 1s from them down, already sit where the column sort puts them.
+      moves = !(__all_sync(0xffffffffu, lab == 0u && pre == 32u * warp) ||
+                __all_sync(0xffffffffu, lab == 0xffffffffu && tot == pre));
     }
+    if (moves) {
 #pragma unroll
-    for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(t, c)];
+      for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(t, c)];
+    }
     __syncthreads();
-    {
+    if (moves) {
       const uint32_t* vzp = zpre + warp * 32;
       const uint32_t* vzt = ztot;
       uint32_t nm = 0;
@@ -209,14 +240,23 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
 
     // Squares of 32 contiguous rows sorted row-major, then the decomposition
     // shifted down by 16 rows.
-    load_row(P, Lm, t, pay, lab);
-    __syncwarp();
-    rows_rowmajor<32>(P, Lm, pay, lab, warp * 32, lane);
+    // Single-label squares (all but the one or two that hold the dirty rows) are
+    // left in place.
+    lab = Lm[lm_idx(t)];
+    if (!groups_uniform<32>(lab)) {
+      load_pay(P, t, pay);
+      __syncwarp();
+      rows_rowmajor<32>(P, Lm, pay, lab, warp * 32, lane);
+    }
     __syncthreads();
     if (warp < 31) {
-      load_row(P, Lm, warp * 32 + 16 + lane, pay, lab);
-      __syncwarp();
-      rows_rowmajor<32>(P, Lm, pay, lab, warp * 32 + 16, lane);
+      const int r = warp * 32 + 16 + lane;
+      lab = Lm[lm_idx(r)];
+      if (!groups_uniform<32>(lab)) {
+        load_pay(P, r, pay);
+        __syncwarp();
+        rows_rowmajor<32>(P, Lm, pay, lab, warp * 32 + 16, lane);
+      }
     }
     __syncthreads();
 

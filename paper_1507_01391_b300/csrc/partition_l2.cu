@@ -12,8 +12,10 @@
 //
 // Layout: payload (r, c) at c*1024 + (r & ~31) + ((r + r/32) mod 32).  A column
 // read by the 32 rows of any square of either balancing round -- rows 32g + t or
-// rows 32t + j, t = 0..31 -- touches 32 distinct banks; the conversion reads and
-// writes along a diagonal schedule that is conflict-free as well.  Labels live as
+// rows 32t + j, t = 0..31 -- touches 32 distinct banks.  The second balancing
+// round writes its sorted squares straight to their places after the conversion
+// (square j becomes column j), so the conversion costs no pass of its own, and
+// sorts that would move nothing are skipped (see the steps below).  Labels live as
 // one 32-bit mask per row (bit c = label of column c; rows rotated the same way);
 // after each sort the new masks follow from the zero counts alone.
 #include "common.cuh"
@@ -153,28 +155,38 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     // Balancing, round 0: squares of 32 contiguous rows (one per warp).
     square_colmajor(P, Lm, pay, lab, [&](int j) { return warp * 32 + j; }, lt, lane);
     __syncthreads();
-    // Round 1: square j takes row j of each of the 32 round-0 squares.
+    // Round 1: square j takes row j of each of the 32 round-0 squares, and is
+    // sorted in column-major order; then the conversion refills the matrix read
+    // column by column into rows.  The two are composed: the item at position rho
+    // of square j's sorted order sits in row 32*(rho mod 32) + j, column rho/32
+    // after the sort, and the conversion moves that cell to row rho, column j.
+    // So square j becomes column j, top to bottom, and every item is written
+    // once.  Squares overlap other squares' columns, hence the block barrier
+    // between all reads and all writes.
     load_row(P, Lm, lane * 32 + warp, pay, lab);
-    __syncwarp();
-    square_colmajor(P, Lm, pay, lab, [&](int j) { return j * 32 + warp; }, lt, lane);
     __syncthreads();
-
-    // Convert: column-major reading order refilled row by row.  Item (32g + l, c)
-    // moves to (32c + g, l).  Thread (g, l) handles column (l + s) mod 32 at step s.
-    lab = Lm[lm_idx(t)];
-    uint32_t mine = 0;  // labels of new row 32*lane + warp: old column `lane` of this warp
+    {
+      const uint32_t Z = (uint32_t)kL2W - warp_sum((uint32_t)__popc(lab));
+      if (lane == 0) ztot[warp] = Z;  // zeros of square (now column) `warp`
+      uint32_t zb = 0;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const uint32_t b = __ballot_sync(0xffffffffu, (lab >> c) & 1u);
-      if (c == lane) mine = b;
+      for (int c = 0; c < 32; ++c) {
+        const uint32_t bit = (lab >> c) & 1u;
+        const uint32_t b = __ballot_sync(0xffffffffu, bit);
+        const uint32_t x = __popc(b & lt);
+        const uint32_t rho = bit ? Z + (32u * c - zb) + x : zb + (uint32_t)lane - x;
+        P[l2_addr((int)rho, warp)] = pay[c];
+        zb += 32u - __popc(b);
+      }
     }
-#pragma unroll
-    for (int s = 0; s < 32; ++s) pay[s] = P[l2_addr(t, (lane + s) & 31)];
     __syncthreads();
+    // Row t now holds a 1 in column j iff t >= (zeros of column j).
+    {
+      uint32_t m = 0;
 #pragma unroll
-    for (int s = 0; s < 32; ++s) P[l2_addr(((lane + s) & 31) * 32 + warp, lane)] = pay[s];
-    Lm[lm_idx(lane * 32 + warp)] = mine;
-    __syncthreads();
+      for (int j = 0; j < 32; ++j) m |= ((uint32_t)t >= ztot[j] ? 1u : 0u) << j;
+      Lm[lm_idx(t)] = m;
+    }
 
     // Divide: 128 sub-problems of 8 contiguous rows, each sorted row-major.  Only
     // the few that hold both labels move anything: a warp whose four are all

@@ -121,6 +121,11 @@ __device__ __forceinline__ void bulk_s2g_evict_first(void* dst, const void* src,
       "r"(smem_u32(src)), "r"(bytes)
       : "memory");
 }
+// Ask L2 to fetch [src, src + bytes) ahead of its use (16-byte aligned, bytes a
+// multiple of 16).
+__device__ __forceinline__ void prefetch_l2_bulk(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_s2g_commit() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }

@@ -152,6 +152,13 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
 #pragma unroll
     for (int c = 0; c < 32; ++c) pay[c] = vals ? __ldcs(vals + base + c * kL2W + t) : (uint32_t)(base + c * kL2W + t);
 
+    // While this matrix is sorted, L2 fetches the block's next one (32 KB pieces).
+    if (t < 8 && tile + gridDim.x < tiles) {
+      const int64_t nb = (tile + gridDim.x) * kL2Items + (int64_t)(t & 3) * (kL2Items / 4);
+      if (t < 4) prefetch_l2_bulk(keys + nb, (unsigned)(kL2Items / 4 * sizeof(uint32_t)));
+      else if (vals) prefetch_l2_bulk(vals + nb, (unsigned)(kL2Items / 4 * sizeof(uint32_t)));
+    }
+
     // Balancing, round 0: squares of 32 contiguous rows (one per warp).
     square_colmajor(P, Lm, pay, lab, [&](int j) { return warp * 32 + j; }, lt, lane);
     __syncthreads();

@@ -1,16 +1,18 @@
-"""Benchmark: bank-conflict-free permute / sort / partition on one B300.
+"""Benchmark: bank-conflict-free sort / permute / w-way partition on one B300.
 
-Prints ONE JSON line.  Headline workload (one "step"): the key-value permutation
-of n = 2^24 uint32 keys with float32 payloads by a uniform random pi
-(out[pi[i]] = in[i]) followed by the tile-local permutation of 2^24 uint32 keys in
-4096-key tiles; value = keys moved per second over both (2 x 2^24 keys per step),
-inputs resident in HBM.  Every input is seeded synthetic data; every input is
-larger than the 126 MB L2, so no flush runs between steps.
+Prints ONE JSON line.  Headline workload (one "step"): the stable key-value radix
+sort of n = 2^26 uint32 keys drawn uniformly from [0, 2^32) with a uint32 payload
+(the input position), 4 digit passes of 8 bits; value = keys sorted per second,
+inputs resident in HBM.  Every input is seeded synthetic data; the keys and
+payloads (512 MB) are larger than the 126 MB L2, so no flush runs between steps.
+The roofline charges the sort the bytes its passes must move: one read of the keys
+for the digit histogram plus 16 bytes per key and pass (68 B/key for 4 passes).
 
-Also reported, per hot-path row (`rows`): the 2^26 key-value radix sort (uniform
-and Zipf keys), the 2^26 w = 256 partition, the 65536-key w = 32 partition, both
-tile-permutation schedules, and whatever else the library implements, each with
-its own CUDA-event timing, bytes model and roofline fraction.
+Also reported, per hot-path row (`rows`): the 2^26 sort on Zipf keys, the key-value
+permutation at 2^24 and 2^26 keys, the tile-local permutation, the w = 256 and
+w = 32 partitions, the splitter partition, the Lemma 1 tile sort, the Lemma 2 0-1
+partition, the batched and autograd forms, each with its own CUDA-event timing,
+bytes model and roofline fraction.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-rows]
 
@@ -36,19 +38,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_PERM = 1 << 24
+N_SORT = 1 << 26
+SORT_MODEL_BYTES = 68  # per key: histogram read 4 + 4 passes x 16 (read and write key and payload)
 TILE = 4096
 METRIC = "Gkeys/s and % of HBM roofline (sort/permute/w-partition); smem bank conflicts"
 UNIT = "Gkeys/s"
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6400.0
 
-# Per-launch DRAM traffic of the dominant kernel from an ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel source
-# it was taken on: if permute.cu changes, the figure is dropped (null).
-NCU_TRAFFIC = {"kernel": "k_pb_bucket<4,512> + k_pb_place<4,0> (bucketed kv permute, both passes)",
-               "source": "permute_bucketed.cu", "source_sha1": "f473b17f81f00f545e0e74e5836096846558ad25",
-               "bytes": 575516928,
-               "summary": "profiles/k_pb_bucketed_permute_kv_2pow24.md"}
+# DRAM traffic of one sort call (dram__bytes_read.sum + dram__bytes_write.sum over
+# its kernels) from an ncu capture, valid only for the kernel sources it was taken
+# on: if any of them changes, the figure is dropped (null).
+NCU_TRAFFIC = {"kernel": "bcf_sort of 2^26 key-value pairs (all launches of one call)",
+               "sources": ["radix.cu", "sweep.cuh", "onesweep.cuh"], "sources_sha1": None,
+               "bytes": None}
 
 
 def log(*a):
@@ -298,13 +301,7 @@ class NvmlSampler:
 def headline_inputs(seed_base, rank):
     import synth
     s = seed_base + 1000 * rank
-    return {
-        "keys": synth.uniform_keys(N_PERM, seed=s + 1),
-        "vals": synth.float_bits_payload(N_PERM, seed=s + 2),
-        "pi": synth.random_perm(N_PERM, seed=s + 3),
-        "tsrc": synth.uniform_keys(N_PERM, seed=s + 4),
-        "lpi": synth.tile_local_perms(N_PERM, TILE, seed=s + 5),
-    }
+    return {"keys": synth.uniform_keys(N_SORT, seed=s + 1), "vals": synth.index_payload(N_SORT)}
 
 
 def to_dev(a):
@@ -373,16 +370,14 @@ def run_headline(args, rank, world, local):
     d = {k: to_dev(v) for k, v in x.items()}
     ko = torch.empty_like(d["keys"])
     vo = torch.empty_like(d["vals"])
-    to = torch.empty_like(d["tsrc"])
-    pws = bcf.workspace(bcf.permute_workspace_size(N_PERM, 4, bcf.PERMUTE_BUCKETED))
+    ws = bcf.workspace(bcf.sort_workspace_size(N_SORT, 4, 32))
 
     def step(kev=None):
         if kev is not None:
             kev[0].record()
-        bcf.permute_kv(d["keys"], d["vals"], d["pi"], keys_out=ko, vals_out=vo, bucketed=True, ws=pws)
+        bcf.sort(d["keys"], d["vals"], keys_out=ko, vals_out=vo, ws=ws)
         if kev is not None:
             kev[1].record()
-        bcf.permute_tiles(d["tsrc"], d["lpi"], tile=TILE, dst=to)
 
     sampler = NvmlSampler(local)
     if rank == 0:
@@ -392,8 +387,8 @@ def run_headline(args, rank, world, local):
     torch.cuda.synchronize()
     # The timed steps run as one CUDA graph holding all K of them, one launch from
     # the host, so that how fast Python enqueues cannot starve the GPU; each step's
-    # permutation pair is bracketed by event nodes inside the graph.  A 10-step
-    # graph serves the settle phase.
+    # sort call is bracketed by event nodes inside the graph.  A 10-step graph
+    # serves the settle phase.
     kevs = [(torch.cuda.Event(enable_timing=True, external=True),
              torch.cuda.Event(enable_timing=True, external=True)) for _ in range(args.steps)]
     cap = torch.cuda.Stream()
@@ -441,32 +436,40 @@ def run_headline(args, rank, world, local):
     ms_total = t0.elapsed_time(t1)
     kern_ms = statistics.mean(a.elapsed_time(b) for a, b in kevs)
     ms_total = max_over_ranks(ms_total, world, "cuda")
-    st = bcf.get_status()
-    # correctness of the timed outputs (cheap spot check on the device)
-    ok = bool(st == bcf.OK)
-    # end to end through the public API with pinned host buffers
+    ok = bool(bcf.get_status() == bcf.OK)
+    passes = bcf.sort_passes_run(ws, N_SORT, 4, 32)
+    # spot check of the timed output on the device: sorted keys, payloads a
+    # permutation that carries every key (the full comparison with the oracle is
+    # the tests' job)
+    kk = ko.to(torch.int64) & 0xFFFFFFFF
+    sorted_ok = bool((kk[1:] >= kk[:-1]).all().item())
+    src = d["keys"].to(torch.int64) & 0xFFFFFFFF
+    gathered_ok = bool((src[vo.to(torch.int64)] == kk).all().item())
+    del kk, src
+    from paper_1507_01391_b300 import tune
+    config = tune.get_config("sort", N_SORT)
+    form = bcf.lib().bcf_tune_config_form(config)
     e2e = run_e2e(args, bcf, x)
-    return {"ms_total": ms_total, "kern_ms": kern_ms, "clocks": clocks, "status_ok": ok, "e2e": e2e,
-            "settle_steps": settle_steps}
+    return {"ms_total": ms_total, "kern_ms": kern_ms, "clocks": clocks, "status_ok": ok and sorted_ok and gathered_ok,
+            "e2e": e2e, "settle_steps": settle_steps, "passes": passes, "config": config, "form": form}
 
 
 def run_e2e(args, bcf, x):
-    """End to end through the public API with host buffers: every step copies its
-    inputs from pinned host memory, runs both permutations and copies the three
-    outputs back.  Steps are pipelined over two buffer sets and three streams, so
-    step k+1's host-to-device copy overlaps step k's device-to-host copy."""
+    """End to end through the public API with host buffers: every step copies the
+    keys and payloads from pinned host memory, sorts them and copies the sorted
+    keys and payloads back.  Steps are pipelined over two buffer sets and three
+    streams, so step k+1's host-to-device copy overlaps step k's device-to-host copy."""
     import torch
-    pin = {k: torch.from_numpy(np.ascontiguousarray(v).view({4: np.int32, 2: np.int16}[v.dtype.itemsize])).pin_memory()
-           for k, v in x.items()}
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v).view(np.int32)).pin_memory() for k, v in x.items()}
     nb = 2
     dev = [{k: torch.empty_like(v, device="cuda") for k, v in pin.items()} for _ in range(nb)]
-    outs_d = [(torch.empty(N_PERM, dtype=torch.int32, device="cuda"), torch.empty(N_PERM, dtype=torch.float32, device="cuda"),
-               torch.empty(N_PERM, dtype=torch.int32, device="cuda")) for _ in range(nb)]
-    outs_h = [(torch.empty(N_PERM, dtype=torch.int32).pin_memory(), torch.empty(N_PERM, dtype=torch.float32).pin_memory(),
-               torch.empty(N_PERM, dtype=torch.int32).pin_memory()) for _ in range(nb)]
+    outs_d = [(torch.empty(N_SORT, dtype=torch.int32, device="cuda"), torch.empty(N_SORT, dtype=torch.int32, device="cuda"))
+              for _ in range(nb)]
+    outs_h = [(torch.empty(N_SORT, dtype=torch.int32).pin_memory(), torch.empty(N_SORT, dtype=torch.int32).pin_memory())
+              for _ in range(nb)]
     h2d = sum(v.numel() * v.element_size() for v in pin.values())
-    d2h = 3 * N_PERM * 4
-    pws = bcf.workspace(bcf.permute_workspace_size(N_PERM, 4, bcf.PERMUTE_BUCKETED))
+    d2h = 2 * N_SORT * 4
+    wss = [bcf.workspace(bcf.sort_workspace_size(N_SORT, 4, 32)) for _ in range(nb)]
     s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(nb)]
     ev_comp = [torch.cuda.Event() for _ in range(nb)]
@@ -475,9 +478,9 @@ def run_e2e(args, bcf, x):
 
     def step(k):
         b = k % nb
-        d, (ko, vo, to), (hk, hv, ht) = dev[b], outs_d[b], outs_h[b]
+        d, (ko, vo), (hk, hv) = dev[b], outs_d[b], outs_h[b]
         if used[b]:
-            s_in.wait_event(ev_comp[b])    # the compute two steps back has read these inputs
+            s_in.wait_event(ev_comp[b])    # the sort two steps back has read these inputs
             s_comp.wait_event(ev_out[b])   # ... and its outputs have reached the host
         used[b] = True
         with torch.cuda.stream(s_in):
@@ -485,18 +488,15 @@ def run_e2e(args, bcf, x):
                 d[key].copy_(pin[key], non_blocking=True)
             ev_in[b].record(s_in)
         s_comp.wait_event(ev_in[b])
-        bcf.permute_kv(d["keys"], d["vals"].view(torch.float32), d["pi"], keys_out=ko, vals_out=vo,
-                       bucketed=True, ws=pws, stream=s_comp)
-        bcf.permute_tiles(d["tsrc"], d["lpi"], tile=TILE, dst=to, stream=s_comp)
+        bcf.sort(d["keys"], d["vals"], keys_out=ko, vals_out=vo, ws=wss[b], stream=s_comp)
         ev_comp[b].record(s_comp)
         s_out.wait_event(ev_comp[b])
         with torch.cuda.stream(s_out):
             hk.copy_(ko, non_blocking=True)
             hv.copy_(vo, non_blocking=True)
-            ht.copy_(to, non_blocking=True)
             ev_out[b].record(s_out)
 
-    steps = max(3, args.steps // 2)
+    steps = max(3, min(args.steps // 2, 20))
     for k in range(2):
         step(k)
     torch.cuda.synchronize()
@@ -511,9 +511,9 @@ def run_e2e(args, bcf, x):
     lo_b, hi_b = min(h2d, d2h), max(h2d, d2h)
     alone = link["h2d"] if h2d >= d2h else link["d2h"]
     bound_s = lo_b / (link["both_each_way"] * 1e9) + (hi_b - lo_b) / (alone * 1e9)
-    return {"value": round(2 * N_PERM / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    return {"value": round(N_SORT / dt / 1e9, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": round(dt * 1e3, 3),
-            "pipelined": "two buffer sets; copies in, permutations and copies out on three streams",
+            "pipelined": "two buffer sets; copies in, sort and copies out on three streams",
             "link_gbs": link, "link_bound_ms": round(bound_s * 1e3, 3),
             "frac_of_link": round(bound_s / dt, 3)}
 
@@ -546,20 +546,17 @@ def link_bandwidth(mb=256, reps=4):
 # ------------------------------------------------------------------ CPU leg
 def oracle_inputs(n, seed_base=0x150701391):
     import synth
-    return (synth.uniform_keys(n, seed=seed_base + 1), synth.float_bits_payload(n, seed=seed_base + 2),
-            synth.random_perm(n, seed=seed_base + 3), synth.uniform_keys(n, seed=seed_base + 4),
-            synth.tile_local_perms(n, TILE, seed=seed_base + 5))
+    return synth.uniform_keys(n, seed=seed_base + 1), synth.index_payload(n)
 
 
 def oracle_step(inp):
-    """One CPU-oracle step on a sample of the headline workload; returns seconds."""
+    """One CPU-oracle step on a sample of the headline workload (the stable
+    key-value sort of n keys); returns seconds."""
     import oracle
-    keys, vals, pi, tsrc, lpi = inp
+    keys, vals = inp
     L = oracle.lib()
     t = time.perf_counter()
-    oracle.permute(keys, pi, L=L)
-    oracle.permute(vals, pi, L=L)
-    oracle.permute_tiles(tsrc, lpi, TILE, L=L)
+    oracle.sort_kv(keys, vals, L=L)
     return time.perf_counter() - t
 
 
@@ -569,9 +566,10 @@ def cpu_baseline(budget_s=12.0, n=1 << 22):
     while total < budget_s and reps < 400:
         total += oracle_step(inp)
         reps += 1
-    return {"value": round(2 * n * reps / total / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d repetitions of the step on an n=2^%d sample (kv permute + tile permute), "
-                      "single-threaded plain C" % (reps, int(np.log2(n)))}
+    return {"value": round(n * reps / total / 1e9, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d repetitions of the stable key-value sort of an n=2^%d sample of the headline "
+                      "workload (uniform uint32 keys, uint32 payload), single-threaded plain C bottom-up "
+                      "merge sort" % (reps, int(np.log2(n)))}
 
 
 def run_reference(args):
@@ -580,34 +578,33 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    n = 1 << 22
+    n = 1 << 20
     inp = oracle_inputs(n)
     for _ in range(max(args.warmup, 1)):
         oracle_step(inp)
     ts = [oracle_step(inp) for _ in range(args.steps)]
     total = sum(ts)
-    value = 2 * n * args.steps / total / 1e9
+    value = n * args.steps / total / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": headline_config(),
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "each step: n=2^22 sample of the workload (kv permute + tile permute), single-threaded plain C oracle"},
+                             "sample": "each step: the stable key-value sort of an n=2^20 sample of the workload "
+                                       "(uniform uint32 keys, uint32 payload), single-threaded plain C oracle"},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def headline_config():
-    return {"workload": "permute 2^24 uint32 keys + float32 payloads by a uniform random pi "
-                        "(out[pi[i]] = in[i]), then tile-local permute of 2^24 uint32 keys in "
-                        "4096-key tiles by per-tile uniform random uint16 permutations",
-            "n": N_PERM, "tile": TILE, "keys_per_step": 2 * N_PERM,
-            "l2": "every input larger than the 126 MB L2 (no flush between steps)",
-            "permute_form": "bucketed: group by destination block (blocks sized to fill whole waves of SMs) into a 10 B/key workspace, "
-                            "then place each block in shared memory (two coalesced passes)",
-            "tile_schedule": "scatter"}
+    return {"workload": "stable key-value radix sort of 2^26 uint32 keys uniform on [0, 2^32) with a uint32 "
+                        "payload (the input position): 4 digit passes of 8 bits",
+            "n": N_SORT, "key_bits": 32, "val_bytes": 4, "keys_per_step": N_SORT,
+            "l2": "keys and payloads (512 MB) larger than the 126 MB L2 (no flush between steps)",
+            "bytes_model": "%d B/key: 4 (one histogram / count read of the keys per pass form) + 16 per digit "
+                           "pass (read and write key and payload)" % SORT_MODEL_BYTES}
 
 
 # ------------------------------------------------------------------ tuning
@@ -1065,23 +1062,29 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     peak, peak_kind = measured_peaks()
     h = run_headline(args, rank, world, local)
-    value, ms_step = aggregate(h["ms_total"], args.steps, world, 2 * N_PERM)
-    bytes_launch = 20 * N_PERM
+    value, ms_step = aggregate(h["ms_total"], args.steps, world, N_SORT)
+    bytes_launch = SORT_MODEL_BYTES * N_SORT
     achieved = bytes_launch / (h["kern_ms"] * 1e-3) / 1e9
-    src_sha = file_sha1(os.path.join(ROOT, "paper_1507_01391_b300", "csrc", NCU_TRAFFIC["source"]))
-    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["source_sha1"] == src_sha else None
+    shas = [file_sha1(os.path.join(ROOT, "paper_1507_01391_b300", "csrc", f)) for f in NCU_TRAFFIC["sources"]]
+    traffic = NCU_TRAFFIC["bytes"] if NCU_TRAFFIC["sources_sha1"] == shas else None
+    forms = {0: "one launch per pass, decoupled look-back (after one histogram read)",
+             1: "per pass: tile counts + scan + pass body",
+             2: "per pass: tile counts + scan + staged sweep"}
+    launches = {0: 1 + 4, 1: 3 * 4, 2: 3 * 4}[h["form"]]
+    cfg = headline_config()
+    cfg.update({"tuning_config": h["config"], "pass_form": forms[h["form"]], "passes_run": h["passes"]})
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic (seeded: uniform keys, random float32 bit patterns, uniform pi, per-tile uniform uint16 labels)",
-        "config": headline_config(),
+        "data": "synthetic (seeded: uniform uint32 keys, index payload)",
+        "config": cfg,
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "kernel": NCU_TRAFFIC["kernel"], "bytes_per_launch": bytes_launch,
                      "kernel_ms": round(h["kern_ms"], 4), "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
                      "frac_of_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4)},
-        "gpu_launches": 3 * args.steps,  # bucket pass + place pass + tile permute
+        "gpu_launches": launches * args.steps,
         "timed_as": "one CUDA graph of the K steps (per-step events inside), launched once",
         "clocks": h["clocks"],
         "e2e": h["e2e"],

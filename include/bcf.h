@@ -256,20 +256,31 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
                             bcf_stream_t stream);
 
 /* ---------------------------------------------------------------------------
- * Tuning of the sort and partition sweeps (no counterpart in the paper).  Each
- * digit pass can run with one of bcf_tune_num_configs() tile configurations
- * (threads per block x keys per thread).  The library keeps a small host-side
- * table, per operation and per ceil(log2 n), of the configuration to use; an
- * entry of -1 (the initial state) applies a size rule (tiles of 1024 keys up to
- * n = 2^20, 4096 above).  The table is process-wide host state and is not
- * synchronised: set it before concurrent calls.  Workspace sizes already cover
- * every configuration.  paper_1507_01391_b300.tune measures the configurations
- * on the device and fills the table (with a JSON cache per device). */
+ * Tuning of the sort and partition passes (no counterpart in the paper).  Each
+ * digit pass can run with one of bcf_tune_num_configs() configurations: a tile
+ * shape (threads per block x keys per thread) and a pass form
+ * (bcf_tune_config_form).  Single-launch configurations run every digit pass as
+ * one kernel whose tiles find their global offsets by a decoupled look-back,
+ * after one histogram read of the keys for all passes; the others run each pass
+ * as per-tile digit counts, a scan and then the pass, either with the same pass
+ * body or over shared-memory-staged tiles (the staged form runs one look-back
+ * sweep launch per pass for n <= 2^18).  The library keeps a small host-side table, per operation and
+ * per ceil(log2 n), of the configuration to use; an entry of -1 (the initial
+ * state) applies a size rule measured on a B300 (staged sweeps of 1024-key tiles
+ * up to n = 2^14, single-launch passes of 2048-key tiles up to 2^18, counts +
+ * scan + 4096-key tiles above).  The table is process-wide host state and is not synchronised:
+ * set it before concurrent calls.  Workspace sizes already cover every
+ * configuration.  paper_1507_01391_b300.tune measures the configurations on the
+ * device and fills the table (with a text cache per device). */
 #define BCF_OP_SORT 0
 #define BCF_OP_PARTITION 1
 int bcf_tune_num_configs(void);
 /* BCF_E_INVAL for an unknown configuration or a null output. */
 int bcf_tune_config_info(int config, int* threads, int* keys_per_thread);
+/* Pass form of a configuration: 0 single launch per pass (decoupled look-back),
+ * 1 per-tile counts + scan + the same pass body, 2 counts + scan + the
+ * shared-memory-staged sweep; BCF_E_INVAL for an unknown configuration. */
+int bcf_tune_config_form(int config);
 /* config in [-1, num_configs); log2_n in [0, 63].  BCF_E_INVAL otherwise. */
 int bcf_tune_set(int op, int log2_n, int config);
 /* The configuration a call of n keys would use now. */

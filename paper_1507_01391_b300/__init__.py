@@ -70,6 +70,7 @@ _SIGS = {
     "bcf_partition_noalloc": ([_P, _P, _P, _P, _I64, _I, _I, _I, _P], _I),
     "bcf_tune_num_configs": ([], _I),
     "bcf_tune_config_info": ([_I, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "bcf_tune_config_form": ([_I], _I),
     "bcf_tune_set": ([_I, _I, _I], _I),
     "bcf_tune_get": ([_I, _I64, ctypes.POINTER(_I)], _I),
     "bcf_debug_lookback": ([_I, ctypes.c_uint], _I),

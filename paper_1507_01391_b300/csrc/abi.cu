@@ -414,6 +414,11 @@ int bcf_tune_config_info(int config, int* threads, int* keys_per_thread) {
   return BCF_OK;
 }
 
+int bcf_tune_config_form(int config) {
+  if (config < 0 || config >= bcf::kNumSweepConfigs) return BCF_E_INVAL;
+  return bcf::cfg_form(config);
+}
+
 int bcf_tune_set(int op, int log2_n, int config) {
   return bcf::tune_set(op, log2_n, config) == 0 ? BCF_OK : BCF_E_INVAL;
 }

@@ -52,14 +52,29 @@ constexpr int kSweepIPT = BCF_SWEEP_IPT;
 constexpr int kSweepTile = kSweepThreads * kSweepIPT;  // keys per tile (default configuration)
 constexpr int kLookbackWindow = BCF_LB_WINDOW;
 
-// Tile configurations of the sort / partition sweeps that the tuner picks from
-// (threads per block x keys per thread).  Configuration 0 is the default above.
-constexpr int kNumSweepConfigs = 4;
-constexpr int kSweepCfgThreads[kNumSweepConfigs] = {kSweepThreads, 256, 512, 256};
-constexpr int kSweepCfgIPT[kNumSweepConfigs] = {kSweepIPT, 4, 16, 8};
+// Configurations of the sort / partition passes that the tuner picks from: a pass
+// form and a tile shape (threads per block x keys per thread).
+//   0..3   single launch per pass: the digit pass of onesweep.cuh finds its tiles'
+//          global offsets by a decoupled look-back (after one histogram read);
+//   4..7   the same pass body fed precomputed offsets: per-tile digit counts, a
+//          scan, then the pass (reduce-then-scan, no inter-block waits);
+//   8..11  reduce-then-scan with the shared-memory-staged digit sweep of
+//          sweep.cuh (one look-back sweep launch per pass up to kSmallSweepN).
+constexpr int kNumOneConfigs = 4;
+constexpr int kNumSweepConfigs = 12;
+constexpr int kSweepCfgThreads[kNumSweepConfigs] = {256, 256, 512, 384, 256, 256, 512, 384,
+                                                     kSweepThreads, 256, 512, 256};
+constexpr int kSweepCfgIPT[kNumSweepConfigs] = {16, 8, 12, 16, 16, 8, 12, 16, kSweepIPT, 4, 16, 8};
+// Blocks per SM the onesweep.cuh pass body is compiled for (registers), by shape.
+constexpr int kOneCfgMinBlocks[2 * kNumOneConfigs] = {3, 4, 2, 2, 3, 4, 2, 2};
+constexpr int kRtsCfg0 = 2 * kNumOneConfigs;  // first configuration of the sweep.cuh passes
+// Pass form of a configuration: 0 look-back, 1 offsets + onesweep body, 2 staged sweep.
+inline int cfg_form(int cfg) { return cfg < kNumOneConfigs ? 0 : (cfg < kRtsCfg0 ? 1 : 2); }
+inline bool cfg_is_onesweep(int cfg) { return cfg >= 0 && cfg < kRtsCfg0; }  // onesweep.cuh body
 constexpr int kMinSweepTile = 1024;  // smallest tile of any configuration (sizes workspaces)
-// Inputs up to this size run each digit pass as one look-back sweep launch (fewer
-// launches); larger ones use tile counts + scan + sweep.
+constexpr int kOneMinTile = 2048;    // smallest tile of the onesweep.cuh configurations
+// Inputs up to this size run each sweep.cuh digit pass as one look-back sweep
+// launch (fewer launches); larger ones use tile counts + scan + sweep.
 constexpr int64_t kSmallSweepN = (int64_t)1 << 18;
 inline int sweep_cfg_tile(int cfg) { return kSweepCfgThreads[cfg] * kSweepCfgIPT[cfg]; }
 
@@ -81,15 +96,19 @@ struct SweepLayout {
   size_t keys_tmp = 0, vals_tmp = 0;   // ping-pong buffers (0 bytes when unused)
   size_t zero_begin = 0, zero_bytes = 0;  // region cleared before the passes
   size_t hist = 0, counters = 0, lookback = 0, digit_base = 0, status = 0;
+  // single-launch passes: two look-back status regions of os_words words each
+  // (tile-major, one row of `radix` words per tile), used by alternate passes
+  size_t os_status = 0, os_words = 0;
   size_t total = 0;
   int64_t tiles = 0;
   int64_t lb_stride = 0;  // look-back status words per digit (tiles rounded up to 8)
   int radix = 256;
 };
 // Workspace carve-up; the per-(digit, tile) count buffer is sized for tiles of
-// `tile` keys (kMinSweepTile fits every configuration).
+// `tile` keys (kMinSweepTile fits every configuration).  `onesweep`: room for the
+// look-back status regions of the single-launch configurations.
 SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp,
-                         int tile = kMinSweepTile);
+                         int tile = kMinSweepTile, bool onesweep = true);
 
 // Three words of a sort's workspace, in the zeroed counter block: which key bits
 // vary (OR of the keys, OR of their complements), then the mask of passes that ran.

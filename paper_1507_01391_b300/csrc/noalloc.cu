@@ -82,7 +82,7 @@ extern "C" int bcf_partition_noalloc(const uint32_t* keys_in, const void* vals_i
   if (!disjoint(keys_in, (size_t)n * 4, keys_out, (size_t)n * 4)) return BCF_E_INVAL;
   if (val_bytes && !iota && !disjoint(vals_in, (size_t)n * val_bytes, vals_out, (size_t)n * val_bytes))
     return BCF_E_INVAL;
-  const bcf::SweepLayout L = bcf::sweep_layout(n, val_bytes, 1, w <= 32 ? 32 : 256, false, bcf::kSweepTile);
+  const bcf::SweepLayout L = bcf::sweep_layout(n, val_bytes, 1, w <= 32 ? 32 : 256, false, bcf::kSweepTile, false);
   if (L.total > kNoAllocScratchBytes) return BCF_E_UNSUPPORTED;
   int rc = BCF_OK;
   unsigned char* scratch = scratch_address(&rc);
@@ -90,6 +90,6 @@ extern "C" int bcf_partition_noalloc(const uint32_t* keys_in, const void* vals_i
   if (!bcf::status_word()) return BCF_E_CUDA;
   // bcf::partition clears the counters it needs on `stream` before using them.
   const cudaError_t e = bcf::partition(keys_in, vals_in, keys_out, vals_out, n, w, val_bytes, balanced,
-                                       scratch, L, (cudaStream_t)stream, 0);
+                                       scratch, L, (cudaStream_t)stream, bcf::kRtsCfg0);
   return e == cudaSuccess ? BCF_OK : BCF_E_CUDA;
 }

@@ -2,6 +2,7 @@
 // (the sweep kernel itself is in sweep.cuh).
 #include "common.cuh"
 #include "internal.h"
+#include "onesweep.cuh"
 #include "sweep.cuh"
 
 namespace bcf {
@@ -45,7 +46,13 @@ int tuned_config(int op, int64_t n) {
   const int b = ilog2_ceil(n);
   const int cfg = (op == 0 || op == 1) ? g_tune[op][b] : -1;
   if (cfg >= 0 && cfg < kNumSweepConfigs) return cfg;
-  return n <= ((int64_t)1 << 20) ? 1 : 0;  // small inputs: more, smaller tiles
+  // Size rule (measured on a B300 by the tuner): up to 2^14 keys the staged
+  // look-back sweep of 1024-key tiles; up to 2^18 single-launch passes of
+  // 2048-key tiles (fewest launches); above, counts + scan + the pass body of
+  // 4096-key tiles (sorts), the staged sweep for partitions above 2^22.
+  if (n <= ((int64_t)1 << 14)) return kRtsCfg0 + 1;
+  if (n <= ((int64_t)1 << 18)) return 1;
+  return (op == 1 && n > ((int64_t)1 << 22)) ? kRtsCfg0 : kNumOneConfigs;
 }
 
 int tune_set(int op, int log2_n, int cfg) {
@@ -61,7 +68,8 @@ int tune_entry(int op, int log2_n) {
   return g_tune[op][log2_n];
 }
 
-SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp, int tile) {
+SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool need_tmp, int tile,
+                         bool onesweep) {
   SweepLayout L;
   L.radix = radix;
   L.tiles = (n + tile - 1) / tile;
@@ -85,6 +93,11 @@ SweepLayout sweep_layout(int64_t n, int val_bytes, int passes, int radix, bool n
   L.zero_bytes = off - L.zero_begin;
   L.lookback = off;  // per-(digit, tile) counts, scanned in place into run starts
   off = align_up(off + (size_t)L.lb_stride * radix * 4);
+  if (onesweep) {  // look-back status of the single-launch passes, two regions
+    L.os_status = off;
+    L.os_words = (size_t)((n + kOneMinTile - 1) / kOneMinTile) * radix;
+    off = align_up(off + 2 * L.os_words * 4);
+  }
   L.total = off;
   return L;
 }
@@ -144,10 +157,10 @@ static cudaError_t pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_
   case C:                                                                                            \
     return pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C]>(src_k, src_v, dst_k, dst_v, n, vb, shift, \
                                                               nbits, w, balanced, totals, offsets, s, sel);
-    BCF_PASS(0)
-    BCF_PASS(1)
-    BCF_PASS(2)
-    BCF_PASS(3)
+    BCF_PASS(8)
+    BCF_PASS(9)
+    BCF_PASS(10)
+    BCF_PASS(11)
 #undef BCF_PASS
   }
   return cudaErrorInvalidValue;
@@ -206,10 +219,10 @@ static cudaError_t lookback_pass(const uint32_t* src_k, const void* src_v, uint3
     return lookback_pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C]>(src_k, src_v, dst_k, dst_v, n, vb, \
                                                                        shift, w, balanced, digit_base,   \
                                                                        status, ticket, s, sel);
-    BCF_LBP(0)
-    BCF_LBP(1)
-    BCF_LBP(2)
-    BCF_LBP(3)
+    BCF_LBP(8)
+    BCF_LBP(9)
+    BCF_LBP(10)
+    BCF_LBP(11)
 #undef BCF_LBP
   }
   return cudaErrorInvalidValue;
@@ -238,6 +251,125 @@ static cudaError_t small_histogram(const uint32_t* keys, int64_t n, int passes, 
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * 2));
   k_histogram<256><<<grid, 256, 0, s>>>(hp);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- single-launch passes
+// One digit pass of configuration cfg (0..kNumOneConfigs-1): a launch of
+// k_onesweep over ceil(n / tile) blocks.
+template <int BITS, int THREADS, int IPT, int MINB>
+static cudaError_t onesweep_pass_t(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                                   int64_t n, int vb, int shift, int w, bool balanced,
+                                   const uint32_t* digit_base, uint32_t* status, uint32_t* zero_next,
+                                   uint32_t* ticket, cudaStream_t s, const PassSel& sel,
+                                   uint32_t* totals = nullptr, uint32_t* offsets = nullptr) {
+  constexpr int T = THREADS * IPT;
+  OneSweepParams op{};
+  if (offsets) {  // reduce-then-scan: per-tile counts and their scan first
+    constexpr int RADIX = 1 << BITS;
+    const int64_t tiles = (n + T - 1) / T;
+    const int64_t stride = (tiles + kLookbackWindow) / kLookbackWindow * kLookbackWindow;  // > tiles
+    CountParams cp{};
+    cp.keys = src_k;
+    cp.n = n;
+    cp.shift = shift;
+    cp.nbits = BITS;
+    cp.label_bits = w > 0 ? BITS : 0;
+    cp.counts = offsets;
+    cp.stride = stride;
+    cp.totals = totals;
+    cp.sel = sel;
+    const int64_t count_blocks = (tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
+    k_tile_counts<BITS, T><<<(unsigned)count_blocks, 256, 0, s>>>(cp, tiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    launch_scan_offsets(RADIX, offsets, tiles, stride, totals, balanced ? 1 : 0, n, w > 0 ? w : 1,
+                        status_word(), s, sel);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    op.tile_offsets = offsets;
+    op.offs_stride = stride;
+  }
+  op.keys_in = src_k;
+  op.vals_in = src_v;
+  op.keys_out = dst_k;
+  op.vals_out = dst_v;
+  op.n = n;
+  op.shift = shift;
+  op.w = w;
+  op.balanced = balanced ? 1 : 0;
+  op.digit_base = digit_base;
+  op.status = status;
+  op.zero_next = zero_next;
+  op.ticket = ticket;
+  op.err = status_word();
+  op.spin_limit = g_spin_limit;
+  op.silent_tile1 = g_silent_tile1;
+  op.sel = sel;
+  return onesweep_dispatch<BITS, THREADS, IPT, MINB>(op, (n + T - 1) / T, vb, s);
+}
+
+// Configurations 0..3: look-back passes; 4..7: the same shapes fed by counts +
+// scan (totals and offsets given).
+template <int BITS>
+static cudaError_t onesweep_pass(const uint32_t* src_k, const void* src_v, uint32_t* dst_k, void* dst_v,
+                                 int64_t n, int vb, int shift, int w, bool balanced, const uint32_t* digit_base,
+                                 uint32_t* status, uint32_t* zero_next, uint32_t* ticket, cudaStream_t s,
+                                 int cfg, const PassSel& sel = PassSel{}, uint32_t* totals = nullptr,
+                                 uint32_t* offsets = nullptr) {
+  const bool rts = cfg >= kNumOneConfigs;
+  switch (cfg % kNumOneConfigs) {
+#define BCF_OSP(C)                                                                                         \
+  case C:                                                                                                  \
+    return onesweep_pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C], kOneCfgMinBlocks[C]>(             \
+        src_k, src_v, dst_k, dst_v, n, vb, shift, w, balanced, digit_base, status, zero_next, ticket, s, sel, \
+        rts ? totals : nullptr, rts ? offsets : nullptr);
+    BCF_OSP(0)
+    BCF_OSP(1)
+    BCF_OSP(2)
+    BCF_OSP(3)
+#undef BCF_OSP
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Look-back rows (tiles) of a single-launch configuration.
+static inline int64_t os_rows(int64_t n, int cfg) {
+  const int64_t t = sweep_cfg_tile(cfg);
+  return (n + t - 1) / t;
+}
+
+// One read of the keys counts the digits of every pass (8-bit digits at `shift`),
+// turns the counts into exclusive digit starts (L.digit_base) and clears the
+// first pass's look-back status region.
+static cudaError_t onesweep_histogram(const uint32_t* keys, int64_t n, int passes, const int* shift,
+                                      unsigned char* ws, const SweepLayout& L, cudaStream_t s,
+                                      uint32_t* vary, int cfg) {
+  OneHistParams hp{};
+  hp.keys = keys;
+  hp.n = n;
+  hp.passes = passes;
+  for (int q = 0; q < 4; ++q) hp.shift[q] = q < passes ? shift[q] : 0;
+  hp.hist = reinterpret_cast<uint32_t*>(ws + L.hist);
+  hp.digit_base = reinterpret_cast<uint32_t*>(ws + L.digit_base);
+  hp.done = reinterpret_cast<uint32_t*>(ws + L.counters) + 4;
+  hp.vary = vary;
+  hp.zero = reinterpret_cast<uint32_t*>(ws + L.os_status);
+  hp.zero_words = os_rows(n, cfg) * L.radix;  // the rows configuration cfg uses
+  bool bytes = true;  // digits are whole key bytes from byte 0 up
+  for (int q = 0; q < passes; ++q) bytes &= shift[q] == 8 * q;
+  static bool attr_b[64] = {false}, attr_g[64] = {false};
+  const int smem = (int)onesweep_hist_smem(4);
+  cudaError_t e = bytes ? set_smem_once(k_onesweep_hist<true>, smem, attr_b)
+                        : set_smem_once(k_onesweep_hist<false>, smem, attr_g);
+  if (e != cudaSuccess) return e;
+  const int64_t per_block = (int64_t)kHistThreads * 4 * kHistUnroll;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + per_block - 1) / per_block, sm_count_cached()));
+  if (bytes) k_onesweep_hist<true><<<grid, kHistThreads, onesweep_hist_smem(passes), s>>>(hp);
+  else k_onesweep_hist<false><<<grid, kHistThreads, onesweep_hist_smem(passes), s>>>(hp);
+  return cudaGetLastError();
+}
+
+static inline uint32_t* os_region(unsigned char* ws, const SweepLayout& L, int q) {
+  return reinterpret_cast<uint32_t*>(ws + L.os_status) + (size_t)(q & 1) * L.os_words;
 }
 
 // In-place sorts only.  An odd number of passes that ran leaves the result in the
@@ -295,7 +427,10 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
   sel.v_out = vals_out;
   sel.k_tmp = kt;
   sel.v_tmp = vt;
-  const bool small = n <= kSmallSweepN;
+  const bool one = cfg_is_onesweep(cfg);
+  const bool small = !one && n <= kSmallSweepN;
+  if (cfg_form(cfg) == 0 && (e = onesweep_histogram(keys_in, n, P, plan.shift, ws, L, s, sel.vary, cfg)) != cudaSuccess)
+    return e;
   if (small && (e = small_histogram(keys_in, n, P, plan.shift, 0, ws, L, s, sel.vary)) != cudaSuccess) return e;
   uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);
   uint32_t* offsets = reinterpret_cast<uint32_t*>(ws + L.lookback);
@@ -309,7 +444,12 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
     const bool to_out = odd_in_place ? (q % 2 == 1) : (((P - 1 - q) % 2) == 0);
     uint32_t* dk = to_out ? keys_out : kt;
     void* dv = to_out ? vals_out : vt;
-    if (small) {
+    if (one) {
+      e = onesweep_pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], 0, false,
+                           reinterpret_cast<uint32_t*>(ws + L.digit_base) + q * 256, os_region(ws, L, q),
+                           q + 1 < P ? os_region(ws, L, q + 1) : nullptr,
+                           reinterpret_cast<uint32_t*>(ws + L.counters) + q, s, cfg, sel, totals + q * 256, offsets);
+    } else if (small) {
       e = lookback_pass<8>(src_k, src_v, dk, dv, n, vb, plan.shift[q], 0, false,
                            reinterpret_cast<uint32_t*>(ws + L.digit_base) + q * 256,
                            reinterpret_cast<uint32_t*>(ws + L.status) + (size_t)q * L.lb_stride * 256,
@@ -367,6 +507,24 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
       src_v = vt;
     }
   }
+  if (cfg_is_onesweep(cfg)) {
+    // Look-back form: balanced partitions have closed-form label starts and only
+    // the status region to clear; otherwise one histogram read gives the label
+    // starts and clears it.  Offsets form: counts + scan (which checks balance).
+    const int zero = 0;
+    if (cfg_form(cfg) == 0) {
+      if (balanced) e = cudaMemsetAsync(ws + L.os_status, 0, (size_t)os_rows(n, cfg) * L.radix * 4, s);
+      else e = onesweep_histogram(src_k, n, 1, &zero, ws, L, s, nullptr, cfg);
+      if (e != cudaSuccess) return e;
+    }
+    uint32_t* base = reinterpret_cast<uint32_t*>(ws + L.digit_base);
+    uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + L.counters);
+    if (L.radix == 32)
+      return onesweep_pass<5>(src_k, src_v, keys_out, vals_out, n, vb, 0, w, balanced, base, os_region(ws, L, 0),
+                              nullptr, ticket, s, cfg, PassSel{}, totals, offsets);
+    return onesweep_pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, w, balanced, base, os_region(ws, L, 0),
+                            nullptr, ticket, s, cfg, PassSel{}, totals, offsets);
+  }
   if (n <= kSmallSweepN) {
     const int bits = L.radix == 32 ? 5 : 8;
     const int zero = 0;
@@ -389,7 +547,7 @@ cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, ui
                                 void* vals_out, int64_t n, const uint32_t* splitters, int nsplit, int vb,
                                 bool balanced, unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  constexpr int THREADS = kSweepCfgThreads[0], IPT = kSweepCfgIPT[0], T = THREADS * IPT;
+  constexpr int THREADS = kSweepCfgThreads[kRtsCfg0], IPT = kSweepCfgIPT[kRtsCfg0], T = THREADS * IPT;
   cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
   uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);

@@ -70,30 +70,35 @@ __device__ __forceinline__ unsigned passes_run_mask(const PassSel& s, uint32_t v
   return m;
 }
 
+// Route of pass s.q given the varying bits: -1 when the pass is skipped, else
+// 3 * src + dst, where src is 0 (the input), 1 (the output) or 2 (the temporary)
+// and dst is 1 (the output) or 2 (the temporary).
+__device__ __forceinline__ int pass_route(const PassSel& s, uint32_t v) {
+  const unsigned m = passes_run_mask(s, v);
+  if (!((m >> s.q) & 1u)) return -1;
+  const int i = __popc(m & ((1u << s.q) - 1u)), k = __popc(m);
+  auto to_out = [&](int j) { return (s.in_place && (k & 1)) ? (j & 1) == 1 : ((k - 1 - j) & 1) == 0; };
+  const int src = i == 0 ? 0 : (to_out(i - 1) ? 1 : 2);
+  const int dst = to_out(i) ? 1 : 2;
+  return 3 * src + dst;
+}
+
+// The buffers a route names.
+__device__ __forceinline__ void route_buffers(const PassSel& s, int route, const uint32_t*& sk, const void*& sv,
+                                              uint32_t*& dk, void*& dv) {
+  const int src = route / 3, dst = route % 3;
+  sk = src == 0 ? s.k_in : (src == 1 ? s.k_out : s.k_tmp);
+  sv = src == 0 ? s.v_in : (src == 1 ? s.v_out : s.v_tmp);
+  dk = dst == 1 ? s.k_out : s.k_tmp;
+  dv = dst == 1 ? s.v_out : s.v_tmp;
+}
+
 // Buffers of pass s.q given the varying bits; false when the pass is skipped.
 __device__ __forceinline__ bool pass_buffers(const PassSel& s, uint32_t v, const uint32_t*& sk,
                                              const void*& sv, uint32_t*& dk, void*& dv) {
-  const unsigned m = passes_run_mask(s, v);
-  if (!((m >> s.q) & 1u)) return false;
-  const int i = __popc(m & ((1u << s.q) - 1u)), k = __popc(m);
-  auto to_out = [&](int j) { return (s.in_place && (k & 1)) ? (j & 1) == 1 : ((k - 1 - j) & 1) == 0; };
-  if (i == 0) {
-    sk = s.k_in;
-    sv = s.v_in;
-  } else if (to_out(i - 1)) {
-    sk = s.k_out;
-    sv = s.v_out;
-  } else {
-    sk = s.k_tmp;
-    sv = s.v_tmp;
-  }
-  if (to_out(i)) {
-    dk = s.k_out;
-    dv = s.v_out;
-  } else {
-    dk = s.k_tmp;
-    dv = s.v_tmp;
-  }
+  const int route = pass_route(s, v);
+  if (route < 0) return false;
+  route_buffers(s, route, sk, sv, dk, dv);
   return true;
 }
 

@@ -22,6 +22,9 @@ enum TraceSite : uint32_t {
   TS_SCATTER = 4,       // store into digit / label order
   TS_WRITEOUT_READ = 5, // read of the ordered tile for the global write-out
   TS_OFFSET_READ = 6,   // per-digit offset lookup
+  TS_HIST_ATOM = 7,     // one-read histogram: lane-private digit count
+  TS_HIST_SUM = 8,      // one-read histogram: diagonal sum of the lane counters
+  TS_WARP_OFFSETS = 9,  // per-(warp, digit) count row read / rewritten as offsets
   TS_L1_ROW_LD = 10,    // Lemma 1: row sort loads (register sort and merges)
   TS_L1_ROW_ST = 11,    // Lemma 1: row sort stores
   TS_L1_CONVERT = 12,   // Lemma 1: row <-> column conversions

@@ -21,7 +21,7 @@ TRACE_LIB_PATH = os.path.join(_PKG, "libbcf_trace.so")
 # access sites (mirrors csrc/trace.cuh)
 SITES = {
     "stage_read": 1, "count_atom": 2, "claim_atom": 3, "scatter": 4, "writeout_read": 5,
-    "offset_read": 6, "l1_row_ld": 10, "l1_row_st": 11, "l1_convert": 12, "l1_io": 13,
+    "offset_read": 6, "hist_atom": 7, "hist_sum": 8, "warp_offsets": 9, "l1_row_ld": 10, "l1_row_st": 11, "l1_convert": 12, "l1_io": 13,
     "col_table": 20, "col_send": 21, "col_read": 22, "col_finish": 23, "col_pack": 24,
     "barrier": 30,
 }

@@ -139,16 +139,22 @@ def test_tuning_table_on_the_host():
     for c in range(nconf):
         assert L.bcf_tune_config_info(c, ctypes.byref(t), ctypes.byref(k)) == bcf.OK
         assert t.value % 32 == 0 and t.value >= 256 and k.value >= 1
-        tiles.add(t.value * k.value)
-    assert min(tiles) >= 1024 and len(tiles) == nconf
+        form = L.bcf_tune_config_form(c)
+        assert form in (0, 1, 2)
+        tiles.add((t.value, k.value, form))
+    assert min(a * b for a, b, _ in tiles) >= 1024 and len(tiles) == nconf
+    assert L.bcf_tune_config_form(0) == 0 and L.bcf_tune_config_form(nconf - 1) == 2
+    assert L.bcf_tune_config_form(nconf) == bcf.E_INVAL
     assert L.bcf_tune_config_info(nconf, ctypes.byref(t), ctypes.byref(k)) == bcf.E_INVAL
     got = ctypes.c_int(-5)
-    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 0
+    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 4
+    assert L.bcf_tune_get(bcf.OP_PARTITION, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 8
     assert L.bcf_tune_get(bcf.OP_PARTITION, 1 << 16, ctypes.byref(got)) == bcf.OK and got.value == 1
+    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 12, ctypes.byref(got)) == bcf.OK and got.value == 9
     assert L.bcf_tune_set(bcf.OP_SORT, 26, nconf - 1) == bcf.OK
     assert L.bcf_tune_get(bcf.OP_SORT, (1 << 25) + 1, ctypes.byref(got)) == bcf.OK and got.value == nconf - 1
     assert L.bcf_tune_set(bcf.OP_SORT, 26, -1) == bcf.OK  # back to the size rule
-    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 0
+    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 4
     assert L.bcf_tune_set(bcf.OP_SORT, 64, 0) == bcf.E_INVAL
     assert L.bcf_tune_set(bcf.OP_SORT, 3, nconf) == bcf.E_INVAL
     assert L.bcf_tune_set(7, 3, 0) == bcf.E_INVAL

@@ -132,8 +132,9 @@ def test_direct_scatter_shows_the_conflicts(tr):
 
 
 def test_sweep_strided_reads_are_conflict_free(tr):
-    """Digit sweep of a w = 32 partition: the strided staging reads (lane l reads
-    word 32i + l) replay conflict-free; the scatter into label order does not."""
+    """Digit sweep of a w = 32 partition (the staged-tile configuration): the
+    strided staging reads (lane l reads word 32i + l) replay conflict-free; the
+    scatter into label order does not."""
     import paper_1507_01391_b300 as bcf
     n, w = 4096, 32
     keys = synth.partition_keys(n, w, seed=4)
@@ -142,13 +143,56 @@ def test_sweep_strided_reads_are_conflict_free(tr):
 
     def run():
         out["k"], out["v"] = bcf.partition(dev(keys), dev(vals), w, balanced=True)
-    rec, _ = tr.capture(run)
+    L = tr.load()
+    assert L.bcf_tune_config_form(8) == 2  # the staged-tile sweep, 256 x 16
+    assert L.bcf_tune_set(bcf.OP_PARTITION, 12, 8) == bcf.OK
+    try:
+        rec, _ = tr.capture(run)
+    finally:
+        L.bcf_tune_set(bcf.OP_PARTITION, 12, -1)
     rk, rv = oracle.partition_kv(keys, vals, w, balanced=True)
     assert bits_equal(host(out["k"], np.uint32), rk) and bits_equal(host(out["v"], np.uint32), rv)
     assert _replay(tr, rec, "stage_read")["hw_conflicts"] == 0
     assert _replay(tr, rec, "writeout_read")["hw_conflicts"] == 0
     sc = _replay(tr, rec, "scatter")
     assert sc is not None and sc["requests"] == n // 32
+    _no_races(rec)
+
+
+@pytest.mark.parametrize("n", [3 * 2048 + 5, 3 * 4096])
+def test_single_launch_sort_trace(tr, n):
+    """The single-launch sort passes: the one-read histogram keeps every lane's
+    counters in the lane's own bank, so its counting atomics and the diagonal sums
+    replay with zero conflicts even under the strict rule; the per-warp offset rows
+    and the ordered write-out read replay conflict-free; the scatter into digit
+    order and the leaders' run claims are random-bank accesses and are counted
+    (reported, not asserted zero).  No word races between barriers."""
+    import paper_1507_01391_b300 as bcf
+    keys = synth.uniform_keys(n, seed=n)
+    vals = synth.index_payload(n)
+    out = {}
+
+    def run():
+        out["k"], out["v"] = bcf.sort(dev(keys), dev(vals))
+    L = tr.load()
+    lg = (n - 1).bit_length()
+    assert L.bcf_tune_config_form(1) == 0  # single launch per pass, 256 x 8
+    assert L.bcf_tune_set(bcf.OP_SORT, lg, 1) == bcf.OK
+    try:
+        rec, _ = tr.capture(run)
+    finally:
+        L.bcf_tune_set(bcf.OP_SORT, lg, -1)
+    rk, rv = oracle.sort_kv(keys, vals)
+    assert bits_equal(host(out["k"], np.uint32), rk) and bits_equal(host(out["v"], np.uint32), rv)
+    for site in ("hist_atom", "hist_sum"):
+        r = _replay(tr, rec, site)
+        assert r is not None and r["hw_conflicts"] == 0 and r["strict_conflicts"] == 0, (site, r)
+    for site in ("warp_offsets", "writeout_read"):
+        r = _replay(tr, rec, site)
+        assert r is not None and r["hw_conflicts"] == 0, (site, r)
+    sc = _replay(tr, rec, "scatter")
+    assert sc is not None and sc["requests"] >= 4 * n // 32  # keys and payloads, four passes
+    assert _replay(tr, rec, "claim_atom") is not None
     _no_races(rec)
 
 

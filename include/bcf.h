@@ -301,9 +301,12 @@ int bcf_tune_load(const char* path, int* applied);
  * the library -- code running inside CUDA stream capture (cudaMalloc is not
  * allowed while a global-mode capture is active), plugins whose host framework
  * owns all device memory, and latency-critical loops that must never enter the
- * allocator.  Same operation, flags and errors as bcf_partition, out of place
- * only (outputs must not overlap the inputs; an overlap returns BCF_E_INVAL),
- * for n <= BCF_NOALLOC_MAX_N (larger n returns BCF_E_UNSUPPORTED).
+ * allocator.  Same operation and errors as bcf_partition with the default
+ * staged-sweep tile configuration (256 threads x 16 keys, not the tuning table),
+ * out of place only (outputs must not overlap the inputs; an overlap returns
+ * BCF_E_INVAL), for n <= BCF_NOALLOC_MAX_N (larger n returns BCF_E_UNSUPPORTED).
+ * flags: BCF_ASSUME_BALANCED only; any other flag (BCF_PARTITION_LEMMA1 among
+ * them) returns BCF_E_UNSUPPORTED.
  * Scratch lives in a fixed device array of about 1 MiB inside libbcf.so, held on
  * every device that loads the library until the process exits; nothing is
  * allocated or freed.  The first call on a device looks the array's address up

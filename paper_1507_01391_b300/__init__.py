@@ -277,8 +277,10 @@ def permute_workspace_size(n, val_bytes=0, flags=0):
 
 def permute(src, pi, dst=None, check=False, row_len=0, stream=None, bucketed=None, ws=None):
     """dst[pi[i]] = src[i] for 4- or 8-byte elements (bcf_permute); with row_len,
-    pi is local to rows of row_len items.  bucketed: None (one scatter pass) or
-    True (two coalesced passes; 4-byte elements, n <= 2^26); ws: optional
+    pi is local to rows of row_len items.  bucketed: True (two coalesced passes;
+    4-byte elements, n <= 2^26), False (one scatter pass), or None: the library's
+    choice, which for a single array is one scatter pass (with payloads,
+    permute_kv picks the bucketed form for 2^20 <= n <= 2^26); ws: optional
     preallocated workspace (uint8 tensor)."""
     torch = _torch()
     _dev_u32(pi, "pi")

@@ -16,6 +16,8 @@
 // no ordering between them) race on it.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "bcf.h"
 #include "common.cuh"
 #include "internal.h"
@@ -36,24 +38,28 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 
 // Device address of g_noalloc_scratch on the current device.  In host code the
 // array's name only stands for the symbol; the address comes from
-// cudaGetSymbolAddress, looked up once per device with that device current.
+// cudaGetSymbolAddress, looked up once per device with that device current.  The
+// per-device cache is atomic: host threads that make their first call at the same
+// time may each look the address up, and they store the same value.
 unsigned char* scratch_address(int* rc) {
-  static unsigned char* addr[64] = {nullptr};
+  static std::atomic<unsigned char*> addr[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     *rc = BCF_E_CUDA;
     return nullptr;
   }
-  if (!addr[dev]) {
+  unsigned char* a = addr[dev].load(std::memory_order_acquire);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       *rc = BCF_E_CUDA;
       return nullptr;
     }
-    addr[dev] = static_cast<unsigned char*>(p);
+    a = static_cast<unsigned char*>(p);
+    addr[dev].store(a, std::memory_order_release);
   }
   *rc = BCF_OK;
-  return addr[dev];
+  return a;
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
@@ -70,6 +76,7 @@ extern "C" int bcf_partition_noalloc(const uint32_t* keys_in, const void* vals_i
                                      int val_bytes, int flags, bcf_stream_t stream) {
   if (n < 0 || w < 1 || (val_bytes != 0 && val_bytes != 4 && val_bytes != 8)) return BCF_E_INVAL;
   if (n > kNoAllocMaxN || w > 256) return BCF_E_UNSUPPORTED;
+  if (flags & ~BCF_ASSUME_BALANCED) return BCF_E_UNSUPPORTED;  // e.g. BCF_PARTITION_LEMMA1
   const bool balanced = (flags & BCF_ASSUME_BALANCED) != 0;
   if (balanced && n % w) return BCF_E_INVAL;
   if (n == 0) return BCF_OK;

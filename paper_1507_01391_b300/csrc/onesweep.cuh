@@ -501,9 +501,12 @@ template <int BITS, int THREADS, int IPT, int VB, int MINB>
 inline cudaError_t launch_onesweep(const OneSweepParams& p, int64_t grid, cudaStream_t s) {
   using S = OneSmem<BITS, THREADS, IPT, VB>;
   auto kern = k_onesweep<BITS, THREADS, IPT, VB, MINB>;
-  static bool attr_set[64] = {false};
-  cudaError_t e = set_smem_once(kern, (int)S::bytes, attr_set);
-  if (e != cudaSuccess) return e;
+  // raised on every launch that needs it (see launch_sweep: no flag shared
+  // between translation units)
+  if (S::bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    if (e != cudaSuccess) return e;
+  }
   if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, THREADS, S::bytes, s>>>(p);
   return cudaGetLastError();

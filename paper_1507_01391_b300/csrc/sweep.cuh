@@ -946,14 +946,12 @@ template <int BITS, int VB, int THREADS = kSweepThreads, int IPT = kSweepIPT, bo
 inline cudaError_t launch_sweep(const SweepParams& p, int64_t grid, cudaStream_t s) {
   using S = SweepSmem<THREADS, IPT, BITS, VB, SPLIT>;
   auto kern = k_sweep<THREADS, IPT, BITS, VB, SPLIT>;
-  static int attr_set[64] = {0};  // per device: the shared-memory limit is set once
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!attr_set[dev]) {
+  // The shared-memory limit is raised on every launch that needs it, not once per
+  // process: this launcher is instantiated in several translation units, and a
+  // flag shared between them could stand for another unit's copy of the kernel.
+  if (S::bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     if (e != cudaSuccess) return e;
-    attr_set[dev] = 1;
   }
   if (grid <= 0) return cudaSuccess;
   kern<<<(unsigned)grid, THREADS, S::bytes, s>>>(p);

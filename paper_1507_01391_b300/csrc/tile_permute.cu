@@ -29,7 +29,14 @@
 
 namespace bcf {
 
-constexpr int kTPThreads = 128;  // four warps per tile
+#ifndef BCF_TP_THREADS
+#define BCF_TP_THREADS 512
+#endif
+constexpr int kTPThreads = BCF_TP_THREADS;  // warps per tile: each lane owns M / warps slots of its row
+#ifndef BCF_TP_ROUNDS
+#define BCF_TP_ROUNDS 3
+#endif
+constexpr int kTPRounds = BCF_TP_ROUNDS;     // colouring rounds before the finish
 
 __device__ __forceinline__ uint32_t mix32(uint64_t x) {
   // splitmix64 finaliser (Steele, Lea & Flood 2014), folded to 32 bits
@@ -54,8 +61,8 @@ struct TPSmem {
   // sorted finish: bitmap of the (bank, slot) label space and scan scratch; the
   // source positions reuse lpi, the packed labels lab and the packed keys tbl
   static constexpr size_t bits = bytes_coloured;
-  static constexpr size_t scr = bits + (size_t)(T / 32) * 4;
-  static constexpr size_t bytes_sorted = scr + 8 * 4;
+  static constexpr size_t scr = bits + (size_t)(T / 32) * 4;           // one word per warp
+  static constexpr size_t bytes_sorted = scr + (size_t)(kTPThreads / 32) * 4;
 };
 
 // Stage the tile's keys and local labels into shared memory.  Returns len.
@@ -209,6 +216,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
   uint32_t* pkl = reinterpret_cast<uint32_t*>(smem + S::lab);     // filled after lab is read
   uint32_t* pkk = reinterpret_cast<uint32_t*>(smem + S::tbl);     // colour table no longer needed
   uint32_t* scr = reinterpret_cast<uint32_t*>(smem + S::scr);
+  static_assert(S::bytes_sorted - S::scr == WARPS * 4, "one scan word per warp");
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int w = tid; w < NW; w += kTPThreads) {
     BCF_TR(&bits[w], 4, 1, TS_COL_TABLE);
@@ -322,7 +330,7 @@ __device__ __forceinline__ void sorted_finish(uint32_t pending, const uint32_t* 
 }
 
 template <int T>
-__global__ void __launch_bounds__(kTPThreads) k_tile_coloured(const uint32_t* __restrict__ src,
+__global__ void __launch_bounds__(kTPThreads, kTPThreads >= 1024 ? 2 : 3) k_tile_coloured(const uint32_t* __restrict__ src,
                                                               uint32_t* __restrict__ dst,
                                                               const uint16_t* __restrict__ lpi,
                                                               int64_t n, uint64_t seed,
@@ -439,7 +447,7 @@ static cudaError_t launch_tiles(const uint32_t* src, uint32_t* dst, const uint16
     static bool ready[64] = {};
     const cudaError_t e = set_smem_once(k, (int)S::bytes_sorted, ready);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)tiles, kTPThreads, bytes, s>>>(src, dst, lpi, n, seed, 3, sorted ? 1 : 0, status_word());
+    k<<<(unsigned)tiles, kTPThreads, bytes, s>>>(src, dst, lpi, n, seed, kTPRounds, sorted ? 1 : 0, status_word());
   } else {
     using SS = TSSmem<T>;
     auto k = k_tile_scatter_stream<T>;

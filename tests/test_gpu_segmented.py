@@ -134,6 +134,39 @@ def test_segmented_sort_graph_capture(bcf):
     assert bcf.get_status() == bcf.OK
 
 
+@pytest.mark.slow
+def test_segmented_sort_batched_full_size_graph_replay(bcf):
+    """The batched workload as the benchmark times it: one call captured in a CUDA
+    graph, replayed on new keys copied into the captured buffers; the replay's
+    output is compared in full with the oracle."""
+    import torch
+    sizes = synth.log_uniform_sizes(10_000, seed=0x4A)
+    offs = synth.offsets_from_sizes(sizes)
+    n = int(offs[-1])
+    kd = dev(synth.uniform_keys(n, seed=0x4B))
+    vd = dev(synth.index_payload(n))
+    od = torch.from_numpy(offs).cuda()
+    ko, vo = torch.empty_like(kd), torch.empty_like(vd)
+    ws = bcf.workspace(bcf.segmented_sort_workspace_size(n, sizes.size, 4, 32))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bcf.segmented_sort(kd, vd, od, keys_out=ko, vals_out=vo, ws=ws)  # warm-up outside capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            bcf.segmented_sort(kd, vd, od, keys_out=ko, vals_out=vo, ws=ws)
+    new = synth.uniform_keys(n, seed=0x4D)
+    kd.copy_(dev(new))
+    torch.cuda.synchronize()
+    g.replay()
+    g.replay()  # a second replay over its own output's inputs: the same answer
+    torch.cuda.synchronize()
+    assert bcf.get_status() == bcf.OK
+    rk, rv = oracle.segmented_sort_kv(new, synth.index_payload(n), offs)
+    assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.uint32), rv)
+
+
 def test_segmented_reports_bad_offsets(bcf):
     import torch
     offs = np.array([0, 10, 5, 20], dtype=np.int64)  # decreasing
@@ -168,6 +201,48 @@ def test_segmented_partition(bcf, balanced):
 def test_segmented_partition_batched_full_size(bcf):
     keys, offs, w = synth.segmented_partition_input(10_000, seed=0x4C)
     _seg_part_case(bcf, keys, synth.index_payload(keys.size), offs, w, True)
+
+
+@pytest.mark.parametrize("balanced", [True, False])
+def test_segmented_partition_graph_capture(bcf, balanced):
+    """The segmented partition is capturable: a graph of one call, replayed on new
+    labels in the same buffers, gives the oracle's answer for the new labels."""
+    import torch
+    keys, offs, w = synth.segmented_partition_input(40, seed=5, hi_log2=14)
+    n = keys.size
+
+    def labels(seed):
+        if balanced:  # the same label multiset per segment, reshuffled
+            g = synth.rng(seed)
+            out = keys.copy()
+            for s in range(w.size):
+                g.shuffle(out[offs[s]:offs[s + 1]])
+            return out
+        return np.concatenate([synth.random_labels(int(offs[s + 1] - offs[s]), int(w[s]), seed=seed + s)
+                               for s in range(w.size)]).astype(np.uint32)
+    kd = dev(labels(1))
+    vd = dev(synth.index_payload(n))
+    od = torch.from_numpy(offs).cuda()
+    wd = dev(w.astype(np.int32))
+    ko, vo = torch.empty_like(kd), torch.empty_like(vd)
+    ws = bcf.workspace(bcf.segmented_partition_workspace_size(n, w.size, 4))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        bcf.segmented_partition(kd, vd, od, wd, balanced=balanced, keys_out=ko, vals_out=vo, ws=ws)
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            bcf.segmented_partition(kd, vd, od, wd, balanced=balanced, keys_out=ko, vals_out=vo, ws=ws)
+    for seed in (2, 3):
+        new = labels(seed)
+        kd.copy_(dev(new))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert bcf.get_status() == bcf.OK
+        rk, rv = oracle.segmented_partition_kv(new, synth.index_payload(n), offs, w, balanced=balanced)
+        assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.uint32), rv)
 
 
 def test_segmented_partition_reports_bad_width(bcf):

@@ -245,8 +245,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
   uint32_t key[IPT];
   auto load_keys = [&](const uint32_t* src, int64_t st, int c) {
     const uint32_t* kin = src + st + wbase + lane;
+    if (c == T) {  // full tile: no per-key test
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) key[j] = (c == T || wbase + j * 32 + lane < c) ? __ldcs(kin + 32 * j) : 0xFFFFFFFFu;
+      for (int j = 0; j < IPT; ++j) key[j] = __ldcs(kin + 32 * j);
+    } else {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) key[j] = wbase + j * 32 + lane < c ? __ldcs(kin + 32 * j) : 0xFFFFFFFFu;
+    }
   };
   {
     const int64_t st = (int64_t)blockIdx.x * T;
@@ -330,6 +335,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       if (j & 1) rk[j >> 1] |= r << 16;
       else rk[j >> 1] = r;
     }
+    // A ragged tile's payloads past the bulk copy are read into the staging area
+    // directly, so that the scatter below reads every payload from there.
+    if (VB == 4 && !iota && !full)
+      for (int i = vfull + tid; i < cnt; i += THREADS) stage[i] = reinterpret_cast<const uint32_t*>(vals_in)[start + i];
     BCF_SYNC();
 
     // 3. per digit: tile count (published at once), tile-exclusive start, and each
@@ -394,36 +403,41 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
     }
     BCF_SYNC();
 
-    // 4a. keys (with 4-byte payloads: pairs) into digit order in shared memory
+    // 4a. keys (with 4-byte payloads: pairs) into digit order in shared memory;
+    // the payload comes from the staging area (padding slots carry stale words,
+    // which are never written out) or is the input position
     if (VB == 4 && !iota) mbar_wait(mbar, 0, p.err);
+    auto scatter = [&](auto iota_tag) {
+      constexpr bool IOTA = decltype(iota_tag)::value;
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) {
-      const uint32_t half = (rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
-      const uint32_t d = digit(key[j]);
-      BCF_TR(&wh[d], 4, 0, TS_OFFSET_READ);
-      const uint32_t pos = wh[d] + half;  // < T, padding included
-      if constexpr (VB == 4) {
-        const int idx = wbase + j * 32 + lane;
-        uint32_t v = 0;
-        if (iota) {
-          v = (uint32_t)(start + idx);
-        } else if (full || idx < vfull) {
-          BCF_TR(&stage[idx], 4, 0, TS_STAGE_READ);
-          v = stage[idx];
-        } else if (idx < cnt) {
-          v = reinterpret_cast<const uint32_t*>(vals_in)[start + idx];
+      for (int j = 0; j < IPT; ++j) {
+        const uint32_t half = (rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+        const uint32_t d = digit(key[j]);
+        BCF_TR(&wh[d], 4, 0, TS_OFFSET_READ);
+        const uint32_t pos = wh[d] + half;  // < T, padding included
+        if constexpr (VB == 4) {
+          const int idx = wbase + j * 32 + lane;
+          uint32_t v;
+          if constexpr (IOTA) {
+            v = (uint32_t)(start + idx);
+          } else {
+            BCF_TR(&stage[idx], 4, 0, TS_STAGE_READ);
+            v = stage[idx];
+          }
+          BCF_TR(&kv_s[pos], 8, 1, TS_SCATTER);
+          kv_s[pos] = ((unsigned long long)v << 32) | key[j];
+        } else {
+          BCF_TR(&keys_s[pos], 4, 1, TS_SCATTER);
+          keys_s[pos] = key[j];
         }
-        BCF_TR(&kv_s[pos], 8, 1, TS_SCATTER);
-        kv_s[pos] = ((unsigned long long)v << 32) | key[j];
-      } else {
-        BCF_TR(&keys_s[pos], 4, 1, TS_SCATTER);
-        keys_s[pos] = key[j];
+        if constexpr (VB == 8) {  // the ranks become positions for the payload stores
+          if (j & 1) rk[j >> 1] = (rk[j >> 1] & 0xFFFFu) | (pos << 16);
+          else rk[j >> 1] = (rk[j >> 1] & 0xFFFF0000u) | pos;
+        }
       }
-      if constexpr (VB == 8) {  // the ranks become positions for the payload stores
-        if (j & 1) rk[j >> 1] = (rk[j >> 1] & 0xFFFFu) | (pos << 16);
-        else rk[j >> 1] = (rk[j >> 1] & 0xFFFF0000u) | pos;
-      }
-    }
+    };
+    if (VB == 4 && iota) scatter(std::true_type{});
+    else scatter(std::false_type{});
     // 4b. 8-byte payloads: loaded now (the keys' registers are free), in flight
     // during the look-back, then stored at their keys' positions
     VT val[VB == 8 ? IPT : 1];

@@ -50,8 +50,11 @@ FALLBACK_HBM_GBS = 6400.0
 # its kernels) from an ncu capture, valid only for the kernel sources it was taken
 # on: if any of them changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "bcf_sort of 2^26 key-value pairs (all launches of one call)",
-               "sources": ["radix.cu", "sweep.cuh", "onesweep.cuh"], "sources_sha1": None,
-               "bytes": None}
+               "sources": ["radix.cu", "sweep.cuh", "onesweep.cuh"],
+               "sources_sha1": ['bfc82e7cfd7c2e6dd747f4b2484931534767f4f5', '7da90a30fb48d8b62c9f4d7ce0927b0808857e3c', '0e2cb28ce5b6d5d9d881895d8ca1f0607f830079'],
+               # 1155.8 MB per call measured at 2^24 keys (3 calls captured), scaled by 4:
+               # every kernel of the call moves bytes in proportion to the keys
+               "bytes": 4623360000}
 
 
 def log(*a):
@@ -997,7 +1000,9 @@ def _case_inputs(name):
         k, lpi = to_dev(synth.uniform_keys(n, seed=1)), to_dev(synth.tile_local_perms(n, TILE, seed=4))
         ko = torch.empty_like(k)
         return lambda: bcf.permute_tiles(k, lpi, tile=TILE, coloured=(name == "tile_coloured"), dst=ko)
-    if name == "sort_kv":
+    if name in ("sort_kv", "sort_kv_2pow26"):
+        if name == "sort_kv_2pow26":
+            n = N_SORT
         k, v = to_dev(synth.uniform_keys(n, seed=0x2A)), to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
@@ -1029,7 +1034,8 @@ def _case_inputs(name):
     raise ValueError(name)
 
 
-CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "partition_w32", "partition_w256",
+CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "sort_kv_2pow26",
+         "partition_w32", "partition_w256",
          "tile_sort", "segmented_sort", "partition_lemma2")
 
 

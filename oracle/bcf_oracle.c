@@ -487,9 +487,15 @@ int oracle_lemma2_partition(uint32_t* lab, uint32_t* pay, int64_t w, int64_t m, 
     return rc;
 }
 
-/* ---- Race check of a trace (between block-wide barriers) ---- */
+/* ---- Race check of a trace ----
+ * Records of store kind 3 mark a block-wide barrier (one per warp), kind 4 a
+ * warp-wide barrier (one per warp).  Two accesses to one word race when they come
+ * from different threads of one block, at least one is a store (atomics are
+ * ordered among themselves and never race), no block barrier lies between them
+ * (the same block epoch of each warp), and they are not both in one warp with a
+ * warp barrier between them (different warp epochs). */
 typedef struct {
-    uint32_t block, epoch, word, thread;
+    uint32_t block, epoch, word, thread, sub;
     int store;
 } race_entry;
 
@@ -502,18 +508,27 @@ static int race_cmp(const void* a, const void* b) {
     return 0;
 }
 
+/* Whether accesses i and j of one group race. */
+static int race_pair(const race_entry* i, const race_entry* j) {
+    if (i->thread == j->thread || (!i->store && !j->store)) return 0;
+    if ((i->thread >> 5) == (j->thread >> 5) && i->sub != j->sub) return 0;  /* warp barrier between */
+    return 1;
+}
+
 int oracle_race_check(const uint32_t* rec, int64_t nrec, int64_t* races, int64_t* words) {
     if (nrec < 0 || !races || !words) return ORACLE_E_ARG;
-    /* barriers seen so far by each (block, warp) */
+    /* block and warp barriers seen so far by each (block, warp) */
     uint32_t* seen = (uint32_t*)calloc((size_t)65536 * 32, sizeof(uint32_t));
+    uint32_t* wseen = (uint32_t*)calloc((size_t)65536 * 32, sizeof(uint32_t));
     int64_t cap = 0;
     for (int64_t r = 0; r < nrec; ++r) {
         const uint32_t kind = (rec[4 * r + 3] >> 8) & 0xFF, width = rec[4 * r + 3] & 0xFF;
         if (kind == 0 || kind == 1) cap += (width + 3) / 4;
     }
     race_entry* e = (race_entry*)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(race_entry));
-    if (!seen || !e) {
+    if (!seen || !wseen || !e) {
         free(seen);
+        free(wseen);
         free(e);
         return ORACLE_E_NOMEM;
     }
@@ -521,15 +536,20 @@ int oracle_race_check(const uint32_t* rec, int64_t nrec, int64_t* races, int64_t
     for (int64_t r = 0; r < nrec; ++r) {
         const uint32_t thread = rec[4 * r + 1] & 0xFFFF, block = rec[4 * r + 1] >> 16;
         const uint32_t kind = (rec[4 * r + 3] >> 8) & 0xFF, width = rec[4 * r + 3] & 0xFF;
-        uint32_t* count = &seen[(size_t)block * 32 + ((thread >> 5) & 31)];
+        const size_t slot = (size_t)block * 32 + ((thread >> 5) & 31);
         if (kind == 3) {
-            *count += 1;
+            seen[slot] += 1;
+            continue;
+        }
+        if (kind == 4) {
+            wseen[slot] += 1;
             continue;
         }
         if (kind != 0 && kind != 1) continue;
         for (uint32_t q = 0; q < (width + 3) / 4; ++q) {
             e[ne].block = block;
-            e[ne].epoch = *count;
+            e[ne].epoch = seen[slot];
+            e[ne].sub = wseen[slot];
             e[ne].word = rec[4 * r + 2] / 4 + q;
             e[ne].thread = thread;
             e[ne].store = (int)kind;
@@ -541,22 +561,19 @@ int oracle_race_check(const uint32_t* rec, int64_t nrec, int64_t* races, int64_t
     for (int64_t a = 0; a < ne;) {
         int64_t b = a;
         while (b < ne && race_cmp(&e[a], &e[b]) == 0) ++b;
-        /* one group: the accesses of one word in one segment of one block */
-        int64_t writer = -1;
+        /* one group: the accesses of one word in one block epoch of one block */
         int race = 0;
-        for (int64_t i = a; i < b; ++i) {
+        for (int64_t i = a; i < b && !race; ++i) {
             if (!e[i].store) continue;
-            if (writer < 0) writer = e[i].thread;
-            else if ((uint32_t)writer != e[i].thread) race = 1;
+            for (int64_t j = a; j < b && !race; ++j)
+                if (j != i) race = race_pair(&e[i], &e[j]);
         }
-        if (writer >= 0)
-            for (int64_t i = a; i < b; ++i)
-                if (!e[i].store && e[i].thread != (uint32_t)writer) race = 1;
         nr += race;
         ++nw;
         a = b;
     }
     free(seen);
+    free(wseen);
     free(e);
     *races = nr;
     *words = nw;

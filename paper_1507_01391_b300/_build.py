@@ -66,7 +66,8 @@ def build(verbose: bool = False, extra: list[str] | None = None, trace: bool = T
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = list(extra or [])
-    jobs = [(s, extra, BUILD) for s in srcs if not s.endswith("trace_abi.cu")]
+    trace_only = ("trace_abi.cu", "bank_probe.cu")  # entry points of the trace build alone
+    jobs = [(s, extra, BUILD) for s in srcs if os.path.basename(s) not in trace_only]
     if trace:
         os.makedirs(os.path.join(BUILD, "trace"), exist_ok=True)
         jobs += [(s, extra + ["-DBCF_TRACE"], os.path.join(BUILD, "trace")) for s in srcs]

@@ -20,6 +20,7 @@
 // after each sort the new masks follow from the zero counts alone.
 #include "common.cuh"
 #include "internal.h"
+#include "trace.cuh"
 
 namespace bcf {
 namespace {
@@ -60,11 +61,14 @@ __device__ __forceinline__ void square_colmajor(uint32_t* P, uint32_t* Lm, const
     const uint32_t b = __ballot_sync(0xffffffffu, bit);
     const uint32_t x = __popc(b & lt);  // 1-items above in this column; lane - x 0-items
     const uint32_t rho = bit ? Z + (32u * c - zb) + x : zb + (uint32_t)lane - x;
-    P[l2_addr(row_of((int)(rho & 31u)), (int)(rho >> 5))] = pay[c];
+    uint32_t* dst = &P[l2_addr(row_of((int)(rho & 31u)), (int)(rho >> 5))];
+    BCF_TR(dst, 4, 1, TS_L2_SQUARE);
+    *dst = pay[c];
     zb += 32u - __popc(b);
   }
   // Cell (j, c) of the sorted square holds a 0 iff 32c + j < Z.
   const int zc = (int)Z > lane ? ((int)Z - lane + 31) / 32 : 0;
+  BCF_TR(&Lm[lm_idx(row_of(lane))], 4, 1, TS_L2_SQUARE);
   Lm[lm_idx(row_of(lane))] = ones_after(zc);
 }
 
@@ -72,7 +76,7 @@ __device__ __forceinline__ void square_colmajor(uint32_t* P, uint32_t* Lm, const
 // row-major order.
 template <int G>
 __device__ __forceinline__ void rows_rowmajor(uint32_t* P, uint32_t* Lm, const uint32_t (&pay)[32],
-                                              uint32_t lab, int row0, int lane) {
+                                              uint32_t lab, int row0, int lane, uint32_t site) {
   const int j = lane & (G - 1);
   const uint32_t zr = 32u - __popc(lab);
   uint32_t incl = zr;
@@ -89,8 +93,11 @@ __device__ __forceinline__ void rows_rowmajor(uint32_t* P, uint32_t* Lm, const u
     const uint32_t bit = (lab >> c) & 1u;
     const uint32_t x = __popc(lab & ((1u << c) - 1u));  // 1-items left of c; c - x 0-items
     const uint32_t rho = bit ? Z + ob + x : zb + (uint32_t)c - x;
-    P[l2_addr(row0 + (int)(rho >> 5), (int)(rho & 31u))] = pay[c];
+    uint32_t* dst = &P[l2_addr(row0 + (int)(rho >> 5), (int)(rho & 31u))];
+    BCF_TR(dst, 4, 1, site);
+    *dst = pay[c];
   }
+  BCF_TR(&Lm[lm_idx(row0 + j)], 4, 1, site);
   Lm[lm_idx(row0 + j)] = ones_after((int)Z - 32 * j);
 }
 
@@ -108,16 +115,23 @@ __device__ __forceinline__ bool groups_uniform(uint32_t lab) {
   return all;
 }
 
-__device__ __forceinline__ void load_pay(const uint32_t* P, int r, uint32_t (&pay)[32]) {
+__device__ __forceinline__ void load_pay(const uint32_t* P, int r, uint32_t (&pay)[32], uint32_t site) {
 #pragma unroll
-  for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(r, c)];
+  for (int c = 0; c < 32; ++c) {
+    BCF_TR(&P[l2_addr(r, c)], 4, 0, site);
+    pay[c] = P[l2_addr(r, c)];
+  }
+}
+
+__device__ __forceinline__ uint32_t load_mask(const uint32_t* Lm, int r, uint32_t site) {
+  BCF_TR(&Lm[lm_idx(r)], 4, 0, site);
+  return Lm[lm_idx(r)];
 }
 
 __device__ __forceinline__ void load_row(const uint32_t* P, const uint32_t* Lm, int r, uint32_t (&pay)[32],
-                                         uint32_t& lab) {
-#pragma unroll
-  for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(r, c)];
-  lab = Lm[lm_idx(r)];
+                                         uint32_t& lab, uint32_t site) {
+  load_pay(P, r, pay, site);
+  lab = load_mask(Lm, r, site);
 }
 
 __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __restrict__ keys,
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
 
     // Balancing, round 0: squares of 32 contiguous rows (one per warp).
     square_colmajor(P, Lm, pay, lab, [&](int j) { return warp * 32 + j; }, lt, lane);
-    __syncthreads();
+    BCF_SYNC();
     // Round 1: square j takes row j of each of the 32 round-0 squares, and is
     // sorted in column-major order; then the conversion refills the matrix read
     // column by column into rows.  The two are composed: the item at position rho
@@ -170,11 +184,14 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
     // So square j becomes column j, top to bottom, and every item is written
     // once.  Squares overlap other squares' columns, hence the block barrier
     // between all reads and all writes.
-    load_row(P, Lm, lane * 32 + warp, pay, lab);
-    __syncthreads();
+    load_row(P, Lm, lane * 32 + warp, pay, lab, TS_L2_CONVERT);
+    BCF_SYNC();
     {
       const uint32_t Z = (uint32_t)kL2W - warp_sum((uint32_t)__popc(lab));
-      if (lane == 0) ztot[warp] = Z;  // zeros of square (now column) `warp`
+      if (lane == 0) {
+        BCF_TR(&ztot[warp], 4, 1, TS_L2_CONVERT);
+        ztot[warp] = Z;  // zeros of square (now column) `warp`
+      }
       uint32_t zb = 0;
 #pragma unroll
       for (int c = 0; c < 32; ++c) {
@@ -182,63 +199,71 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
         const uint32_t b = __ballot_sync(0xffffffffu, bit);
         const uint32_t x = __popc(b & lt);
         const uint32_t rho = bit ? Z + (32u * c - zb) + x : zb + (uint32_t)lane - x;
+        BCF_TR(&P[l2_addr((int)rho, warp)], 4, 1, TS_L2_CONVERT);
         P[l2_addr((int)rho, warp)] = pay[c];
         zb += 32u - __popc(b);
       }
     }
-    __syncthreads();
+    BCF_SYNC();
     // Row t now holds a 1 in column j iff t >= (zeros of column j).
     {
       uint32_t m = 0;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) m |= ((uint32_t)t >= ztot[j] ? 1u : 0u) << j;
+      for (int j = 0; j < 32; ++j) {
+        BCF_TR(&ztot[j], 4, 0, TS_L2_CONVERT);
+        m |= ((uint32_t)t >= ztot[j] ? 1u : 0u) << j;
+      }
+      BCF_TR(&Lm[lm_idx(t)], 4, 1, TS_L2_CONVERT);
       Lm[lm_idx(t)] = m;
     }
 
     // Divide: 128 sub-problems of 8 contiguous rows, each sorted row-major.  Only
     // the few that hold both labels move anything: a warp whose four are all
     // single-label leaves them in place.
-    lab = Lm[lm_idx(t)];
+    lab = load_mask(Lm, t, TS_L2_DIVIDE);
     if (!groups_uniform<8>(lab)) {
-      load_pay(P, t, pay);
-      __syncwarp();
-      rows_rowmajor<8>(P, Lm, pay, lab, warp * 32 + (lane & ~7), lane);
+      load_pay(P, t, pay, TS_L2_DIVIDE);
+      BCF_SYNCWARP();
+      rows_rowmajor<8>(P, Lm, pay, lab, warp * 32 + (lane & ~7), lane, TS_L2_DIVIDE);
     }
-    __syncthreads();
+    BCF_SYNC();
 
     // Column sorts: each column, top to bottom, stably 0s then 1s.  The row's
     // payloads are read after the counts (and before the barrier that precedes
     // any write).
-    lab = Lm[lm_idx(t)];
+    lab = load_mask(Lm, t, TS_L2_COLUMN);
     uint32_t myz = 0;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const uint32_t b = __ballot_sync(0xffffffffu, (lab >> c) & 1u);
       if (c == lane) myz = 32u - __popc(b);
     }
+    BCF_TR(&zw[warp * 32 + lane], 4, 1, TS_L2_COLUMN);
     zw[warp * 32 + lane] = myz;
-    __syncthreads();
+    BCF_SYNC();
     bool moves;  // does any item of this warp's rows change place?
     {
       uint32_t pre = 0, tot = 0;  // of column `lane`
 #pragma unroll 4
       for (int g = 0; g < 32; ++g) {
+        BCF_TR(&zw[g * 32 + lane], 4, 0, TS_L2_COLUMN);
         const uint32_t z = zw[g * 32 + lane];
         pre += g < warp ? z : 0u;
         tot += z;
       }
+      BCF_TR(&zpre[warp * 32 + lane], 4, 1, TS_L2_COLUMN);
       zpre[warp * 32 + lane] = pre;
-      if (warp == 0) ztot[lane] = tot;
+      if (warp == 0) {
+        BCF_TR(&ztot[lane], 4, 1, TS_L2_COLUMN);
+        ztot[lane] = tot;
+      }
       // Rows of 0s with only 0s above them in every column, or rows of 1s with
       // only 1s from them down, already sit where the column sort puts them.
       moves = !(__all_sync(0xffffffffu, lab == 0u && pre == 32u * warp) ||
                 __all_sync(0xffffffffu, lab == 0xffffffffu && tot == pre));
     }
-    if (moves) {
-#pragma unroll
-      for (int c = 0; c < 32; ++c) pay[c] = P[l2_addr(t, c)];
-    }
-    __syncthreads();
+    if (moves) load_pay(P, t, pay, TS_L2_COLUMN);
+    BCF_SYNC();
     if (moves) {
       const uint32_t* vzp = zpre + warp * 32;
       const uint32_t* vzt = ztot;
@@ -247,54 +272,62 @@ __global__ void __launch_bounds__(1024, 1) k_partition_l2(const uint32_t* __rest
       for (int c = 0; c < 32; ++c) {
         const uint32_t bit = (lab >> c) & 1u;
         const uint32_t b = __ballot_sync(0xffffffffu, bit);
+        BCF_TR(&vzp[c], 4, 0, TS_L2_COLUMN);
+        BCF_TR(&vzt[c], 4, 0, TS_L2_COLUMN);
         const uint32_t zp = vzp[c], zt = vzt[c];
         const uint32_t x = __popc(b & lt);
         const uint32_t rho = bit ? zt + (32u * warp - zp) + x : zp + (uint32_t)lane - x;
+        BCF_TR(&P[l2_addr((int)rho, c)], 4, 1, TS_L2_COLUMN);
         P[l2_addr((int)rho, c)] = pay[c];
         nm |= ((uint32_t)t >= zt ? 1u : 0u) << c;
       }
+      BCF_TR(&Lm[lm_idx(t)], 4, 1, TS_L2_COLUMN);
       Lm[lm_idx(t)] = nm;
     }
-    __syncthreads();
+    BCF_SYNC();
 
     // Squares of 32 contiguous rows sorted row-major, then the decomposition
     // shifted down by 16 rows.
     // Single-label squares (all but the one or two that hold the dirty rows) are
     // left in place.
-    lab = Lm[lm_idx(t)];
+    lab = load_mask(Lm, t, TS_L2_ROWS);
     if (!groups_uniform<32>(lab)) {
-      load_pay(P, t, pay);
-      __syncwarp();
-      rows_rowmajor<32>(P, Lm, pay, lab, warp * 32, lane);
+      load_pay(P, t, pay, TS_L2_ROWS);
+      BCF_SYNCWARP();
+      rows_rowmajor<32>(P, Lm, pay, lab, warp * 32, lane, TS_L2_ROWS);
     }
-    __syncthreads();
+    BCF_SYNC();
     if (warp < 31) {
       const int r = warp * 32 + 16 + lane;
-      lab = Lm[lm_idx(r)];
+      lab = load_mask(Lm, r, TS_L2_SHIFTED);
       if (!groups_uniform<32>(lab)) {
-        load_pay(P, r, pay);
-        __syncwarp();
-        rows_rowmajor<32>(P, Lm, pay, lab, warp * 32 + 16, lane);
+        load_pay(P, r, pay, TS_L2_SHIFTED);
+        BCF_SYNCWARP();
+        rows_rowmajor<32>(P, Lm, pay, lab, warp * 32 + 16, lane, TS_L2_SHIFTED);
       }
     }
-    __syncthreads();
+    BCF_SYNC();
 
     // Write-out in row-major order (output item r*m + c), staged through a
     // padded row-major copy so that both sides are conflict-free and coalesced.
-    load_row(P, Lm, t, pay, lab);
-    __syncthreads();
+    load_row(P, Lm, t, pay, lab, TS_L2_IO);
+    BCF_SYNC();
 #pragma unroll
-    for (int c = 0; c < 32; ++c) P[t * 33 + c] = pay[c];
-    __syncthreads();
+    for (int c = 0; c < 32; ++c) {
+      BCF_TR(&P[t * 33 + c], 4, 1, TS_L2_IO);
+      P[t * 33 + c] = pay[c];
+    }
+    BCF_SYNC();
     uint32_t* vo = vals_out + base;
     uint32_t* ko = keys_out + base;
 #pragma unroll 4
     for (int i = 0; i < 32; ++i) {
       const int q = i * kL2W + t, r = q >> 5, c = q & 31;
+      BCF_TR(&P[r * 33 + c], 4, 0, TS_L2_IO);
       __stcs(vo + q, P[r * 33 + c]);
-      __stcs(ko + q, (Lm[lm_idx(r)] >> c) & 1u);
+      __stcs(ko + q, (load_mask(Lm, r, TS_L2_IO) >> c) & 1u);
     }
-    __syncthreads();
+    BCF_SYNC();
   }
 }
 
@@ -311,5 +344,7 @@ cudaError_t partition_lemma2(const uint32_t* keys, const uint32_t* vals, uint32_
   k_partition_l2<<<(unsigned)grid, 1024, kL2Smem, s>>>(keys, vals, keys_out, vals_out, tiles, status_word());
   return cudaGetLastError();
 }
+
+BCF_TRACE_INSTALLER(partition_l2)
 
 }  // namespace bcf

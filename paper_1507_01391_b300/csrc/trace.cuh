@@ -3,11 +3,12 @@
 // In a trace build every instrumented shared-memory access appends one record per
 // active lane to a caller-provided device buffer: (request id, thread index |
 // block index << 16, shared-window byte address, width | store << 8 | site << 16),
-// and every block-wide barrier taken through BCF_SYNC() one record per warp.  All lanes of one warp-wide
-// access share the request id, so the trace can be replayed through the bank model
-// of Sec. 1 (32 banks of 4-byte words; a request conflicts when two of its lanes
-// need different words of one bank).  Without BCF_TRACE the macro is empty and the
-// kernels are unchanged.
+// and every barrier taken through BCF_SYNC() (block-wide) or BCF_SYNCWARP()
+// (warp-wide) one record per warp.  All lanes of one warp-wide access share the
+// request id, so the trace can be replayed through the bank model of Sec. 1 (32
+// banks of 4-byte words; a request conflicts when two of its lanes need different
+// words of one bank).  Without BCF_TRACE the macro is empty and the kernels are
+// unchanged.
 #pragma once
 
 #include "common.cuh"
@@ -34,7 +35,15 @@ enum TraceSite : uint32_t {
   TS_COL_READ = 22,     // colouring: reading own row (labels, items)
   TS_COL_FINISH = 23,   // colouring: finishing sends (greedy or sorted)
   TS_COL_PACK = 24,     // colouring, sorted finish: ordering and packing the leftovers
-  TS_BARRIER = 30,      // a block-wide barrier (one record per warp; store field 3)
+  TS_L2_SQUARE = 40,    // Lemma 2: balancing round 0 (column-major square sorts)
+  TS_L2_CONVERT = 41,   // Lemma 2: balancing round 1 composed with the conversion
+  TS_L2_DIVIDE = 42,    // Lemma 2: 8-row sub-problems sorted row-major
+  TS_L2_COLUMN = 43,    // Lemma 2: column sorts (counts and moves)
+  TS_L2_ROWS = 44,      // Lemma 2: squares of 32 contiguous rows, row-major
+  TS_L2_SHIFTED = 45,   // Lemma 2: the same squares shifted down by 16 rows
+  TS_L2_IO = 47,        // Lemma 2: the padded row-major write-out copy
+  TS_BARRIER = 30,      // a barrier (one record per warp; store field 3 block-wide, 4 warp-wide)
+  TS_PROBE = 50,        // the bank-conflict probe kernels
 };
 
 #ifdef BCF_TRACE
@@ -71,9 +80,10 @@ __device__ __forceinline__ void trace_access(const void* p, uint32_t width, uint
   }
 }
 
-// After a block-wide barrier every warp appends one barrier record, so a replay
+// After a block-wide barrier every warp appends one barrier record (store field 3),
+// and after a warp-wide barrier the warp appends one (store field 4), so a replay
 // can split each warp's accesses into the segments between barriers.
-__device__ __forceinline__ void trace_barrier() {
+__device__ __forceinline__ void trace_barrier(uint32_t kind = 3u) {
   const TraceState t = g_bcf_trace;
   if (!t.count || (threadIdx.x & 31u) != (uint32_t)(__ffs(__activemask()) - 1)) return;
   const unsigned long long r = atomicAdd(t.count, 1ull);
@@ -82,7 +92,7 @@ __device__ __forceinline__ void trace_barrier() {
     o[0] = (uint32_t)r;
     o[1] = (uint32_t)threadIdx.x | ((uint32_t)blockIdx.x << 16);
     o[2] = 0;
-    o[3] = 0u | (3u << 8) | ((uint32_t)TS_BARRIER << 16);
+    o[3] = 0u | (kind << 8) | ((uint32_t)TS_BARRIER << 16);
   }
 }
 #define BCF_TR(ptr, width, store, site) ::bcf::trace_access((ptr), (width), (store), (site))
@@ -91,10 +101,16 @@ __device__ __forceinline__ void trace_barrier() {
     __syncthreads();             \
     ::bcf::trace_barrier();      \
   } while (0)
+#define BCF_SYNCWARP()           \
+  do {                           \
+    __syncwarp();                \
+    ::bcf::trace_barrier(4u);    \
+  } while (0)
 #else
 #define BCF_TR(ptr, width, store, site) ((void)0)
 #define BCF_TRACE_INSTALLER(name)
 #define BCF_SYNC() __syncthreads()
+#define BCF_SYNCWARP() __syncwarp()
 #endif
 // Sub-word accesses are traced as the 4-byte word that holds them.
 #define BCF_TR_WORD(ptr, store, site) \

@@ -14,6 +14,8 @@ cudaError_t trace_install_radix(const TraceState& t);
 cudaError_t trace_install_segmented(const TraceState& t);
 cudaError_t trace_install_tile_permute(const TraceState& t);
 cudaError_t trace_install_partition_l1(const TraceState& t);
+cudaError_t trace_install_partition_l2(const TraceState& t);
+cudaError_t trace_install_bank_probe(const TraceState& t);
 }  // namespace bcf
 
 namespace {
@@ -24,6 +26,8 @@ int install(const bcf::TraceState& t) {
   if (bcf::trace_install_segmented(t) != cudaSuccess) return BCF_E_CUDA;
   if (bcf::trace_install_tile_permute(t) != cudaSuccess) return BCF_E_CUDA;
   if (bcf::trace_install_partition_l1(t) != cudaSuccess) return BCF_E_CUDA;
+  if (bcf::trace_install_partition_l2(t) != cudaSuccess) return BCF_E_CUDA;
+  if (bcf::trace_install_bank_probe(t) != cudaSuccess) return BCF_E_CUDA;
   return BCF_OK;
 }
 }  // namespace

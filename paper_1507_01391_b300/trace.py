@@ -24,6 +24,8 @@ SITES = {
     "offset_read": 6, "hist_atom": 7, "hist_sum": 8, "warp_offsets": 9, "l1_row_ld": 10, "l1_row_st": 11, "l1_convert": 12, "l1_io": 13,
     "col_table": 20, "col_send": 21, "col_read": 22, "col_finish": 23, "col_pack": 24,
     "barrier": 30,
+    "l2_square": 40, "l2_convert": 41, "l2_divide": 42, "l2_column": 43, "l2_rows": 44, "l2_shifted": 45,
+    "l2_io": 47, "probe": 50,
 }
 
 _trace_lib = None
@@ -43,6 +45,9 @@ def load() -> ctypes.CDLL:
         L.bcf_trace_begin.restype = ctypes.c_int
         L.bcf_trace_end.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         L.bcf_trace_end.restype = ctypes.c_int
+        L.bcf_trace_bank_probe.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 2 + [ctypes.c_int] * 2 + [
+            ctypes.c_void_p]
+        L.bcf_trace_bank_probe.restype = ctypes.c_int
         _trace_lib = L
     return _trace_lib
 
@@ -82,7 +87,7 @@ def capture(fn, max_records: int = 1 << 22):
 
 def fields(rec):
     """Split records into (request, lane, address, width, store, site) arrays
-    (barrier records have store 3 and width 0)."""
+    (barrier records have store 3, or 4 for a warp barrier, and width 0)."""
     return (rec[:, 0].astype(np.int64), (rec[:, 1] & 31).astype(np.int32), rec[:, 2].astype(np.uint32),
             (rec[:, 3] & 0xFF).astype(np.int32), ((rec[:, 3] >> 8) & 0xFF).astype(np.int32),
             (rec[:, 3] >> 16).astype(np.int32))
@@ -90,4 +95,4 @@ def fields(rec):
 
 def accesses(rec):
     """The records without the barrier ones."""
-    return rec[((rec[:, 3] >> 8) & 0xFF) != 3]
+    return rec[((rec[:, 3] >> 8) & 0xFF) < 3]

@@ -121,7 +121,7 @@ def test_trace_build_exports_both_headers():
     hdr = os.path.join(os.path.dirname(bcf.HEADER), "bcf_trace.h")
     text = re.sub(r"/\*.*?\*/", "", open(hdr).read(), flags=re.S)
     trace_names = set(re.findall(r"\b(bcf_[a-z0-9_]+)\s*\(", text))
-    assert trace_names == {"bcf_trace_begin", "bcf_trace_end"}
+    assert trace_names == {"bcf_trace_begin", "bcf_trace_end", "bcf_trace_bank_probe"}
     nm = lambda p: {l.split()[-1] for l in subprocess.run(["nm", "-D", "--defined-only", p], capture_output=True,
                                                           text=True).stdout.splitlines() if " T " in l}
     tlib = os.path.join(os.path.dirname(bcf._LIB_PATH), "libbcf_trace.so")
@@ -169,3 +169,17 @@ def test_lookback_testing_aid_arguments():
     L = bcf.lib()
     assert L.bcf_debug_lookback(3, 0) == bcf.E_INVAL
     assert L.bcf_debug_lookback(-1, 0) == bcf.OK
+
+
+def test_bank_probe_argument_checks():
+    """The probe entry point rejects bad arguments before launching (CPU)."""
+    from paper_1507_01391_b300 import trace
+    L = trace.load()
+    P = ctypes.c_void_p
+    a, b = P(0x10000), P(0x20000)
+    assert L.bcf_trace_bank_probe(7, 0, 0, a, b, 1, 1, None) == bcf.E_INVAL
+    assert L.bcf_trace_bank_probe(0, 4, 0, a, b, 1, 1, None) == bcf.E_INVAL
+    assert L.bcf_trace_bank_probe(-1, 0, 0, a, b, 1, 1, None) == bcf.E_INVAL
+    assert L.bcf_trace_bank_probe(0, 0, 0, None, b, 1, 1, None) == bcf.E_INVAL
+    assert L.bcf_trace_bank_probe(0, 0, 0, a, b, 0, 1, None) == bcf.E_INVAL
+    assert L.bcf_trace_bank_probe(0, 0, 0, a, b, 1, 0, None) == bcf.E_INVAL

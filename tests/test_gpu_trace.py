@@ -235,3 +235,81 @@ def test_segmented_small_path_has_no_races(tr):
     rk, rv = oracle.segmented_sort_kv(keys, vals, offs)
     assert bits_equal(host(out["k"], np.uint32), rk) and bits_equal(host(out["v"], np.uint32), rv)
     _no_races(rec)
+
+
+L2_SITES = ("l2_square", "l2_convert", "l2_divide", "l2_column", "l2_rows", "l2_shifted", "l2_io")
+
+
+@pytest.mark.parametrize("p", [0.5, 0.03])
+def test_lemma2_partition_trace(tr, p):
+    """Lemma 2's 0-1 partition (two 1024 x 32 matrices): the result is the oracle's,
+    no two threads race on a word (warp barriers order each step sort's reads
+    before its writes), and every step's accesses replay through the bank model;
+    the per-step counts under both rules are printed (pytest -s)."""
+    import paper_1507_01391_b300 as bcf
+    n = 2 * 32768
+    keys = synth.bernoulli_labels(n, p, seed=31)
+    vals = synth.index_payload(n)
+    out = {}
+
+    def run():
+        out["k"], out["v"] = bcf.partition_lemma2(dev(keys), dev(vals))
+    rec, total = tr.capture(run)
+    assert total == rec.shape[0]
+    ko, vo = host(out["k"], np.uint32), host(out["v"], np.uint32)
+    for t in range(2):
+        a = slice(t * 32768, (t + 1) * 32768)
+        lo, po = oracle.lemma2_partition(keys[a].reshape(32, 1024).T, vals[a].reshape(32, 1024).T)
+        assert np.array_equal(ko[a], lo.ravel()) and bits_equal(vo[a], po.ravel())
+    _, _, _, _, store, _ = tr.fields(rec)
+    assert np.count_nonzero(store == 4) > 0  # the step sorts' warp barriers were recorded
+    seen = {site: _replay(tr, rec, site) for site in L2_SITES}
+    for site in ("l2_square", "l2_convert", "l2_column", "l2_io"):
+        assert seen[site] is not None, site
+    # The step sorts scatter a run of 0-items and a run of 1-items, each to
+    # consecutive positions: a square's column step is at most 2-way, and so is
+    # every access of the shifted squares (the row rotation maps lanes 0 and 31 of
+    # a window to one bank).  The padded row-major write-out is conflict-free.
+    for site in ("l2_square", "l2_convert", "l2_shifted"):
+        if seen[site] is not None:
+            assert seen[site]["wavefronts"] <= 2 * seen[site]["requests"], (site, seen[site])
+    assert seen["l2_io"]["hw_conflicts"] == 0
+    _no_races(rec)
+
+
+PROBE_BLOCKS, PROBE_REPS = 3 * 148, 32
+
+
+@pytest.mark.parametrize("pattern", range(7))
+def test_bank_probe_patterns(tr, pattern):
+    """The probe kernels (one shared-memory access pattern of the Lemma 1 tile sort
+    each): the traced copy replays with zero hardware conflicts in the bank model
+    and no races; the untraced copies run with every kind of global traffic
+    beside them, and the traffic that does not feed the checksum (none / store,
+    and L1 / L2-only gathers of the same words) leaves it unchanged."""
+    import ctypes
+
+    import torch
+
+    L = tr.load()
+    OK = 0
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    blocks = PROBE_BLOCKS
+    gin = torch.arange(blocks * 4096, dtype=torch.int32, device="cuda")
+    outs = []
+
+    def run():
+        gout = torch.zeros(blocks * (4096 + 256), dtype=torch.int32, device="cuda")
+        assert L.bcf_trace_bank_probe(pattern, 0, 1, ptr(gin), ptr(gout), 2, 2, None) == OK
+    rec, total = tr.capture(run)
+    assert total == rec.shape[0]
+    r = _replay(tr, rec, "probe")
+    assert r is not None and r["hw_conflicts"] == 0, r
+    _no_races(rec)
+    for traffic in range(4):
+        gout = torch.zeros(blocks * (4096 + 256), dtype=torch.int32, device="cuda")
+        assert L.bcf_trace_bank_probe(pattern, traffic, 0, ptr(gin), ptr(gout), blocks, PROBE_REPS, None) == OK
+        torch.cuda.synchronize()
+        outs.append(gout[blocks * 4096:].cpu())
+    assert torch.equal(outs[0], outs[3]) and torch.equal(outs[1], outs[2])
+    assert not torch.equal(outs[0], outs[1])

@@ -488,6 +488,23 @@ def test_race_check_rules(orc):
     assert (races, words) == (0, 5)
 
 
+def _wbar(thread, block=0):
+    return [0, thread | (block << 16), 0, (4 << 8) | (30 << 16)]
+
+
+def test_race_check_warp_barriers(orc):
+    """A warp barrier orders the accesses of one warp's lanes, not those of two warps;
+    a block barrier still splits everything."""
+    R = lambda rows: orc.race_check(np.array(rows, dtype=np.uint32))[0]
+    assert R([_rec(0, 64, 1), _wbar(0), _rec(7, 64, 0)]) == 0              # same warp, barrier between
+    assert R([_rec(0, 64, 1), _rec(7, 64, 0)]) == 1                        # same warp, none
+    assert R([_rec(0, 64, 1), _wbar(0), _wbar(32), _rec(40, 64, 0)]) == 1  # two warps: not ordered
+    assert R([_rec(7, 64, 0), _wbar(0), _rec(0, 64, 1)]) == 0              # read, barrier, then write
+    assert R([_rec(0, 64, 1), _wbar(0), _rec(7, 64, 1), _rec(9, 64, 0)]) == 1  # 7 and 9 after it, unordered
+    # a block barrier between makes the warp epochs irrelevant
+    assert R([_rec(0, 64, 1), _wbar(0), _bar(0), _bar(32), _rec(40, 64, 0)]) == 0
+
+
 # ------------------------------------------------- Lemma 2 (0-1 partition) ----
 def _l2_inputs(w, m, seed):
     """Random labels at several densities and structured ones (all 0, all 1, one

@@ -51,6 +51,7 @@ constexpr int kSweepThreads = BCF_SWEEP_THREADS;
 constexpr int kSweepIPT = BCF_SWEEP_IPT;
 constexpr int kSweepTile = kSweepThreads * kSweepIPT;  // keys per tile (default configuration)
 constexpr int kLookbackWindow = BCF_LB_WINDOW;
+static_assert(kLookbackWindow % 4 == 0, "count rows are read and written as 16-byte vectors");
 
 // Configurations of the sort / partition passes that the tuner picks from: a pass
 // form and a tile shape (threads per block x keys per thread).

@@ -174,6 +174,49 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* scratc
   return before + x - v;
 }
 
+// Exclusive scans of N independent values per thread over the block, in one set
+// of barriers; total[k] gets the sum of sequence k.  scratch holds N * 32 words.
+template <int THREADS, int N>
+__device__ __forceinline__ void block_excl_scan_n(const uint32_t (&v)[N], uint32_t (&out)[N], uint32_t* scratch,
+                                                  uint32_t (&total)[N]) {
+  constexpr int WARPS = THREADS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] = v[k];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x[k], o);
+      if (lane >= o) x[k] += y;
+    }
+  }
+  if (lane == 31)
+#pragma unroll
+    for (int k = 0; k < N; ++k) scratch[k * 32 + warp] = x[k];
+  BCF_SYNC();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      uint32_t t = lane < WARPS ? scratch[k * 32 + lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < WARPS) scratch[k * 32 + lane] = t;
+    }
+  }
+  BCF_SYNC();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    out[k] = (warp ? scratch[k * 32 + warp - 1] : 0u) + x[k] - v[k];
+    total[k] = scratch[k * 32 + WARPS - 1];
+  }
+  BCF_SYNC();
+}
+
 // ------------------------------------------------------------- histogram
 struct HistParams {
   const uint32_t* keys;
@@ -500,27 +543,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* count
                                                                  int64_t stride, const uint32_t* totals,
                                                                  int balanced, int64_t n, int w,
                                                                  unsigned* status, PassSel sel) {
-  __shared__ uint32_t scratch[32];
+  constexpr int R = kScanPerThread / 4;
+  __shared__ uint32_t scratch[R * 32];
   __shared__ uint32_t s_base;
   const int d = blockIdx.x;
   const int tid = threadIdx.x;
   uint32_t* row = counts + (size_t)d * stride;
-  // The first chunk's counts are loaded before the digit start is summed, so
-  // that the two global reads overlap.
-  uint32_t v[kScanPerThread];
-  auto load = [&](int64_t i0) {
-    if (i0 + kScanPerThread <= tiles) {  // 64-byte aligned: four 16-byte loads
+  // A chunk is kScanPerThread / 4 rounds; in round r thread t holds the four
+  // counts at r * 4 * kScanThreads + 4t, so every warp-wide load and store covers
+  // 512 contiguous bytes (rows start 16-byte aligned: every caller's stride is a
+  // multiple of the look-back window, 4 or 8 words).  The rounds' sums are
+  // scanned together, one set of barriers per chunk.  The first chunk's counts
+  // are loaded before the digit start is summed, so that the two global reads
+  // overlap.
+  constexpr int64_t CH = (int64_t)kScanThreads * kScanPerThread;
+  uint4 v[R];
+  auto at = [&](int64_t c0, int r) { return c0 + (int64_t)r * 4 * kScanThreads + 4 * tid; };
+  auto load = [&](int64_t c0) {
 #pragma unroll
-      for (int j = 0; j < kScanPerThread; j += 4) {
-        const uint4 x = *reinterpret_cast<const uint4*>(row + i0 + j);
-        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+    for (int r = 0; r < R; ++r) {
+      const int64_t i0 = at(c0, r);
+      if (i0 + 4 <= tiles) {
+        v[r] = *reinterpret_cast<const uint4*>(row + i0);
+      } else {
+        v[r].x = i0 < tiles ? row[i0] : 0u;
+        v[r].y = i0 + 1 < tiles ? row[i0 + 1] : 0u;
+        v[r].z = i0 + 2 < tiles ? row[i0 + 2] : 0u;
+        v[r].w = i0 + 3 < tiles ? row[i0 + 3] : 0u;
       }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kScanPerThread; ++j) v[j] = (i0 + j < tiles) ? row[i0 + j] : 0u;
     }
   };
-  load((int64_t)tid * kScanPerThread);
+  load(0);
   __shared__ int s_skip;
   if (tid < 32) {  // digit start: warp-wide sum of the smaller digits' totals
     uint32_t b = 0;
@@ -542,20 +595,33 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_offsets_t(uint32_t* count
   BCF_SYNC();
   if (s_skip) return;
   uint32_t carry = s_base;
-  for (int64_t c0 = 0; c0 < tiles; c0 += (int64_t)kScanThreads * kScanPerThread) {
-    const int64_t i0 = c0 + (int64_t)tid * kScanPerThread;
-    if (c0 > 0) load(i0);
-    uint32_t sum = 0;
+  for (int64_t c0 = 0; c0 < tiles; c0 += CH) {
+    if (c0 > 0) load(c0);
+    uint32_t sum[R], ex[R], total[R];
 #pragma unroll
-    for (int j = 0; j < kScanPerThread; ++j) sum += v[j];
-    uint32_t total;
-    uint32_t run = carry + block_excl_scan<kScanThreads>(sum, scratch, &total);
+    for (int r = 0; r < R; ++r) sum[r] = v[r].x + v[r].y + v[r].z + v[r].w;
+    block_excl_scan_n<kScanThreads, R>(sum, ex, scratch, total);
 #pragma unroll
-    for (int j = 0; j < kScanPerThread; ++j) {
-      if (i0 + j < tiles) row[i0 + j] = run;
-      run += v[j];
+    for (int r = 0; r < R; ++r) {
+      uint32_t run = carry + ex[r];
+      uint4 o;
+      o.x = run;
+      run += v[r].x;
+      o.y = run;
+      run += v[r].y;
+      o.z = run;
+      run += v[r].z;
+      o.w = run;
+      const int64_t i0 = at(c0, r);
+      if (i0 + 4 <= tiles) {
+        *reinterpret_cast<uint4*>(row + i0) = o;
+      } else {
+        if (i0 < tiles) row[i0] = o.x;
+        if (i0 + 1 < tiles) row[i0 + 1] = o.y;
+        if (i0 + 2 < tiles) row[i0 + 2] = o.z;
+      }
+      carry += total[r];
     }
-    carry += total;
   }
   if (tid == 0 && tiles < stride) row[tiles] = carry;  // end of the digit's runs
 }

@@ -369,7 +369,10 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
   static_assert(kCountTilesPerBlock == 4, "fast path counts four tiles at once");
   __shared__ uint32_t h[RADIX];
   __shared__ uint32_t tot[RADIX];
-  __shared__ uint32_t h4[FAST ? 4 : 1][RADIX];
+  __shared__ __align__(16) uint32_t h4[FAST ? 4 : 1][RADIX];
+  // fast path: lane-private byte counters, counter (tile t, digit d) of lane l is
+  // byte d mod 4 of lc[t][d / 4][l]
+  __shared__ __align__(16) uint32_t lc[FAST ? 4 : 1][FAST ? RADIX / 4 : 1][32];
   const int tid = threadIdx.x;
   for (int i = tid; i < RADIX; i += 256) tot[i] = 0;
   const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
@@ -410,11 +413,20 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
     o0 |= ~x.x | ~x.y | ~x.z | ~x.w;
   };
   if constexpr (FAST && NV <= 4) {
-    // Four full tiles: every load in flight before any count, one histogram per
-    // tile, and the four counts of a digit stored together (the count rows'
-    // stride is a multiple of 16 words and t0 a multiple of 4).
+    // Four full tiles: every load in flight before any count, and the four counts
+    // of a digit stored together (the count rows' stride is a multiple of 4 words
+    // and t0 a multiple of 4).  The counters are private to a lane -- lane l only
+    // ever adds to words in bank l -- so the 32 lanes of a counting atomic touch
+    // 32 different banks whatever the digits (the conflict avoidance condition of
+    // Sec. 1).  A byte suffices: a lane's counter of one tile sees at most T / 32
+    // keys.  Thread (t, g) then sums the 32 lane words of digit group g of tile t,
+    // reading them along a diagonal so that the 8 threads of one 16-byte access
+    // phase read 8 different bank quads.
+    static_assert(T / 32 <= 255 && RADIX % 32 == 0, "byte counters, whole 16-byte phases");
     if (!segmented && (t0 + 4) * T <= p.n) {
-      for (int i = tid; i < 4 * RADIX; i += 256) h4[i / RADIX][i % RADIX] = 0;
+      const int lane = tid & 31;
+      uint4* lz = reinterpret_cast<uint4*>(&lc[0][0][0]);
+      for (int i = tid; i < RADIX * 8; i += 256) lz[i] = make_uint4(0u, 0u, 0u, 0u);
       uint4 x[4][NV];
       const uint4* k4 = reinterpret_cast<const uint4*>(p.keys + t0 * T);
 #pragma unroll
@@ -422,16 +434,37 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
 #pragma unroll
         for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
       BCF_SYNC();
+      auto count = [&](int t, uint32_t k) {
+        const uint32_t d = dig(k);
+        BCF_TR(&lc[t][d >> 2][lane], 4, 2, TS_TILE_COUNT_ATOM);
+        atomicAdd(&lc[t][d >> 2][lane], 1u << (8 * (d & 3u)));
+      };
 #pragma unroll
       for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          atomicAdd(&h4[t][dig(x[t][q].x)], 1u);
-          atomicAdd(&h4[t][dig(x[t][q].y)], 1u);
-          atomicAdd(&h4[t][dig(x[t][q].z)], 1u);
-          atomicAdd(&h4[t][dig(x[t][q].w)], 1u);
+          count(t, x[t][q].x);
+          count(t, x[t][q].y);
+          count(t, x[t][q].z);
+          count(t, x[t][q].w);
           if (fill_vary) or4(x[t][q]);
         }
+      BCF_SYNC();
+      if (tid < RADIX) {  // RADIX pairs (tile, group of four digits)
+        const int t = tid / (RADIX / 4), g = tid % (RADIX / 4);
+        const uint4* row = reinterpret_cast<const uint4*>(&lc[t][g][0]);
+        uint32_t ev = 0, od = 0;  // bytes 0 and 2, bytes 1 and 3: 16-bit sums
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          BCF_TR(&row[(m + g) & 7], 16, 0, TS_TILE_COUNT_SUM);
+          const uint4 w = row[(m + g) & 7];
+          ev += (w.x & 0x00FF00FFu) + (w.y & 0x00FF00FFu) + (w.z & 0x00FF00FFu) + (w.w & 0x00FF00FFu);
+          od += ((w.x >> 8) & 0x00FF00FFu) + ((w.y >> 8) & 0x00FF00FFu) + ((w.z >> 8) & 0x00FF00FFu) +
+                ((w.w >> 8) & 0x00FF00FFu);
+        }
+        BCF_TR(&h4[t][4 * g], 16, 1, TS_TILE_COUNT_SUM);
+        *reinterpret_cast<uint4*>(&h4[t][4 * g]) = make_uint4(ev & 0xFFFFu, od & 0xFFFFu, ev >> 16, od >> 16);
+      }
       BCF_SYNC();
       for (int d = tid; d < RADIX; d += 256) {
         const uint4 c = make_uint4(h4[0][d], h4[1][d], h4[2][d], h4[3][d]);

@@ -26,6 +26,8 @@ enum TraceSite : uint32_t {
   TS_HIST_ATOM = 7,     // one-read histogram: lane-private digit count
   TS_HIST_SUM = 8,      // one-read histogram: diagonal sum of the lane counters
   TS_WARP_OFFSETS = 9,  // per-(warp, digit) count row read / rewritten as offsets
+  TS_TILE_COUNT_ATOM = 14,  // per-tile counts: lane-private byte counters
+  TS_TILE_COUNT_SUM = 15,   // per-tile counts: diagonal sum of the lane words
   TS_L1_ROW_LD = 10,    // Lemma 1: row sort loads (register sort and merges)
   TS_L1_ROW_ST = 11,    // Lemma 1: row sort stores
   TS_L1_CONVERT = 12,   // Lemma 1: row <-> column conversions

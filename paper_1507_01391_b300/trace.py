@@ -22,6 +22,7 @@ TRACE_LIB_PATH = os.path.join(_PKG, "libbcf_trace.so")
 SITES = {
     "stage_read": 1, "count_atom": 2, "claim_atom": 3, "scatter": 4, "writeout_read": 5,
     "offset_read": 6, "hist_atom": 7, "hist_sum": 8, "warp_offsets": 9, "l1_row_ld": 10, "l1_row_st": 11, "l1_convert": 12, "l1_io": 13,
+    "tile_count_atom": 14, "tile_count_sum": 15,
     "col_table": 20, "col_send": 21, "col_read": 22, "col_finish": 23, "col_pack": 24,
     "barrier": 30,
     "l2_square": 40, "l2_convert": 41, "l2_divide": 42, "l2_column": 43, "l2_rows": 44, "l2_shifted": 45,

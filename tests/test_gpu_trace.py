@@ -196,6 +196,40 @@ def test_single_launch_sort_trace(tr, n):
     _no_races(rec)
 
 
+@pytest.mark.parametrize("n", [8 * 4096, 8 * 4096 + 3 * 1024 + 7])
+def test_tile_count_sort_trace(tr, n):
+    """The reduce-then-scan sort passes (counts, scan, pass body): the per-tile
+    count kernel keeps every lane's byte counters in the lane's own bank, so its
+    counting atomics replay with zero conflicts under both rules (full groups of
+    four tiles; a ragged remainder takes the shared-histogram path), and the
+    diagonal 16-byte sums of the lane words with zero under the hardware rule (the
+    strict rule counts the four words of one lane's 16-byte access as four lanes on
+    a bank).  No word races between barriers."""
+    import paper_1507_01391_b300 as bcf
+    keys = synth.uniform_keys(n, seed=n + 1)
+    vals = synth.index_payload(n)
+    out = {}
+
+    def run():
+        out["k"], out["v"] = bcf.sort(dev(keys), dev(vals))
+    L = tr.load()
+    lg = (n - 1).bit_length()
+    assert L.bcf_tune_config_form(4) == 1  # counts + scan + pass body, 256 x 16
+    assert L.bcf_tune_set(bcf.OP_SORT, lg, 4) == bcf.OK
+    try:
+        rec, _ = tr.capture(run)
+    finally:
+        L.bcf_tune_set(bcf.OP_SORT, lg, -1)
+    rk, rv = oracle.sort_kv(keys, vals)
+    assert bits_equal(host(out["k"], np.uint32), rk) and bits_equal(host(out["v"], np.uint32), rv)
+    r = _replay(tr, rec, "tile_count_atom")
+    assert r is not None and r["hw_conflicts"] == 0 and r["strict_conflicts"] == 0, r
+    r = _replay(tr, rec, "tile_count_sum")
+    assert r is not None and r["hw_conflicts"] == 0 and r["wavefronts"] == 4 * r["requests"], r
+    assert _replay(tr, rec, "tile_count_atom")["requests"] == 4 * (8 * 4096 // 32)  # four passes, full tiles
+    _no_races(rec)
+
+
 def test_lemma1_partition_replays_conflict_free(tr):
     """The Lemma 1 tile partition: every shared access of its schedule replays
     with zero hardware conflicts (the label counts are the only atomics)."""

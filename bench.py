@@ -619,6 +619,8 @@ def run_tuning():
     res.update({"partition": {}})
     res["partition"].update(tune.autotune(ops=("partition",), log2_sizes=[26], w=256, reps=3)["partition"])
     res["partition"].update(tune.autotune(ops=("partition",), log2_sizes=[16], w=32, reps=5)["partition"])
+    # the batched sort's 10,000 segments hold 2.9e8 keys: ceil(log2) = 29
+    res.update(tune.autotune(ops=("segmented_sort",), log2_sizes=[29], reps=3))
     out = {}
     for op, tab in res.items():
         out[op] = {"2^%d" % k: {"config": best, "threads_x_keys": "%dx%d" % tune.configs()[best],
@@ -634,6 +636,7 @@ def run_rows(which, peak):
 
     import paper_1507_01391_b300 as bcf
     import synth
+    from paper_1507_01391_b300 import tune
     rows = {}
     plain_ns = {}  # ns per key of the plain forms, for the batched / autograd ratios
 
@@ -819,9 +822,16 @@ def run_rows(which, peak):
             ws = bcf.workspace(bcf.segmented_sort_workspace_size(n, 10_000, 4, 32))
             ms_eager, _ = ev_ms(lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws), 2, 5)
             ms, _ = graph_ms(lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws), 2, 5)
+            cfg = tune.get_config("segmented_sort", n)
+            form = bcf.lib().bcf_tune_config_form(cfg)
+            launches = 2 + 4 * 4  # plan, small segments; per digit pass counts, scan, digit starts, pass
             add("segmented_sort_batched_10k", n, 16 * small + 68 * (n - small), ms,
                 "%d keys, one CUDA-graph replay (eager call %.3f ms); segments <= 4096 keys sorted whole in "
-                "shared memory (16 B/key), longer ones by 4 digit passes + counts (68 B/key model)" % (n, ms_eager))
+                "shared memory (16 B/key), longer ones by 4 digit passes + counts (68 B/key model); tuned "
+                "configuration %d (%s, 256 x 16), %d kernel launches and one memset per call" % (
+                    n, ms_eager, cfg, "pass body fed scanned offsets" if form == 1 else "staged sweep", launches))
+            rows["segmented_sort_batched_10k"].update({"tuned_config": cfg, "pass_form": form,
+                                                       "kernel_launches_per_call": launches})
             plain_ns["segmented_sort_batched_10k"] = ms * 1e6 / n
             del k, v, ko, vo, ws
         if want("segmented_partition_batched_10k"):
@@ -867,14 +877,28 @@ def run_rows(which, peak):
                                                              ws=wss), 3, 10)
             ws = bcf.workspace(bcf.sort_workspace_size(B * n, 4, 20))
             ms_plain, _ = graph_ms(lambda: bcf.sort(kf, vf, key_bits=20, keys_out=ko, vals_out=vo, ws=ws), 3, 10)
+            # the plain pair of the same work: the per-row kv sort (forward) and the
+            # scatter of the upstream gradient by the sort's permutation (backward)
+            gflat = g.reshape(-1)
+            perm_rows = torch.empty_like(kf)
+            bcf.segmented_sort(kf, None, offs, key_bits=20, keys_out=ko, vals_out=perm_rows, ws=wss,
+                               index_payload=True)
+            go = torch.empty_like(gflat)
+
+            def plain_pair():
+                bcf.segmented_sort(kf, vf, offs, key_bits=20, keys_out=ko, vals_out=vo, ws=wss)
+                bcf.permute(gflat, perm_rows, dst=go)
+            ms_pair, _ = graph_ms(plain_pair, 3, 10)
             add("autograd_sort_by_key_64x65536", B * n, B * n * (3 * 16 + 12 + 12), ms,
                 "forward (per-row sort with index payload + gather) and backward scatter, one CUDA-graph "
                 "replay (eager %.3f ms); forward alone %.4f ms vs the plain per-row kv sort %.4f ms; "
+                "plain pair (per-row kv sort + scatter of the gradient) %.4f ms; "
                 "plain flat kv sort of all keys %.4f ms; the 2^22-key working set stays in L2, so the HBM "
-                "fraction is nominal" % (ms_eager, ms_fwd, ms_rows, ms_plain))
+                "fraction is nominal" % (ms_eager, ms_fwd, ms_rows, ms_pair, ms_plain))
             r = rows["autograd_sort_by_key_64x65536"]
             r.update({"fwd_ms": round(ms_fwd, 4), "plain_rows_sort_ms": round(ms_rows, 4),
                       "ratio_fwd_vs_plain_rows_sort": round(ms_fwd / ms_rows, 3),
+                      "plain_pair_ms": round(ms_pair, 4), "ratio_fwdbwd_vs_plain_pair": round(ms / ms_pair, 3),
                       "plain_flat_sort_ms": round(ms_plain, 4), "ratio_fwdbwd_vs_plain_flat_sort": round(ms / ms_plain, 3),
                       "eager_ms": round(ms_eager, 4)})
         if want("autograd_permute_rows_64x65536"):

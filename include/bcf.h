@@ -274,6 +274,12 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
  * device and fills the table (with a text cache per device). */
 #define BCF_OP_SORT 0
 #define BCF_OP_PARTITION 1
+/* Batched sort (bcf_segmented_sort, keyed by ceil(log2 n_total)): its plan cuts
+ * the long segments into 4096-key tiles, so only the counts + scan
+ * configurations of 256 x 16 apply (bcf_tune_set refuses the others with
+ * BCF_E_INVAL); without an entry the long segments' passes use the pass body fed
+ * scanned offsets (form 1). */
+#define BCF_OP_SEGMENTED_SORT 2
 int bcf_tune_num_configs(void);
 /* BCF_E_INVAL for an unknown configuration or a null output. */
 int bcf_tune_config_info(int config, int* threads, int* keys_per_thread);
@@ -281,7 +287,9 @@ int bcf_tune_config_info(int config, int* threads, int* keys_per_thread);
  * 1 per-tile counts + scan + the same pass body, 2 counts + scan + the
  * shared-memory-staged sweep; BCF_E_INVAL for an unknown configuration. */
 int bcf_tune_config_form(int config);
-/* config in [-1, num_configs); log2_n in [0, 63].  BCF_E_INVAL otherwise. */
+/* op in [BCF_OP_SORT, BCF_OP_SEGMENTED_SORT]; config in [-1, num_configs) (for
+ * BCF_OP_SEGMENTED_SORT -1 or a 256 x 16 configuration of form 1 or 2); log2_n
+ * in [0, 63].  BCF_E_INVAL otherwise. */
 int bcf_tune_set(int op, int log2_n, int config);
 /* The configuration a call of n keys would use now. */
 int bcf_tune_get(int op, int64_t n, int* config);

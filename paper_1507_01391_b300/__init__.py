@@ -77,7 +77,7 @@ _SIGS = {
     "bcf_tune_save": ([ctypes.c_char_p], _I),
     "bcf_tune_load": ([ctypes.c_char_p, ctypes.POINTER(_I)], _I),
 }
-OP_SORT, OP_PARTITION = 0, 1
+OP_SORT, OP_PARTITION, OP_SEGMENTED_SORT = 0, 1, 2
 NOALLOC_MAX_N = 1 << 22
 
 

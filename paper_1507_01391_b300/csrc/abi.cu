@@ -419,12 +419,15 @@ int bcf_tune_config_form(int config) {
   return bcf::cfg_form(config);
 }
 
+static_assert(bcf::kOpSegmentedSort == BCF_OP_SEGMENTED_SORT && bcf::kTuneOps == BCF_OP_SEGMENTED_SORT + 1,
+              "tuning operations of the header and the table");
+
 int bcf_tune_set(int op, int log2_n, int config) {
   return bcf::tune_set(op, log2_n, config) == 0 ? BCF_OK : BCF_E_INVAL;
 }
 
 int bcf_tune_get(int op, int64_t n, int* config) {
-  if ((op != BCF_OP_SORT && op != BCF_OP_PARTITION) || n < 0 || !config) return BCF_E_INVAL;
+  if (op < BCF_OP_SORT || op > BCF_OP_SEGMENTED_SORT || n < 0 || !config) return BCF_E_INVAL;
   *config = bcf::tuned_config(op, n);
   return BCF_OK;
 }
@@ -464,7 +467,7 @@ int bcf_tune_save(const char* path) {
   if (!f) return BCF_E_INVAL;
   std::fprintf(f, "%s\n", kTuneHeader);
   for (const std::string& l : keep) std::fputs(l.c_str(), f);
-  for (int op = 0; op < 2; ++op)
+  for (int op = 0; op < bcf::kTuneOps; ++op)
     for (int b = 0; b < 64; ++b) {
       const int c = bcf::tune_entry(op, b);
       if (c >= 0) std::fprintf(f, "%s\t%d\t%d\t%d\n", key.c_str(), op, b, c);

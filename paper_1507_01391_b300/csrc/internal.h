@@ -72,6 +72,14 @@ constexpr int kRtsCfg0 = 2 * kNumOneConfigs;  // first configuration of the swee
 // Pass form of a configuration: 0 look-back, 1 offsets + onesweep body, 2 staged sweep.
 inline int cfg_form(int cfg) { return cfg < kNumOneConfigs ? 0 : (cfg < kRtsCfg0 ? 1 : 2); }
 inline bool cfg_is_onesweep(int cfg) { return cfg >= 0 && cfg < kRtsCfg0; }  // onesweep.cuh body
+// Tuning table operations: flat sort, flat partition, batched (segmented) sort.
+constexpr int kOpSegmentedSort = 2;
+constexpr int kTuneOps = 3;
+// The batched sort's plan cuts segments into tiles of kSweepTile keys, so its
+// passes take the counts + scan forms of that tile shape only.
+inline bool cfg_segment_capable(int cfg) {
+  return cfg >= kNumOneConfigs && cfg < kNumSweepConfigs && kSweepCfgThreads[cfg] * kSweepCfgIPT[cfg] == kSweepTile;
+}
 constexpr int kMinSweepTile = 1024;  // smallest tile of any configuration (sizes workspaces)
 constexpr int kOneMinTile = 2048;    // smallest tile of the onesweep.cuh configurations
 // Inputs up to this size run each sweep.cuh digit pass as one look-back sweep

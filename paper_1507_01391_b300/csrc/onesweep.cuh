@@ -165,6 +165,17 @@ struct OneSweepParams {
   unsigned spin_limit;         // polls before a wait gives up (0: kSpinLimit)
   int silent_tile1;            // testing aid: 1 + a tile that never publishes (0: none)
   PassSel sel;                 // sel.vary != nullptr: buffers (or a skip) decided on the device
+  // segment mode (seg_offs != nullptr; offsets mode, sorts only): tile t is
+  // piece t - seg_tile0[s] of segment s = tile_seg[t] (tiles past *num_tiles do
+  // nothing), tile_offsets holds running sums over all tiles, and a tile's run
+  // start is its running sum minus the one at its segment's first tile plus the
+  // segment's digit start seg_base[seg_slot[s] * RADIX + digit].
+  const int64_t* seg_offs;
+  const int32_t* tile_seg;
+  const int32_t* seg_tile0;
+  const int32_t* seg_slot;
+  const uint32_t* seg_base;
+  const uint32_t* num_tiles;
 };
 
 // Look-back predecessors read per round trip (one coalesced row load each).
@@ -183,13 +194,14 @@ struct OneSmem {
   // payloads.
   static constexpr size_t keys = 0;
   static constexpr size_t vals = (size_t)T * 4;                     // 8-byte payloads
-  static constexpr size_t stage = (size_t)T * 8;                    // 4-byte payloads
-  static constexpr size_t whist = (size_t)T * (4 + VB) + (VB == 4 ? (size_t)T * 4 : 0);
+  static constexpr size_t stage = (size_t)T * 8;                    // 4-byte payloads (+ 3 words of
+                                                                    // a segment's misalignment)
+  static constexpr size_t whist = (size_t)T * (4 + VB) + (VB == 4 ? (size_t)T * 4 + 16 : 0);
   static constexpr size_t gofs = whist + (size_t)WARPS * RADIX * 4;
   static constexpr size_t scratch = gofs + (size_t)RADIX * 4;  // scan scratch
   static constexpr size_t mbar = scratch + 32 * 4;
-  static constexpr size_t info = mbar + 16;
-  static constexpr size_t bytes = info + 16;
+  static constexpr size_t info = mbar + 16;   // ints: tile, route, segment, piece, slot; then lo, hi
+  static constexpr size_t bytes = info + 48;
   static_assert(mbar % 8 == 0, "mbarrier alignment");
 };
 
@@ -213,8 +225,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
   uint32_t* scratch = reinterpret_cast<uint32_t*>(smem + S::scratch);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
   int* s_info = reinterpret_cast<int*>(smem + S::info);
+  int64_t* s_bounds = reinterpret_cast<int64_t*>(smem + S::info + 32);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool segmented = p.seg_offs != nullptr;
 
   // The next pass's status row of this block is cleared whatever this pass does:
   // the previous pass (the row's last user) has finished, and the next one needs
@@ -235,6 +249,17 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
     if (route >= 0 && p.sel.vary && blockIdx.x == 0) atomicOr(p.sel.ran, 1u << p.sel.q);
     s_info[1] = route;
   }
+  if (segmented && tid == 64) {  // the tile's segment, piece and bounds (two round trips)
+    const int tile = (int)blockIdx.x;
+    const int seg = (uint32_t)tile < ld_relaxed(p.num_tiles) ? p.tile_seg[tile] : -1;
+    s_info[2] = seg;
+    if (seg >= 0) {
+      s_info[3] = tile - p.seg_tile0[seg];
+      s_info[4] = p.seg_slot[seg];
+      s_bounds[0] = p.seg_offs[seg];
+      s_bounds[1] = p.seg_offs[seg + 1];
+    }
+  }
   for (int i = tid; i < WARPS * RADIX; i += THREADS) whist[i] = 0u;
   // 1. warp-striped key loads, every warp-wide load one contiguous 128-byte line.
   // They are issued for tile blockIdx.x from the launch's input before the ticket
@@ -253,32 +278,38 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       for (int j = 0; j < IPT; ++j) key[j] = wbase + j * 32 + lane < c ? __ldcs(kin + 32 * j) : 0xFFFFFFFFu;
     }
   };
-  {
+  if (!segmented) {
     const int64_t st = (int64_t)blockIdx.x * T;
     load_keys(p.keys_in, st, (int)min((int64_t)T, p.n - st));
   }
   BCF_SYNC();
   const int route = s_info[1];
   if (route < 0) return;  // skipped pass: nothing to move
+  if (segmented && s_info[2] < 0) return;  // more blocks than tiles this time
   const uint32_t* keys_in = p.keys_in;
   const void* vals_in = p.vals_in;
   uint32_t* keys_out = p.keys_out;
   void* vals_out = p.vals_out;
   if (p.sel.vary) route_buffers(p.sel, route, keys_in, vals_in, keys_out, vals_out);
   const int tile = s_info[0];
-  const int64_t start = (int64_t)tile * T;
-  const int cnt = (int)min((int64_t)T, p.n - start);
+  const int64_t start = segmented ? s_bounds[0] + (int64_t)s_info[3] * T : (int64_t)tile * T;
+  const int cnt = (int)min((int64_t)T, (segmented ? s_bounds[1] : p.n) - start);
   const bool label_mode = p.w > 0;
   const bool iota = VB == 4 && vals_in == nullptr;
   const int shift = label_mode ? 0 : p.shift;
   uint32_t* wh = whist + warp * RADIX;
-  if (tile != (int)blockIdx.x || keys_in != p.keys_in) load_keys(keys_in, start, cnt);
+  if (segmented || tile != (int)blockIdx.x || keys_in != p.keys_in) load_keys(keys_in, start, cnt);
   // 4-byte payloads arrive by one bulk copy into the staging area while the keys
-  // are ranked (the tile start is 16-byte aligned; a ragged end is read directly).
-  const int vfull = (VB == 4 && !iota) ? (cnt & ~3) : 0;
+  // are ranked.  The copy starts at the 16-byte boundary at or below the tile's
+  // first payload, vsh words early (0 but for a segment's pieces), so item i of
+  // the tile is stage[vsh + i]; the ragged end past the copy is read directly.
+  const uint32_t* vin4 = reinterpret_cast<const uint32_t*>(vals_in);
+  const int vsh = (VB == 4 && !iota) ? (int)((reinterpret_cast<uintptr_t>(vin4 + start) & 15u) >> 2) : 0;
+  const int vcopy = (VB == 4 && !iota) ? ((vsh + cnt) & ~3) : 0;  // words copied
+  const int vcov = vcopy > 0 ? vcopy - vsh : 0;                    // tile items they cover
   if (VB == 4 && !iota && tid == 0) {
-    mbar_arrive_expect_tx(mbar, (unsigned)vfull * 4u);
-    if (vfull) bulk_g2s(stage, reinterpret_cast<const uint32_t*>(vals_in) + start, (unsigned)vfull * 4u, mbar);
+    mbar_arrive_expect_tx(mbar, (unsigned)vcopy * 4u);
+    if (vcopy) bulk_g2s(stage, vin4 + start - vsh, (unsigned)vcopy * 4u, mbar);
   }
   // Lane l holds entry l of the peer table of the low digit bits, and (its low
   // bits reused) entry l mod 2^(BITS - LO) of the table of the high bits.
@@ -337,8 +368,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
     }
     // A ragged tile's payloads past the bulk copy are read into the staging area
     // directly, so that the scatter below reads every payload from there.
-    if (VB == 4 && !iota && !full)
-      for (int i = vfull + tid; i < cnt; i += THREADS) stage[i] = reinterpret_cast<const uint32_t*>(vals_in)[start + i];
+    if (VB == 4 && !iota && vcov < cnt)
+      for (int i = vcov + tid; i < cnt; i += THREADS) stage[vsh + i] = vin4[start + i];
     BCF_SYNC();
 
     // 3. per digit: tile count (published at once), tile-exclusive start, and each
@@ -421,8 +452,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
           if constexpr (IOTA) {
             v = (uint32_t)(start + idx);
           } else {
-            BCF_TR(&stage[idx], 4, 0, TS_STAGE_READ);
-            v = stage[idx];
+            BCF_TR(&stage[vsh + idx], 4, 0, TS_STAGE_READ);
+            v = stage[vsh + idx];
           }
           BCF_TR(&kv_s[pos], 8, 1, TS_SCATTER);
           kv_s[pos] = ((unsigned long long)v << 32) | key[j];
@@ -452,7 +483,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
     if (tid < RADIX) {
       uint32_t base;
       if (p.tile_offsets) {  // balanced counts were checked by the scan
-        base = p.tile_offsets[(size_t)tid * p.offs_stride + tile];
+        const uint32_t* row = p.tile_offsets + (size_t)tid * p.offs_stride;
+        base = row[tile];
+        if (segmented)  // running sums over all tiles: rebase at the segment's first tile
+          base = p.seg_base[(size_t)s_info[4] * RADIX + tid] + (base - row[tile - s_info[3]]);
       } else if (label_mode && p.balanced) {
         const int64_t per = p.n / p.w;
         base = (uint32_t)min((int64_t)tid * per, p.n);

@@ -24,12 +24,12 @@ PassPlan plan_passes(int key_bits) {
 
 // ------------------------------------------------------------- tuning table
 namespace {
-int8_t g_tune[2][64];  // [op][log2 n]: configuration, -1 = size rule
+int8_t g_tune[kTuneOps][64];  // [op][log2 n]: configuration, -1 = size rule
 bool g_tune_init = false;
 
 void tune_init() {
   if (g_tune_init) return;
-  for (int op = 0; op < 2; ++op)
+  for (int op = 0; op < kTuneOps; ++op)
     for (int b = 0; b < 64; ++b) g_tune[op][b] = -1;
   g_tune_init = true;
 }
@@ -44,8 +44,11 @@ int ilog2_ceil(int64_t n) {
 int tuned_config(int op, int64_t n) {
   tune_init();
   const int b = ilog2_ceil(n);
-  const int cfg = (op == 0 || op == 1) ? g_tune[op][b] : -1;
+  const int cfg = (op >= 0 && op < kTuneOps) ? g_tune[op][b] : -1;
   if (cfg >= 0 && cfg < kNumSweepConfigs) return cfg;
+  // Batched sorts: the long segments' passes with the pass body fed scanned
+  // offsets (measured faster than the staged sweep on the 10,000-segment batch).
+  if (op == kOpSegmentedSort) return kNumOneConfigs;
   // Size rule (measured on a B300 by the tuner): up to 2^14 keys the staged
   // look-back sweep of 1024-key tiles; up to 2^18 single-launch passes of
   // 2048-key tiles (fewest launches); above, counts + scan + the pass body of
@@ -57,14 +60,15 @@ int tuned_config(int op, int64_t n) {
 
 int tune_set(int op, int log2_n, int cfg) {
   tune_init();
-  if ((op != 0 && op != 1) || log2_n < 0 || log2_n >= 64 || cfg < -1 || cfg >= kNumSweepConfigs) return -1;
+  if (op < 0 || op >= kTuneOps || log2_n < 0 || log2_n >= 64 || cfg < -1 || cfg >= kNumSweepConfigs) return -1;
+  if (op == kOpSegmentedSort && cfg >= 0 && !cfg_segment_capable(cfg)) return -1;
   g_tune[op][log2_n] = (int8_t)cfg;
   return 0;
 }
 
 int tune_entry(int op, int log2_n) {
   tune_init();
-  if ((op != 0 && op != 1) || log2_n < 0 || log2_n >= 64) return -1;
+  if (op < 0 || op >= kTuneOps || log2_n < 0 || log2_n >= 64) return -1;
   return g_tune[op][log2_n];
 }
 

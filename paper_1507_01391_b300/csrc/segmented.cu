@@ -23,6 +23,7 @@
 // Launch grids are host-side upper bounds; blocks without work exit at once.
 #include "common.cuh"
 #include "internal.h"
+#include "onesweep.cuh"
 #include "sweep.cuh"
 #include "tile_sort.cuh"
 
@@ -387,6 +388,10 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
   }
 
   const int P = plan.passes;
+  // Sorts take the pass form the tuning table names for this batch size: the
+  // pass body fed scanned offsets (form 1) or the staged sweep (form 2), both of
+  // 4096-key tiles; partitions (per-segment widths, balanced checks) the staged sweep.
+  const bool body_form = !label && cfg_form(tuned_config(kOpSegmentedSort, n_total)) == 1;
   uint32_t* kt = U32(L.keys_tmp);
   void* vt = vb ? (void*)(ws + L.vals_tmp) : nullptr;
   const uint32_t* src_k = keys_in;
@@ -419,6 +424,31 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
       k_seg_digit_base<<<(unsigned)L.slots_cap, 256, 0, s>>>(offsets, L.lb_stride, U32(L.seg_base), I32(L.slot_seg),
                                                              I32(L.seg_tile0), offs, ctr, kSweepTile);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (body_form) {
+      static_assert(kSweepTile == 256 * 16, "the batched sort's tiles are the 256 x 16 body's");
+      OneSweepParams op{};
+      op.keys_in = src_k;
+      op.vals_in = src_v;
+      op.keys_out = dk;
+      op.vals_out = dv;
+      op.n = n_total;
+      op.shift = plan.shift[q];
+      op.tile_offsets = offsets;
+      op.offs_stride = L.lb_stride;
+      op.err = st;
+      op.seg_offs = offs;
+      op.tile_seg = I32(L.tile_seg);
+      op.seg_tile0 = I32(L.seg_tile0);
+      op.seg_slot = I32(L.seg_slot);
+      op.seg_base = U32(L.seg_base);
+      op.num_tiles = ctr + C_NTILES;
+      if ((e = onesweep_dispatch<8, 256, 16, kOneCfgMinBlocks[kNumOneConfigs]>(op, L.tiles_cap, vb, s)) !=
+          cudaSuccess)
+        return e;
+      src_k = dk;
+      src_v = dv;
+      continue;
     }
     SweepParams sp{};
     sp.tile_offsets = offsets;

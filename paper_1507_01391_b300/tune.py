@@ -14,9 +14,9 @@ import ctypes
 import os
 import statistics
 
-from . import OK, OP_PARTITION, OP_SORT, BcfError, lib
+from . import OK, OP_PARTITION, OP_SEGMENTED_SORT, OP_SORT, BcfError, lib
 
-OPS = {"sort": OP_SORT, "partition": OP_PARTITION}
+OPS = {"sort": OP_SORT, "partition": OP_PARTITION, "segmented_sort": OP_SEGMENTED_SORT}
 
 
 def configs():
@@ -29,6 +29,16 @@ def configs():
             raise BcfError(1, "bcf_tune_config_info")
         out.append((t.value, k.value))
     return out
+
+
+def candidates(op: str):
+    """Configurations the table accepts for `op`: every one for the flat sort and
+    partition; for the batched sort the 256 x 16 counts + scan forms (its plan
+    cuts segments into 4096-key tiles)."""
+    L = lib()
+    if op != "segmented_sort":
+        return list(range(L.bcf_tune_num_configs()))
+    return [c for c, shape in enumerate(configs()) if shape == (256, 16) and L.bcf_tune_config_form(c) in (1, 2)]
 
 
 def set_config(op: str, log2_n: int, config: int) -> None:
@@ -84,10 +94,21 @@ def _time(fn, reps, inner):
 def _workload(op, n, w):
     import torch
 
-    from . import partition, partition_workspace_size, sort, sort_workspace_size, workspace
+    from . import (partition, partition_workspace_size, segmented_sort, segmented_sort_workspace_size, sort,
+                   sort_workspace_size, workspace)
     g = torch.Generator(device="cuda").manual_seed(0x150701391 + n)
     vals = torch.arange(n, dtype=torch.int32, device="cuda")
     ko, vo = torch.empty_like(vals), torch.empty_like(vals)
+    if op == "segmented_sort":  # log-uniform segment sizes in [32, 2^18], n keys in all
+        gc = torch.Generator().manual_seed(0x150701391 + n)
+        sizes = []
+        while sum(sizes) < n:
+            sizes.append(int(2 ** (5 + 13 * torch.rand(1, generator=gc).item())))
+        sizes[-1] -= sum(sizes) - n
+        offs = torch.tensor([0] + sizes, dtype=torch.int64).cumsum(0).cuda()
+        keys = torch.randint(-2**31, 2**31, (n,), dtype=torch.int32, device="cuda", generator=g)
+        ws = workspace(segmented_sort_workspace_size(n, len(sizes), 4, 32))
+        return lambda: segmented_sort(keys, vals, offs, keys_out=ko, vals_out=vo, ws=ws)
     if op == "sort":
         keys = torch.randint(-2**31, 2**31, (n,), dtype=torch.int32, device="cuda", generator=g)
         ws = workspace(sort_workspace_size(n, 4, 32))
@@ -110,7 +131,7 @@ def autotune(ops=("sort", "partition"), log2_sizes=range(12, 27, 2), w=256, reps
             fn = _workload(op, n, w)
             times = {}
             inner = max(1, min(32, (1 << 22) >> k))  # about 2^22 keys per replay
-            for c in range(len(configs())):
+            for c in candidates(op):
                 set_config(op, k, c)  # read at capture time: each config gets its own graph
                 times[c] = _time(fn, reps, inner)
             best = min(times, key=times.get)

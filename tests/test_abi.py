@@ -171,6 +171,23 @@ def test_lookback_testing_aid_arguments():
     assert L.bcf_debug_lookback(-1, 0) == bcf.OK
 
 
+def test_batched_sort_tuning_entries():
+    """The batched sort's table takes only the 256 x 16 counts + scan forms and
+    defaults to the pass body fed scanned offsets (host only)."""
+    L = bcf.lib()
+    c = ctypes.c_int(-5)
+    assert L.bcf_tune_get(bcf.OP_SEGMENTED_SORT, 1 << 28, ctypes.byref(c)) == bcf.OK and c.value == 4
+    assert L.bcf_tune_get(bcf.OP_SEGMENTED_SORT, 100, ctypes.byref(c)) == bcf.OK and c.value == 4
+    for cfg, ok in [(4, True), (8, True), (0, False), (1, False), (5, False), (9, False), (10, False)]:
+        assert (L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, 20, cfg) == bcf.OK) == ok, cfg
+    assert L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, 20, 8) == bcf.OK
+    assert L.bcf_tune_get(bcf.OP_SEGMENTED_SORT, 1 << 20, ctypes.byref(c)) == bcf.OK and c.value == 8
+    assert L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, 20, -1) == bcf.OK
+    assert L.bcf_tune_get(bcf.OP_SEGMENTED_SORT, 1 << 20, ctypes.byref(c)) == bcf.OK and c.value == 4
+    assert L.bcf_tune_set(3, 20, 4) == bcf.E_INVAL
+    assert L.bcf_tune_get(3, 1 << 20, ctypes.byref(c)) == bcf.E_INVAL
+
+
 def test_bank_probe_argument_checks():
     """The probe entry point rejects bad arguments before launching (CPU)."""
     from paper_1507_01391_b300 import trace

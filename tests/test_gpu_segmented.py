@@ -97,6 +97,36 @@ def test_segmented_sort_index_payload(bcf):
     assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(perm, np.uint32), rv)
 
 
+@pytest.mark.parametrize("config", [4, 8])
+@pytest.mark.parametrize("vb", [0, 4, 8])
+def test_segmented_sort_pass_forms(bcf, config, vb):
+    """Both pass forms the tuning table can name for a batch -- the pass body fed
+    scanned offsets (configuration 4) and the staged sweep (8) -- give the
+    oracle's result: segment starts off the 16-byte grid (payload copies that
+    begin mid-vector), ragged last pieces, empty and small segments between long
+    ones, and (4-byte payloads) the index-payload mode."""
+    import torch
+    L = bcf.lib()
+    sizes = [1, 10_000, 3, 8193, 5, 70_001, 0, 4097, 12_288, 2, 4099]
+    offs = synth.offsets_from_sizes(sizes)
+    n = int(offs[-1])
+    lg = (n - 1).bit_length()
+    assert L.bcf_tune_config_form(config) == (1 if config == 4 else 2)
+    assert L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, lg, config) == bcf.OK
+    try:
+        keys = synth.uniform_keys(n, seed=40 + vb)
+        vals = None if vb == 0 else (synth.float_bits_payload(n, seed=41) if vb == 4
+                                     else synth.uniform_keys(2 * n, seed=42).view(np.uint64))
+        _seg_sort_case(bcf, keys, vals, offs)
+        _seg_sort_case(bcf, synth.random_labels(n, 7, seed=43), vals, offs, key_bits=20)
+        if vb == 4:
+            ko, perm = bcf.segmented_sort(dev(keys), None, torch.from_numpy(offs).cuda(), index_payload=True)
+            rk, rv = oracle.segmented_sort_kv(keys, synth.index_payload(n), offs)
+            assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(perm, np.uint32), rv)
+    finally:
+        L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, lg, -1)
+
+
 @pytest.mark.slow
 def test_segmented_sort_batched_full_size(bcf):
     """The batched workload: 10,000 segments, sizes log-uniform in [32, 2^18]."""

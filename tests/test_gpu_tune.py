@@ -57,6 +57,22 @@ def test_autotune_and_cache(bcf, tmp_path):
     assert tune.get_config("sort", 1 << 14) == res["sort"][14][0]
 
 
+def test_autotune_batched_sort(bcf, tmp_path):
+    """The batched sort's entries: only its two 4096-key counts + scan forms are
+    timed, the fastest is kept, saved and loaded back."""
+    from paper_1507_01391_b300 import tune
+    assert tune.candidates("segmented_sort") == [4, 8]
+    res = tune.autotune(ops=("segmented_sort",), log2_sizes=[16], reps=2)
+    best, times = res["segmented_sort"][16]
+    assert set(times) == {4, 8} and best == min(times, key=times.get)
+    assert tune.get_config("segmented_sort", 1 << 16) == best
+    path = tune.save(res, str(tmp_path / "tune.txt"))
+    tune.set_config("segmented_sort", 16, -1)
+    assert tune.get_config("segmented_sort", 1 << 16) == 4
+    assert tune.load(path) and tune.get_config("segmented_sort", 1 << 16) == best
+    tune.set_config("segmented_sort", 16, -1)
+
+
 def test_tune_cache_keeps_other_devices(bcf, tmp_path):
     """bcf_tune_save rewrites only this device's lines of the cache file."""
     from paper_1507_01391_b300 import tune

@@ -51,10 +51,10 @@ FALLBACK_HBM_GBS = 6400.0
 # on: if any of them changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "bcf_sort of 2^26 key-value pairs (all launches of one call)",
                "sources": ["radix.cu", "sweep.cuh", "onesweep.cuh"],
-               "sources_sha1": ['bfc82e7cfd7c2e6dd747f4b2484931534767f4f5', '7da90a30fb48d8b62c9f4d7ce0927b0808857e3c', '0e2cb28ce5b6d5d9d881895d8ca1f0607f830079'],
-               # 1155.8 MB per call measured at 2^24 keys (3 calls captured), scaled by 4:
+               "sources_sha1": ['0775af4f43422a42bb65c6b92e41f56f7979936c', '172735430c1d79d3ba6d83674130307cebf4670f', 'f27a700ebf206b039507bc3d41e9e7ac22e15512'],
+               # 1156.2 MB per call measured at 2^24 keys (3 calls captured), scaled by 4:
                # every kernel of the call moves bytes in proportion to the keys
-               "bytes": 4623360000}
+               "bytes": 4624933000}
 
 
 def log(*a):

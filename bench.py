@@ -52,9 +52,9 @@ FALLBACK_HBM_GBS = 6400.0
 NCU_TRAFFIC = {"kernel": "bcf_sort of 2^26 key-value pairs (all launches of one call)",
                "sources": ["radix.cu", "sweep.cuh", "onesweep.cuh"],
                "sources_sha1": ['0775af4f43422a42bb65c6b92e41f56f7979936c', '172735430c1d79d3ba6d83674130307cebf4670f', 'f27a700ebf206b039507bc3d41e9e7ac22e15512'],
-               # 1156.2 MB per call measured at 2^24 keys (3 calls captured), scaled by 4:
-               # every kernel of the call moves bytes in proportion to the keys
-               "bytes": 4624933000}
+               # one call at 2^26 keys (its 12 launches, one counter pass each):
+               # 5352.7 MB, the tile counts re-reading the keys every pass included
+               "bytes": 5352700000}
 
 
 def log(*a):

@@ -134,3 +134,27 @@ def test_sort_skip_in_place_8_byte_payloads(bcf, n, kind):
     rk, rv = oracle.sort_kv(keys, vals)
     assert bits_equal(host(ko, np.uint32), rk)
     assert bits_equal(host(vo, np.uint64), rv)
+
+
+@pytest.mark.parametrize("config", [4, 5, 6, 7])
+@pytest.mark.parametrize("kind", ["uniform", "middle_bytes", "top_byte_constant", "one_bit_in_top"])
+def test_counts_pass_forms_skip_passes(bcf, config, kind):
+    """Every counts + scan + pass body configuration (tile shapes 256x16, 256x8,
+    512x12, 384x16) with passes skipped on the device: whole groups of four count
+    tiles and a ragged tail, bit-exact against the oracle."""
+    L = bcf.lib()
+    n = 5 * 16384 + 1234
+    lg = (n - 1).bit_length()
+    assert L.bcf_tune_config_form(config) == 1
+    assert L.bcf_tune_set(bcf.OP_SORT, lg, config) == bcf.OK
+    try:
+        keys = _keys(n, kind, seed=config * 7 + len(kind))
+        vals = synth.float_bits_payload(n, seed=config)
+        ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
+        ko, vo = bcf.sort(dev(keys), dev(vals), ws=ws)
+        assert bcf.get_status() == bcf.OK
+        assert bcf.sort_passes_run(ws, n, 4, 32) == _expected_passes(kind, False)
+        rk, rv = oracle.sort_kv(keys, vals)
+        assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.uint32), rv)
+    finally:
+        L.bcf_tune_set(bcf.OP_SORT, lg, -1)

@@ -260,7 +260,15 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       s_bounds[1] = p.seg_offs[seg + 1];
     }
   }
-  for (int i = tid; i < WARPS * RADIX; i += THREADS) whist[i] = 0u;
+  // In offsets mode the flat tile is the block's own and its run starts were
+  // scanned before the launch: fetch them now, so that the round trip overlaps the
+  // key loads and the ranking instead of holding the block after its scatter.
+  uint32_t pre_base = 0;
+  if (p.tile_offsets && !segmented && tid < RADIX)
+    pre_base = __ldcg(p.tile_offsets + (size_t)tid * p.offs_stride + blockIdx.x);
+  static_assert(S::whist % 16 == 0, "count rows are cleared 16 bytes at a time");
+  for (int i = tid; i < WARPS * RADIX / 4; i += THREADS)
+    reinterpret_cast<uint4*>(whist)[i] = make_uint4(0u, 0u, 0u, 0u);
   // 1. warp-striped key loads, every warp-wide load one contiguous 128-byte line.
   // They are issued for tile blockIdx.x from the launch's input before the ticket
   // and the route are known: blocks start in index order and passes are rarely
@@ -297,6 +305,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
   const bool label_mode = p.w > 0;
   const bool iota = VB == 4 && vals_in == nullptr;
   const int shift = label_mode ? 0 : p.shift;
+  // An 8-bit digit is a whole key byte (the host plans passes at shifts 8q and
+  // refuses others), taken with one byte permute.
+  const uint32_t psel = 0x4440u + ((uint32_t)shift >> 3);
+  auto digit = [&](uint32_t k) -> uint32_t {
+    if constexpr (BITS == 8) return __byte_perm(k, 0u, psel);
+    else return (k >> shift) & DMASK;
+  };
   uint32_t* wh = whist + warp * RADIX;
   if (segmented || tile != (int)blockIdx.x || keys_in != p.keys_in) load_keys(keys_in, start, cnt);
   // 4-byte payloads arrive by one bulk copy into the staging area while the keys
@@ -330,7 +345,6 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       for (int j = 0; j < IPT; ++j) bad |= valid_at(j) && key[j] >= (uint32_t)p.w;
       if (bad) set_status(p.err, DEV_BAD_KEY);
     }
-    auto digit = [&](uint32_t k) -> uint32_t { return (k >> shift) & DMASK; };
 
     // 2. per-warp ranking.  One ballot per digit bit; each lane turns them into
     // its entries of two tables -- the lanes whose low digit bits equal the lane
@@ -375,11 +389,13 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
     // 3. per digit: tile count (published at once), tile-exclusive start, and each
     // warp's start inside the tile.
     uint32_t count = 0;
+    uint32_t wc[WARPS];  // this digit's warp counts, reused for the warps' starts below
     if (tid < RADIX) {
 #pragma unroll
       for (int q = 0; q < WARPS; ++q) {
         BCF_TR(&whist[q * RADIX + tid], 4, 0, TS_WARP_OFFSETS);
-        count += whist[q * RADIX + tid];
+        wc[q] = whist[q * RADIX + tid];
+        count += wc[q];
       }
       if (tid == RADIX - 1) count -= (uint32_t)(T - cnt);  // the ragged tile's padding
       if (!p.tile_offsets && tile + 1 != p.silent_tile1)
@@ -425,11 +441,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       uint32_t run = tile_excl;
 #pragma unroll
       for (int q = 0; q < WARPS; ++q) {
-        BCF_TR(&whist[q * RADIX + tid], 4, 0, TS_WARP_OFFSETS);
-        const uint32_t c = whist[q * RADIX + tid];
         BCF_TR(&whist[q * RADIX + tid], 4, 1, TS_WARP_OFFSETS);
         whist[q * RADIX + tid] = run;
-        run += c;
+        run += wc[q];
       }
     }
     BCF_SYNC();
@@ -484,9 +498,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       uint32_t base;
       if (p.tile_offsets) {  // balanced counts were checked by the scan
         const uint32_t* row = p.tile_offsets + (size_t)tid * p.offs_stride;
-        base = row[tile];
+        base = pre_base;
         if (segmented)  // running sums over all tiles: rebase at the segment's first tile
-          base = p.seg_base[(size_t)s_info[4] * RADIX + tid] + (base - row[tile - s_info[3]]);
+          base = p.seg_base[(size_t)s_info[4] * RADIX + tid] + (row[tile] - row[tile - s_info[3]]);
       } else if (label_mode && p.balanced) {
         const int64_t per = p.n / p.w;
         base = (uint32_t)min((int64_t)tid * per, p.n);
@@ -529,7 +543,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
         v = vals_s[i];
       }
     }
-    const uint32_t d = (k >> shift) & DMASK;
+    const uint32_t d = digit(k);
     BCF_TR(&gofs[d], 4, 0, TS_OFFSET_READ);
     const uint32_t dst = gofs[d] + (uint32_t)i;
     if (dst < n32) {
@@ -549,6 +563,7 @@ template <int BITS, int THREADS, int IPT, int VB, int MINB>
 inline cudaError_t launch_onesweep(const OneSweepParams& p, int64_t grid, cudaStream_t s) {
   using S = OneSmem<BITS, THREADS, IPT, VB>;
   auto kern = k_onesweep<BITS, THREADS, IPT, VB, MINB>;
+  if (BITS == 8 && p.w == 0 && (p.shift & 7)) return cudaErrorInvalidValue;  // digits are whole bytes
   // raised on every launch that needs it (see launch_sweep: no flag shared
   // between translation units)
   if (S::bytes > 48 * 1024) {

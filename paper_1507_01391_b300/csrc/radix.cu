@@ -8,15 +8,15 @@
 namespace bcf {
 
 // ------------------------------------------------------------- host side
-// Passes of 8-bit digits from the least significant end; the last pass of a key
-// width that is not a multiple of 8 starts at key_bits - 8 and overlaps the one
-// before it.  That is still a correct LSD sort: every pass is stable, so after a
-// pass the keys are ordered by all the bits it and the earlier passes covered.
+// Passes of 8-bit digits from the least significant end: digit q is key byte q.
+// A key width that is not a multiple of 8 leaves the top pass with fewer varying
+// bits (keys are below 2^key_bits, so the byte's upper bits are zero); the digit
+// stays a whole byte, which the pass body takes with one byte permute.
 PassPlan plan_passes(int key_bits) {
   PassPlan pl;
   pl.passes = (key_bits + 7) / 8;
   for (int q = 0; q < pl.passes; ++q) {
-    pl.shift[q] = std::min(8 * q, std::max(key_bits - 8, 0));
+    pl.shift[q] = 8 * q;
     pl.nbits[q] = 8;
   }
   return pl;

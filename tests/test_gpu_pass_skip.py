@@ -74,17 +74,16 @@ def test_sort_skips_constant_digits(bcf, n, kind, in_place, payload):
 
 @pytest.mark.parametrize("key_bits", [20, 24])
 def test_sort_skips_with_fewer_key_bits(bcf, key_bits):
-    """key_bits < 32 plans fewer passes (overlapping digits for 20 bits); keys below
-    2^16 leave the passes above bit 16 without a varying digit."""
+    """key_bits < 32 plans fewer passes (key bytes 0..2 for 20 and 24 bits); keys
+    below 2^16 leave the pass of byte 2 without a varying digit."""
     n = 300_001
     keys = synth.uniform_keys(n, seed=3, bits=16)
     vals = synth.index_payload(n)
     ws = bcf.workspace(bcf.sort_workspace_size(n, 4, key_bits))
     ko, vo = bcf.sort(dev(keys), dev(vals), key_bits=key_bits, ws=ws)
     assert bcf.get_status() == bcf.OK
-    # 20 bits: digits at 0, 8, 12 (the last covers bits 12-19, of which 12-15 vary);
-    # 24 bits: digits at 0, 8, 16 (bits 16-23 never vary)
-    assert bcf.sort_passes_run(ws, n, 4, key_bits) == (3 if key_bits == 20 else 2)
+    # 20 and 24 bits: digits at shifts 0, 8, 16 (bits 16-23 never vary)
+    assert bcf.sort_passes_run(ws, n, 4, key_bits) == 2
     rk, rv = oracle.sort_kv(keys, vals)
     assert bits_equal(host(ko, np.uint32), rk)
     assert bits_equal(host(vo, np.uint32), rv)

@@ -51,10 +51,10 @@ FALLBACK_HBM_GBS = 6400.0
 # on: if any of them changes, the figure is dropped (null).
 NCU_TRAFFIC = {"kernel": "bcf_sort of 2^26 key-value pairs (all launches of one call)",
                "sources": ["radix.cu", "sweep.cuh", "onesweep.cuh"],
-               "sources_sha1": ['0775af4f43422a42bb65c6b92e41f56f7979936c', '172735430c1d79d3ba6d83674130307cebf4670f', 'f27a700ebf206b039507bc3d41e9e7ac22e15512'],
+               "sources_sha1": ['701aa95ce050f88b18adf5d1e615d0c295cca8da', '172735430c1d79d3ba6d83674130307cebf4670f', '5ab8b7d7159ba88019052e55e44c2b60dbccbb19'],
                # one call at 2^26 keys (its 12 launches, one counter pass each):
-               # 5352.7 MB, the tile counts re-reading the keys every pass included
-               "bytes": 5352700000}
+               # 5349.4 MB, the tile counts re-reading the keys every pass included
+               "bytes": 5349400000}
 
 
 def log(*a):

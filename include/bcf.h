@@ -266,9 +266,9 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
  * body or over shared-memory-staged tiles (the staged form runs one look-back
  * sweep launch per pass for n <= 2^18).  The library keeps a small host-side table, per operation and
  * per ceil(log2 n), of the configuration to use; an entry of -1 (the initial
- * state) applies a size rule measured on a B300 (staged sweeps of 1024-key tiles
+ * state) applies a size rule measured on a B300 (staged sweeps of 2048-key tiles
  * up to n = 2^14, single-launch passes of 2048-key tiles up to 2^18, counts +
- * scan + 4096-key tiles above).  The table is process-wide host state and is not synchronised:
+ * scan + the pass body of 4096-key tiles above).  The table is process-wide host state and is not synchronised:
  * set it before concurrent calls.  Workspace sizes already cover every
  * configuration.  paper_1507_01391_b300.tune measures the configurations on the
  * device and fills the table (with a text cache per device). */

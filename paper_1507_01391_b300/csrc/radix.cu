@@ -49,13 +49,13 @@ int tuned_config(int op, int64_t n) {
   // Batched sorts: the long segments' passes with the pass body fed scanned
   // offsets (measured faster than the staged sweep on the 10,000-segment batch).
   if (op == kOpSegmentedSort) return kNumOneConfigs;
-  // Size rule (measured on a B300 by the tuner): up to 2^14 keys the staged
-  // look-back sweep of 1024-key tiles; up to 2^18 single-launch passes of
-  // 2048-key tiles (fewest launches); above, counts + scan + the pass body of
-  // 4096-key tiles (sorts), the staged sweep for partitions above 2^22.
-  if (n <= ((int64_t)1 << 14)) return kRtsCfg0 + 1;
+  // Size rule (measured on a B300 by the tuner, sorts and balanced 256-way
+  // partitions alike): up to 2^14 keys the staged look-back sweep of 2048-key
+  // tiles; up to 2^18 single-launch passes of 2048-key tiles (fewest launches);
+  // above, counts + scan + the pass body of 4096-key tiles.
+  if (n <= ((int64_t)1 << 14)) return kRtsCfg0 + 3;
   if (n <= ((int64_t)1 << 18)) return 1;
-  return (op == 1 && n > ((int64_t)1 << 22)) ? kRtsCfg0 : kNumOneConfigs;
+  return kNumOneConfigs;
 }
 
 int tune_set(int op, int log2_n, int cfg) {

@@ -148,9 +148,9 @@ def test_tuning_table_on_the_host():
     assert L.bcf_tune_config_info(nconf, ctypes.byref(t), ctypes.byref(k)) == bcf.E_INVAL
     got = ctypes.c_int(-5)
     assert L.bcf_tune_get(bcf.OP_SORT, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 4
-    assert L.bcf_tune_get(bcf.OP_PARTITION, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 8
+    assert L.bcf_tune_get(bcf.OP_PARTITION, 1 << 26, ctypes.byref(got)) == bcf.OK and got.value == 4
     assert L.bcf_tune_get(bcf.OP_PARTITION, 1 << 16, ctypes.byref(got)) == bcf.OK and got.value == 1
-    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 12, ctypes.byref(got)) == bcf.OK and got.value == 9
+    assert L.bcf_tune_get(bcf.OP_SORT, 1 << 12, ctypes.byref(got)) == bcf.OK and got.value == 11
     assert L.bcf_tune_set(bcf.OP_SORT, 26, nconf - 1) == bcf.OK
     assert L.bcf_tune_get(bcf.OP_SORT, (1 << 25) + 1, ctypes.byref(got)) == bcf.OK and got.value == nconf - 1
     assert L.bcf_tune_set(bcf.OP_SORT, 26, -1) == bcf.OK  # back to the size rule

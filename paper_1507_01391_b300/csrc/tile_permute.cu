@@ -351,48 +351,54 @@ __global__ void __launch_bounds__(kTPThreads, kTPThreads >= 1024 ? 2 : 3) k_tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t tile = blockIdx.x;
   const int len = stage_tile<T>(src, lpi, n, tile, in_s, lpi_s, mbar, status);
-  // Row l's labels must sit in bank l: with 16-bit labels two lanes share a word,
-  // and lanes reading different slots of one row pair would collide.
-  for (int q = threadIdx.x; q < T; q += kTPThreads) {
-    if (q < len) BCF_TR_WORD(&lpi_s[q], 0, TS_COL_READ);
-    BCF_TR(&lab[q], 4, 1, TS_COL_READ);
-    lab[q] = q < len ? (uint32_t)lpi_s[q] : 0u;
-  }
-  BCF_SYNC();
-
-  // Pending slots of this thread; labels outside the tile are dropped (and flagged).
+  // This thread's labels, read once into registers.  All lanes of a warp read the
+  // same slot at once, so the two lanes of each 16-bit pair read one word and a
+  // request touches 16 distinct banks.  Pending slots of this thread: labels
+  // outside the tile are dropped (and flagged).
+  uint32_t labr[SPW];
   uint32_t pending = 0;
+#pragma unroll
   for (int c = 0; c < SPW; ++c) {
-    const int s = warp * SPW + c, q = s * 32 + lane;
+    const int q = (warp * SPW + c) * 32 + lane;
+    labr[c] = 0u;
     if (q < len) {
-      BCF_TR(&lab[q], 4, 0, TS_COL_READ);
-      if ((int)lab[q] < len) pending |= 1u << c;
+      BCF_TR_WORD(&lpi_s[q], 0, TS_COL_READ);
+      labr[c] = lpi_s[q];
+      if ((int)labr[c] < len) pending |= 1u << c;
       else set_status(status, DEV_BAD_PERM);
     }
   }
+  // The sorted finish reads pending labels by slot, from lanes at different slots:
+  // it gets them widened to one word each, so row l's labels sit in bank l.
+  if (sorted) {
+    for (int q = threadIdx.x; q < T; q += kTPThreads) {
+      if (q < len) BCF_TR_WORD(&lpi_s[q], 0, TS_COL_READ);
+      BCF_TR(&lab[q], 4, 1, TS_COL_READ);
+      lab[q] = q < len ? (uint32_t)lpi_s[q] : 0u;
+    }
+  }
 
+  // The colour table starts empty; afterwards every send step empties the entry it
+  // has just sent, so each round begins with an empty table.
+  for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) {
+    BCF_TR(&tbl[k * 32 + lane], 4, 1, TS_COL_TABLE);
+    tbl[k * 32 + lane] = EMPTY;
+  }
+  BCF_SYNC();
   for (int r = 0; r < rounds; ++r) {
     // Coloring: h(i) for destination bank i, drawn fresh every round (held by lane i).
     const uint32_t h_lane = mix32(seed ^ ((uint64_t)tile << 20) ^ ((uint64_t)r << 8) ^ (uint64_t)lane) & (M - 1);
-    for (int k = warp * SPW; k < (warp + 1) * SPW; ++k) {
-      BCF_TR(&tbl[k * 32 + lane], 4, 1, TS_COL_TABLE);
-      tbl[k * 32 + lane] = EMPTY;
-    }
-    BCF_SYNC();
     // Claim the first free entry of each colour in this row; an item whose colour
-    // is already taken stays pending for the next round.
-    uint32_t todo = pending;
-    while (__any_sync(0xffffffffu, todo != 0)) {
-      const int c = todo ? __ffs(todo) - 1 : 0;
-      const int s = warp * SPW + c;
-      if (todo) BCF_TR(&lab[s * 32 + lane], 4, 0, TS_COL_READ);
-      const uint32_t p = todo ? lab[s * 32 + lane] : 0u;
-      const uint32_t hi = __shfl_sync(0xffffffffu, h_lane, p & 31u);  // h(i), i = p mod 32
-      if (todo) {
-        todo &= todo - 1;
+    // is already taken stays pending for the next round.  Slot by slot, in the
+    // same order on every lane, so the loop has no divergent trip count.
+#pragma unroll
+    for (int c = 0; c < SPW; ++c) {
+      const uint32_t p = labr[c];
+      const uint32_t hi = __shfl_sync(0xffffffffu, h_lane, (int)(p & 31u));  // h(i), i = p mod 32
+      if ((pending >> c) & 1u) {
         const uint32_t k = ((p >> 5) - hi) & (M - 1);
         BCF_TR(&tbl[k * 32 + lane], 4, 2, TS_COL_TABLE);
-        if (atomicCAS(&tbl[k * 32 + lane], EMPTY, (p << 8) | (uint32_t)s) == EMPTY)
+        if (atomicCAS(&tbl[k * 32 + lane], EMPTY, (p << 8) | (uint32_t)(warp * SPW + c)) == EMPTY)
           pending &= ~(1u << c);
       }
     }
@@ -407,6 +413,8 @@ __global__ void __launch_bounds__(kTPThreads, kTPThreads >= 1024 ? 2 : 3) k_tile
         BCF_TR(&in_s[(e & 0xFFu) * 32 + lane], 4, 0, TS_COL_READ);
         BCF_TR(&out_s[e >> 8], 4, 1, TS_COL_SEND);
         out_s[e >> 8] = in_s[(e & 0xFFu) * 32 + lane];
+        BCF_TR(&tbl[k * 32 + lane], 4, 1, TS_COL_TABLE);
+        tbl[k * 32 + lane] = EMPTY;
       }
     }
     BCF_SYNC();
@@ -421,8 +429,10 @@ __global__ void __launch_bounds__(kTPThreads, kTPThreads >= 1024 ? 2 : 3) k_tile
   while (__any_sync(0xffffffffu, pending != 0)) {
     const int c = pending ? __ffs(pending) - 1 : 0;
     const int s = warp * SPW + c;
-    if (pending) BCF_TR(&lab[s * 32 + lane], 4, 0, TS_COL_READ);
-    const uint32_t p = pending ? lab[s * 32 + lane] : 0u;
+    uint32_t p = 0u;
+#pragma unroll
+    for (int u = 0; u < SPW; ++u)  // the label of slot c, from registers
+      if (u == c && pending) p = labr[u];
     const uint32_t bank = pending ? (p & 31u) : 32u + (uint32_t)lane;  // idle lanes never collide
     const unsigned peers = __match_any_sync(0xffffffffu, bank);
     if (pending && lane == __ffs(peers) - 1) {

@@ -15,9 +15,12 @@
 //
 // Row sort: the 16 threads of a row's team (one lane in each half-warp of the 8
 // warps) each sort 16 consecutive items of the row in registers with Batcher's
-// bitonic network, then four merge-path rounds merge runs of 16 -> 256 inside the
-// row's own banks.  Conversions move one item per row per half-warp phase along
-// a diagonal, so the 16 lanes of a phase read 16 different rows as well.
+// odd-even merge sorting network (63 comparators), then four merge-path rounds
+// merge runs of 16 -> 256 inside the row's own banks.  A row sorted descending is
+// sorted ascending on its complemented items (complemented when loaded, restored
+// by the last merge round), so every comparison runs one way.  Conversions move
+// one item per row per half-warp phase along a diagonal, so the 16 lanes of a
+// phase read 16 different rows as well.
 #pragma once
 
 #include "common.cuh"
@@ -32,29 +35,27 @@ constexpr int kL1Tile = kL1Rows * kL1Cols;
 constexpr int kL1PerThread = kL1Cols / 16;  // items of a row per team member
 constexpr size_t kL1SmemBytes = 2ull * kL1Tile * 8;
 
-__device__ __forceinline__ void cas_u64(unsigned long long& a, unsigned long long& b, bool up) {
-  const bool swap = up ? (a > b) : (a < b);
+__device__ __forceinline__ void cas_u64(unsigned long long& a, unsigned long long& b) {
+  const bool swap = a > b;
   const unsigned long long x = swap ? b : a, y = swap ? a : b;
   a = x;
   b = y;
 }
 
-// Bitonic sort of 16 registers, ascending if up.
-__device__ __forceinline__ void sort16(unsigned long long (&v)[16], bool up) {
+// Ascending sort of 16 registers by Batcher's odd-even merge sort (Batcher 1968):
+// for merge widths p = 1, 2, 4, 8 and strides k = p, p/2, ..., 1, compare
+// elements i + j and i + j + k when both lie in the same block of 2p; 63
+// comparators, all indices known at compile time.
+__device__ __forceinline__ void sort16(unsigned long long (&v)[16]) {
 #pragma unroll
-  for (int k = 2; k <= 16; k <<= 1) {
+  for (int p = 1; p < 16; p <<= 1)
 #pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1) {
+    for (int k = p; k >= 1; k >>= 1)
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int l = i ^ j;
-        if (l > i) {
-          const bool dir = ((i & k) == 0) ? up : !up;
-          cas_u64(v[i], v[l], dir);
-        }
-      }
-    }
-  }
+      for (int j = k % p; j + k < 16; j += 2 * k)
+#pragma unroll
+        for (int i = 0; i < k; ++i)
+          if (i + j + k < 16 && (i + j) / (2 * p) == (i + j + k) / (2 * p)) cas_u64(v[i + j], v[i + j + k]);
 }
 
 // Sort every row of S (ascending, or alternating when alt: row 0 ascending).
@@ -64,13 +65,14 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
   const int r = lane & 15;                    // row
   const int t = warp * 2 + (lane >> 4);       // team member 0..15
   const bool up = !(alt && (r & 1));
+  const unsigned long long flip = up ? 0ull : ~0ull;  // descending rows sort complemented items
   unsigned long long v[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 0, TS_L1_ROW_LD);
-    v[i] = S[(t * 16 + i) * kL1Rows + r];
+    v[i] = S[(t * 16 + i) * kL1Rows + r] ^ flip;
   }
-  sort16(v, up);
+  sort16(v);
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 1, TS_L1_ROW_ST);
@@ -94,21 +96,21 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
       BCF_TR(&A[mid * kL1Rows], 8, 0, TS_L1_ROW_LD);
       BCF_TR(&B[(d - 1 - mid) * kL1Rows], 8, 0, TS_L1_ROW_LD);
       const unsigned long long a = A[mid * kL1Rows], b = B[(d - 1 - mid) * kL1Rows];
-      const bool a_first = up ? (a < b) : (a > b);
-      if (a_first) lo = mid + 1;
+      if (a < b) lo = mid + 1;
       else hi = mid;
     }
     int i = lo, j = d - lo;
     unsigned long long* out = dst + (size_t)(base + d) * kL1Rows + r;
+    const unsigned long long oflip = 2 * L == kL1Cols ? flip : 0ull;  // the last round restores the items
 #pragma unroll 4
     for (int s = 0; s < 16; ++s) {
       if (i < L) BCF_TR(&A[i * kL1Rows], 8, 0, TS_L1_ROW_LD);
       if (j < L) BCF_TR(&B[j * kL1Rows], 8, 0, TS_L1_ROW_LD);
       const unsigned long long a = i < L ? A[i * kL1Rows] : 0ull;
       const unsigned long long b = j < L ? B[j * kL1Rows] : 0ull;
-      const bool take_a = (j >= L) || (i < L && (up ? (a < b) : (a > b)));
+      const bool take_a = (j >= L) || (i < L && a < b);
       BCF_TR(&out[s * kL1Rows], 8, 1, TS_L1_ROW_ST);
-      out[s * kL1Rows] = take_a ? a : b;
+      out[s * kL1Rows] = (take_a ? a : b) ^ oflip;
       i += take_a;
       j += !take_a;
     }

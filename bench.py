@@ -669,6 +669,10 @@ def run_rows(which, peak):
         ms, _ = graph_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=wsl,
                                                flags=bcf.PARTITION_LEMMA1), 3, 20, inner=20)
         add("partition_w32_n65536_lemma1", n, 16 * n, ms, "Lemma 1 tile schedule (conflict-free); graph replay")
+        ms, _ = graph_ms(lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws,
+                                               flags=bcf.PARTITION_DIRECT), 3, 20, inner=20)
+        add("partition_w32_n65536_direct", n, 16 * n, ms, "direct write-out: no shared-memory scatter, every "
+            "shared access conflict-free (label = bank); graph replay")
         ku = to_dev(synth.random_labels(n, w, seed=0x150701392))
         ms, _ = graph_ms(lambda: bcf.partition(ku, v, w, keys_out=ko, vals_out=vo, ws=ws), 3, 20, inner=20)
         add("partition_w32_n65536_unbalanced", n, 20 * n, ms, "histogram read + one sweep; graph replay")
@@ -1031,13 +1035,14 @@ def _case_inputs(name):
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.sort_workspace_size(n, 4, 32))
         return lambda: bcf.sort(k, v, keys_out=ko, vals_out=vo, ws=ws)
-    if name in ("partition_w32", "partition_w256"):
-        w = 32 if name == "partition_w32" else 256
+    if name in ("partition_w32", "partition_w256", "partition_w32_direct"):
+        w = 256 if name == "partition_w256" else 32
         m = 65536 if w == 32 else n
         k, v = to_dev(synth.partition_keys(m, w, seed=5)), to_dev(synth.index_payload(m))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.partition_workspace_size(m, w, 4, bcf.ASSUME_BALANCED))
-        return lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws)
+        fl = bcf.PARTITION_DIRECT if name == "partition_w32_direct" else 0
+        return lambda: bcf.partition(k, v, w, balanced=True, keys_out=ko, vals_out=vo, ws=ws, flags=fl)
     if name == "tile_sort":
         k, v = to_dev(synth.uniform_keys(n, seed=7)), to_dev(synth.index_payload(n))
         ko, vo = torch.empty_like(k), torch.empty_like(v)
@@ -1059,7 +1064,7 @@ def _case_inputs(name):
 
 
 CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "sort_kv_2pow26",
-         "partition_w32", "partition_w256",
+         "partition_w32", "partition_w256", "partition_w32_direct",
          "tile_sort", "segmented_sort", "partition_lemma2")
 
 

@@ -63,6 +63,7 @@ typedef struct CUstream_st* bcf_stream_t;
 #define BCF_PERMUTE_FUSED 0x40    /* permute_kv: one pass for keys and payloads */
 #define BCF_PERMUTE_BUCKETED 0x80 /* permute: two coalesced passes through ws */
 #define BCF_TILES_SORTED_FINISH 0x100 /* permute_tiles, coloured: Sec. 3 finishing step */
+#define BCF_PARTITION_DIRECT 0x200 /* partition, w <= 32: no shared-memory scatter */
 
 /* Message for a status code (static string; never NULL). */
 const char* bcf_status_string(int status);
@@ -119,6 +120,14 @@ int bcf_sort_passes_run(const void* ws, int64_t n, int val_bytes, int key_bits, 
  *           their own banks, conflict-free row/column conversions -- instead of
  *           the rank-and-scatter sweep.  Same (stable) result, slower; its
  *           shared-memory schedule has no bank conflicts.
+ *           BCF_PARTITION_DIRECT (w <= 32 only, else BCF_E_UNSUPPORTED; not with
+ *           BCF_PARTITION_LEMMA1): every label is its own bank, so ranking keys
+ *           per warp and finding their runs touches one word per label; each key
+ *           is then stored from its registers straight to its global place
+ *           instead of being scattered into label order in shared memory first.
+ *           Same result, no bank conflicts in any shared access; its scattered
+ *           global stores make it about 1.1x the default at 2^16-2^18 keys and
+ *           slower beyond (it suits small partitions).
  *  A label >= w -> device status BCF_E_BAD_KEY.  In place allowed (uses ws).
  * n must be < 2^30. */
 int bcf_partition_workspace_size(int64_t n, int w, int val_bytes, int flags, size_t* bytes);

@@ -30,6 +30,7 @@ PARTITION_LEMMA1 = 0x20
 PERMUTE_FUSED = 0x40
 PERMUTE_BUCKETED = 0x80
 TILES_SORTED_FINISH = 0x100
+PARTITION_DIRECT = 0x200
 # Sizes from which permute()/permute_kv() pick the bucketed form by default.
 BUCKETED_MIN_N = 1 << 20
 BUCKETED_MAX_N = 1 << 26

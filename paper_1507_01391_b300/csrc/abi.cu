@@ -175,6 +175,7 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
   if (rc) return rc;
   if (w < 1) return BCF_E_INVAL;
   if (w > 256 || n >= kMaxSweepN) return BCF_E_UNSUPPORTED;
+  if ((flags & BCF_PARTITION_DIRECT) && (w > 32 || (flags & BCF_PARTITION_LEMMA1))) return BCF_E_UNSUPPORTED;
   const bool balanced = (flags & BCF_ASSUME_BALANCED) != 0;
   if (balanced && n % w) return BCF_E_INVAL;
   if (n == 0) return BCF_OK;
@@ -192,7 +193,7 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
   if (!device_ready()) return BCF_E_CUDA;
   return cuda_rc(bcf::partition(keys_in, vals_in, keys_out, vals_out, n, w, val_bytes, balanced,
                                 static_cast<unsigned char*>(ws), L, (cudaStream_t)stream,
-                                bcf::tuned_config(BCF_OP_PARTITION, n)));
+                                bcf::tuned_config(BCF_OP_PARTITION, n), (flags & BCF_PARTITION_DIRECT) != 0));
 }
 
 // Splitter partition: the sweep layout of a 256-bucket partition, always with

@@ -137,7 +137,8 @@ cudaError_t radix_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
 // Single-pass stable partition by label (see bcf_partition).
 cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                       void* vals_out, int64_t n, int w, int val_bytes, bool balanced,
-                      unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg = 0);
+                      unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg = 0,
+                      bool direct = false);
 
 // Partition with the Lemma 1 tile schedule (BCF_PARTITION_LEMMA1); same layout.
 cudaError_t partition_lemma1(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,

@@ -165,6 +165,10 @@ struct OneSweepParams {
   unsigned spin_limit;         // polls before a wait gives up (0: kSpinLimit)
   int silent_tile1;            // testing aid: 1 + a tile that never publishes (0: none)
   PassSel sel;                 // sel.vary != nullptr: buffers (or a skip) decided on the device
+  // direct (partitions by at most 32 labels): every key goes from its registers
+  // straight to its global place; no digit-order staging in shared memory, so
+  // every shared access of the pass is conflict-free (label = bank)
+  int direct;
   // segment mode (seg_offs != nullptr; offsets mode, sorts only): tile t is
   // piece t - seg_tile0[s] of segment s = tile_seg[t] (tiles past *num_tiles do
   // nothing), tile_offsets holds running sums over all tiles, and a tile's run
@@ -481,8 +485,10 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
         }
       }
     };
-    if (VB == 4 && iota) scatter(std::true_type{});
-    else scatter(std::false_type{});
+    if (!p.direct) {
+      if (VB == 4 && iota) scatter(std::true_type{});
+      else scatter(std::false_type{});
+    }
     // 4b. 8-byte payloads: loaded now (the keys' registers are free), in flight
     // during the look-back, then stored at their keys' positions
     VT val[VB == 8 ? IPT : 1];
@@ -511,7 +517,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       }
       gofs[tid] = base + excl - tile_excl;
     }
-    if constexpr (VB == 8) {
+    if (VB == 8 && !p.direct) {
 #pragma unroll
       for (int j = 0; j < IPT; ++j) {
         const uint32_t pos = (rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
@@ -520,6 +526,36 @@ __global__ void __launch_bounds__(THREADS, MINB) k_onesweep(OneSweepParams p) {
       }
     }
     BCF_SYNC();
+    if (p.direct) {
+      // global place = the run start of the key's label in this tile, plus its
+      // warp's start inside the run, plus its rank among the warp's peers
+      VT* vo = reinterpret_cast<VT*>(vals_out);
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        if (!valid_at(j)) continue;
+        const uint32_t half = (rk[j >> 1] >> (16 * (j & 1))) & 0xFFFFu;
+        const uint32_t d = digit(key[j]);
+        BCF_TR(&wh[d], 4, 0, TS_OFFSET_READ);
+        BCF_TR(&gofs[d], 4, 0, TS_OFFSET_READ);
+        const uint32_t dst = gofs[d] + wh[d] + half;
+        if (dst >= (uint32_t)p.n) continue;
+        keys_out[dst] = key[j];
+        if constexpr (VB == 4) {
+          const int idx = wbase + j * 32 + lane;
+          uint32_t v;
+          if (iota) {
+            v = (uint32_t)(start + idx);
+          } else {
+            BCF_TR(&stage[vsh + idx], 4, 0, TS_STAGE_READ);
+            v = stage[vsh + idx];
+          }
+          vo[dst] = v;
+        } else if constexpr (VB == 8) {
+          vo[dst] = val[j];
+        }
+      }
+      return;
+    }
   }
 
   // 5. write-out: consecutive threads take consecutive ordered positions, so the

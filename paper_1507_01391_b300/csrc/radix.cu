@@ -265,9 +265,11 @@ static cudaError_t onesweep_pass_t(const uint32_t* src_k, const void* src_v, uin
                                    int64_t n, int vb, int shift, int w, bool balanced,
                                    const uint32_t* digit_base, uint32_t* status, uint32_t* zero_next,
                                    uint32_t* ticket, cudaStream_t s, const PassSel& sel,
-                                   uint32_t* totals = nullptr, uint32_t* offsets = nullptr) {
+                                   uint32_t* totals = nullptr, uint32_t* offsets = nullptr,
+                                   bool direct = false) {
   constexpr int T = THREADS * IPT;
   OneSweepParams op{};
+  op.direct = direct ? 1 : 0;
   if (offsets) {  // reduce-then-scan: per-tile counts and their scan first
     constexpr int RADIX = 1 << BITS;
     const int64_t tiles = (n + T - 1) / T;
@@ -318,14 +320,14 @@ static cudaError_t onesweep_pass(const uint32_t* src_k, const void* src_v, uint3
                                  int64_t n, int vb, int shift, int w, bool balanced, const uint32_t* digit_base,
                                  uint32_t* status, uint32_t* zero_next, uint32_t* ticket, cudaStream_t s,
                                  int cfg, const PassSel& sel = PassSel{}, uint32_t* totals = nullptr,
-                                 uint32_t* offsets = nullptr) {
+                                 uint32_t* offsets = nullptr, bool direct = false) {
   const bool rts = cfg >= kNumOneConfigs;
   switch (cfg % kNumOneConfigs) {
 #define BCF_OSP(C)                                                                                         \
   case C:                                                                                                  \
     return onesweep_pass_t<BITS, kSweepCfgThreads[C], kSweepCfgIPT[C], kOneCfgMinBlocks[C]>(             \
         src_k, src_v, dst_k, dst_v, n, vb, shift, w, balanced, digit_base, status, zero_next, ticket, s, sel, \
-        rts ? totals : nullptr, rts ? offsets : nullptr);
+        rts ? totals : nullptr, rts ? offsets : nullptr, direct);
     BCF_OSP(0)
     BCF_OSP(1)
     BCF_OSP(2)
@@ -491,8 +493,11 @@ int sort_passes_run(const unsigned char* ws, const SweepLayout& L, const PassPla
 
 cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                       void* vals_out, int64_t n, int w, int vb, bool balanced,
-                      unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg) {
+                      unsigned char* ws, const SweepLayout& L, cudaStream_t s, int cfg, bool direct) {
   if (n == 0) return cudaSuccess;
+  // The direct write-out exists in the pass body only (a partition by at most 32
+  // labels): take its single-launch or counts + scan form of the same size class.
+  if (direct && !cfg_is_onesweep(cfg)) cfg = n <= kSmallSweepN ? 1 : kNumOneConfigs;
   cudaError_t e = cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_bytes, s);
   if (e != cudaSuccess) return e;
   uint32_t* totals = reinterpret_cast<uint32_t*>(ws + L.hist);
@@ -523,9 +528,9 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
     }
     uint32_t* base = reinterpret_cast<uint32_t*>(ws + L.digit_base);
     uint32_t* ticket = reinterpret_cast<uint32_t*>(ws + L.counters);
-    if (L.radix == 32)
+    if (L.radix == 32)  // at most 32 labels: each label its own bank
       return onesweep_pass<5>(src_k, src_v, keys_out, vals_out, n, vb, 0, w, balanced, base, os_region(ws, L, 0),
-                              nullptr, ticket, s, cfg, PassSel{}, totals, offsets);
+                              nullptr, ticket, s, cfg, PassSel{}, totals, offsets, direct);
     return onesweep_pass<8>(src_k, src_v, keys_out, vals_out, n, vb, 0, w, balanced, base, os_region(ws, L, 0),
                             nullptr, ticket, s, cfg, PassSel{}, totals, offsets);
   }

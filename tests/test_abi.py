@@ -77,6 +77,10 @@ def test_argument_checks_reject_without_launching():
     assert L.bcf_sort(a, None, b, None, 10, 4, 32, ws, 1 << 20, None) == bcf.E_INVAL  # vals missing
     assert L.bcf_partition(a, None, b, None, 10, 3, 0, bcf.ASSUME_BALANCED, ws, 1 << 20, None) == bcf.E_INVAL
     assert L.bcf_partition(a, None, b, None, 10, 300, 0, 0, ws, 1 << 20, None) == bcf.E_UNSUPPORTED
+    # the direct write-out serves at most 32 labels, and not with the Lemma 1 schedule
+    assert L.bcf_partition(a, None, b, None, 64, 33, 0, bcf.PARTITION_DIRECT, ws, 1 << 20, None) == bcf.E_UNSUPPORTED
+    assert L.bcf_partition(a, None, b, None, 64, 32, 0, bcf.PARTITION_DIRECT | bcf.PARTITION_LEMMA1, ws, 1 << 20,
+                           None) == bcf.E_UNSUPPORTED
     assert L.bcf_permute(a, P(0x10010), b, 64, 0, 4, 0, None, 0, None) == bcf.E_INVAL  # overlap
     assert L.bcf_permute(a, b, None, 64, 0, 4, 0, None, 0, None) == bcf.E_INVAL
     assert L.bcf_permute(a, b, ws, 64, 0, 3, 0, None, 0, None) == bcf.E_INVAL

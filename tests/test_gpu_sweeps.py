@@ -201,6 +201,48 @@ def test_partition_lemma1_reports_bad_label(bcf):
     assert bcf.get_status() == bcf.E_BAD_KEY
 
 
+# ------------------------------------------- direct write-out (w <= 32)
+@pytest.mark.parametrize("w,balanced,n", [(32, True, 65536), (32, False, 3 * 4096 + 5), (1, True, 4096),
+                                          (7, False, 1000), (16, True, 1 << 18), (32, False, (1 << 18) + 77),
+                                          (31, False, 700_001), (32, True, 1 << 20)])
+@pytest.mark.parametrize("vb", [0, 4, 8])
+def test_partition_direct_write_out(bcf, w, balanced, n, vb):
+    """Keys stored from registers straight to their global places: the same
+    stable partition, on both sides of the single-launch / counts + scan boundary,
+    ragged tails, every payload width."""
+    if balanced:
+        n -= n % w
+    keys = synth.partition_keys(n, w, seed=w + n) if balanced else synth.random_labels(n, w, seed=w + n)
+    vals = {0: None, 4: synth.float_bits_payload(n, seed=3),
+            8: synth.uniform_keys(2 * n, seed=4).view(np.uint64)}[vb]
+    ko, vo = bcf.partition(dev(keys), None if vals is None else dev(vals), w, balanced=balanced,
+                           flags=bcf.PARTITION_DIRECT)
+    assert bcf.get_status() == bcf.OK
+    rk, rv = oracle.partition_kv(keys, vals, w, balanced=balanced)
+    assert bits_equal(host(ko, np.uint32), rk)
+    if vals is not None:
+        assert bits_equal(host(vo, vals.dtype), rv)
+
+
+def test_partition_direct_index_payload_and_bad_label(bcf):
+    """Position payloads (vals NULL with 4-byte payloads) and a bad label."""
+    n, w = 3 * 4096 + 1, 24
+    keys = synth.random_labels(n, w, seed=11)
+    L = bcf.lib()
+    kd, ko, vo = dev(keys), dev(np.zeros(n, np.uint32)), dev(np.zeros(n, np.uint32))
+    ws = bcf.workspace(bcf.partition_workspace_size(n, w, 4, bcf.PARTITION_DIRECT))
+    import ctypes
+    P = ctypes.c_void_p
+    assert L.bcf_partition(P(kd.data_ptr()), None, P(ko.data_ptr()), P(vo.data_ptr()), n, w, 4,
+                           bcf.PARTITION_DIRECT, P(ws.data_ptr()), ws.numel(), None) == bcf.OK
+    assert bcf.get_status() == bcf.OK
+    rk, rv = oracle.partition_kv(keys, synth.index_payload(n), w)
+    assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.uint32), rv)
+    keys[4242] = w
+    bcf.partition(dev(keys), None, w, flags=bcf.PARTITION_DIRECT)
+    assert bcf.get_status() == bcf.E_BAD_KEY
+
+
 # ------------------------------------------------------ bounded look-back waits
 @pytest.mark.parametrize("op", ["partition", "sort"])
 def test_lookback_wait_gives_up(bcf, op):

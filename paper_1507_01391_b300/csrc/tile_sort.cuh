@@ -58,6 +58,44 @@ __device__ __forceinline__ void sort16(unsigned long long (&v)[16]) {
           if (i + j + k < 16 && (i + j) / (2 * p) == (i + j + k) / (2 * p)) cas_u64(v[i + j], v[i + j + k]);
 }
 
+// One merge round of a row sort: runs [2bL, 2bL+L) and [2bL+L, 2bL+2L) of row r
+// of src are merged into dst; team member t writes merged positions [16t, 16t+16)
+// of its block, found by a merge-path search.  LAST: the items are restored from
+// their complements (flip) as they are written.
+template <int L, bool LAST>
+__device__ __forceinline__ void l1_merge_round(const unsigned long long* src, unsigned long long* dst, int r,
+                                               int t, unsigned long long flip) {
+  const int o0 = t * 16;
+  const int base = (o0 / (2 * L)) * (2 * L);
+  const int d = o0 - base;
+  const unsigned long long* A = src + (size_t)base * kL1Rows + r;
+  const unsigned long long* B = src + (size_t)(base + L) * kL1Rows + r;
+  int lo = d > L ? d - L : 0, hi = d < L ? d : L;
+  while (lo < hi) {  // smallest i whose A[i] comes after B[d-1-i]
+    const int mid = (lo + hi) >> 1;
+    BCF_TR(&A[mid * kL1Rows], 8, 0, TS_L1_ROW_LD);
+    BCF_TR(&B[(d - 1 - mid) * kL1Rows], 8, 0, TS_L1_ROW_LD);
+    const unsigned long long a = A[mid * kL1Rows], b = B[(d - 1 - mid) * kL1Rows];
+    if (a < b) lo = mid + 1;
+    else hi = mid;
+  }
+  int i = lo, j = d - lo;
+  unsigned long long* out = dst + (size_t)(base + d) * kL1Rows + r;
+#pragma unroll 4
+  for (int s = 0; s < 16; ++s) {
+    if (i < L) BCF_TR(&A[i * kL1Rows], 8, 0, TS_L1_ROW_LD);
+    if (j < L) BCF_TR(&B[j * kL1Rows], 8, 0, TS_L1_ROW_LD);
+    const unsigned long long a = i < L ? A[i * kL1Rows] : 0ull;
+    const unsigned long long b = j < L ? B[j * kL1Rows] : 0ull;
+    const bool take_a = (j >= L) || (i < L && a < b);
+    BCF_TR(&out[s * kL1Rows], 8, 1, TS_L1_ROW_ST);
+    out[s * kL1Rows] = LAST ? ((take_a ? a : b) ^ flip) : (take_a ? a : b);
+    i += take_a;
+    j += !take_a;
+  }
+  BCF_SYNC();
+}
+
 // Sort every row of S (ascending, or alternating when alt: row 0 ascending).
 // Uses D as the merge buffer; the sorted rows end in S.
 __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned long long* D, bool alt) {
@@ -79,47 +117,13 @@ __device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned lon
     S[(t * 16 + i) * kL1Rows + r] = v[i];
   }
   BCF_SYNC();
-  unsigned long long* src = S;
-  unsigned long long* dst = D;
-#pragma unroll 1
-  for (int L = 16; L < kL1Cols; L <<= 1) {
-    // merge runs [2bL, 2bL+L) and [2bL+L, 2bL+2L) of row r; this thread writes
-    // merged positions [16t, 16t+16) of its block
-    const int o0 = t * 16;
-    const int base = (o0 / (2 * L)) * (2 * L);
-    const int d = o0 - base;
-    const unsigned long long* A = src + (size_t)base * kL1Rows + r;
-    const unsigned long long* B = src + (size_t)(base + L) * kL1Rows + r;
-    int lo = d > L ? d - L : 0, hi = d < L ? d : L;
-    while (lo < hi) {  // smallest i whose A[i] comes after B[d-1-i]
-      const int mid = (lo + hi) >> 1;
-      BCF_TR(&A[mid * kL1Rows], 8, 0, TS_L1_ROW_LD);
-      BCF_TR(&B[(d - 1 - mid) * kL1Rows], 8, 0, TS_L1_ROW_LD);
-      const unsigned long long a = A[mid * kL1Rows], b = B[(d - 1 - mid) * kL1Rows];
-      if (a < b) lo = mid + 1;
-      else hi = mid;
-    }
-    int i = lo, j = d - lo;
-    unsigned long long* out = dst + (size_t)(base + d) * kL1Rows + r;
-    const unsigned long long oflip = 2 * L == kL1Cols ? flip : 0ull;  // the last round restores the items
-#pragma unroll 4
-    for (int s = 0; s < 16; ++s) {
-      if (i < L) BCF_TR(&A[i * kL1Rows], 8, 0, TS_L1_ROW_LD);
-      if (j < L) BCF_TR(&B[j * kL1Rows], 8, 0, TS_L1_ROW_LD);
-      const unsigned long long a = i < L ? A[i * kL1Rows] : 0ull;
-      const unsigned long long b = j < L ? B[j * kL1Rows] : 0ull;
-      const bool take_a = (j >= L) || (i < L && a < b);
-      BCF_TR(&out[s * kL1Rows], 8, 1, TS_L1_ROW_ST);
-      out[s * kL1Rows] = (take_a ? a : b) ^ oflip;
-      i += take_a;
-      j += !take_a;
-    }
-    BCF_SYNC();
-    unsigned long long* tmp = src;
-    src = dst;
-    dst = tmp;
-  }
-  // four rounds (16 -> 256): the result is back in S
+  // four merge rounds (runs of 16 -> 256), each specialised on its run length;
+  // the last one restores the complemented rows, and the result is back in S
+  static_assert(kL1Cols == 256 && kL1PerThread == 16, "runs of 16 merged four times fill a row");
+  l1_merge_round<16, false>(S, D, r, t, flip);
+  l1_merge_round<32, false>(D, S, r, t, flip);
+  l1_merge_round<64, false>(S, D, r, t, flip);
+  l1_merge_round<128, true>(D, S, r, t, flip);
 }
 
 // Row-major -> column-major: N(r, c) = M(c / 16, (c % 16) * 16 + r).

@@ -1,7 +1,8 @@
 """GPU parity over many seeded random configurations: sizes from 0 to a few hundred
 thousand (both sides of the single-launch limit and of every tile size), key
-widths, payload widths, balanced and unbalanced partitions, splitters, permutation
-forms and in-place calls -- each compared bit-exact with the CPU oracle."""
+widths, payload widths, balanced and unbalanced partitions (sweep, Lemma 1 tiles,
+direct write-out), splitters, permutation forms and in-place calls -- each
+compared bit-exact with the CPU oracle."""
 import numpy as np
 import pytest
 
@@ -68,15 +69,17 @@ def test_fuzz_partition(bcf, case):
         keys = synth.random_labels(n, w, seed=case)
     vb = int(g.choice([0, 4, 8]))
     vals = _payload(g, n, vb)
-    mode = g.choice(["sweep", "lemma1", "splitters"])
+    mode = g.choice(["sweep", "lemma1", "splitters", "direct"])
+    if mode == "direct" and w > 32:  # the direct write-out serves at most 32 labels
+        mode = "sweep"
     kd, vd = dev(keys), (None if vals is None else dev(vals))
     if mode == "splitters":
         spl = np.arange(1, w, dtype=np.uint32)  # bucket = label
         ko, vo = bcf.partition_splitters(kd, vd, dev(spl) if w > 1 else dev(np.zeros(4, np.uint32))[:0],
                                          balanced=balanced)
     else:
-        ko, vo = bcf.partition(kd, vd, w, balanced=balanced,
-                               flags=bcf.PARTITION_LEMMA1 if mode == "lemma1" else 0)
+        flags = {"lemma1": bcf.PARTITION_LEMMA1, "direct": bcf.PARTITION_DIRECT}.get(mode, 0)
+        ko, vo = bcf.partition(kd, vd, w, balanced=balanced, flags=flags)
     assert bcf.get_status() == bcf.OK
     rk, rv = oracle.partition_kv(keys, vals, w, balanced=balanced)
     assert bits_equal(host(ko, np.uint32), rk)

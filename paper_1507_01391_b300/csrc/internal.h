@@ -108,6 +108,7 @@ struct SweepLayout {
   // single-launch passes: two look-back status regions of os_words words each
   // (tile-major, one row of `radix` words per tile), used by alternate passes
   size_t os_status = 0, os_words = 0;
+  size_t labels = 0;  // splitter partition: one bucket byte per key
   size_t total = 0;
   int64_t tiles = 0;
   int64_t lb_stride = 0;  // look-back status words per digit (tiles rounded up to 8)

@@ -585,6 +585,7 @@ cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, ui
   cp.totals = totals;
   cp.splitters = splitters;
   cp.nsplit = nsplit;
+  cp.labels = ws + L.labels;
   const int64_t count_blocks = (tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
   k_tile_counts<8, T, true><<<(unsigned)count_blocks, 256, 0, s>>>(cp, tiles);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -603,6 +604,7 @@ cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, ui
   sp.status = status_word();
   sp.splitters = splitters;
   sp.nsplit = nsplit;
+  sp.labels = ws + L.labels;
   return sweep_dispatch<8, THREADS, IPT, true>(sp, tiles, vb, s);
 }
 

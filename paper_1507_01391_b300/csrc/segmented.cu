@@ -229,7 +229,7 @@ __device__ __forceinline__ void sort_bin(const uint32_t* __restrict__ keys_in, c
 // Persistent blocks: sort every small segment whole with the Lemma 1 schedule --
 // first the segments that take a tile each, then the bins of tiny segments.
 template <int VB>
-__global__ void __launch_bounds__(kL1Threads) k_seg_small(const uint32_t* __restrict__ keys_in,
+__global__ void __launch_bounds__(kL1Threads, 3) k_seg_small(const uint32_t* __restrict__ keys_in,
                                                           const void* __restrict__ vals_in,
                                                           uint32_t* __restrict__ keys_out,
                                                           void* __restrict__ vals_out,

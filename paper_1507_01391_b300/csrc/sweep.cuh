@@ -135,6 +135,7 @@ struct SweepParams {
   // splitter mode (k_sweep<..., SPLIT = true>): digit = number of splitters <= key
   const uint32_t* splitters;   // nsplit ascending values
   int nsplit;                  // 0..255
+  const uint8_t* labels;       // splitter mode: each key's bucket, written by the tile counts
   PassSel sel;                 // sel.vary != nullptr: buffers (or a skip) decided on the device
 };
 
@@ -351,6 +352,7 @@ struct CountParams {
   const uint32_t* num_tiles;
   const uint32_t* splitters;     // splitter mode: digit = number of splitters <= key
   int nsplit;
+  uint8_t* labels;               // splitter mode, unsegmented: bucket of key i stored at labels[i]
   PassSel sel;                   // sel.vary != nullptr: pass 0 fills vary, later passes may skip
 };
 
@@ -382,6 +384,11 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
   auto dig = [&](uint32_t x) -> uint32_t {
     if constexpr (SPLIT) return split_bucket(spl, p.nsplit, x);
     else return (x >> shift) & mask;
+  };
+  // splitter mode: the buckets of keys i..i+3 (i a multiple of 4) kept for the sweep
+  auto put4 = [&](int64_t i, uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3) {
+    if constexpr (SPLIT)
+      if (p.labels) *reinterpret_cast<uint32_t*>(p.labels + i) = d0 | (d1 << 8) | (d2 << 16) | (d3 << 24);
   };
   const int64_t t0 = (int64_t)blockIdx.x * kCountTilesPerBlock;
   const bool segmented = p.seg_offs != nullptr;
@@ -434,19 +441,19 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
 #pragma unroll
         for (int q = 0; q < NV; ++q) x[t][q] = __ldcs(k4 + t * (T / 4) + tid + 256 * q);
       BCF_SYNC();
-      auto count = [&](int t, uint32_t k) {
+      auto count = [&](int t, uint32_t k) -> uint32_t {
         const uint32_t d = dig(k);
         BCF_TR(&lc[t][d >> 2][lane], 4, 2, TS_TILE_COUNT_ATOM);
         atomicAdd(&lc[t][d >> 2][lane], 1u << (8 * (d & 3u)));
+        return d;
       };
 #pragma unroll
       for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
-          count(t, x[t][q].x);
-          count(t, x[t][q].y);
-          count(t, x[t][q].z);
-          count(t, x[t][q].w);
+          const uint32_t d0 = count(t, x[t][q].x), d1 = count(t, x[t][q].y);
+          const uint32_t d2 = count(t, x[t][q].z), d3 = count(t, x[t][q].w);
+          put4((t0 + t) * T + 4 * (tid + 256 * q), d0, d1, d2, d3);
           if (fill_vary) or4(x[t][q]);
         }
       BCF_SYNC();
@@ -486,6 +493,16 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
     for (int i = tid; i < RADIX; i += 256) h[i] = 0;
     BCF_SYNC();
     const uint32_t* k = p.keys + start;
+    // four keys i..i+3 of an unsegmented tile counted (and, splitter mode, their buckets kept)
+    auto count4 = [&](const uint4& xv, int64_t i) {
+      const uint32_t d0 = dig(xv.x), d1 = dig(xv.y), d2 = dig(xv.z), d3 = dig(xv.w);
+      atomicAdd(&h[d0], 1u);
+      atomicAdd(&h[d1], 1u);
+      atomicAdd(&h[d2], 1u);
+      atomicAdd(&h[d3], 1u);
+      put4(i, d0, d1, d2, d3);
+      if (fill_vary) or4(xv);
+    };
     if (segmented) {
       // Segment starts need not be 16-byte aligned: 16-byte loads of the aligned
       // window around the tile (at most T/1024 + 1 per thread, all in flight
@@ -526,25 +543,14 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
 #pragma unroll
       for (int q = 0; q < NV; ++q) x[q] = __ldcs(reinterpret_cast<const uint4*>(k) + tid + 256 * q);
 #pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        atomicAdd(&h[dig(x[q].x)], 1u);
-        atomicAdd(&h[dig(x[q].y)], 1u);
-        atomicAdd(&h[dig(x[q].z)], 1u);
-        atomicAdd(&h[dig(x[q].w)], 1u);
-        if (fill_vary) or4(x[q]);
-      }
+      for (int q = 0; q < NV; ++q) count4(x[q], start + 4 * (tid + 256 * q));
     } else {
       const int nv = cnt >> 2;
-      for (int v = tid; v < nv; v += 256) {
-        const uint4 x = __ldcs(reinterpret_cast<const uint4*>(k) + v);
-        atomicAdd(&h[dig(x.x)], 1u);
-        atomicAdd(&h[dig(x.y)], 1u);
-        atomicAdd(&h[dig(x.z)], 1u);
-        atomicAdd(&h[dig(x.w)], 1u);
-        if (fill_vary) or4(x);
-      }
+      for (int v = tid; v < nv; v += 256) count4(__ldcs(reinterpret_cast<const uint4*>(k) + v), start + 4 * v);
       for (int i = nv * 4 + tid; i < cnt; i += 256) {
-        atomicAdd(&h[dig(k[i])], 1u);
+        const uint32_t d = dig(k[i]);
+        atomicAdd(&h[d], 1u);
+        if (SPLIT && p.labels) p.labels[start + i] = (uint8_t)d;
         if (fill_vary) {
           o1 |= k[i];
           o0 |= ~k[i];
@@ -798,6 +804,18 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
     for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
       vals_s[vsh + i] = reinterpret_cast<const VT*>(p.vals_in)[start + i];
   }
+  // Splitter mode: the buckets the tile counts kept, four per register, loaded
+  // while the tile is staged (lane l of warp q takes items q*32*IPT + 32j + l).
+  uint32_t dl[SPLIT ? (IPT + 3) / 4 : 1] = {};
+  if constexpr (SPLIT) {
+    if (p.labels) {
+#pragma unroll
+      for (int j = 0; j < IPT; ++j) {
+        const int idx = warp * 32 * IPT + j * 32 + lane;
+        if (idx < cnt) dl[j >> 2] |= (uint32_t)__ldcs(p.labels + start + idx) << (8 * (j & 3));
+      }
+    }
+  }
   BCF_SYNC();  // mbarrier initialised before anyone waits on it
   mbar_wait(mbar, 0, p.status);
   BCF_SYNC();
@@ -823,12 +841,18 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
       if (label_mode && valid && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
     }
-    // Splitter mode: every key's bucket once, four 8-bit digits per register.
+    // Splitter mode: every key's bucket once, four 8-bit digits per register --
+    // the ones the tile counts kept, or searched here.
     uint32_t dg[SPLIT ? (IPT + 3) / 4 : 1] = {};
     if constexpr (SPLIT) {
+      if (p.labels) {
 #pragma unroll
-      for (int j = 0; j < IPT; ++j)
-        if (in_tile(wbase + j * 32 + lane)) dg[j >> 2] |= split_bucket(spl, p.nsplit, key[j]) << (8 * (j & 3));
+        for (int j = 0; j < (IPT + 3) / 4; ++j) dg[j] = dl[j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < IPT; ++j)
+          if (in_tile(wbase + j * 32 + lane)) dg[j >> 2] |= split_bucket(spl, p.nsplit, key[j]) << (8 * (j & 3));
+      }
     }
     auto digit = [&](int j) -> uint32_t {
       if constexpr (SPLIT) return (dg[j >> 2] >> (8 * (j & 3))) & 0xFFu;

@@ -20,7 +20,11 @@
 // sorted ascending on its complemented items (complemented when loaded, restored
 // by the last merge round), so every comparison runs one way.  Conversions move
 // one item per row per half-warp phase along a diagonal, so the 16 lanes of a
-// phase read 16 different rows as well.
+// phase read 16 different rows as well.  The first four conversions are done by
+// the loads of the row sort that follows each: a thread reads its 16 items of the
+// converted matrix straight from the unconverted one, in an order that keeps the
+// lanes of a phase on 16 different rows.  After a row -> column-major conversion
+// those 16 items are every 16th item of one sorted row, so they need no network.
 #pragma once
 
 #include "common.cuh"
@@ -45,17 +49,21 @@ __device__ __forceinline__ void cas_u64(unsigned long long& a, unsigned long lon
 // Ascending sort of 16 registers by Batcher's odd-even merge sort (Batcher 1968):
 // for merge widths p = 1, 2, 4, 8 and strides k = p, p/2, ..., 1, compare
 // elements i + j and i + j + k when both lie in the same block of 2p; 63
-// comparators, all indices known at compile time.
+// comparators.  p and k are template arguments so that every loop unrolls and
+// every register index is a constant: the 16 items stay in registers.
+template <int P, int K>
+__device__ __forceinline__ void oem_merge16(unsigned long long (&v)[16]) {
+#pragma unroll
+  for (int j = K % P; j + K < 16; j += 2 * K)
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i + j + K < 16 && (i + j) / (2 * P) == (i + j + K) / (2 * P)) cas_u64(v[i + j], v[i + j + K]);
+  if constexpr (K > 1) oem_merge16<P, K / 2>(v);
+}
+template <int P = 1>
 __device__ __forceinline__ void sort16(unsigned long long (&v)[16]) {
-#pragma unroll
-  for (int p = 1; p < 16; p <<= 1)
-#pragma unroll
-    for (int k = p; k >= 1; k >>= 1)
-#pragma unroll
-      for (int j = k % p; j + k < 16; j += 2 * k)
-#pragma unroll
-        for (int i = 0; i < k; ++i)
-          if (i + j + k < 16 && (i + j) / (2 * p) == (i + j + k) / (2 * p)) cas_u64(v[i + j], v[i + j + k]);
+  oem_merge16<P, P>(v);
+  if constexpr (2 * P < 16) sort16<2 * P>(v);
 }
 
 // One merge round of a row sort: runs [2bL, 2bL+L) and [2bL+L, 2bL+2L) of row r
@@ -96,21 +104,53 @@ __device__ __forceinline__ void l1_merge_round(const unsigned long long* src, un
   BCF_SYNC();
 }
 
-// Sort every row of S (ascending, or alternating when alt: row 0 ascending).
-// Uses D as the merge buffer; the sorted rows end in S.
-__device__ __forceinline__ void l1_sort_rows(unsigned long long* S, unsigned long long* D, bool alt) {
+// Where a row sort takes its items from.
+enum L1Load {
+  kL1Own,       // the rows of S
+  kL1FromRows,  // row -> column-major conversion of src, whose rows are sorted alternating (row 0 ascending)
+  kL1FromCols,  // column -> row-major conversion of src
+};
+
+// Sort every row (ascending, or alternating when alt: row 0 ascending) of S, or of
+// the conversion of src (LOAD), into S.  Uses D as the merge buffer; the sorted
+// rows end in S.  With a conversion, src is D or unused, never S.
+template <int LOAD>
+__device__ __forceinline__ void l1_sort_rows(const unsigned long long* src, unsigned long long* S,
+                                             unsigned long long* D, bool alt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = lane & 15;                    // row
-  const int t = warp * 2 + (lane >> 4);       // team member 0..15
+  const int t = (r + warp * 2 + (lane >> 4)) & 15;  // team member: 16 different ones in a half-warp
   const bool up = !(alt && (r & 1));
   const unsigned long long flip = up ? 0ull : ~0ull;  // descending rows sort complemented items
   unsigned long long v[16];
+  if constexpr (LOAD == kL1FromRows) {
+    // Position 16t + i of row r is src(t, 16i + r); src's row t is sorted ascending
+    // for even t and descending for odd t, so read in that order the 16 items are
+    // sorted.  The lanes of a half-warp read 16 different rows t.  (alt is false.)
+    const int i0 = (t & 1) ? 15 : 0, di = (t & 1) ? -1 : 1;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 0, TS_L1_ROW_LD);
-    v[i] = S[(t * 16 + i) * kL1Rows + r] ^ flip;
+    for (int k = 0; k < 16; ++k) {
+      const int i = i0 + di * k;
+      BCF_TR(&src[(i * 16 + r) * kL1Rows + t], 8, 0, TS_L1_CONVERT);
+      v[k] = src[(i * 16 + r) * kL1Rows + t];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      if constexpr (LOAD == kL1FromCols) {
+        // Position 16t + i of row r is src(i, 16r + t); lane r reads i = (k + r)
+        // mod 16 in step k, so a half-warp's lanes read 16 different rows.  The
+        // network sorts whatever order they arrive in.
+        const int i = (k + r) & 15;
+        BCF_TR(&src[(r * 16 + t) * kL1Rows + i], 8, 0, TS_L1_CONVERT);
+        v[k] = src[(r * 16 + t) * kL1Rows + i] ^ flip;
+      } else {
+        BCF_TR(&S[(t * 16 + k) * kL1Rows + r], 8, 0, TS_L1_ROW_LD);
+        v[k] = S[(t * 16 + k) * kL1Rows + r] ^ flip;
+      }
+    }
+    sort16(v);
   }
-  sort16(v);
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     BCF_TR(&S[(t * 16 + i) * kL1Rows + r], 8, 1, TS_L1_ROW_ST);
@@ -143,32 +183,18 @@ __device__ __forceinline__ void l1_row_to_col(const unsigned long long* M, unsig
   BCF_SYNC();
 }
 
-// Column-major -> row-major: M(R, C) = N(C % 16, R * 16 + C / 16).
-__device__ __forceinline__ void l1_col_to_row(const unsigned long long* N, unsigned long long* M) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int p = lane & 15, g = warp * 2 + (lane >> 4);
-  const int r = (p + g) & 15;
-#pragma unroll 4
-  for (int j = 0; j < 16; ++j) {
-    const int C = j * 16 + r;
-    BCF_TR(&N[(p * 16 + j) * kL1Rows + r], 8, 0, TS_L1_CONVERT);
-    BCF_TR(&M[C * kL1Rows + p], 8, 1, TS_L1_CONVERT);
-    M[C * kL1Rows + p] = N[(p * 16 + j) * kL1Rows + r];
-  }
-  BCF_SYNC();
-}
-
 // The Lemma 1 schedule on items already built in X; afterwards Y[t] holds the
-// item of sorted position t.
+// item of sorted position t.  Twice: sort rows alternating, convert to
+// column-major, sort rows ascending, convert to row-major; then sort rows
+// ascending and convert to column-major.  The first four conversions are fused
+// into the row sorts after them.
 __device__ __forceinline__ void lemma1_schedule(unsigned long long* X, unsigned long long* Y) {
+  l1_sort_rows<kL1Own>(nullptr, X, Y, true);
 #pragma unroll 1
   for (int rep = 0; rep < 2; ++rep) {
-    l1_sort_rows(X, Y, true);
-    l1_row_to_col(X, Y);
-    l1_sort_rows(Y, X, false);
-    l1_col_to_row(Y, X);
+    l1_sort_rows<kL1FromRows>(X, Y, X, false);
+    l1_sort_rows<kL1FromCols>(Y, X, Y, rep == 0);  // the second time: the final ascending sort
   }
-  l1_sort_rows(X, Y, false);
   l1_row_to_col(X, Y);
 }
 

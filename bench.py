@@ -771,9 +771,9 @@ def run_rows(which, peak):
         ws = bcf.workspace(bcf.partition_splitters_workspace_size(n, 255, 4))
         ms, _ = graph_ms(lambda: bcf.partition_splitters(k, v, sd, keys_out=ko, vals_out=vo, ws=ws), 3, 10, inner=2)
         add("partition_splitters_255_2pow26", n, 16 * n, ms, "sample-sort bucketing: 256 buckets from 255 "
-            "sampled splitters (one search per key in shared memory, by the tile counts, which keep each bucket "
-            "as a byte); tile counts (4 B/key read, 1 B/key written) + sweep (16 B/key + 1 B/key of buckets), "
-            "model charges 16 B/key")
+            "sampled splitters (one prefix-table search per key in shared memory, by the tile counts, which keep "
+            "each bucket as a byte); tile counts (4 B/key read, 1 B/key written) + sweep (16 B/key + 1 B/key of "
+            "buckets), model charges 16 B/key")
         del k, v, sd, ko, vo, ws
     if want("partition_w256_2pow26"):
         n, w = 1 << 26, 256

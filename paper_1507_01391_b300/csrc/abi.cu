@@ -198,11 +198,12 @@ int bcf_partition(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_o
 
 // Splitter partition: the sweep layout of a 256-bucket partition, always with
 // room for an in-place copy and for the reduce-then-scan counts at any size,
-// plus one byte per key for the buckets.
+// plus one byte per key for the buckets and the splitter search's prefix table.
 static bcf::SweepLayout splitter_layout(int64_t n, int val_bytes) {
   bcf::SweepLayout L = bcf::sweep_layout(n, val_bytes, 1, 256, true, bcf::kMinSweepTile, false);
   L.labels = L.total;  // each key's bucket, kept by the tile counts for the sweep
-  L.total = bcf::align_up(L.total + (size_t)n);
+  L.split_table = bcf::align_up(L.total + (size_t)n);
+  L.total = bcf::align_up(L.split_table + (size_t)bcf::kSplitPrefixes * 2 + 8);  // 16 bits per prefix, window
   return L;
 }
 

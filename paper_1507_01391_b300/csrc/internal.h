@@ -80,6 +80,9 @@ constexpr int kTuneOps = 3;
 inline bool cfg_segment_capable(int cfg) {
   return cfg >= kNumOneConfigs && cfg < kNumSweepConfigs && kSweepCfgThreads[cfg] * kSweepCfgIPT[cfg] == kSweepTile;
 }
+// Splitter partition: the search's prefix table covers the keys' top 12 bits.
+constexpr int kSplitPrefixBits = 12;
+constexpr int kSplitPrefixes = 1 << kSplitPrefixBits;
 constexpr int kMinSweepTile = 1024;  // smallest tile of any configuration (sizes workspaces)
 constexpr int kOneMinTile = 2048;    // smallest tile of the onesweep.cuh configurations
 // Inputs up to this size run each sweep.cuh digit pass as one look-back sweep
@@ -108,7 +111,8 @@ struct SweepLayout {
   // single-launch passes: two look-back status regions of os_words words each
   // (tile-major, one row of `radix` words per tile), used by alternate passes
   size_t os_status = 0, os_words = 0;
-  size_t labels = 0;  // splitter partition: one bucket byte per key
+  size_t labels = 0;       // splitter partition: one bucket byte per key
+  size_t split_table = 0;  // splitter partition: prefix table of the splitter search
   size_t total = 0;
   int64_t tiles = 0;
   int64_t lb_stride = 0;  // look-back status words per digit (tiles rounded up to 8)

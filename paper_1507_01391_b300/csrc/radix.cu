@@ -552,6 +552,47 @@ cudaError_t partition(const uint32_t* keys_in, const void* vals_in, uint32_t* ke
 
 // w-way partition by w - 1 splitters (sample-sort bucketing): one reduce-then-scan
 // pass whose digit is the number of splitters <= key, default tile configuration.
+// The prefix table of split_bucket (one block of 256 threads), built from the
+// ascending splitters: the window (first splitter, shift), the counts of splitters
+// per prefix, then their exclusive scan.  The entries are followed by the window's
+// two words.  A descending pair of splitters is flagged in the status word (the
+// prefixes are clamped, so such a table stays in bounds).
+__global__ void __launch_bounds__(256) k_split_table(const uint32_t* __restrict__ spl, int nsplit,
+                                                     uint16_t* __restrict__ table, unsigned* status) {
+  constexpr int PER = kSplitPrefixes / 256;
+  __shared__ uint32_t cnt[kSplitPrefixes];
+  __shared__ uint32_t scratch[32];
+  const int tid = threadIdx.x;
+  const uint32_t base = nsplit ? spl[0] : 0u;
+  const uint32_t range = nsplit ? spl[nsplit - 1] - base : 0u;
+  const uint32_t sh = (uint32_t)max(0, (32 - __clz(range)) - kSplitPrefixBits);  // range >> sh < 2^12
+  for (int i = tid; i < kSplitPrefixes; i += 256) cnt[i] = 0;
+  BCF_SYNC();
+  for (int i = tid; i < nsplit; i += 256) {
+    const uint32_t v = spl[i];
+    atomicAdd(&cnt[min((v - base) >> sh, (uint32_t)(kSplitPrefixes - 1))], 1u);
+    if (i > 0 && spl[i - 1] > v) set_status(status, DEV_BAD_KEY);
+  }
+  BCF_SYNC();
+  uint32_t c[PER], sum = 0;
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    c[j] = cnt[tid * PER + j];
+    sum += c[j];
+  }
+  uint32_t total;
+  uint32_t lo = block_excl_scan<256>(sum, scratch, &total);
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    table[tid * PER + j] = (uint16_t)(lo | ((lo + c[j]) << 8));  // nsplit <= 255: both fit a byte
+    lo += c[j];
+  }
+  if (tid == 0) {
+    reinterpret_cast<uint32_t*>(table + kSplitPrefixes)[0] = base;
+    reinterpret_cast<uint32_t*>(table + kSplitPrefixes)[1] = sh;
+  }
+}
+
 cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, uint32_t* keys_out,
                                 void* vals_out, int64_t n, const uint32_t* splitters, int nsplit, int vb,
                                 bool balanced, unsigned char* ws, const SweepLayout& L, cudaStream_t s) {
@@ -585,7 +626,10 @@ cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, ui
   cp.totals = totals;
   cp.splitters = splitters;
   cp.nsplit = nsplit;
+  cp.split_table = reinterpret_cast<const uint16_t*>(ws + L.split_table);
   cp.labels = ws + L.labels;
+  k_split_table<<<1, 256, 0, s>>>(splitters, nsplit, reinterpret_cast<uint16_t*>(ws + L.split_table), status_word());
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int64_t count_blocks = (tiles + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
   k_tile_counts<8, T, true><<<(unsigned)count_blocks, 256, 0, s>>>(cp, tiles);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -602,8 +646,6 @@ cudaError_t partition_splitters(const uint32_t* keys_in, const void* vals_in, ui
   sp.lb_stride = stride;
   sp.tile_offsets = offsets;
   sp.status = status_word();
-  sp.splitters = splitters;
-  sp.nsplit = nsplit;
   sp.labels = ws + L.labels;
   return sweep_dispatch<8, THREADS, IPT, true>(sp, tiles, vb, s);
 }

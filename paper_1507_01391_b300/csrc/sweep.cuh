@@ -132,10 +132,9 @@ struct SweepParams {
   // makes a later tile's bounded wait run out
   unsigned spin_limit;
   int silent_tile1;
-  // splitter mode (k_sweep<..., SPLIT = true>): digit = number of splitters <= key
-  const uint32_t* splitters;   // nsplit ascending values
-  int nsplit;                  // 0..255
-  const uint8_t* labels;       // splitter mode: each key's bucket, written by the tile counts
+  // splitter mode (k_sweep<..., SPLIT = true>): digit = number of splitters <= key,
+  // each key's bucket as the tile counts kept it
+  const uint8_t* labels;
   PassSel sel;                 // sel.vary != nullptr: buffers (or a skip) decided on the device
 };
 
@@ -308,32 +307,25 @@ __global__ void __launch_bounds__(THREADS) k_histogram(HistParams p) {
 }
 
 // Bucket of key k among nsplit ascending splitters: the number of splitters <= k.
-// The splitters, padded to 255 with 0xFFFFFFFF, sit in shared memory as a perfect
-// binary search tree in level order (node i at spl[i], children 2i and 2i+1): the
-// nodes of one level are consecutive words, so the first six levels of a warp's
-// searches never share a bank.  After eight steps i - 256 counts the tree's
-// values <= k; the clamp removes the padding (which only 0xFFFFFFFF reaches).
-__device__ __forceinline__ uint32_t split_bucket(const uint32_t* spl, int nsplit, uint32_t k) {
-  uint32_t i = 1;
-#pragma unroll
-  for (int l = 0; l < 8; ++l) i = 2 * i + (spl[i] <= k ? 1u : 0u);
-  return min(i - 256u, (uint32_t)nsplit);
-}
-
-// Build the search tree of split_bucket from the ascending splitters (every thread
-// of the block takes part; a barrier must follow) and, given a status word, flag
-// a descending pair.  Node i at level l (2^l <= i < 2^(l+1)) holds the sorted
-// value of rank (2 (i - 2^l) + 1) 2^(7-l) - 1.
-__device__ __forceinline__ void stage_splitters(const uint32_t* src, int nsplit, uint32_t* spl, int nthreads,
-                                                unsigned* status) {
-  for (int i = 1 + (int)threadIdx.x; i < 256; i += nthreads) {
-    const int l = 31 - __clz(i);
-    const int r = ((2 * (i - (1 << l)) + 1) << (7 - l)) - 1;
-    spl[i] = r < nsplit ? src[r] : 0xFFFFFFFFu;
+// A prefix table narrows the search.  The splitters span [base, base + range];
+// prefix P of a key k >= base is (k - base) >> sh, sh the smallest shift that
+// leaves every splitter's prefix below kSplitPrefixes (keys below base take prefix
+// 0, keys past the last prefix the last).  Entry P is lo | hi << 8: lo counts the
+// splitters below the prefix's first value and [lo, hi) are the splitters with
+// prefix P.  The bucket is lo plus the number of those <= k, found by a binary
+// search over powers of two -- no step at all for the prefixes that hold no
+// splitter, most of them when 255 splitters share 4096 prefixes.
+__device__ __forceinline__ uint32_t split_bucket(const uint32_t* spl, const uint16_t* spt, uint32_t base,
+                                                 uint32_t sh, uint32_t k) {
+  const uint32_t e = spt[min((max(k, base) - base) >> sh, (uint32_t)(kSplitPrefixes - 1))];
+  uint32_t b = e & 0xFFu, len = (e >> 8) - b;  // the prefix's splitters: spl[b, b + len)
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    const bool right = spl[b + half] <= k;
+    b = right ? b + half + 1 : b;
+    len = right ? len - half - 1 : half;
   }
-  if (status)
-    for (int i = 1 + (int)threadIdx.x; i < nsplit; i += nthreads)
-      if (src[i - 1] > src[i]) set_status(status, DEV_BAD_KEY);
+  return b;
 }
 
 // ------------------------------------------------------------- reduce-then-scan
@@ -350,8 +342,9 @@ struct CountParams {
   const int32_t* tile_seg;
   const int32_t* seg_tile0;
   const uint32_t* num_tiles;
-  const uint32_t* splitters;     // splitter mode: digit = number of splitters <= key
-  int nsplit;
+  const uint32_t* splitters;     // splitter mode: digit = number of splitters <= key,
+  int nsplit;                    //   found through the prefix table k_split_table builds
+  const uint16_t* split_table;
   uint8_t* labels;               // splitter mode, unsegmented: bucket of key i stored at labels[i]
   PassSel sel;                   // sel.vary != nullptr: pass 0 fills vary, later passes may skip
 };
@@ -380,9 +373,17 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
   const uint32_t mask = p.label_bits ? ((1u << p.label_bits) - 1u) : (uint32_t)(RADIX - 1);
   const int shift = p.label_bits ? 0 : p.shift;
   __shared__ uint32_t spl[SPLIT ? 256 : 1];
-  if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, 256, nullptr);  // read after a barrier below
+  __shared__ __align__(16) uint16_t spt[SPLIT ? kSplitPrefixes : 1];
+  if constexpr (SPLIT) {  // read after a barrier below
+    for (int i = tid; i < p.nsplit; i += 256) spl[i] = p.splitters[i];
+    for (int i = tid; i < kSplitPrefixes / 8; i += 256)
+      reinterpret_cast<uint4*>(spt)[i] = reinterpret_cast<const uint4*>(p.split_table)[i];
+  }
+  // the table's window: its first splitter and the prefix shift, after the entries
+  const uint32_t sbase = SPLIT ? reinterpret_cast<const uint32_t*>(p.split_table + kSplitPrefixes)[0] : 0u;
+  const uint32_t ssh = SPLIT ? reinterpret_cast<const uint32_t*>(p.split_table + kSplitPrefixes)[1] : 0u;
   auto dig = [&](uint32_t x) -> uint32_t {
-    if constexpr (SPLIT) return split_bucket(spl, p.nsplit, x);
+    if constexpr (SPLIT) return split_bucket(spl, spt, sbase, ssh, x);
     else return (x >> shift) & mask;
   };
   // splitter mode: the buckets of keys i..i+3 (i a multiple of 4) kept for the sweep
@@ -692,8 +693,7 @@ struct SweepSmem {
   static constexpr size_t scratch = gofs + (size_t)RADIX * 4;
   static constexpr size_t mbar = scratch + 32 * 4;
   static constexpr size_t info = mbar + 8;                 // tile, seg
-  static constexpr size_t spl = info + 16;                 // splitter mode: splitters
-  static constexpr size_t sdig = spl + (SPLIT ? 256 * 4 : 0);  // splitter mode: digit of each ordered key
+  static constexpr size_t sdig = info + 16;                // splitter mode: digit of each ordered key
   static constexpr size_t mbins = (sdig + (SPLIT ? (size_t)T : 0) + 15) / 16 * 16;  // peer masks
   static constexpr size_t bytes = mbins + (BCF_PEERS_MATCH == 2 ? (size_t)WARPS * RADIX * 4 : 0);
   static_assert(scratch % 8 == 0, "scratch also carries pointers; mbar needs 8-byte alignment");
@@ -718,7 +718,6 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   uint32_t* scratch = reinterpret_cast<uint32_t*>(smem + S::scratch);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + S::mbar);
   int* s_info = reinterpret_cast<int*>(smem + S::info);
-  uint32_t* spl = reinterpret_cast<uint32_t*>(smem + S::spl);
   uint8_t* sdig = reinterpret_cast<uint8_t*>(smem + S::sdig);
   uint32_t* mbins = reinterpret_cast<uint32_t*>(smem + S::mbins);
 
@@ -798,7 +797,6 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
 #if BCF_PEERS_MATCH == 2
   for (int i = tid; i < S::WARPS * RADIX; i += THREADS) mbins[i] = 0;
 #endif
-  if constexpr (SPLIT) stage_splitters(p.splitters, p.nsplit, spl, THREADS, p.status);
   for (int i = max(kfull - ksh, 0) + tid; i < cnt; i += THREADS) keys_s[ksh + i] = p.keys_in[start + i];
   if (VB && !iota) {
     for (int i = max(vfull - vsh, 0) + tid; i < cnt; i += THREADS)
@@ -808,12 +806,10 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
   // while the tile is staged (lane l of warp q takes items q*32*IPT + 32j + l).
   uint32_t dl[SPLIT ? (IPT + 3) / 4 : 1] = {};
   if constexpr (SPLIT) {
-    if (p.labels) {
 #pragma unroll
-      for (int j = 0; j < IPT; ++j) {
-        const int idx = warp * 32 * IPT + j * 32 + lane;
-        if (idx < cnt) dl[j >> 2] |= (uint32_t)__ldcs(p.labels + start + idx) << (8 * (j & 3));
-      }
+    for (int j = 0; j < IPT; ++j) {
+      const int idx = warp * 32 * IPT + j * 32 + lane;
+      if (idx < cnt) dl[j >> 2] |= (uint32_t)__ldcs(p.labels + start + idx) << (8 * (j & 3));
     }
   }
   BCF_SYNC();  // mbarrier initialised before anyone waits on it
@@ -841,21 +837,9 @@ __global__ void __launch_bounds__(THREADS, (VB == 8 ? 2 : BCF_SWEEP_MINBLOCKS) *
       if (VB) val[j] = !valid ? VT(0) : (iota ? VT(start + idx) : vals_s[vsh + idx]);
       if (label_mode && valid && key[j] >= (uint32_t)w) set_status(p.status, DEV_BAD_KEY);
     }
-    // Splitter mode: every key's bucket once, four 8-bit digits per register --
-    // the ones the tile counts kept, or searched here.
-    uint32_t dg[SPLIT ? (IPT + 3) / 4 : 1] = {};
-    if constexpr (SPLIT) {
-      if (p.labels) {
-#pragma unroll
-        for (int j = 0; j < (IPT + 3) / 4; ++j) dg[j] = dl[j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < IPT; ++j)
-          if (in_tile(wbase + j * 32 + lane)) dg[j >> 2] |= split_bucket(spl, p.nsplit, key[j]) << (8 * (j & 3));
-      }
-    }
+    // Splitter mode: the keys' buckets, four 8-bit digits per register.
     auto digit = [&](int j) -> uint32_t {
-      if constexpr (SPLIT) return (dg[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+      if constexpr (SPLIT) return (dl[j >> 2] >> (8 * (j & 3))) & 0xFFu;
       else return (key[j] >> shift) & DMASK;
     };
 

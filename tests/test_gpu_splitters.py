@@ -68,6 +68,22 @@ def test_partition_splitters_duplicates_and_equal_splitters(bcf):
     _case(bcf, keys, synth.index_payload(n), spl)
 
 
+@pytest.mark.parametrize("key_bits", [1, 8, 13, 20, 31])
+@pytest.mark.parametrize("nsplit", [1, 2, 255])
+def test_partition_splitters_narrow_key_ranges(bcf, key_bits, nsplit):
+    """Keys confined to [0, 2^key_bits) (offset away from 0 for some widths), so the
+    splitters span a narrow window of values, and splitters that share values or
+    fall outside the keys' range."""
+    n = 6 * TILE + 77
+    offset = np.uint32(0 if key_bits % 2 else 0x9E3779B9 >> key_bits)
+    keys = (synth.uniform_keys(n, seed=key_bits) >> np.uint32(32 - key_bits)) + offset
+    spl = _sample_splitters(keys, nsplit, seed=nsplit)
+    if nsplit == 255:  # a splitter above every key and one below
+        spl[0], spl[-1] = 0, 0xFFFFFFFF
+        spl = np.sort(spl).astype(np.uint32)
+    _case(bcf, keys.astype(np.uint32), synth.index_payload(n), spl)
+
+
 def test_partition_splitters_balanced_and_in_place(bcf):
     n, w = 16 * TILE, 64
     keys = (synth.random_perm(n, seed=5) * 7).astype(np.uint32)  # distinct keys

@@ -169,7 +169,7 @@ struct OneSweepParams {
   // straight to its global place; no digit-order staging in shared memory, so
   // every shared access of the pass is conflict-free (label = bank)
   int direct;
-  // segment mode (seg_offs != nullptr; offsets mode, sorts only): tile t is
+  // segment mode (seg_offs != nullptr; offsets mode): tile t is
   // piece t - seg_tile0[s] of segment s = tile_seg[t] (tiles past *num_tiles do
   // nothing), tile_offsets holds running sums over all tiles, and a tile's run
   // start is its running sum minus the one at its segment's first tile plus the

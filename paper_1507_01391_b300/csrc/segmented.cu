@@ -146,12 +146,15 @@ __global__ void __launch_bounds__(kPlanThreads) k_seg_plan(PlanParams p) {
 // Digit starts of every long segment for one pass, from that pass's running
 // tile sums: the segment holds run[d][t0 + tiles] - run[d][t0] keys of digit d;
 // an exclusive scan over d, offset by the segment's start, gives the starts.
+// seg_w != nullptr (a balanced partition): every label below the segment's width
+// must hold len / w keys, else the status records it.
 __global__ void __launch_bounds__(256) k_seg_digit_base(const uint32_t* __restrict__ run,
                                                         int64_t stride, uint32_t* __restrict__ seg_base,
                                                         const int32_t* __restrict__ slot_seg,
                                                         const int32_t* __restrict__ seg_tile0,
                                                         const int64_t* __restrict__ offs,
-                                                        const uint32_t* __restrict__ ctr, int tile) {
+                                                        const uint32_t* __restrict__ ctr, int tile,
+                                                        const int32_t* __restrict__ seg_w, unsigned* status) {
   __shared__ uint32_t scratch[32];
   const int64_t slot = blockIdx.x;
   if (slot >= (int64_t)ctr[C_NLARGE]) return;
@@ -161,6 +164,10 @@ __global__ void __launch_bounds__(256) k_seg_digit_base(const uint32_t* __restri
   const int t1 = t0 + (int)((len + tile - 1) / tile);
   const uint32_t* r = run + (size_t)threadIdx.x * stride;
   const uint32_t c = r[t1] - r[t0];
+  if (seg_w) {
+    const int w = max(seg_w[seg], 1);
+    if (c != ((int)threadIdx.x < w ? (uint32_t)(len / w) : 0u)) set_status(status, DEV_NOT_BALANCED);
+  }
   uint32_t tot;
   const uint32_t e = block_excl_scan<256>(c, scratch, &tot);
   seg_base[(size_t)slot * 256 + threadIdx.x] = (uint32_t)lo + e;
@@ -388,10 +395,13 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
   }
 
   const int P = plan.passes;
-  // Sorts take the pass form the tuning table names for this batch size: the
-  // pass body fed scanned offsets (form 1) or the staged sweep (form 2), both of
-  // 4096-key tiles; partitions (per-segment widths, balanced checks) the staged sweep.
-  const bool body_form = !label && cfg_form(tuned_config(kOpSegmentedSort, n_total)) == 1;
+  // Sorts and partitions take the pass form the tuning table names for this
+  // batch size: the pass body fed scanned offsets (form 1) or the staged sweep
+  // (form 2), both of 4096-key tiles.  The body takes every segment's digit
+  // starts from the counts (a balanced partition's closed-form starts are the
+  // same; k_seg_digit_base checks the counts); the staged sweep computes a
+  // balanced partition's starts and checks itself.
+  const bool body_form = cfg_form(tuned_config(kOpSegmentedSort, n_total)) == 1;
   uint32_t* kt = U32(L.keys_tmp);
   void* vt = vb ? (void*)(ws + L.vals_tmp) : nullptr;
   const uint32_t* src_k = keys_in;
@@ -415,14 +425,17 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
     cp.tile_seg = I32(L.tile_seg);
     cp.seg_tile0 = I32(L.seg_tile0);
     cp.num_tiles = ctr + C_NTILES;
+    cp.seg_w = label && body_form ? seg_w : nullptr;
+    cp.status = st;
     const int64_t count_blocks = (L.tiles_cap + kCountTilesPerBlock - 1) / kCountTilesPerBlock;
     k_tile_counts<8, kSweepTile, false, false><<<(unsigned)count_blocks, 256, 0, s>>>(cp, L.tiles_cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     launch_scan_offsets(256, offsets, L.tiles_cap, L.lb_stride, nullptr, 0, n_total, 1, st, s);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (!balanced) {
+    if (!balanced || body_form) {
       k_seg_digit_base<<<(unsigned)L.slots_cap, 256, 0, s>>>(offsets, L.lb_stride, U32(L.seg_base), I32(L.slot_seg),
-                                                             I32(L.seg_tile0), offs, ctr, kSweepTile);
+                                                             I32(L.seg_tile0), offs, ctr, kSweepTile,
+                                                             balanced ? seg_w : nullptr, st);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (body_form) {
@@ -434,6 +447,7 @@ static cudaError_t run_segments(const uint32_t* keys_in, const void* vals_in, ui
       op.vals_out = dv;
       op.n = n_total;
       op.shift = plan.shift[q];
+      op.w = label ? 256 : 0;  // the tile counts check each segment's labels against seg_w
       op.tile_offsets = offsets;
       op.offs_stride = L.lb_stride;
       op.err = st;

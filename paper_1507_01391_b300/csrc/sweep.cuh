@@ -342,6 +342,8 @@ struct CountParams {
   const int32_t* tile_seg;
   const int32_t* seg_tile0;
   const uint32_t* num_tiles;
+  const int32_t* seg_w;          // segment mode, partition: labels of segment s must be < seg_w[s]
+  unsigned* status;              //   (a larger one is recorded as DEV_BAD_KEY here)
   const uint32_t* splitters;     // splitter mode: digit = number of splitters <= key,
   int nsplit;                    //   found through the prefix table k_split_table builds
   const uint16_t* split_table;
@@ -485,10 +487,13 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
   }
   for (int64_t tile = t0; tile < min(t0 + kCountTilesPerBlock, tiles); ++tile) {
     int64_t start = tile * T, hi = p.n;
+    uint32_t wseg = 0;  // segment mode with seg_w: the segment's label bound
     if (segmented) {
       const int seg = p.tile_seg[tile];
       start = p.seg_offs[seg] + (tile - p.seg_tile0[seg]) * (int64_t)T;
       hi = p.seg_offs[seg + 1];
+      if constexpr (!FAST)  // the segment-mode instance
+        if (p.seg_w) wseg = (uint32_t)p.seg_w[seg];
     }
     const int cnt = (int)min((int64_t)T, hi - start);
     for (int i = tid; i < RADIX; i += 256) h[i] = 0;
@@ -528,6 +533,7 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
           xv[j] = make_uint4(x[0], x[1], x[2], x[3]);
         }
       }
+      bool bad = false;
 #pragma unroll
       for (int j = 0; j < NVS; ++j) {
         const int v = tid + 256 * j;
@@ -536,8 +542,12 @@ __global__ void __launch_bounds__(256, 3) k_tile_counts(CountParams p, int64_t t
         const uint32_t x[4] = {xv[j].x, xv[j].y, xv[j].z, xv[j].w};
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-          if (e0 + c >= 0 && e0 + c < cnt) atomicAdd(&h[dig(x[c])], 1u);
+          if (e0 + c >= 0 && e0 + c < cnt) {
+            atomicAdd(&h[dig(x[c])], 1u);
+            if constexpr (!FAST) bad |= p.seg_w && x[c] >= wseg;
+          }
       }
+      if (!FAST && bad) set_status(p.status, DEV_BAD_KEY);
     } else if (cnt == T) {  // full tile: all T/1024 vector loads in flight before counting
       constexpr int NV = T / 1024;
       uint4 x[NV];

@@ -275,6 +275,30 @@ def test_segmented_partition_graph_capture(bcf, balanced):
         assert bits_equal(host(ko, np.uint32), rk) and bits_equal(host(vo, np.uint32), rv)
 
 
+@pytest.mark.parametrize("balanced", [True, False])
+def test_segmented_partition_reports_bad_label_and_unbalanced_counts(bcf, balanced):
+    """A label at its segment's width is flagged (E_BAD_KEY; with balanced=True the
+    counts it upsets are reported first, E_NOT_BALANCED), and with balanced=True a
+    segment whose labels are not equally frequent is flagged (E_NOT_BALANCED)."""
+    import torch
+    offs = np.array([0, 4096 * 2 + 64, 4096 * 2 + 128, 4096 * 3 + 128], dtype=np.int64)
+    w = np.array([32, 64, 128], dtype=np.int32)
+    keys = np.concatenate([np.tile(np.arange(int(w[s]), dtype=np.uint32), int(offs[s + 1] - offs[s]) // int(w[s]))
+                           for s in range(3)])
+    keys = np.concatenate([synth.rng(s).permutation(keys[offs[s]:offs[s + 1]]) for s in range(3)]).astype(np.uint32)
+    od, wd = torch.from_numpy(offs).cuda(), dev(w)
+    _seg_part_case(bcf, keys, None, offs, w, balanced)  # well-formed: OK
+    bad = keys.copy()
+    bad[int(offs[1]) + 7] = 64  # segment 1 has width 64 (and, balanced, one label fewer)
+    bcf.segmented_partition(dev(bad), None, od, wd, balanced=balanced)
+    assert bcf.get_status() == (bcf.E_NOT_BALANCED if balanced else bcf.E_BAD_KEY)  # both flagged when balanced
+    if balanced:
+        skew = keys.copy()
+        skew[int(offs[2]) + 3] = (int(skew[int(offs[2]) + 3]) + 1) % 128  # one label one more, another one fewer
+        bcf.segmented_partition(dev(skew), None, od, wd, balanced=True)
+        assert bcf.get_status() == bcf.E_NOT_BALANCED
+
+
 def test_segmented_partition_reports_bad_width(bcf):
     import torch
     offs = np.array([0, 64, 128], dtype=np.int64)

@@ -1061,12 +1061,28 @@ def _case_inputs(name):
         ko, vo = torch.empty_like(k), torch.empty_like(v)
         ws = bcf.workspace(bcf.segmented_sort_workspace_size(m, 10_000, 4, 32))
         return lambda: bcf.segmented_sort(k, v, offs, keys_out=ko, vals_out=vo, ws=ws)
+    if name == "segmented_partition":  # 10,000 segments, w in {32, 64, 128, 256}, balanced
+        keys, offs_np, w = synth.segmented_partition_input(10_000, seed=0x4C)
+        k, v = to_dev(keys), to_dev(synth.index_payload(keys.size))
+        offs, wd = torch.from_numpy(offs_np).cuda(), to_dev(w.astype(np.int32))
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.segmented_partition_workspace_size(keys.size, w.size, 4))
+        return lambda: bcf.segmented_partition(k, v, offs, wd, balanced=True, keys_out=ko, vals_out=vo, ws=ws)
+    if name == "partition_splitters":  # 2^26 uniform keys, 255 splitters sampled from them
+        m = 1 << 26
+        keys = synth.uniform_keys(m, seed=0x2D)
+        sample = np.sort(keys[synth.rng(7).integers(0, m, size=255 * 16)])
+        spl = sample[(np.arange(1, 256) * sample.size) // 256].astype(np.uint32)
+        k, v, sd = to_dev(keys), to_dev(synth.index_payload(m)), to_dev(spl)
+        ko, vo = torch.empty_like(k), torch.empty_like(v)
+        ws = bcf.workspace(bcf.partition_splitters_workspace_size(m, 255, 4))
+        return lambda: bcf.partition_splitters(k, v, sd, keys_out=ko, vals_out=vo, ws=ws)
     raise ValueError(name)
 
 
 CASES = ("permute_kv", "permute_kv_scatter", "tile_scatter", "tile_coloured", "sort_kv", "sort_kv_2pow26",
          "partition_w32", "partition_w256", "partition_w32_direct",
-         "tile_sort", "segmented_sort", "partition_lemma2")
+         "tile_sort", "segmented_sort", "partition_lemma2", "segmented_partition", "partition_splitters")
 
 
 def run_case(args):

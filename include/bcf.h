@@ -255,7 +255,13 @@ int bcf_segmented_sort(const uint32_t* keys_in, const void* vals_in, uint32_t* k
                        int val_bytes, int key_bits, void* ws, size_t ws_bytes,
                        bcf_stream_t stream);
 
-/* w_per_seg: DEVICE int32[nseg], each in 1..256.  flags: BCF_ASSUME_BALANCED. */
+/* Stable partition of every segment by its labels (the partition problem, Sec. 1,
+ * per segment).  w_per_seg: DEVICE int32[nseg], each in 1..256 (else BCF_E_INVAL);
+ * the labels of segment s must be < w_per_seg[s] (else the device status
+ * BCF_E_BAD_KEY).  flags: BCF_ASSUME_BALANCED -- every label of segment s holds
+ * len_s / w_per_seg[s] keys (else BCF_E_NOT_BALANCED).  Every segment, short or
+ * long, goes through one label pass whose tiles cover all segments at once, in
+ * the pass form the BCF_OP_SEGMENTED_SORT entry names. */
 int bcf_segmented_partition_workspace_size(int64_t n_total, int64_t nseg, int val_bytes,
                                            size_t* bytes);
 int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
@@ -287,7 +293,8 @@ int bcf_segmented_partition(const uint32_t* keys_in, const void* vals_in,
  * the long segments into 4096-key tiles, so only the counts + scan
  * configurations of 256 x 16 apply (bcf_tune_set refuses the others with
  * BCF_E_INVAL); without an entry the long segments' passes use the pass body fed
- * scanned offsets (form 1). */
+ * scanned offsets (form 1).  The batched partition (bcf_segmented_partition)
+ * takes its pass form from the same entry. */
 #define BCF_OP_SEGMENTED_SORT 2
 int bcf_tune_num_configs(void);
 /* BCF_E_INVAL for an unknown configuration or a null output. */

@@ -227,6 +227,32 @@ def test_segmented_partition(bcf, balanced):
     _seg_part_case(bcf, keys, synth.index_payload(keys.size), offs, w, balanced)
 
 
+@pytest.mark.parametrize("config", [4, 8])
+@pytest.mark.parametrize("vb", [0, 4, 8])
+@pytest.mark.parametrize("balanced", [True, False])
+def test_segmented_partition_pass_forms(bcf, config, vb, balanced):
+    """Both pass forms the batched tuning entry can name -- the pass body fed
+    scanned offsets (4) and the staged sweep (8) -- partition every segment as the
+    oracle does: segments of every width, empty ones, starts off the 16-byte grid,
+    ragged last pieces."""
+    L = bcf.lib()
+    w = np.array([32, 256, 7, 64, 1, 128, 200, 3], dtype=np.int32)
+    sizes = [32 * 300, 256 * 40, 7 * 3, 0, 5, 128 * 70, 200 * 21, 3 * 1001]
+    offs = synth.offsets_from_sizes(sizes)
+    n = int(offs[-1])
+    g = synth.rng(11 + vb)
+    keys = np.concatenate([(g.permutation(np.arange(sizes[s]) % w[s]) if balanced
+                            else g.integers(0, w[s], sizes[s])) for s in range(w.size)]).astype(np.uint32)
+    vals = None if vb == 0 else (synth.float_bits_payload(n, seed=12) if vb == 4
+                                 else synth.uniform_keys(2 * n, seed=13).view(np.uint64))
+    lg = (n - 1).bit_length()
+    assert L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, lg, config) == bcf.OK
+    try:
+        _seg_part_case(bcf, keys, vals, offs, w, balanced)
+    finally:
+        L.bcf_tune_set(bcf.OP_SEGMENTED_SORT, lg, -1)
+
+
 @pytest.mark.slow
 def test_segmented_partition_batched_full_size(bcf):
     keys, offs, w = synth.segmented_partition_input(10_000, seed=0x4C)

@@ -60,7 +60,9 @@ int bcf_trace_end(uint64_t* records);
 #define BCF_PROBE_CONVERT 4   /* row-major -> column-major along a diagonal (load + store) */
 #define BCF_PROBE_MERGE 5     /* merge-path search: any column of the lane's own row */
 #define BCF_PROBE_READ32 6    /* 32-bit lane-contiguous reads */
-#define BCF_PROBE_PATTERNS 7
+#define BCF_PROBE_FROM_ROWS 7 /* row sort's load fused with a row -> column-major conversion */
+#define BCF_PROBE_FROM_COLS 8 /* row sort's load fused with a column -> row-major conversion */
+#define BCF_PROBE_PATTERNS 9
 #define BCF_PROBE_NONE 0      /* no global traffic beside the pattern */
 #define BCF_PROBE_GATHER 1    /* a 4-byte gather from the block's 16 KB of gin, cached in L1 */
 #define BCF_PROBE_GATHER_L2 2 /* the same gather from L2 only */

@@ -106,6 +106,18 @@ __global__ void __launch_bounds__(kPrThreads) k_bank_probe(const uint32_t* __res
         const unsigned long long v = X[col * kPrRows + r];
         acc ^= (uint32_t)v ^ (uint32_t)(v >> 32);
         beside<G>(gin, gout, blk, (uint32_t)v, (uint32_t)(tid + i * kPrThreads), acc);
+      } else if constexpr (P == BCF_PROBE_FROM_ROWS) {  // cell (t, 16i + r), t = (r + half-warp) mod 16
+        const int t = (r + tm) & 15, c = 16 * ((t & 1) ? 15 - i : i) + r;
+        rec<TR>(&X[c * kPrRows + t], 8, 0);
+        const unsigned long long v = X[c * kPrRows + t];
+        acc ^= (uint32_t)v ^ (uint32_t)(v >> 32);
+        beside<G>(gin, gout, blk, (uint32_t)v, (uint32_t)(tid + i * kPrThreads), acc);
+      } else if constexpr (P == BCF_PROBE_FROM_COLS) {  // cell ((i + r) mod 16, 16r + t)
+        const int t = (r + tm) & 15, idx = (r * 16 + t) * kPrRows + ((i + r) & 15);
+        rec<TR>(&X[idx], 8, 0);
+        const unsigned long long v = X[idx];
+        acc ^= (uint32_t)v ^ (uint32_t)(v >> 32);
+        beside<G>(gin, gout, blk, (uint32_t)v, (uint32_t)(tid + i * kPrThreads), acc);
       } else if constexpr (P == BCF_PROBE_READ32) {  // 32-bit lane-contiguous read
         const uint32_t* W = reinterpret_cast<const uint32_t*>(Y);
         const int t = tid + i * kPrThreads;
@@ -146,6 +158,8 @@ ProbeFn pick_probe(int pattern, int traffic, int traced) {
     case BCF_PROBE_ROW_ST: return pick_g<BCF_PROBE_ROW_ST>(traffic, traced);
     case BCF_PROBE_CONVERT: return pick_g<BCF_PROBE_CONVERT>(traffic, traced);
     case BCF_PROBE_MERGE: return pick_g<BCF_PROBE_MERGE>(traffic, traced);
+    case BCF_PROBE_FROM_ROWS: return pick_g<BCF_PROBE_FROM_ROWS>(traffic, traced);
+    case BCF_PROBE_FROM_COLS: return pick_g<BCF_PROBE_FROM_COLS>(traffic, traced);
     default: return pick_g<BCF_PROBE_READ32>(traffic, traced);
   }
 }

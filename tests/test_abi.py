@@ -198,7 +198,7 @@ def test_bank_probe_argument_checks():
     L = trace.load()
     P = ctypes.c_void_p
     a, b = P(0x10000), P(0x20000)
-    assert L.bcf_trace_bank_probe(7, 0, 0, a, b, 1, 1, None) == bcf.E_INVAL
+    assert L.bcf_trace_bank_probe(9, 0, 0, a, b, 1, 1, None) == bcf.E_INVAL
     assert L.bcf_trace_bank_probe(0, 4, 0, a, b, 1, 1, None) == bcf.E_INVAL
     assert L.bcf_trace_bank_probe(-1, 0, 0, a, b, 1, 1, None) == bcf.E_INVAL
     assert L.bcf_trace_bank_probe(0, 0, 0, None, b, 1, 1, None) == bcf.E_INVAL

@@ -342,7 +342,7 @@ def test_lemma2_partition_trace(tr, p):
 PROBE_BLOCKS, PROBE_REPS = 3 * 148, 32
 
 
-@pytest.mark.parametrize("pattern", range(7))
+@pytest.mark.parametrize("pattern", range(9))
 def test_bank_probe_patterns(tr, pattern):
     """The probe kernels (one shared-memory access pattern of the Lemma 1 tile sort
     each): the traced copy replays with zero hardware conflicts in the bank model

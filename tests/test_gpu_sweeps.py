@@ -267,3 +267,52 @@ def test_lookback_wait_gives_up(bcf, op):
         _partition_case(bcf, keys, vals, w, True)
     else:
         _sort_case(bcf, keys, vals)
+
+
+@pytest.mark.slow
+def test_sort_largest_size_by_properties(bcf):
+    """The largest sort the library takes (n < 2^30; here 2^30 - 4099 keys, a ragged
+    last tile), too large for the oracle, checked by what determines a stable sort's
+    output at any size: the keys come out ascending (as uint32), the returned
+    permutation is a permutation and carries every key from its input position, and
+    equal keys keep their input order."""
+    import torch
+    n = (1 << 30) - 4099
+    g = torch.Generator(device="cuda").manual_seed(0x51)
+    keys = torch.randint(-(1 << 31), 1 << 31, (n,), dtype=torch.int32, device="cuda", generator=g)
+    keys[: n // 8] &= 0xFFFF  # an eighth of the keys below 2^16: long runs of equal keys
+    ko, perm = bcf.sort(keys, None, index_payload=True)
+    assert bcf.get_status() == bcf.OK
+    s = ko ^ torch.tensor(-(1 << 31), dtype=torch.int32, device="cuda")  # uint32 order as int32 order
+    assert bool((s[1:] >= s[:-1]).all())
+    assert bool((perm >= 0).all()) and bool((perm < n).all())
+    seen = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    seen[perm.long()] = 1
+    assert bool(seen.all())  # n indices, every one hit: a permutation
+    del seen
+    assert torch.equal(keys[perm.long()], ko)
+    tie = s[1:] == s[:-1]
+    assert bool((perm[1:][tie] > perm[:-1][tie]).all())
+
+
+@pytest.mark.slow
+def test_partition_largest_size_by_properties(bcf):
+    """A 256-way partition of 2^30 - 4099 labels with index payloads (n < 2^30, the
+    largest the library takes), checked by the properties that make a stable
+    partition unique: labels non-decreasing, payloads a permutation that carries
+    every label from its input position, equal labels in input order."""
+    import torch
+    n = (1 << 30) - 4099
+    g = torch.Generator(device="cuda").manual_seed(0x52)
+    keys = torch.randint(0, 256, (n,), dtype=torch.int32, device="cuda", generator=g)
+    idx = torch.arange(n, dtype=torch.int32, device="cuda")
+    ko, perm = bcf.partition(keys, idx, 256)
+    assert bcf.get_status() == bcf.OK
+    assert bool((ko[1:] >= ko[:-1]).all())
+    seen = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    seen[perm.long()] = 1
+    assert bool(seen.all())
+    del seen
+    assert torch.equal(keys[perm.long()], ko)
+    tie = ko[1:] == ko[:-1]
+    assert bool((perm[1:][tie] > perm[:-1][tie]).all())
